@@ -1,0 +1,172 @@
+"""FP64 CPU oracle for the RKETD-FDTD scheme -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+leg may import this package. The product path (the CUDA library and its Python
+binding) never imports it. The C sources here are compiled with gcc into
+oracle/_build/ (serial build and an OpenMP build of the same file).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SOURCES = ["rketd_oracle.c"]
+_LOCK = threading.Lock()
+_LIBS = {}
+
+
+def build(omp: bool = False, force: bool = False, mutant: int = 0) -> str:
+    """Compiles the oracle with gcc (-O2 -ffp-contract=off); returns the .so path.
+
+    `mutant` > 0 builds a copy with one planted mistake (tests only: they check
+    that the pins reject it).
+    """
+    os.makedirs(_BUILD, exist_ok=True)
+    name = "liboracle_omp.so" if omp else "liboracle.so"
+    if mutant:
+        name = f"liboracle_mut{mutant}.so"
+    out = os.path.join(_BUILD, name)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in srcs):
+        return out
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+    if omp:
+        cmd.append("-fopenmp")
+    if mutant:
+        cmd.append(f"-DOR_MUTANT={int(mutant)}")
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(cmd + srcs + ["-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+class OrGrid1D(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int64), ("dz", ctypes.c_double), ("dt", ctypes.c_double),
+        ("bc", ctypes.c_int32), ("cpml_cells", ctypes.c_int32),
+        ("cpml_m", ctypes.c_double), ("cpml_sigma_max", ctypes.c_double),
+        ("cpml_kappa_max", ctypes.c_double), ("cpml_alpha_max", ctypes.c_double),
+        ("src_cell", ctypes.c_int64), ("src_tau", ctypes.c_double), ("src_t0", ctypes.c_double),
+        ("src_amp", ctypes.c_double), ("n_probes", ctypes.c_int32), ("n_freq", ctypes.c_int32),
+    ]
+
+
+def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
+    key = (omp, mutant)
+    with _LOCK:
+        if key not in _LIBS:
+            L = ctypes.CDLL(build(omp, mutant=mutant))
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int64)
+            L.or_run1d.argtypes = [ctypes.POINTER(OrGrid1D), dp, dp, ip, dp, ctypes.c_int64, ctypes.c_int64,
+                                   dp, dp, dp, dp, dp, dp, dp, dp]
+            L.or_run1d.restype = ctypes.c_int
+            L.or_phi1.argtypes = [ctypes.c_double]
+            L.or_phi1.restype = ctypes.c_double
+            L.or_phi2.argtypes = [ctypes.c_double]
+            L.or_phi2.restype = ctypes.c_double
+            L.or_threads.restype = ctypes.c_int
+            _LIBS[key] = L
+        return _LIBS[key]
+
+
+def cpml_defaults(dz: float, m: float = 3.0):
+    """CPML grading used for the long-domain runs: m = 3, sigma_max = 0.8 (m+1)/(eta0 dz),
+    kappa_max = 1, alpha_max = 0.05 S/m."""
+    eta0 = np.sqrt(1.25663706212e-6 / 8.8541878128e-12)
+    return m, 0.8 * (m + 1) / (eta0 * dz), 1.0, 0.05
+
+
+def make_grid(slab, cpml=None) -> OrGrid1D:
+    g = OrGrid1D()
+    g.nz = slab.nz
+    g.dz = slab.dz
+    g.dt = slab.dt
+    g.bc = 1 if slab.bc == "cpml" else 0
+    g.cpml_cells = slab.cpml_cells if slab.bc == "cpml" else 0
+    m, smax, kmax, amax = cpml if cpml is not None else cpml_defaults(slab.dz)
+    g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = m, smax, kmax, amax
+    g.src_cell = slab.src_cell
+    g.src_tau = slab.src_tau
+    g.src_t0 = slab.src_t0
+    g.src_amp = slab.src_amp
+    g.n_probes = len(slab.probes)
+    g.n_freq = len(slab.freq_hz)
+    return g
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class State1D:
+    """Oracle state in SI units: E^n, H^{n-1/2}, J^n, CPML memories, DFT sums, step index."""
+
+    def __init__(self, slab):
+        nz = slab.nz
+        self.E = np.zeros(nz)
+        self.H = np.zeros(nz - 1)
+        self.J = np.zeros(nz)
+        self.psiE = np.zeros(nz)
+        self.psiH = np.zeros(nz - 1)
+        self.X = np.zeros((len(slab.probes), len(slab.freq_hz)), dtype=np.complex128)
+        self.n = 0
+
+    def copy(self):
+        c = object.__new__(State1D)
+        for k, v in self.__dict__.items():
+            setattr(c, k, v.copy() if isinstance(v, np.ndarray) else v)
+        return c
+
+
+def run1d(slab, steps: Optional[int] = None, state: Optional[State1D] = None, series: bool = False,
+          omp: bool = False, cpml=None, mutant: int = 0):
+    """Runs the oracle for `steps` steps (default slab.steps) from `state` (default zero fields).
+
+    Returns (state, series) where series is [n_probes, steps] or None.
+    """
+    L = lib(omp, mutant)
+    steps = slab.steps if steps is None else steps
+    st = State1D(slab) if state is None else state
+    g = make_grid(slab, cpml)
+    wp2 = np.ascontiguousarray(slab.wp2, dtype=np.float64)
+    nu = np.ascontiguousarray(slab.nu, dtype=np.float64)
+    probes = np.ascontiguousarray(np.asarray(slab.probes, dtype=np.int64))
+    freqs = np.ascontiguousarray(slab.freq_hz, dtype=np.float64)
+    xr = np.ascontiguousarray(st.X.real.copy())
+    xi = np.ascontiguousarray(st.X.imag.copy())
+    ser = np.zeros((len(slab.probes), steps)) if series else None
+    rc = L.or_run1d(ctypes.byref(g), _dp(wp2), _dp(nu), probes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                    _dp(freqs), st.n, steps, _dp(st.E), _dp(st.H), _dp(st.J), _dp(st.psiE), _dp(st.psiH),
+                    _dp(xr), _dp(xi), _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)())
+    if rc != 0:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    st.X = xr + 1j * xi
+    st.n += steps
+    return st, ser
+
+
+def phi1(x: float) -> float:
+    return lib().or_phi1(x)
+
+
+def phi2(x: float) -> float:
+    return lib().or_phi2(x)
+
+
+def threads(omp: bool = True) -> int:
+    return lib(omp).or_threads()
+
+
+def reflection_transmission(X_tot: np.ndarray, X_inc: np.ndarray):
+    """R = (X_R^tot - X_R^inc)/X_R^inc at probe 0 and T = X_T^tot/X_T^inc at probe 1."""
+    R = (X_tot[0] - X_inc[0]) / X_inc[0]
+    T = X_tot[1] / X_inc[1] if X_tot.shape[0] > 1 else None
+    return R, T

@@ -1,0 +1,282 @@
+/*
+ * rketd_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, serial, FP64 CPU implementation of the RKETD-FDTD scheme for an
+ * unmagnetized (Drude) plasma, written directly from the paper's equations in
+ * SI units with no normalisation, no blocking and no fusion. It is the oracle
+ * that the CUDA library is checked against. Only tests/, the smoke() entry of
+ * __graft_entry__ and the cpu_baseline leg of bench.py load this file; the
+ * CUDA library never includes, links or calls it, and the two share no code.
+ *
+ * Compiled with -ffp-contract=off so that every multiply and add rounds on its
+ * own. The OpenMP build (-fopenmp) parallelises only the independent per-cell
+ * loops, so its fields are bitwise equal to the serial build.
+ *
+ * Model (paper Sec. II): Eqs. 4-6, the 1D curl equations with the Drude current
+ *   -dHy/dz = eps0 dEx/dt + Jx,  dEx/dz = -mu0 dHy/dt,  dJx/dt + nu Jx = eps0 wp^2 Ex.
+ * One time step n -> n+1, in the order the paper derives it:
+ *   1. H^{n+1/2} from H^{n-1/2} and E^n by Eq. 14 (the printed "dx" read as dz);
+ *   2. E^{n+1} from Eq. 12 with J^{n+1} taken from Eq. 11 and solved for E^{n+1}
+ *      (the corrected Eq. 13: every term on the right is divided by the
+ *      denominator D of the printed E^n coefficient);
+ *   3. J^{n+1} from Eq. 11 with E^n and E^{n+1};
+ *   4. soft source of Eq. 15 added to E^{n+1} at the source cell;
+ *   5. end cells: first-order Mur, or PEC walls behind a CPML;
+ *   6. running DFT of E^{n+1} at the probe cells.
+ * Eq. 11 is used rather than Eq. 10: integrating the linear interpolant of F
+ * between t_n and t_{n+1} against e^{nu tau} in Eq. 7 gives Eq. 11's terms.
+ *
+ * Parity pins: see tests/test_oracle_pins.py (discrete transfer matrix,
+ * continuous slab, wp = 0 reduction, nu = 0 energy balance, Courant limit,
+ * per-step algebra of Eqs. 11 and 12, CPML reflection).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_EPS0 8.8541878128e-12
+#define OR_MU0 1.25663706212e-6
+#define OR_PI 3.14159265358979323846
+
+typedef struct {
+  int64_t nz;          /* E nodes 0..nz-1; H nodes k+1/2 for k = 0..nz-2 */
+  double dz, dt;       /* m, s */
+  int32_t bc;          /* 0: first-order Mur at both ends; 1: CPML with PEC outer walls */
+  int32_t cpml_cells;  /* CPML thickness in cells (bc == 1) */
+  double cpml_m, cpml_sigma_max, cpml_kappa_max, cpml_alpha_max;
+  int64_t src_cell;    /* soft source cell */
+  double src_tau, src_t0, src_amp;
+  int32_t n_probes, n_freq;
+} or_grid1d;
+
+/* phi1(x) = (1 - e^{-x})/x and phi2(x) = (e^{-x} - 1 + x)/x^2 with x = nu*dt: the two
+ * integrals that turn Eq. 7 into Eq. 11 ((1 - e^{-nu dt})/nu = dt*phi1 and
+ * (e^{-nu dt} - 1 + nu dt)/(nu^2 dt) = dt*phi2). Their limits at x = 0 are 1 and 1/2.
+ * For x < 1 the Taylor series sum_k (-x)^k/(k+1)! and sum_k (-x)^k/(k+2)! are summed
+ * in nested form (40 terms, truncation below 1e-47); otherwise expm1 avoids the
+ * cancellation in 1 - e^{-x}. */
+double or_phi1(double x) {
+  if (x < 1.0) {
+    double s = 1.0;
+    for (int j = 41; j >= 2; --j) s = 1.0 + (-x) / (double)j * s;
+    return s;
+  }
+  return -expm1(-x) / x;
+}
+
+double or_phi2(double x) {
+  if (x < 1.0) {
+    double s = 1.0;
+    for (int j = 42; j >= 3; --j) s = 1.0 + (-x) / (double)j * s;
+    return 0.5 * s;
+  }
+  return (expm1(-x) + x) / (x * x);
+}
+
+/* Eq. 15 soft-source pulse, normalised by tau: amp*((t-t0)/tau)*exp(-(t-t0)^2/(2 tau^2)). */
+double or_source(const or_grid1d* g, double t) {
+  double u = (t - g->src_t0) / g->src_tau;
+  return g->src_amp * u * exp(-0.5 * u * u);
+}
+
+/* CPML grading at relative depth rho in (0, 1] (Roden-Gedney convolutional PML):
+ * sigma = sigma_max rho^m, kappa = 1 + (kappa_max-1) rho^m, alpha = alpha_max (1-rho),
+ * b = exp(-(sigma/kappa + alpha) dt/eps0), c = sigma (b-1) / (sigma kappa + kappa^2 alpha). */
+static void or_cpml_point(const or_grid1d* g, double rho, double* b, double* c, double* kappa) {
+  double pm = pow(rho, g->cpml_m);
+  double sigma = g->cpml_sigma_max * pm;
+  double kap = 1.0 + (g->cpml_kappa_max - 1.0) * pm;
+  double alpha = g->cpml_alpha_max * (1.0 - rho);
+  double bb = exp(-(sigma / kap + alpha) * g->dt / OR_EPS0);
+  double den = sigma * kap + kap * kap * alpha;
+  *b = bb;
+  *c = (sigma == 0.0 || den == 0.0) ? 0.0 : sigma * (bb - 1.0) / den;
+  *kappa = kap;
+}
+
+/* Relative CPML depth of a node at position x (in cells): 0 outside the layers. */
+static double or_cpml_rho(const or_grid1d* g, double x) {
+  double n = (double)g->cpml_cells;
+  double right_inner = (double)(g->nz - 1) - n;
+  if (g->bc != 1 || g->cpml_cells <= 0) return 0.0;
+  if (x < n) return (n - x) / n;
+  if (x > right_inner) return (x - right_inner) / n;
+  return 0.0;
+}
+
+/* Validates the problem; returns 0 or a negative code. */
+static int or_check(const or_grid1d* g, const int64_t* probe_cells) {
+  if (g->nz < 4 || g->dz <= 0 || g->dt <= 0) return -1;
+  if (g->src_cell < 1 || g->src_cell > g->nz - 2) return -2;
+  for (int p = 0; p < g->n_probes; ++p)
+    if (probe_cells[p] < 0 || probe_cells[p] >= g->nz) return -3;
+  if (g->bc == 1 && (g->cpml_cells < 1 || 2 * g->cpml_cells + 2 > g->nz)) return -4;
+  return 0;
+}
+
+/*
+ * Advances the state (E^n, H^{n-1/2}, J^n, CPML psi) by n_steps steps starting at step
+ * index n_start, accumulating the running DFT X_p(f) += E_p^{m} exp(-j 2 pi f m dt) for
+ * every new step index m = n_start+1 .. n_start+n_steps. All arrays are SI, caller-owned:
+ *   wp2[nz], nu[nz]   plasma frequency squared (rad^2/s^2) and collision frequency (1/s)
+ *   E[nz], J[nz], psiE[nz]; H[nz-1], psiH[nz-1]      (in/out)
+ *   X_re/X_im[n_probes*n_freq]                        (in/out, accumulated)
+ *   series[n_probes*n_steps] (may be NULL): E at each probe after each step.
+ * Returns 0, or a negative code for invalid input (nothing is modified then).
+ */
+int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int64_t* probe_cells,
+             const double* freq_hz, int64_t n_start, int64_t n_steps, double* E, double* H, double* J,
+             double* psiE, double* psiH, double* X_re, double* X_im, double* series) {
+  int rc = or_check(g, probe_cells);
+  if (rc) return rc;
+  const int64_t nz = g->nz;
+  const double dt = g->dt, dz = g->dz;
+  /* Per-cell constants of Eqs. 11 and 13, evaluated once. */
+  double* a = (double*)malloc(sizeof(double) * nz);
+  double* b1 = (double*)malloc(sizeof(double) * nz);
+  double* b2 = (double*)malloc(sizeof(double) * nz);
+  double* cEE = (double*)malloc(sizeof(double) * nz);
+  double* cEH = (double*)malloc(sizeof(double) * nz);
+  double* cEJ = (double*)malloc(sizeof(double) * nz);
+  double* pbE = (double*)calloc(nz, sizeof(double));
+  double* pcE = (double*)calloc(nz, sizeof(double));
+  double* pkE = (double*)malloc(sizeof(double) * nz);
+  double* pbH = (double*)calloc(nz, sizeof(double));
+  double* pcH = (double*)calloc(nz, sizeof(double));
+  double* pkH = (double*)malloc(sizeof(double) * nz);
+  char* inE = (char*)calloc(nz, 1);
+  char* inH = (char*)calloc(nz, 1);
+  for (int64_t k = 0; k < nz; ++k) {
+    double x = nu[k] * dt;
+    /* Eq. 11: J^{n+1} = a J^n + beta1 E^n + beta2 (E^{n+1} - E^n) with
+       a = e^{-nu dt}, beta1 = eps0 wp^2 (1 - a)/nu, beta2 = eps0 wp^2 (a - 1 + nu dt)/(nu^2 dt). */
+    a[k] = exp(-x);
+    b1[k] = OR_EPS0 * wp2[k] * dt * or_phi1(x);
+    b2[k] = OR_EPS0 * wp2[k] * dt * or_phi2(x);
+    /* Eq. 12 with Eq. 11 substituted and solved for E^{n+1} (Eq. 13 with the /D on every term):
+       D E^{n+1} = (1 - dt/(2 eps0) (beta1 - beta2)) E^n - dt/eps0 curlH - dt/(2 eps0) (1 + a) J^n,
+       D = 1 + dt/(2 eps0) beta2. */
+    double D = 1.0 + dt / (2.0 * OR_EPS0) * b2[k];
+    cEE[k] = (1.0 - dt / (2.0 * OR_EPS0) * (b1[k] - b2[k])) / D;
+    cEH[k] = (dt / OR_EPS0) / D;
+    cEJ[k] = (dt / (2.0 * OR_EPS0)) * (1.0 + a[k]) / D;
+    pkE[k] = 1.0;
+    pkH[k] = 1.0;
+    double rE = or_cpml_rho(g, (double)k);
+    if (rE > 0.0) {
+      inE[k] = 1;
+      or_cpml_point(g, rE, &pbE[k], &pcE[k], &pkE[k]);
+    }
+    if (k < nz - 1) {
+      double rH = or_cpml_rho(g, (double)k + 0.5);
+      if (rH > 0.0) {
+        inH[k] = 1;
+        or_cpml_point(g, rH, &pbH[k], &pcH[k], &pkH[k]);
+      }
+    }
+  }
+  /* Mur coefficient (S-1)/(S+1), S = c dt/dz with c = 1/sqrt(mu0 eps0). */
+  const double S = dt / (sqrt(OR_MU0 * OR_EPS0) * dz);
+  const double q = (S - 1.0) / (S + 1.0);
+#if defined(OR_MUTANT) && OR_MUTANT == 4
+  /* planted mistake: Mur coefficient with the wrong sign */
+  const double qq = -q;
+#define q qq
+#endif
+
+  for (int64_t step = 0; step < n_steps; ++step) {
+    const int64_t n = n_start + step; /* advancing E^n -> E^{n+1} */
+    /* 1. Eq. 14: H^{n+1/2}_{k+1/2} = H^{n-1/2}_{k+1/2} - dt/(mu0 dz) (E^n_{k+1} - E^n_k). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (nz > 8192)
+#endif
+    for (int64_t k = 0; k < nz - 1; ++k) {
+      double dE = E[k + 1] - E[k];
+      double curl;
+      if (inH[k]) {
+        psiH[k] = pbH[k] * psiH[k] + pcH[k] * (dE / dz);
+        curl = dE / (pkH[k] * dz) + psiH[k];
+      } else {
+        curl = dE / dz;
+      }
+      H[k] = H[k] - dt / OR_MU0 * curl;
+    }
+    const double E0_old = E[0], E1_old = E[1];
+    const double ENm1_old = E[nz - 1], ENm2_old = E[nz - 2];
+    /* 2-3. Eq. 13 (corrected) for E^{n+1}, then Eq. 11 for J^{n+1}. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (nz > 8192)
+#endif
+    for (int64_t k = 1; k < nz - 1; ++k) {
+      double dH = H[k] - H[k - 1];
+      double curl;
+      if (inE[k]) {
+        psiE[k] = pbE[k] * psiE[k] + pcE[k] * (dH / dz);
+        curl = dH / (pkE[k] * dz) + psiE[k];
+      } else {
+        curl = dH / dz;
+      }
+      double En = E[k];
+      double Enew = cEE[k] * En - cEH[k] * curl - cEJ[k] * J[k];
+#if defined(OR_MUTANT) && OR_MUTANT == 1
+      /* planted mistake: Eq. 13 as printed (no 1/D on the curl and J terms) */
+      Enew = cEE[k] * En - (dt / OR_EPS0) * curl - (dt / (2.0 * OR_EPS0)) * (1.0 + a[k]) * J[k];
+#endif
+#if defined(OR_MUTANT) && OR_MUTANT == 2
+      /* planted mistake: E^n and E^{n+1} swapped in the last term of Eq. 11 */
+      J[k] = a[k] * J[k] + b1[k] * En + b2[k] * (En - Enew);
+#else
+      J[k] = a[k] * J[k] + b1[k] * En + b2[k] * (Enew - En);
+#endif
+      E[k] = Enew;
+    }
+    /* 4. Eq. 15 soft source at t = (n+1) dt. */
+    E[g->src_cell] = E[g->src_cell] + or_source(g, (double)(n + 1) * dt);
+    /* 5. End cells. */
+    if (g->bc == 1) {
+      E[0] = 0.0;
+      E[nz - 1] = 0.0;
+    } else {
+      E[0] = E1_old + q * (E[1] - E0_old);
+      E[nz - 1] = ENm2_old + q * (E[nz - 2] - ENm1_old);
+    }
+    /* 6. Running DFT at the probes. */
+    const double t = (double)(n + 1) * dt;
+    for (int p = 0; p < g->n_probes; ++p) {
+      const double e = E[probe_cells[p]];
+      if (series) series[(int64_t)p * n_steps + step] = e;
+      for (int f = 0; f < g->n_freq; ++f) {
+        const double ph = 2.0 * OR_PI * freq_hz[f] * t;
+        X_re[p * g->n_freq + f] += e * cos(ph);
+#if defined(OR_MUTANT) && OR_MUTANT == 3
+        /* planted mistake: DFT kernel e^{+j w t} */
+        X_im[p * g->n_freq + f] += e * sin(ph);
+#else
+        X_im[p * g->n_freq + f] -= e * sin(ph);
+#endif
+      }
+    }
+  }
+  free(a); free(b1); free(b2); free(cEE); free(cEH); free(cEJ);
+  free(pbE); free(pcE); free(pkE); free(pbH); free(pcH); free(pkH); free(inE); free(inH);
+  return 0;
+}
+
+/* Number of OpenMP threads this build uses (1 for the serial build). */
+int or_threads(void) {
+#ifdef _OPENMP
+  int n = 1;
+#pragma omp parallel
+  {
+#pragma omp single
+    n = omp_get_num_threads();
+  }
+  return n;
+#else
+  return 1;
+#endif
+}

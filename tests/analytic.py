@@ -1,0 +1,249 @@
+"""Closed forms that pin the FP64 oracle (test infrastructure).
+
+Nothing here calls the oracle or the CUDA library; every formula is derived
+from the paper's equations or from textbook electromagnetics:
+
+* `lattice_eps`   -- permittivity of the *discrete* RKETD-Yee scheme at one
+  frequency: substituting E^n_k = E_k z^n, H at z^{n+1/2}, z = e^{j w dt} into
+  Eqs. 11, 12 and 14 gives E_{k+1} - 2 E_k + E_{k-1} = -q_k E_k with
+  q_k = (2 sin(theta/2)/S)^2 eps_k and
+  eps_k = 1 + w_k cos(theta/2) (phi1 - phi2 + phi2 z) / (2j sin(theta/2) (z - a_k)),
+  w_k = wp_k^2 dt^2, a_k = e^{-nu_k dt}.
+* `slab_rt_lattice` -- reflection/transmission of the slab on the infinite
+  lattice (transfer recursion through the slab, fit of incident/reflected
+  waves in vacuum).
+* `domain_response` -- exact steady-state response of the whole finite lattice,
+  including the first-order Mur end rows and the soft source; R and T from two
+  such solves (plasma and vacuum) are what the running DFT converges to as the
+  window grows.
+* `fresnel_slab` -- continuous (Airy) slab with eps_r = 1 - wp^2/(w (w - j nu)).
+"""
+from __future__ import annotations
+
+import math
+
+import mpmath as mp
+import numpy as np
+from scipy.linalg import solve_banded
+
+EPS0 = 8.8541878128e-12
+MU0 = 1.25663706212e-6
+
+
+def courant(dz: float, dt: float) -> float:
+    return dt / (math.sqrt(MU0 * EPS0) * dz)
+
+
+def phi_mp(x: float):
+    """phi1 = (1 - e^{-x})/x, phi2 = (e^{-x} - 1 + x)/x^2 to 40 digits (limits 1, 1/2 at x = 0)."""
+    with mp.workdps(40):
+        X = mp.mpf(x)
+        if X == 0:
+            return 1.0, 0.5
+        e = mp.exp(-X)
+        return float((1 - e) / X), float((e - 1 + X) / X ** 2)
+
+
+def _material_cache(wp2: np.ndarray, nu: np.ndarray, dt: float):
+    """Unique (wp2, nu) pairs with their e^{-nu dt}, phi1, phi2."""
+    pairs = {}
+    for w, n in zip(wp2.tolist(), nu.tolist()):
+        if (w, n) not in pairs:
+            p1, p2 = phi_mp(n * dt)
+            pairs[(w, n)] = (w * dt * dt, math.exp(-n * dt), p1, p2)
+    return pairs
+
+
+def lattice_eps(theta: np.ndarray, w: float, a: float, p1: float, p2: float) -> np.ndarray:
+    """Discrete permittivity of one cell at normalised frequencies theta = w dt."""
+    z = np.exp(1j * theta)
+    s = np.sin(theta / 2)
+    c = np.cos(theta / 2)
+    return 1.0 + w * c * (p1 - p2 + p2 * z) / (2j * s * (z - a))
+
+
+def lattice_q(theta: np.ndarray, S: float, wp2: np.ndarray, nu: np.ndarray, dt: float) -> np.ndarray:
+    """q_k(theta) for every cell: shape [len(theta), nz]."""
+    cache = _material_cache(wp2, nu, dt)
+    s = np.sin(theta / 2)
+    out = np.empty((len(theta), len(wp2)), dtype=np.complex128)
+    keys = list(zip(wp2.tolist(), nu.tolist()))
+    epsd = {k: lattice_eps(theta, *v) for k, v in cache.items()}
+    for i, k in enumerate(keys):
+        out[:, i] = (2 * s / S) ** 2 * epsd[k]
+    return out
+
+
+def vacuum_K(theta: np.ndarray, S: float) -> np.ndarray:
+    """Numerical wavenumber per cell: cos K = 1 - 2 sin^2(theta/2)/S^2 (Yee dispersion)."""
+    return np.arccos(1 - 2 * np.sin(theta / 2) ** 2 / S ** 2)
+
+
+def slab_rt_lattice(wp2, nu, dz, dt, freqs, p_r, p_t):
+    """R, T of the plasma region on the infinite lattice, referred to the probe cells.
+
+    Start right of the slab with a purely transmitted wave e^{-jKk}, iterate
+    E_{k-1} = (2 - q_k) E_k - E_{k+1} to the left vacuum, fit A e^{-jKk} + B e^{jKk}.
+    R = (B/A) e^{2jK p_r} (what (X_tot - X_inc)/X_inc measures at p_r), T = 1/A.
+    """
+    wp2 = np.asarray(wp2, float)
+    nu = np.asarray(nu, float)
+    S = courant(dz, dt)
+    theta = 2 * np.pi * np.asarray(freqs) * dt
+    idx = np.nonzero(wp2)[0]
+    lo, hi = int(idx[0]), int(idx[-1])
+    assert lo - 2 > p_r and hi + 2 < p_t
+    K = vacuum_K(theta, S)
+    sub = slice(lo - 2, hi + 3)
+    q = lattice_q(theta, S, wp2[sub], nu[sub], dt)  # cells lo-2 .. hi+2
+    n = hi - lo + 5
+    Ek1 = np.exp(-1j * K * (hi + 2))  # E_{k+1}
+    Ek = np.exp(-1j * K * (hi + 1))  # E_k
+    for j in range(n - 2, 0, -1):  # local j = cell - (lo-2); k from hi+1 down to lo-1
+        Em1 = (2 - q[:, j]) * Ek - Ek1
+        Ek1, Ek = Ek, Em1
+    # Ek = E at cell lo-2, Ek1 = E at cell lo-1 (both vacuum)
+    k0 = lo - 2
+    e0, e1 = Ek, Ek1
+    # e0 = A e^{-jK k0} + B e^{jK k0}; e1 = A e^{-jK(k0+1)} + B e^{jK(k0+1)}
+    m00 = np.exp(-1j * K * k0)
+    m01 = np.exp(1j * K * k0)
+    m10 = np.exp(-1j * K * (k0 + 1))
+    m11 = np.exp(1j * K * (k0 + 1))
+    det = m00 * m11 - m01 * m10
+    A = (e0 * m11 - m01 * e1) / det
+    B = (m00 * e1 - e0 * m10) / det
+    R = (B / A) * np.exp(2j * K * p_r)
+    T = 1.0 / A
+    return R, T
+
+
+def domain_response(wp2, nu, dz, dt, freqs, src_cell, cells):
+    """Steady-state phasors at `cells` of the finite lattice driven by a unit soft source.
+
+    Rows: interior E_{k-1} + (q_k - 2) E_k + E_{k+1} = delta_{k, src}; first-order Mur at
+    both ends, E_0 (z + q) - E_1 (1 + q z) = 0 with q = (S-1)/(S+1) and the mirror row.
+    The source scale is common to the plasma and vacuum solves and cancels in R and T.
+    """
+    wp2 = np.asarray(wp2, float)
+    nu = np.asarray(nu, float)
+    nz = len(wp2)
+    S = courant(dz, dt)
+    qm = (S - 1) / (S + 1)
+    theta = 2 * np.pi * np.asarray(freqs) * dt
+    qq = lattice_q(theta, S, wp2, nu, dt)
+    out = np.empty((len(theta), len(cells)), dtype=np.complex128)
+    for i, th in enumerate(theta):
+        z = np.exp(1j * th)
+        ab = np.zeros((3, nz), dtype=np.complex128)  # banded: upper, diag, lower
+        ab[0, 1:] = 1.0
+        ab[1, :] = qq[i] - 2.0
+        ab[2, :-1] = 1.0
+        # Mur rows
+        ab[1, 0] = z + qm
+        ab[0, 1] = -(1 + qm * z)
+        ab[1, nz - 1] = z + qm
+        ab[2, nz - 2] = -(1 + qm * z)
+        rhs = np.zeros(nz, dtype=np.complex128)
+        rhs[src_cell] = 1.0
+        sol = solve_banded((1, 1), ab, rhs)
+        out[i] = sol[list(cells)]
+    return out
+
+
+def domain_rt(slab):
+    """R and T the running DFT converges to for a Mur-terminated slab problem."""
+    cells = slab.probes
+    tot = domain_response(slab.wp2, slab.nu, slab.dz, slab.dt, slab.freq_hz, slab.src_cell, cells)
+    inc = domain_response(np.zeros(slab.nz), np.zeros(slab.nz), slab.dz, slab.dt, slab.freq_hz,
+                          slab.src_cell, cells)
+    R = (tot[:, 0] - inc[:, 0]) / inc[:, 0]
+    T = tot[:, 1] / inc[:, 1]
+    return R, T
+
+
+def fresnel_slab(freqs, wp2: float, nu: float, d: float):
+    """Continuous slab of thickness d in vacuum, e^{+jwt} convention.
+
+    eps_r = 1 - wp^2/(w (w - j nu)), n = sqrt(eps_r) with Im n <= 0, r = (1-n)/(1+n),
+    delta = n k0 d, R = r (1 - e^{-2j delta})/(1 - r^2 e^{-2j delta}),
+    T e^{-j k0 d} = (1 - r^2) e^{-j delta}/(1 - r^2 e^{-2j delta}).
+    Returns (|R|, |T|).
+    """
+    c = 1.0 / math.sqrt(MU0 * EPS0)
+    w = 2 * np.pi * np.asarray(freqs, float)
+    eps = 1 - wp2 / (w * (w - 1j * nu))
+    n = np.sqrt(eps.astype(np.complex128))
+    n = np.where(n.imag > 0, -n, n)
+    r = (1 - n) / (1 + n)
+    k0 = w / c
+    ph = np.exp(-2j * n * k0 * d)
+    R = r * (1 - ph) / (1 - r * r * ph)
+    T = (1 - r * r) * np.exp(-1j * n * k0 * d) / (1 - r * r * ph)
+    return np.abs(R), np.abs(T)
+
+
+def plain_yee_vacuum(nz, dz, dt, steps, src_cell, src, probes):
+    """Textbook 1D Yee leapfrog in SI (Eqs. 12 and 14 with J = 0), first-order Mur ends.
+
+    `src(t)` is added to E at src_cell after each E update. Returns (E, H, series).
+    """
+    S = courant(dz, dt)
+    qm = (S - 1) / (S + 1)
+    E = np.zeros(nz)
+    H = np.zeros(nz - 1)
+    ser = np.zeros((len(probes), steps))
+    for n in range(steps):
+        H = H - dt / MU0 * ((E[1:] - E[:-1]) / dz)
+        e0, e1, em1, em2 = E[0], E[1], E[-1], E[-2]
+        E[1:-1] = E[1:-1] - (dt / EPS0) * ((H[1:] - H[:-1]) / dz)
+        E[src_cell] = E[src_cell] + src((n + 1) * dt)
+        E[0] = e1 + qm * (E[1] - e0)
+        E[-1] = em2 + qm * (E[-2] - em1)
+        ser[:, n] = E[probes]
+    return E, H, ser
+
+
+def normalized_run(slab, steps):
+    """Independent NumPy restatement of the scheme in normalised variables (mur ends).
+
+    E~ = E, H~ = eta0 H, J~ = (dt/eps0) J, S = c dt/dz. Per step:
+    H~ -= S (E_{k+1} - E_k)                                        (Eq. 14)
+    E' = [(1 - w(phi1 - phi2)/2) E - S (H~_{k+1/2} - H~_{k-1/2}) - (1 + a)/2 J~]/(1 + w phi2/2)
+                                                                   (Eqs. 11 + 12 solved)
+    J~' = a J~ + w phi1 E + w phi2 (E' - E)                         (Eq. 11)
+    then the Eq. 15 soft source and first-order Mur ends. Returns (E, H (SI), J (SI), X).
+    """
+    nz = slab.nz
+    dt, dz = slab.dt, slab.dz
+    S = courant(dz, dt)
+    qm = (S - 1) / (S + 1)
+    eta0 = math.sqrt(MU0 / EPS0)
+    cache = _material_cache(np.asarray(slab.wp2, float), np.asarray(slab.nu, float), dt)
+    keys = list(zip(np.asarray(slab.wp2, float).tolist(), np.asarray(slab.nu, float).tolist()))
+    w = np.array([cache[k][0] for k in keys])
+    a = np.array([cache[k][1] for k in keys])
+    p1 = np.array([cache[k][2] for k in keys])
+    p2 = np.array([cache[k][3] for k in keys])
+    D = 1 + w * p2 / 2
+    E = np.zeros(nz)
+    Ht = np.zeros(nz - 1)
+    Jt = np.zeros(nz)
+    P = len(slab.probes)
+    X = np.zeros((P, len(slab.freq_hz)), dtype=np.complex128)
+    f = np.asarray(slab.freq_hz)
+    for n in range(steps):
+        Ht = Ht - S * (E[1:] - E[:-1])
+        e0, e1, em1, em2 = E[0], E[1], E[-1], E[-2]
+        En = E[1:-1].copy()
+        i = slice(1, -1)
+        Enew = ((1 - w[i] * (p1[i] - p2[i]) / 2) * En - S * (Ht[1:] - Ht[:-1]) - (1 + a[i]) / 2 * Jt[i]) / D[i]
+        Jt[i] = a[i] * Jt[i] + w[i] * p1[i] * En + w[i] * p2[i] * (Enew - En)
+        E[i] = Enew
+        t = (n + 1) * dt
+        u = (t - slab.src_t0) / slab.src_tau
+        E[slab.src_cell] += slab.src_amp * u * math.exp(-0.5 * u * u)
+        E[0] = e1 + qm * (E[1] - e0)
+        E[-1] = em2 + qm * (E[-2] - em1)
+        X += E[slab.probes][:, None] * np.exp(-2j * np.pi * f[None, :] * t)
+    return E, Ht / eta0, Jt * EPS0 / dt, X
