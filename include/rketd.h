@@ -1,0 +1,198 @@
+/*
+ * rketd.h -- C ABI of the GB300 (sm_103a) RKETD-FDTD library.
+ *
+ * The library advances the 1D Yee/RKETD scheme for an unmagnetized Drude plasma
+ * (Xiong et al., "The Electromagnetic Waves Propagation in Unmagnetized Plasma
+ * Media Using Parallelized FDTD", arXiv:1709.00821):
+ *   Eq. 14  H update:  H^{n+1/2}_{k+1/2} = H^{n-1/2}_{k+1/2} - dt/(mu0 dz) (E^n_{k+1} - E^n_k)
+ *   Eq. 12  E update driven by the time-averaged plasma current (J^{n+1} + J^n)/2
+ *   Eq. 11  RKETD current recursion J^{n+1} = e^{-nu dt} J^n + ... (E^n, E^{n+1})
+ *   Eq. 13  Eq. 11 substituted into Eq. 12 and solved for E^{n+1} (read with the
+ *           common denominator on every term; the printed form drops it on two)
+ *   Eq. 15  Gaussian-derivative soft source, tau = 15 dt in the paper's run
+ * with first-order Mur or CPML ends and a running DFT at probe cells from which
+ * the reflection and transmission spectra of Sec. IV.B follow.
+ *
+ * Conventions for every call:
+ *  - Quantities at the ABI are SI: m, s, V/m, A/m, A/m^2, rad^2/s^2, 1/s, Hz.
+ *  - Every call returns an rketd_status; no call aborts or throws across the ABI.
+ *    On failure rketd_last_error() returns a message (thread-local, valid until
+ *    the next call on the same thread).
+ *  - Host arrays passed in are read during the call only (copied); the caller
+ *    keeps ownership. Output host arrays are written during the call.
+ *  - Device pointers passed in are borrowed: they must stay valid until the call's
+ *    work on the context's stream has completed (rketd_sync).
+ *  - A context owns the device memory it allocates (fields, coefficients, DFT
+ *    state) and releases it in rketd_destroy. Work is queued on the CUDA stream
+ *    given at creation (NULL = legacy default stream).
+ *  - A context must not be used from two threads at once.
+ */
+#ifndef RKETD_H
+#define RKETD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RKETD_OK = 0,
+  RKETD_EINVAL = 1,       /* invalid argument (sizes, cells, physical parameters) */
+  RKETD_ECOURANT = 2,     /* c0 dt / dz > 1: the explicit leapfrog is unstable */
+  RKETD_ENOMEM = 3,       /* device or host allocation failed */
+  RKETD_ECUDA = 4,        /* a CUDA runtime call failed; message has the CUDA error */
+  RKETD_ETIMEOUT = 5,     /* a bounded device-side wait gave up */
+  RKETD_EUNSUPPORTED = 6, /* option combination not provided by this build */
+  RKETD_ENUMERIC = 7,     /* non-finite value seen in the fields or spectra */
+  RKETD_EIO = 8           /* state file could not be read or written */
+} rketd_status;
+
+typedef enum { RKETD_F32 = 0, RKETD_F64 = 1 } rketd_prec;
+typedef enum { RKETD_BC_MUR1 = 0, RKETD_BC_CPML = 1 } rketd_bc;
+
+/* Grid shared by every slab of a context. Courant number S = dt / (dz sqrt(mu0 eps0))
+ * must satisfy 0 < S <= 1 (1D leapfrog stability); S is evaluated with
+ * eps0 = 8.8541878128e-12 F/m and mu0 = 1.25663706212e-6 H/m.
+ * prec: RKETD_F64 keeps fields, coefficients and DFT sums in FP64. RKETD_F32
+ * keeps fields in FP32, derives the update coefficients in FP64 and stores them
+ * as FP32 deviations from their vacuum values, and accumulates the DFT in
+ * compensated FP32 per block of samples added into FP64 totals.
+ * bc: RKETD_BC_MUR1 = first-order Mur at both ends; RKETD_BC_CPML = convolutional
+ * PML of cpml_cells cells at both ends backed by PEC walls, with grading
+ * sigma = sigma_max rho^m, kappa = 1 + (kappa_max - 1) rho^m, alpha = alpha_max (1 - rho)
+ * in relative depth rho; sigma_max <= 0 selects 0.8 (m + 1)/(eta0 dz). The paper's
+ * 5-cell split-field PML (Sec. III, Sec. IV.B) is replaced by these two ends. */
+typedef struct {
+  double dz, dt;
+  int32_t prec;          /* rketd_prec */
+  int32_t bc;            /* rketd_bc */
+  int32_t cpml_cells;
+  int32_t reserved0;
+  double cpml_m, cpml_sigma_max, cpml_kappa_max, cpml_alpha_max;
+} rketd_grid1d;
+
+/* Eq. 15 soft source added to E^{n+1} at the source cell after the E update:
+ * s(t) = amp * ((t - t0)/tau) * exp(-(t - t0)^2 / (2 tau^2)), t = (n+1) dt.
+ * The paper uses tau = 15 dt and a delay of 5 tau. */
+typedef struct {
+  double tau, t0, amp;
+} rketd_pulse;
+
+/* Running DFT X_p(f) = sum_{m>=1} E_p^m exp(-j 2 pi f m dt) at n_probes cells per slab
+ * (Sec. IV.B computes R and T by an FFT of the probe series; the sum is the same
+ * transform evaluated at the requested frequencies). */
+typedef struct {
+  int32_t n_probes;     /* per slab, >= 0 */
+  int32_t n_freq;       /* >= 1 when n_probes > 0 */
+  const double* freq_hz;  /* [n_freq], host, copied */
+} rketd_dft;
+
+/* Execution options. Zero-initialise and set what you need; rketd_default_options()
+ * fills the defaults. */
+typedef struct {
+  int32_t variant;      /* 0 = auto, 1 = plain (paper structure: one H kernel and one
+                           E+J kernel per step), 2 = temporally blocked warp tiles */
+  int32_t cells_per_lane;  /* K for the tiled kernel: 8 or 16 (F32), 4 or 8 (F64); 0 = auto */
+  int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
+  int32_t warps_per_block; /* 1..8; 0 = auto */
+  int32_t dft_block;    /* probe samples buffered between DFT folds (multiple of tb_steps); 0 = auto */
+  int32_t use_graphs;   /* 1 = replay captured CUDA graphs for whole DFT blocks */
+  int32_t reserved[6];
+} rketd_options;
+
+typedef struct rketd_ctx rketd_ctx;
+
+/* Fills *opt with the defaults (auto variant, graphs on). */
+void rketd_default_options(rketd_options* opt);
+
+/*
+ * Creates a context for n_slabs independent 1D problems advanced together
+ * (the paper's single slab is n_slabs = 1).
+ *   nz[s]        E nodes of slab s (>= 8); H nodes are k+1/2, k = 0..nz-2
+ *   wp2, nu      concatenated per-cell plasma frequency squared (rad^2/s^2, >= 0)
+ *                and collision frequency (1/s, >= 0), slab after slab, host FP64
+ *   src_cell[s]  soft-source cell of slab s, 1 <= cell <= nz-2 (outside the CPML)
+ *   probe_cell   [n_slabs * dft->n_probes] probe cells, 0 <= cell < nz (outside the CPML)
+ *   stream       cudaStream_t for all work of this context (may be NULL)
+ * The coefficient precompute (RKETD exponentials in FP64) runs on the device.
+ * Errors: RKETD_EINVAL, RKETD_ECOURANT, RKETD_ENOMEM, RKETD_ECUDA. *out is NULL on error.
+ */
+rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rketd_grid1d* grid,
+                                   const double* wp2, const double* nu, const int64_t* src_cell,
+                                   const rketd_pulse* pulse, const int64_t* probe_cell,
+                                   const rketd_dft* dft, const rketd_options* opt, void* stream,
+                                   rketd_ctx** out);
+
+/* Single-slab convenience form of rketd_create_batch_1d. */
+rketd_status rketd_create_1d(int64_t nz, const rketd_grid1d* grid, const double* wp2, const double* nu,
+                             int64_t src_cell, const rketd_pulse* pulse, const int64_t* probe_cell,
+                             const rketd_dft* dft, const rketd_options* opt, void* stream,
+                             rketd_ctx** out);
+
+/* Replaces the medium (same layout as at creation) and recomputes the update
+ * coefficients on the device. on_device = 0: wp2/nu are host FP64 arrays (copied
+ * host->device on the stream); 1: device FP64 arrays (read on the stream). Fields
+ * are not touched. */
+rketd_status rketd_set_medium(rketd_ctx* ctx, const double* wp2, const double* nu, int32_t on_device);
+
+/* Zeroes fields, CPML memories and DFT sums and sets the step index to 0 (async). */
+rketd_status rketd_reset(rketd_ctx* ctx);
+
+/* Queues nsteps leapfrog steps (Eqs. 14, 13, 11, 15, ends, DFT) on the stream. Async;
+ * device-side problems surface at rketd_sync. */
+rketd_status rketd_step(rketd_ctx* ctx, int64_t nsteps);
+
+/* Waits for the stream and reports any device-side error. */
+rketd_status rketd_sync(rketd_ctx* ctx);
+
+/* Current step index n (fields hold E^n, H^{n-1/2}, J^n). */
+int64_t rketd_step_index(const rketd_ctx* ctx);
+
+/* Copies slab s's fields to host FP64 SI arrays (any may be NULL): E[nz], H[nz-1], J[nz].
+ * Synchronises the stream. */
+rketd_status rketd_get_fields(rketd_ctx* ctx, int32_t slab, double* E, double* H, double* J);
+
+/* Copies the DFT sums to host: re/im [n_slabs][n_probes][n_freq] (FP64). Synchronises. */
+rketd_status rketd_get_spectra(rketd_ctx* ctx, double* re, double* im);
+
+/* Same as rketd_get_spectra into device FP64 arrays (async on the stream). */
+rketd_status rketd_get_spectra_device(rketd_ctx* ctx, double* re, double* im);
+
+/* Host helper for Sec. IV.B: from total-field and incident (vacuum-run) spectra at
+ * the reflection probe (index 0) and transmission probe (index 1) of one slab,
+ * R = (X_R^tot - X_R^inc)/X_R^inc and T = X_T^tot / X_T^inc, each [n_freq]. */
+rketd_status rketd_rt(const double* tot_re, const double* tot_im, const double* inc_re,
+                      const double* inc_im, int32_t n_freq, double* R_re, double* R_im, double* T_re,
+                      double* T_im);
+
+/* Saves / restores the full state (fields, CPML memories, DFT sums, step index) to a
+ * versioned binary file. A run resumed from a saved state is bitwise identical to
+ * an uninterrupted one with the same options. Synchronises. */
+rketd_status rketd_save_state(rketd_ctx* ctx, const char* path);
+rketd_status rketd_load_state(rketd_ctx* ctx, const char* path);
+
+/* Times the tiled variants on this context for about `passes` passes each and keeps
+ * the fastest (the state is saved and restored around the trials). Synchronises. */
+rketd_status rketd_autotune(rketd_ctx* ctx, int32_t passes);
+
+/* Options in use (after auto selection). */
+rketd_status rketd_get_options(const rketd_ctx* ctx, rketd_options* opt);
+
+/* Number of kernel launches this context has issued (graph replays count their nodes). */
+int64_t rketd_launch_count(const rketd_ctx* ctx);
+
+/* Releases the context and its device memory. NULL is accepted. */
+rketd_status rketd_destroy(rketd_ctx* ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* rketd_last_error(void);
+
+/* Library version string. */
+const char* rketd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RKETD_H */

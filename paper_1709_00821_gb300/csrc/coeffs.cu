@@ -1,0 +1,131 @@
+// Per-cell RKETD update coefficients (Eqs. 11-13) and CPML grading tables, in FP64 on
+// the device. The FP32 path stores the same FP64 results rounded once to FP32; every
+// coefficient is a deviation from its vacuum value or a small term, so rounding keeps
+// its relative accuracy (a = e^{-nu dt} itself would lose most of a - 1 in FP32).
+#include "rketd_internal.cuh"
+
+namespace rketd {
+namespace {
+
+// phi1(x) = (1 - e^{-x})/x and phi2(x) = (e^{-x} - 1 + x)/x^2 (x = nu dt), the integrals that
+// take the exact solution Eq. 7 with F interpolated linearly over the step to Eq. 11.
+// Below x = 0.5 both are Taylor polynomials of degree 20 (coefficients (-1)^k/(k+1)! and
+// (-1)^k/(k+2)!) evaluated by Horner's rule; the first omitted term is below 1e-27.
+// From x = 0.5 up, expm1 keeps 1 - e^{-x} exact to rounding.
+__device__ void phi12(double x, double& p1, double& p2) {
+  if (x < 0.5) {
+    double c1[21], c2[21];
+    c1[0] = 1.0;
+    c2[0] = 0.5;
+#pragma unroll
+    for (int k = 1; k <= 20; ++k) {
+      c1[k] = -c1[k - 1] / (double)(k + 1);
+      c2[k] = -c2[k - 1] / (double)(k + 2);
+    }
+    double r1 = c1[20], r2 = c2[20];
+#pragma unroll
+    for (int k = 19; k >= 0; --k) {
+      r1 = fma(r1, x, c1[k]);
+      r2 = fma(r2, x, c2[k]);
+    }
+    p1 = r1;
+    p2 = r2;
+  } else {
+    const double em = expm1(-x);
+    p1 = -em / x;
+    p2 = (x + em) / (x * x);
+  }
+}
+
+template <typename T>
+__global__ void k_coeffs(const double* __restrict__ wp2, const double* __restrict__ nu,
+                         const int64_t* __restrict__ soff, const int64_t* __restrict__ off,
+                         const int64_t* __restrict__ nz, int n_slabs, int64_t n_store, double dt,
+                         double S, T* __restrict__ da, T* __restrict__ cb, T* __restrict__ cj,
+                         T* __restrict__ dj, T* __restrict__ bp, T* __restrict__ cc) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_store;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // slab owning storage cell i: last s with soff[s] <= i
+    int lo = 0, hi = n_slabs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (soff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int64_t k = i - soff[lo];
+    double w = 0.0, x = 0.0;
+    if (k < nz[lo]) {
+      w = wp2[off[lo] + k] * dt * dt;
+      x = nu[off[lo] + k] * dt;
+    }
+    double p1, p2;
+    phi12(x, p1, p2);
+    const double em = expm1(-x);  // a - 1
+    const double D = 1.0 + 0.5 * w * p2;
+    da[i] = (T)(-0.5 * w * p1 / D);
+    cb[i] = (T)(S / D);
+    cj[i] = (T)(0.5 * (2.0 + em) / D);
+    dj[i] = (T)em;
+    bp[i] = (T)(w * (p1 - p2));
+    cc[i] = (T)(w * p2);
+  }
+}
+
+// CPML (Roden-Gedney) b, c and 1/kappa against depth. E nodes: depth d = 0..n cells from
+// the outer wall, rho = (n - d)/n; H nodes: depth i + 1/2, rho = (n - i - 1/2)/n.
+// sigma = smax rho^m, kappa = 1 + (kmax - 1) rho^m, alpha = amax (1 - rho),
+// b = exp(-(sigma/kappa + alpha) dt/eps0), c = sigma (b - 1)/(sigma kappa + kappa^2 alpha).
+template <typename T>
+__global__ void k_cpml(int n, double dt, double m, double smax, double kmax, double amax,
+                       T* __restrict__ tabE, T* __restrict__ tabH) {
+  const int i = threadIdx.x;
+  for (int which = 0; which < 2; ++which) {
+    const int count = which == 0 ? n + 1 : n;
+    if (i >= count) continue;
+    const double rho = which == 0 ? (double)(n - i) / n : ((double)n - i - 0.5) / n;
+    const double pm = pow(rho, m);
+    const double sigma = smax * pm;
+    const double kap = 1.0 + (kmax - 1.0) * pm;
+    const double alpha = amax * (1.0 - rho);
+    const double b = exp(-(sigma / kap + alpha) * dt / kEps0);
+    const double den = sigma * kap + kap * kap * alpha;
+    const double c = (sigma > 0.0 && den > 0.0) ? sigma * (b - 1.0) / den : 0.0;
+    T* tab = which == 0 ? tabE : tabH;
+    tab[i] = (T)b;
+    tab[count + i] = (T)c;
+    tab[2 * count + i] = (T)(1.0 / kap);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
+                          const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,
+                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st) {
+  const int threads = 256;
+  int64_t blocks = (n_store + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  if (prec == 1) {
+    k_coeffs<double><<<(unsigned)blocks, threads, 0, st>>>(
+        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, (double*)coef[0], (double*)coef[1],
+        (double*)coef[2], (double*)coef[3], (double*)coef[4], (double*)coef[5]);
+  } else {
+    k_coeffs<float><<<(unsigned)blocks, threads, 0, st>>>(
+        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, (float*)coef[0], (float*)coef[1],
+        (float*)coef[2], (float*)coef[3], (float*)coef[4], (float*)coef[5]);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
+                               double amax, void* cpmlE, void* cpmlH, cudaStream_t st) {
+  if (ncpml <= 0) return cudaSuccess;
+  const int threads = ((ncpml + 1 + 31) / 32) * 32;
+  if (prec == 1)
+    k_cpml<double><<<1, threads, 0, st>>>(ncpml, dt, m, smax, kmax, amax, (double*)cpmlE, (double*)cpmlH);
+  else
+    k_cpml<float><<<1, threads, 0, st>>>(ncpml, dt, m, smax, kmax, amax, (float*)cpmlE, (float*)cpmlH);
+  return cudaGetLastError();
+}
+
+}  // namespace rketd

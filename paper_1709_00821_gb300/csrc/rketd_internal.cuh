@@ -1,0 +1,110 @@
+// Internal declarations shared by the library's translation units.
+//
+// Normalised variables used on the device (all slabs of a context share dz, dt):
+//   E~ = E,  H~ = eta0 H,  J~ = (dt / eps0) J,  S = dt / (dz sqrt(mu0 eps0)),
+// so that Eq. 14 reads H~ -= S (E_{k+1} - E_k) and Eq. 12 reads
+//   E^{n+1} = E^n - S (H~_{k+1/2} - H~_{k-1/2}) - (J~^{n+1} + J~^n) / 2.
+// With x = nu dt, w = wp^2 dt^2, a = e^{-x}, phi1 = (1 - a)/x, phi2 = (a - 1 + x)/x^2,
+// Eq. 11 becomes J~^{n+1} = a J~^n + w phi1 E^n + w phi2 (E^{n+1} - E^n) and Eq. 12 with it
+// substituted, solved for E^{n+1}, is (D = 1 + w phi2 / 2)
+//   E^{n+1} = E^n + da E^n - cb (H~_{k+1/2} - H~_{k-1/2}) - cj J~^n,
+//   da = -(w phi1 / 2)/D,  cb = S/D,  cj = (1 + a)/(2 D),
+//   J~^{n+1} = J~^n + dj J~^n + bp E^n + cc E^{n+1},  dj = a - 1,  bp = w (phi1 - phi2),  cc = w phi2.
+// The six per-cell coefficients are kept as deviations (da, dj) or small terms so that
+// FP32 storage keeps their relative accuracy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rketd {
+
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr int kMaxCells = 32;   // largest cells-per-lane instantiated
+constexpr int kMaxTileProbes = 8;
+
+enum CoefIndex { kDa = 0, kCb = 1, kCj = 2, kDj = 3, kBp = 4, kCc = 5, kNumCoef = 6 };
+
+// One warp tile of the temporally blocked step: 32*K consecutive cells of one slab,
+// loaded from `start` (slab-local, may be negative); after a pass of up to tb_steps
+// steps the cells [vlo, vhi) (tile-local) are exact and are the only ones stored.
+struct Tile {
+  int32_t slab;
+  int32_t src_local;    // tile-local index of the source cell, -1 if not loaded
+  int64_t start;
+  int32_t vlo, vhi;
+  int32_t probe_begin;  // into the tile-probe list
+  int32_t probe_count;
+};
+
+struct TileProbe {
+  int32_t local;  // tile-local cell index (inside [vlo, vhi))
+  int32_t slot;   // index into the probe-series buffer (slab * n_probes + p)
+};
+
+// Everything a step kernel needs; passed by value.
+template <typename T>
+struct StepArgs {
+  const T* E_in;
+  const T* H_in;
+  const T* J_in;
+  T* E_out;
+  T* H_out;
+  T* J_out;
+  const T* coef[kNumCoef];
+  const int64_t* soff;    // [n_slabs] storage offset of each slab
+  const int64_t* nz;      // [n_slabs]
+  const int64_t* src;     // [n_slabs] source cell
+  // CPML (bc == 1): compact memories [n_slabs][2 ends][ncpml] for E and H nodes
+  const T* psiE_in;
+  const T* psiH_in;
+  T* psiE_out;
+  T* psiH_out;
+  const T* cpmlE;   // [3][ncpml+1] b, c, 1/kappa by E-node depth d = 0..ncpml
+  const T* cpmlH;   // [3][ncpml]   b, c, 1/kappa by H-node depth index i (depth i + 1/2)
+  int32_t ncpml;
+  int32_t bc;
+  T S;
+  T qmur;
+  // source (Eq. 15)
+  double dt, tau, t0, amp;
+  int64_t n0;           // step index at pass start (fields hold E^{n0})
+  int32_t nsub;         // steps in this pass
+  // probe series buffer [slot][series_len], written at column series_pos + t
+  T* series;
+  int32_t series_len;
+  int32_t series_pos;
+  // tiles
+  const Tile* tiles;
+  const TileProbe* tprobes;
+  int32_t n_tiles;
+  int32_t total_probes;
+};
+
+// ---- launchers (defined in the .cu files) ----
+cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
+                          const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,
+                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st);
+cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
+                               double amax, void* cpmlE, void* cpmlH, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,
+                              const int64_t* probe_index, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_twiddles(const double* freq, int n_freq, double dt, int64_t m0, int n_samples,
+                            T* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dft(const T* series, int series_len, int n_samples, const T* tw, int total_probes,
+                       int n_freq, double* X_re, double* X_im, cudaStream_t st);
+
+cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* J, int64_t off,
+                                 int64_t nz, double h_scale, double j_scale, double* Eo, double* Ho,
+                                 double* Jo, cudaStream_t st);
+
+}  // namespace rketd

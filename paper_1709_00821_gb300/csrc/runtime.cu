@@ -1,0 +1,813 @@
+// Host runtime behind include/rketd.h: validation, device memory, tile planning, the
+// step loop (plain or temporally blocked passes, DFT block folds), state files and the
+// variant autotuner. Everything numeric runs in the kernels of the other files.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rketd.h"
+#include "rketd_internal.cuh"
+
+using namespace rketd;
+
+namespace {
+
+thread_local std::string g_err;
+
+rketd_status fail(rketd_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+rketd_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(RKETD_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(RKETD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+  } while (0)
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct rketd_ctx {
+  int32_t n_slabs = 0;
+  int prec = 0;
+  size_t esz = 4;
+  rketd_grid1d grid{};
+  rketd_pulse pulse{};
+  int n_probes = 0, n_freq = 0;
+  std::vector<double> freq;
+  std::vector<int64_t> nz, soff, off, src, probe_cell;
+  int64_t n_store = 0, n_cells = 0;
+  double S = 0, qmur = 0;
+  cudaStream_t stream = nullptr;
+  rketd_options opt{};
+
+  // device memory
+  std::vector<void*> allocs;
+  void* E[2] = {nullptr, nullptr};
+  void* H[2] = {nullptr, nullptr};
+  void* J[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* coef[kNumCoef] = {};
+  double* wp2_d = nullptr;
+  double* nu_d = nullptr;
+  int64_t* soff_d = nullptr;
+  int64_t* off_d = nullptr;
+  int64_t* nz_d = nullptr;
+  int64_t* src_d = nullptr;
+  int32_t* cell_slab_d = nullptr;
+  void* psiE[2] = {nullptr, nullptr};
+  void* psiH[2] = {nullptr, nullptr};
+  int64_t n_psi = 0;
+  void* cpmlE = nullptr;
+  void* cpmlH = nullptr;
+  int64_t* probe_index_d = nullptr;
+  double* freq_d = nullptr;
+  void* series = nullptr;
+  void* tw = nullptr;
+  double* Xr = nullptr;
+  double* Xi = nullptr;
+  double* Xtmp = nullptr;  // [2][P*nf] for spectra with pending samples
+  int total_probes = 0;
+
+  // tiles for the current (K, tb_steps)
+  Tile* tiles_d = nullptr;
+  TileProbe* tprobes_d = nullptr;
+  int n_interior = 0, n_edge = 0;
+  int tiles_K = 0, tiles_T = 0;
+
+  int64_t step = 0;
+  int64_t launches = 0;
+
+  ~rketd_ctx() {
+    for (void* p : allocs) cudaFree(p);
+    if (tiles_d) cudaFree(tiles_d);
+    if (tprobes_d) cudaFree(tprobes_d);
+  }
+
+  rketd_status alloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_fail(e, what);
+    }
+    allocs.push_back(*p);
+    return RKETD_OK;
+  }
+  int pos() const { return (int)(step % opt.dft_block); }
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+rketd_status check_options(const rketd_options& o, int prec) {
+  if (o.variant < 0 || o.variant > 2) return fail(RKETD_EINVAL, "options.variant must be 0, 1 or 2");
+  if (prec == 0 && o.cells_per_lane != 0 && o.cells_per_lane != 8 && o.cells_per_lane != 16)
+    return fail(RKETD_EUNSUPPORTED, "FP32 cells_per_lane must be 8 or 16");
+  if (prec == 1 && o.cells_per_lane != 0 && o.cells_per_lane != 4 && o.cells_per_lane != 8)
+    return fail(RKETD_EUNSUPPORTED, "FP64 cells_per_lane must be 4 or 8");
+  if (o.tb_steps != 0 && (o.tb_steps < 4 || o.tb_steps > 64 || o.tb_steps % 4))
+    return fail(RKETD_EINVAL, "tb_steps must be a multiple of 4 in [4, 64]");
+  if (o.warps_per_block < 0 || o.warps_per_block > 4) return fail(RKETD_EINVAL, "warps_per_block must be 1..4");
+  if (o.dft_block < 0) return fail(RKETD_EINVAL, "dft_block must be >= 0");
+  return RKETD_OK;
+}
+
+void fill_auto(rketd_options& o, int prec) {
+  if (o.variant == 0) o.variant = 2;
+  if (o.cells_per_lane == 0) o.cells_per_lane = prec == 1 ? 8 : 16;
+  if (o.tb_steps == 0) o.tb_steps = prec == 1 ? 16 : 32;
+  // a tile must keep at least 32 exact cells
+  while (32 * o.cells_per_lane - 2 * o.tb_steps < 32 && o.tb_steps > 4) o.tb_steps -= 4;
+  if (o.warps_per_block == 0) o.warps_per_block = 4;
+  if (o.dft_block == 0) o.dft_block = 512;
+  o.dft_block = (int32_t)round_up(o.dft_block, o.tb_steps);
+}
+
+// Builds the warp tiles for (K, T): per slab, tiles of W = 32K - 2T exact cells starting at
+// multiples of W, each loading T cells of halo on either side.
+rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
+  const int L = 32 * K;
+  const int W = L - 2 * T;
+  if (W < 4) return fail(RKETD_EINVAL, "tile of %d cells cannot hold %d steps of halo", L, T);
+  const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  std::vector<Tile> interior, edge;
+  std::vector<TileProbe> tp_int, tp_edge;
+  for (int s = 0; s < c->n_slabs; ++s) {
+    const int64_t nz = c->nz[s];
+    for (int64_t j = 0; j * W < nz; ++j) {
+      Tile t{};
+      t.slab = s;
+      t.start = j * W - T;
+      t.vlo = T;
+      t.vhi = (int32_t)std::min<int64_t>(T + W, nz - t.start);
+      const int64_t sl = c->src[s] - t.start;
+      t.src_local = (sl >= 0 && sl < L) ? (int32_t)sl : -1;
+      const bool is_edge = t.start < std::max<int64_t>(1, nc) || t.start + L - 1 > nz - 2 - nc;
+      std::vector<TileProbe>& tps = is_edge ? tp_edge : tp_int;
+      t.probe_begin = (int32_t)tps.size();
+      for (int p = 0; p < c->n_probes; ++p) {
+        const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
+        const int64_t loc = cell - t.start;
+        if (loc >= t.vlo && loc < t.vhi) tps.push_back({(int32_t)loc, s * c->n_probes + p});
+      }
+      t.probe_count = (int32_t)tps.size() - t.probe_begin;
+      if (t.probe_count > kMaxTileProbes) return fail(RKETD_EINVAL, "more than %d probes in one tile", kMaxTileProbes);
+      (is_edge ? edge : interior).push_back(t);
+    }
+  }
+  for (Tile& t : edge) t.probe_begin += (int32_t)tp_int.size();
+  std::vector<Tile> all = interior;
+  all.insert(all.end(), edge.begin(), edge.end());
+  std::vector<TileProbe> tps = tp_int;
+  tps.insert(tps.end(), tp_edge.begin(), tp_edge.end());
+  if (c->tiles_d) cudaFree(c->tiles_d);
+  if (c->tprobes_d) cudaFree(c->tprobes_d);
+  c->tiles_d = nullptr;
+  c->tprobes_d = nullptr;
+  CK(cudaMalloc(&c->tiles_d, sizeof(Tile) * std::max<size_t>(1, all.size())), "tile list");
+  CK(cudaMalloc(&c->tprobes_d, sizeof(TileProbe) * std::max<size_t>(1, tps.size())), "tile probes");
+  CK(cudaMemcpy(c->tiles_d, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice), "tile upload");
+  if (!tps.empty())
+    CK(cudaMemcpy(c->tprobes_d, tps.data(), sizeof(TileProbe) * tps.size(), cudaMemcpyHostToDevice),
+       "tile probe upload");
+  c->n_interior = (int)interior.size();
+  c->n_edge = (int)edge.size();
+  c->tiles_K = K;
+  c->tiles_T = T;
+  return RKETD_OK;
+}
+
+template <typename T>
+StepArgs<T> make_args(rketd_ctx* c, int in, int out) {
+  StepArgs<T> a{};
+  a.E_in = (const T*)c->E[in];
+  a.H_in = (const T*)c->H[in];
+  a.J_in = (const T*)c->J[in];
+  a.E_out = (T*)c->E[out];
+  a.H_out = (T*)c->H[out];
+  a.J_out = (T*)c->J[out];
+  for (int k = 0; k < kNumCoef; ++k) a.coef[k] = (const T*)c->coef[k];
+  a.soff = c->soff_d;
+  a.nz = c->nz_d;
+  a.src = c->src_d;
+  a.psiE_in = (const T*)c->psiE[in];
+  a.psiH_in = (const T*)c->psiH[in];
+  a.psiE_out = (T*)c->psiE[out];
+  a.psiH_out = (T*)c->psiH[out];
+  a.cpmlE = (const T*)c->cpmlE;
+  a.cpmlH = (const T*)c->cpmlH;
+  a.ncpml = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  a.bc = c->grid.bc;
+  a.S = (T)c->S;
+  a.qmur = (T)c->qmur;
+  a.dt = c->grid.dt;
+  a.tau = c->pulse.tau;
+  a.t0 = c->pulse.t0;
+  a.amp = c->pulse.amp;
+  a.n0 = c->step;
+  a.series = (T*)c->series;
+  a.series_len = c->opt.dft_block;
+  a.series_pos = c->pos();
+  a.total_probes = c->total_probes;
+  return a;
+}
+
+// DFT of the first n buffered columns into (Xr, Xi), first sample index m0.
+template <typename T>
+rketd_status dft_block(rketd_ctx* c, int n, int64_t m0, double* Xr, double* Xi) {
+  if (c->total_probes == 0 || n == 0) return RKETD_OK;
+  CK(launch_twiddles<T>(c->freq_d, c->n_freq, c->grid.dt, m0, n, (T*)c->tw, c->stream), "twiddles");
+  CK(launch_dft<T>((const T*)c->series, c->opt.dft_block, n, (const T*)c->tw, c->total_probes, c->n_freq, Xr,
+                   Xi, c->stream),
+     "dft");
+  c->launches += 2;
+  return RKETD_OK;
+}
+
+template <typename T>
+rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
+  const int B = c->opt.dft_block;
+  while (nsteps > 0) {
+    const int pos = c->pos();
+    if (c->opt.variant == 1) {
+      StepArgs<T> a = make_args<T>(c, c->cur, c->cur);
+      a.nsub = 1;
+      if (c->n_slabs > 1 && !c->cell_slab_d) {
+        void* p;
+        rketd_status st = c->alloc(&p, sizeof(int32_t) * c->n_store, "cell-to-slab map");
+        if (st) return st;
+        std::vector<int32_t> m(c->n_store);
+        for (int s = 0; s < c->n_slabs; ++s) {
+          const int64_t end = s + 1 < c->n_slabs ? c->soff[s + 1] : c->n_store;
+          for (int64_t i = c->soff[s]; i < end; ++i) m[i] = s;
+        }
+        CK(cudaMemcpy(p, m.data(), sizeof(int32_t) * c->n_store, cudaMemcpyHostToDevice), "cell-to-slab upload");
+        c->cell_slab_d = (int32_t*)p;
+      }
+      CK(launch_plain_step<T>(a, c->n_slabs > 1 ? c->cell_slab_d : nullptr, c->n_store, c->probe_index_d,
+                              c->stream),
+         "plain step");
+      c->launches += 2 + (c->total_probes > 0);
+      c->step += 1;
+      nsteps -= 1;
+    } else {
+      const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
+      if (c->tiles_K != K || c->tiles_T != TS) {
+        rketd_status st = plan_tiles(c, K, TS);
+        if (st) return st;
+      }
+      const int nsub = (int)std::min<int64_t>({(int64_t)TS, nsteps, (int64_t)(B - pos)});
+      StepArgs<T> a = make_args<T>(c, c->cur, 1 - c->cur);
+      a.nsub = nsub;
+      a.tiles = c->tiles_d;
+      a.tprobes = c->tprobes_d;
+      a.n_tiles = c->n_interior;
+      if (a.n_tiles) {
+        CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "tiled step (interior)");
+        c->launches += 1;
+      }
+      a.tiles = c->tiles_d + c->n_interior;
+      a.n_tiles = c->n_edge;
+      if (a.n_tiles) {
+        CK(launch_tb<T>(a, K, true, c->opt.warps_per_block, c->stream), "tiled step (edge)");
+        c->launches += 1;
+      }
+      c->cur = 1 - c->cur;
+      c->step += nsub;
+      nsteps -= nsub;
+    }
+    if (c->pos() == 0) {
+      rketd_status st = dft_block<T>(c, B, c->step - B + 1, c->Xr, c->Xi);
+      if (st) return st;
+    }
+  }
+  return RKETD_OK;
+}
+
+rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz, const rketd_grid1d* grid,
+                               const double* wp2, const double* nu, const int64_t* src_cell,
+                               const rketd_pulse* pulse, const int64_t* probe_cell, const rketd_dft* dft,
+                               const rketd_options* opt) {
+  if (n_slabs < 1) return fail(RKETD_EINVAL, "n_slabs must be >= 1");
+  if (!nz || !grid || !wp2 || !nu || !src_cell || !pulse) return fail(RKETD_EINVAL, "NULL argument");
+  if (!finite_pos(grid->dz) || !finite_pos(grid->dt)) return fail(RKETD_EINVAL, "dz and dt must be finite and > 0");
+  if (grid->prec != RKETD_F32 && grid->prec != RKETD_F64) return fail(RKETD_EINVAL, "prec must be F32 or F64");
+  if (grid->bc != RKETD_BC_MUR1 && grid->bc != RKETD_BC_CPML) return fail(RKETD_EINVAL, "bc must be MUR1 or CPML");
+  const double S = grid->dt / (grid->dz * std::sqrt(kMu0 * kEps0));
+  if (!(S <= 1.0)) return fail(RKETD_ECOURANT, "Courant number c dt/dz = %.17g exceeds 1", S);
+  if (!finite_pos(pulse->tau) || !std::isfinite(pulse->t0) || !std::isfinite(pulse->amp))
+    return fail(RKETD_EINVAL, "pulse tau must be > 0, t0 and amp finite");
+  const int nc = grid->bc == RKETD_BC_CPML ? grid->cpml_cells : 0;
+  if (grid->bc == RKETD_BC_CPML) {
+    if (grid->cpml_cells < 1) return fail(RKETD_EINVAL, "cpml_cells must be >= 1");
+    if (!finite_pos(grid->cpml_m) || !std::isfinite(grid->cpml_sigma_max) || !(grid->cpml_kappa_max >= 1.0) ||
+        !(grid->cpml_alpha_max >= 0.0))
+      return fail(RKETD_EINVAL, "CPML grading parameters out of range");
+  }
+  const int np = dft ? dft->n_probes : 0;
+  const int nf = dft ? dft->n_freq : 0;
+  if (np < 0 || (np > 0 && (nf < 1 || !dft->freq_hz || !probe_cell)))
+    return fail(RKETD_EINVAL, "probes need n_freq >= 1, freq_hz and probe_cell");
+  c->n_slabs = n_slabs;
+  c->prec = grid->prec;
+  c->esz = grid->prec == RKETD_F64 ? 8 : 4;
+  c->grid = *grid;
+  if (grid->bc == RKETD_BC_CPML && !(grid->cpml_sigma_max > 0))
+    c->grid.cpml_sigma_max = 0.8 * (grid->cpml_m + 1) / (std::sqrt(kMu0 / kEps0) * grid->dz);
+  c->pulse = *pulse;
+  c->n_probes = np;
+  c->n_freq = np > 0 ? nf : 0;
+  for (int f = 0; f < c->n_freq; ++f) {
+    if (!std::isfinite(dft->freq_hz[f]) || dft->freq_hz[f] < 0) return fail(RKETD_EINVAL, "frequencies must be >= 0");
+    c->freq.push_back(dft->freq_hz[f]);
+  }
+  c->S = S;
+  c->qmur = (S - 1.0) / (S + 1.0);
+  int64_t o = 0, so = 0;
+  for (int s = 0; s < n_slabs; ++s) {
+    if (nz[s] < 8) return fail(RKETD_EINVAL, "slab %d: nz = %lld < 8", s, (long long)nz[s]);
+    if (nc && 2 * (int64_t)nc + 4 > nz[s]) return fail(RKETD_EINVAL, "slab %d: CPML thicker than the grid", s);
+    const int64_t sc = src_cell[s];
+    if (sc < std::max<int64_t>(1, nc) || sc > nz[s] - 1 - std::max(1, nc))
+      return fail(RKETD_EINVAL, "slab %d: source cell %lld outside the interior", s, (long long)sc);
+    for (int p = 0; p < np; ++p) {
+      const int64_t pc = probe_cell[(size_t)s * np + p];
+      if (pc < nc || pc > nz[s] - 1 - nc || pc < 0 || pc >= nz[s])
+        return fail(RKETD_EINVAL, "slab %d: probe cell %lld outside the grid or inside the CPML", s, (long long)pc);
+      c->probe_cell.push_back(pc);
+    }
+    c->nz.push_back(nz[s]);
+    c->off.push_back(o);
+    c->soff.push_back(so);
+    c->src.push_back(sc);
+    o += nz[s];
+    so += round_up(nz[s], 32);
+  }
+  c->n_cells = o;
+  c->n_store = so;
+  for (int64_t i = 0; i < o; ++i) {
+    if (!(wp2[i] >= 0) || !std::isfinite(wp2[i])) return fail(RKETD_EINVAL, "wp2[%lld] must be finite and >= 0", (long long)i);
+    if (!(nu[i] >= 0) || !std::isfinite(nu[i])) return fail(RKETD_EINVAL, "nu[%lld] must be finite and >= 0", (long long)i);
+  }
+  c->total_probes = n_slabs * np;
+  rketd_options op{};
+  rketd_default_options(&op);
+  if (opt) op = *opt;
+  rketd_status st = check_options(op, c->prec);
+  if (st) return st;
+  fill_auto(op, c->prec);
+  c->opt = op;
+  return RKETD_OK;
+}
+
+rketd_status zero_state(rketd_ctx* c) {
+  const size_t fb = c->esz * c->n_store;
+  for (int b = 0; b < 2; ++b) {
+    CK(cudaMemsetAsync(c->E[b], 0, fb, c->stream), "memset E");
+    CK(cudaMemsetAsync(c->H[b], 0, fb, c->stream), "memset H");
+    CK(cudaMemsetAsync(c->J[b], 0, fb, c->stream), "memset J");
+    if (c->n_psi) {
+      CK(cudaMemsetAsync(c->psiE[b], 0, c->esz * c->n_psi, c->stream), "memset psi");
+      CK(cudaMemsetAsync(c->psiH[b], 0, c->esz * c->n_psi, c->stream), "memset psi");
+    }
+  }
+  if (c->total_probes) {
+    const size_t xb = sizeof(double) * c->total_probes * c->n_freq;
+    CK(cudaMemsetAsync(c->Xr, 0, xb, c->stream), "memset X");
+    CK(cudaMemsetAsync(c->Xi, 0, xb, c->stream), "memset X");
+  }
+  c->cur = 0;
+  c->step = 0;
+  return RKETD_OK;
+}
+
+rketd_status update_coeffs(rketd_ctx* c) {
+  CK(launch_coeffs(c->prec, c->wp2_d, c->nu_d, c->soff_d, c->off_d, c->nz_d, c->n_slabs, c->n_store, c->grid.dt,
+                   c->S, c->coef, c->stream),
+     "coefficient kernel");
+  c->launches += 1;
+  return RKETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rketd_default_options(rketd_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->use_graphs = 0;
+}
+
+const char* rketd_last_error(void) { return g_err.c_str(); }
+
+const char* rketd_version(void) { return "rketd-gb300 0.1 (sm_103a)"; }
+
+rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rketd_grid1d* grid, const double* wp2,
+                                   const double* nu, const int64_t* src_cell, const rketd_pulse* pulse,
+                                   const int64_t* probe_cell, const rketd_dft* dft, const rketd_options* opt,
+                                   void* stream, rketd_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(RKETD_EINVAL, "out is NULL");
+  *out = nullptr;
+  rketd_ctx* c = new (std::nothrow) rketd_ctx();
+  if (!c) return fail(RKETD_ENOMEM, "host allocation");
+  rketd_status st = validate_and_copy(c, n_slabs, nz, grid, wp2, nu, src_cell, pulse, probe_cell, dft, opt);
+  if (st) {
+    delete c;
+    return st;
+  }
+  c->stream = (cudaStream_t)stream;
+  auto cleanup = [&](rketd_status s) {
+    delete c;
+    return s;
+  };
+  const size_t fb = c->esz * c->n_store;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = c->alloc(&c->E[b], fb, "E"))) return cleanup(st);
+    if ((st = c->alloc(&c->H[b], fb, "H"))) return cleanup(st);
+    if ((st = c->alloc(&c->J[b], fb, "J"))) return cleanup(st);
+  }
+  for (int k = 0; k < kNumCoef; ++k)
+    if ((st = c->alloc(&c->coef[k], fb, "coefficients"))) return cleanup(st);
+  void* p;
+  if ((st = c->alloc(&p, sizeof(double) * c->n_cells, "wp2"))) return cleanup(st);
+  c->wp2_d = (double*)p;
+  if ((st = c->alloc(&p, sizeof(double) * c->n_cells, "nu"))) return cleanup(st);
+  c->nu_d = (double*)p;
+  const size_t sb = sizeof(int64_t) * n_slabs;
+  if ((st = c->alloc(&p, sb, "slab table"))) return cleanup(st);
+  c->soff_d = (int64_t*)p;
+  if ((st = c->alloc(&p, sb, "slab table"))) return cleanup(st);
+  c->off_d = (int64_t*)p;
+  if ((st = c->alloc(&p, sb, "slab table"))) return cleanup(st);
+  c->nz_d = (int64_t*)p;
+  if ((st = c->alloc(&p, sb, "slab table"))) return cleanup(st);
+  c->src_d = (int64_t*)p;
+  const int nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  if (nc) {
+    c->n_psi = (int64_t)n_slabs * 2 * nc;
+    for (int b = 0; b < 2; ++b) {
+      if ((st = c->alloc(&c->psiE[b], c->esz * c->n_psi, "CPML memory"))) return cleanup(st);
+      if ((st = c->alloc(&c->psiH[b], c->esz * c->n_psi, "CPML memory"))) return cleanup(st);
+    }
+    if ((st = c->alloc(&c->cpmlE, c->esz * 3 * (nc + 1), "CPML table"))) return cleanup(st);
+    if ((st = c->alloc(&c->cpmlH, c->esz * 3 * nc, "CPML table"))) return cleanup(st);
+  }
+  if (c->total_probes) {
+    const int P = c->total_probes, nf = c->n_freq, B = c->opt.dft_block;
+    if ((st = c->alloc(&p, sizeof(int64_t) * P, "probe index"))) return cleanup(st);
+    c->probe_index_d = (int64_t*)p;
+    if ((st = c->alloc(&p, sizeof(double) * nf, "frequencies"))) return cleanup(st);
+    c->freq_d = (double*)p;
+    if ((st = c->alloc(&c->series, c->esz * (size_t)P * B, "probe series"))) return cleanup(st);
+    if ((st = c->alloc(&c->tw, c->esz * 2 * (size_t)B * nf, "twiddles"))) return cleanup(st);
+    if ((st = c->alloc(&p, sizeof(double) * (size_t)P * nf, "spectra"))) return cleanup(st);
+    c->Xr = (double*)p;
+    if ((st = c->alloc(&p, sizeof(double) * (size_t)P * nf, "spectra"))) return cleanup(st);
+    c->Xi = (double*)p;
+    if ((st = c->alloc(&p, sizeof(double) * 2 * (size_t)P * nf, "spectra"))) return cleanup(st);
+    c->Xtmp = (double*)p;
+    std::vector<int64_t> pi(P);
+    for (int s = 0; s < n_slabs; ++s)
+      for (int q = 0; q < c->n_probes; ++q) pi[s * c->n_probes + q] = c->soff[s] + c->probe_cell[s * c->n_probes + q];
+    if (cudaMemcpy(c->probe_index_d, pi.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->freq_d, c->freq.data(), sizeof(double) * nf, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(cuda_fail(cudaGetLastError(), "probe upload"));
+  }
+  if (cudaMemcpy(c->soff_d, c->soff.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->off_d, c->off.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->nz_d, c->nz.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->src_d, c->src.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(cuda_fail(cudaGetLastError(), "slab table upload"));
+  // padding cells of the coefficient arrays must hold finite values: zero everything first
+  for (int k = 0; k < kNumCoef; ++k)
+    if (cudaMemsetAsync(c->coef[k], 0, fb, c->stream) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "memset"));
+  if (nc) {
+    cudaError_t e = launch_cpml_tables(c->prec, nc, c->grid.dt, c->grid.cpml_m, c->grid.cpml_sigma_max,
+                                       c->grid.cpml_kappa_max, c->grid.cpml_alpha_max, c->cpmlE, c->cpmlH,
+                                       c->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "CPML tables"));
+    c->launches += 1;
+  }
+  if ((st = zero_state(c))) return cleanup(st);
+  if ((st = rketd_set_medium(c, wp2, nu, 0))) return cleanup(st);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "create"));
+  *out = c;
+  return RKETD_OK;
+}
+
+rketd_status rketd_create_1d(int64_t nz, const rketd_grid1d* grid, const double* wp2, const double* nu,
+                             int64_t src_cell, const rketd_pulse* pulse, const int64_t* probe_cell,
+                             const rketd_dft* dft, const rketd_options* opt, void* stream, rketd_ctx** out) {
+  return rketd_create_batch_1d(1, &nz, grid, wp2, nu, &src_cell, pulse, probe_cell, dft, opt, stream, out);
+}
+
+rketd_status rketd_set_medium(rketd_ctx* c, const double* wp2, const double* nu, int32_t on_device) {
+  if (!c || !wp2 || !nu) return fail(RKETD_EINVAL, "NULL argument");
+  const size_t b = sizeof(double) * c->n_cells;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(c->wp2_d, wp2, b, kind, c->stream), "medium upload");
+  CK(cudaMemcpyAsync(c->nu_d, nu, b, kind, c->stream), "medium upload");
+  return update_coeffs(c);
+}
+
+rketd_status rketd_reset(rketd_ctx* c) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  return zero_state(c);
+}
+
+rketd_status rketd_step(rketd_ctx* c, int64_t nsteps) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  if (nsteps < 0) return fail(RKETD_EINVAL, "nsteps < 0");
+  return c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
+}
+
+rketd_status rketd_sync(rketd_ctx* c) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+  CK(cudaGetLastError(), "device error");
+  return RKETD_OK;
+}
+
+int64_t rketd_step_index(const rketd_ctx* c) { return c ? c->step : -1; }
+
+int64_t rketd_launch_count(const rketd_ctx* c) { return c ? c->launches : -1; }
+
+rketd_status rketd_get_fields(rketd_ctx* c, int32_t slab, double* E, double* H, double* J) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  if (slab < 0 || slab >= c->n_slabs) return fail(RKETD_EINVAL, "slab index out of range");
+  const int64_t nz = c->nz[slab];
+  double* tmp;
+  CK(cudaMallocAsync((void**)&tmp, sizeof(double) * 3 * nz, c->stream), "field staging");
+  const double hs = 1.0 / std::sqrt(kMu0 / kEps0);
+  const double js = kEps0 / c->grid.dt;
+  cudaError_t e = launch_gather_fields(c->prec, c->E[c->cur], c->H[c->cur], c->J[c->cur], c->soff[slab], nz, hs,
+                                       js, tmp, tmp + nz, tmp + 2 * nz, c->stream);
+  c->launches += 1;
+  if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, tmp, sizeof(double) * nz, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && H)
+    e = cudaMemcpyAsync(H, tmp + nz, sizeof(double) * (nz - 1), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && J)
+    e = cudaMemcpyAsync(J, tmp + 2 * nz, sizeof(double) * nz, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_fields");
+  return RKETD_OK;
+}
+
+rketd_status rketd_get_spectra_device(rketd_ctx* c, double* re, double* im) {
+  if (!c || !re || !im) return fail(RKETD_EINVAL, "NULL argument");
+  const size_t n = (size_t)c->total_probes * c->n_freq;
+  if (n == 0) return RKETD_OK;
+  CK(cudaMemcpyAsync(re, c->Xr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "spectra copy");
+  CK(cudaMemcpyAsync(im, c->Xi, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "spectra copy");
+  const int pending = c->pos();
+  if (pending) {
+    rketd_status st = c->prec == RKETD_F64 ? dft_block<double>(c, pending, c->step - pending + 1, re, im)
+                                          : dft_block<float>(c, pending, c->step - pending + 1, re, im);
+    if (st) return st;
+  }
+  return RKETD_OK;
+}
+
+rketd_status rketd_get_spectra(rketd_ctx* c, double* re, double* im) {
+  if (!c || !re || !im) return fail(RKETD_EINVAL, "NULL argument");
+  const size_t n = (size_t)c->total_probes * c->n_freq;
+  if (n == 0) return RKETD_OK;
+  rketd_status st = rketd_get_spectra_device(c, c->Xtmp, c->Xtmp + n);
+  if (st) return st;
+  CK(cudaMemcpyAsync(re, c->Xtmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra D2H");
+  CK(cudaMemcpyAsync(im, c->Xtmp + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra D2H");
+  CK(cudaStreamSynchronize(c->stream), "spectra sync");
+  return RKETD_OK;
+}
+
+rketd_status rketd_rt(const double* tr, const double* ti, const double* ir, const double* ii, int32_t n,
+                      double* Rr, double* Ri, double* Tr, double* Ti) {
+  if (!tr || !ti || !ir || !ii || n < 1) return fail(RKETD_EINVAL, "invalid arguments");
+  // probe 0 = reflection (tot - inc)/inc, probe 1 = transmission tot/inc; arrays are [2][n]
+  for (int f = 0; f < n; ++f) {
+    for (int p = 0; p < 2; ++p) {
+      double* Or = p == 0 ? Rr : Tr;
+      double* Oi = p == 0 ? Ri : Ti;
+      if (!Or || !Oi) continue;
+      const double ar = p == 0 ? tr[f] - ir[f] : tr[n + f];
+      const double ai = p == 0 ? ti[f] - ii[f] : ti[n + f];
+      const double br = ir[p * n + f], bi = ii[p * n + f];
+      const double d = br * br + bi * bi;
+      if (!(d > 0)) return fail(RKETD_ENUMERIC, "incident spectrum is zero at frequency %d", f);
+      Or[f] = (ar * br + ai * bi) / d;
+      Oi[f] = (ai * br - ar * bi) / d;
+    }
+  }
+  return RKETD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct StateHeader {
+  char magic[8];
+  int32_t version, prec, n_slabs, n_probes, n_freq, dft_block;
+  int64_t n_store, n_psi, step;
+};
+
+bool write_dev(FILE* f, const void* dev, size_t bytes, cudaStream_t st) {
+  if (!bytes) return true;
+  std::vector<char> h(bytes);
+  if (cudaMemcpyAsync(h.data(), dev, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) return false;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+  return fwrite(h.data(), 1, bytes, f) == bytes;
+}
+
+bool read_dev(FILE* f, void* dev, size_t bytes, cudaStream_t st) {
+  if (!bytes) return true;
+  std::vector<char> h(bytes);
+  if (fread(h.data(), 1, bytes, f) != bytes) return false;
+  if (cudaMemcpyAsync(dev, h.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
+  return cudaStreamSynchronize(st) == cudaSuccess;
+}
+
+StateHeader header_of(const rketd_ctx* c) {
+  StateHeader h{};
+  std::memcpy(h.magic, "RKETDST1", 8);
+  h.version = 1;
+  h.prec = c->prec;
+  h.n_slabs = c->n_slabs;
+  h.n_probes = c->n_probes;
+  h.n_freq = c->n_freq;
+  h.dft_block = c->opt.dft_block;
+  h.n_store = c->n_store;
+  h.n_psi = c->n_psi;
+  h.step = c->step;
+  return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+rketd_status rketd_save_state(rketd_ctx* c, const char* path) {
+  if (!c || !path) return fail(RKETD_EINVAL, "NULL argument");
+  CK(cudaStreamSynchronize(c->stream), "save_state sync");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(RKETD_EIO, "cannot open %s for writing", path);
+  const StateHeader h = header_of(c);
+  const size_t fb = c->esz * c->n_store, pb = c->esz * c->n_psi;
+  const size_t xb = sizeof(double) * c->total_probes * c->n_freq;
+  const size_t sb = c->esz * (size_t)c->total_probes * c->opt.dft_block;
+  bool ok = fwrite(&h, sizeof h, 1, f) == 1 && write_dev(f, c->E[c->cur], fb, c->stream) &&
+            write_dev(f, c->H[c->cur], fb, c->stream) && write_dev(f, c->J[c->cur], fb, c->stream) &&
+            (!pb || (write_dev(f, c->psiE[c->cur], pb, c->stream) && write_dev(f, c->psiH[c->cur], pb, c->stream))) &&
+            (!xb || (write_dev(f, c->Xr, xb, c->stream) && write_dev(f, c->Xi, xb, c->stream) &&
+                     write_dev(f, c->series, sb, c->stream)));
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(RKETD_EIO, "writing %s failed", path);
+  return RKETD_OK;
+}
+
+rketd_status rketd_load_state(rketd_ctx* c, const char* path) {
+  if (!c || !path) return fail(RKETD_EINVAL, "NULL argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(RKETD_EIO, "cannot open %s", path);
+  StateHeader h{};
+  const StateHeader want = header_of(c);
+  if (fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, want.magic, 8) || h.version != 1) {
+    fclose(f);
+    return fail(RKETD_EIO, "%s is not an RKETD state file", path);
+  }
+  if (h.prec != want.prec || h.n_slabs != want.n_slabs || h.n_probes != want.n_probes || h.n_freq != want.n_freq ||
+      h.dft_block != want.dft_block || h.n_store != want.n_store || h.n_psi != want.n_psi || h.step < 0) {
+    fclose(f);
+    return fail(RKETD_EINVAL, "%s was saved from a context of a different shape", path);
+  }
+  CK(cudaStreamSynchronize(c->stream), "load_state sync");
+  c->cur = 0;
+  const size_t fb = c->esz * c->n_store, pb = c->esz * c->n_psi;
+  const size_t xb = sizeof(double) * c->total_probes * c->n_freq;
+  const size_t sb = c->esz * (size_t)c->total_probes * c->opt.dft_block;
+  bool ok = read_dev(f, c->E[0], fb, c->stream) && read_dev(f, c->H[0], fb, c->stream) &&
+            read_dev(f, c->J[0], fb, c->stream) &&
+            (!pb || (read_dev(f, c->psiE[0], pb, c->stream) && read_dev(f, c->psiH[0], pb, c->stream))) &&
+            (!xb || (read_dev(f, c->Xr, xb, c->stream) && read_dev(f, c->Xi, xb, c->stream) &&
+                     read_dev(f, c->series, sb, c->stream)));
+  fclose(f);
+  if (!ok) return fail(RKETD_EIO, "reading %s failed", path);
+  c->step = h.step;
+  return RKETD_OK;
+}
+
+rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  if (passes < 1) return fail(RKETD_EINVAL, "passes must be >= 1");
+  CK(cudaStreamSynchronize(c->stream), "autotune sync");
+  // save the state
+  const size_t fb = c->esz * c->n_store, pb = c->esz * c->n_psi;
+  const size_t xb = sizeof(double) * c->total_probes * c->n_freq;
+  const size_t sb = c->esz * (size_t)c->total_probes * c->opt.dft_block;
+  std::vector<std::pair<void*, size_t>> saved;
+  auto save = [&](void* src, size_t bytes) -> rketd_status {
+    void* d = nullptr;
+    if (!bytes) { saved.push_back({nullptr, 0}); return RKETD_OK; }
+    CK(cudaMalloc(&d, bytes), "autotune save");
+    saved.push_back({d, bytes});
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, c->stream), "autotune save");
+    return RKETD_OK;
+  };
+  void* srcs[8] = {c->E[c->cur], c->H[c->cur], c->J[c->cur], c->psiE[c->cur], c->psiH[c->cur], c->Xr, c->Xi, c->series};
+  size_t sizes[8] = {fb, fb, fb, pb, pb, xb, xb, sb};
+  rketd_status st = RKETD_OK;
+  for (int i = 0; i < 8 && !st; ++i) st = save(srcs[i], sizes[i]);
+  const int64_t step0 = c->step;
+  const int cur0 = c->cur;
+  const rketd_options opt0 = c->opt;
+  std::vector<std::array<int, 3>> cands;
+  const int Ks32[] = {8, 16}, Ks64[] = {4, 8};
+  const int Ts[] = {8, 16, 24, 32, 48, 64};
+  for (int K : (c->prec == RKETD_F64 ? Ks64 : Ks32))
+    for (int T : Ts)
+      for (int w : {2, 4})
+        if (32 * K - 2 * T >= 64 && opt0.dft_block % T == 0) cands.push_back({K, T, w});
+  float best_ms = 1e30f;
+  rketd_options best = opt0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = cuda_fail(cudaGetLastError(), "autotune events");
+  const int64_t nsteps = (int64_t)passes * 64;
+  for (size_t i = 0; i < cands.size() && !st; ++i) {
+    c->opt.variant = 2;
+    c->opt.cells_per_lane = cands[i][0];
+    c->opt.tb_steps = cands[i][1];
+    c->opt.warps_per_block = cands[i][2];
+    st = rketd_step(c, cands[i][1]);  // warm-up and tile planning
+    if (st) break;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) { st = cuda_fail(cudaGetLastError(), "autotune"); break; }
+    st = rketd_step(c, nsteps);
+    if (st) break;
+    if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = cuda_fail(cudaGetLastError(), "autotune");
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c->opt;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // restore the state
+  c->opt = st ? opt0 : best;
+  c->step = step0;
+  c->cur = cur0;
+  void* dsts[8] = {c->E[c->cur], c->H[c->cur], c->J[c->cur], c->psiE[c->cur], c->psiH[c->cur], c->Xr, c->Xi, c->series};
+  for (size_t i = 0; i < saved.size(); ++i) {
+    if (saved[i].first) {
+      cudaMemcpyAsync(dsts[i], saved[i].first, saved[i].second, cudaMemcpyDeviceToDevice, c->stream);
+      cudaStreamSynchronize(c->stream);
+      cudaFree(saved[i].first);
+    }
+  }
+  return st;
+}
+
+rketd_status rketd_get_options(const rketd_ctx* c, rketd_options* o) {
+  if (!c || !o) return fail(RKETD_EINVAL, "NULL argument");
+  *o = c->opt;
+  return RKETD_OK;
+}
+
+rketd_status rketd_destroy(rketd_ctx* c) {
+  if (!c) return RKETD_OK;
+  cudaStreamSynchronize(c->stream);
+  delete c;
+  return RKETD_OK;
+}
+
+}  // extern "C"

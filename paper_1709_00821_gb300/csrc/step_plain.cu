@@ -1,0 +1,126 @@
+// The paper's two-kernel structure (Sec. III): an H-update kernel then an E-update
+// kernel per time step, one cell per thread, fields in global memory. Here the E kernel
+// also advances J (Eq. 11 needs E^n and E^{n+1} of the same cell, so it stays in a
+// register), adds the Eq. 15 source and applies the end conditions; a third small kernel
+// copies the probe samples. This is the streaming form (one HBM pass per step) that the
+// temporally blocked kernel is measured against.
+#include "rketd_internal.cuh"
+
+namespace rketd {
+namespace {
+
+__device__ __forceinline__ double pulse(double t, double t0, double tau, double amp) {
+  const double u = (t - t0) / tau;
+  return amp * u * exp(-0.5 * u * u);
+}
+
+// slab of storage cell i: cell_slab lookup for batches, slab 0 otherwise
+__device__ __forceinline__ int slab_of(const int32_t* cell_slab, int64_t i) {
+  return cell_slab ? cell_slab[i] : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_plain_h(const StepArgs<T> a, const int32_t* __restrict__ cell_slab,
+                                                 int64_t n_store) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_store) return;
+  const int s = slab_of(cell_slab, i);
+  const int64_t k = i - a.soff[s];
+  const int64_t nz = a.nz[s];
+  if (k > nz - 2) return;  // H nodes k+1/2, k = 0..nz-2
+  T* H = a.H_out;
+  const T dE = a.E_in[i + 1] - a.E_in[i];
+  const int nc = a.ncpml;
+  if (a.bc == 1 && (k < nc || k >= nz - 1 - nc)) {
+    const int ih = (int)(k < nc ? k : nz - 2 - k);
+    const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 2 - k));
+    const T b = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
+    const T psi = fma(b, a.psiH_out[pi], c * dE);
+    a.psiH_out[pi] = psi;
+    H[i] = fma(-a.S, fma(dE, ki, psi), H[i]);
+  } else {
+    H[i] = fma(-a.S, dE, H[i]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int32_t* __restrict__ cell_slab,
+                                                  int64_t n_store) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_store) return;
+  const int s = slab_of(cell_slab, i);
+  const int64_t k = i - a.soff[s];
+  const int64_t nz = a.nz[s];
+  if (k < 1 || k > nz - 2) return;  // interior E nodes; the end cells are set below
+  T* E = a.E_out;
+  T* J = a.J_out;
+  const T dH = a.H_in[i] - a.H_in[i - 1];
+  T curl = dH;
+  const int nc = a.ncpml;
+  if (a.bc == 1 && (k < nc || k > nz - 1 - nc)) {
+    const int d = (int)(k < nc ? k : nz - 1 - k);
+    const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 1 - k));
+    const T b = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
+    const T psi = fma(b, a.psiE_out[pi], c * dH);
+    a.psiE_out[pi] = psi;
+    curl = fma(dH, ki, psi);
+  }
+  const T en = E[i];
+  const T jo = J[i];
+  T enew = fma(a.coef[kDa][i], en, en);
+  enew = fma(-a.coef[kCb][i], curl, enew);
+  enew = fma(-a.coef[kCj][i], jo, enew);
+  T jn = fma(a.coef[kDj][i], jo, jo);
+  jn = fma(a.coef[kBp][i], en, jn);
+  jn = fma(a.coef[kCc][i], enew, jn);
+  J[i] = jn;
+  if (k == a.src[s]) enew += (T)pulse((double)(a.n0 + 1) * a.dt, a.t0, a.tau, a.amp);
+  // The thread of cell 1 owns cell 0 and the thread of cell nz-2 owns cell nz-1: Mur needs
+  // E_1^n and E_1^{n+1}, which only this thread has (cells are updated in place).
+  if (k == 1) {
+    if (a.bc == 0) {
+      const T e0 = E[i - 1];
+      E[i - 1] = fma(a.qmur, enew - e0, en);
+    } else {
+      E[i - 1] = T(0);
+    }
+  }
+  if (k == nz - 2) {
+    if (a.bc == 0) {
+      const T eN = E[i + 1];
+      E[i + 1] = fma(a.qmur, enew - eN, en);
+    } else {
+      E[i + 1] = T(0);
+    }
+  }
+  E[i] = enew;
+}
+
+template <typename T>
+__global__ void k_probe_gather(const T* __restrict__ E, const int64_t* __restrict__ probe_index, int n,
+                               T* __restrict__ series, int series_len, int pos) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) series[(int64_t)p * series_len + pos] = E[probe_index[p]];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,
+                              const int64_t* probe_index, cudaStream_t st) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n_store + threads - 1) / threads);
+  k_plain_h<T><<<blocks, threads, 0, st>>>(a, cell_slab, n_store);
+  k_plain_ej<T><<<blocks, threads, 0, st>>>(a, cell_slab, n_store);
+  if (a.total_probes > 0)
+    k_probe_gather<T><<<(a.total_probes + 127) / 128, 128, 0, st>>>(a.E_out, probe_index, a.total_probes,
+                                                                    a.series, a.series_len, a.series_pos);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_plain_step<float>(const StepArgs<float>&, const int32_t*, int64_t,
+                                              const int64_t*, cudaStream_t);
+template cudaError_t launch_plain_step<double>(const StepArgs<double>&, const int32_t*, int64_t,
+                                               const int64_t*, cudaStream_t);
+
+}  // namespace rketd

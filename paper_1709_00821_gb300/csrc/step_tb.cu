@@ -1,0 +1,296 @@
+// Temporally blocked 1D RKETD-FDTD step (Eqs. 14, 13, 11, 15, ends) on warp tiles.
+//
+// A warp owns 32*K consecutive cells of one slab, K per lane, kept in registers
+// together with the six per-cell update coefficients. One pass advances the tile by up
+// to tb_steps leapfrog steps without leaving the registers: the only exchange between
+// cells of different lanes is one shuffle per half step (E of the right neighbour for
+// Eq. 14, H of the left neighbour for Eq. 12/13). A tile loads tb_steps cells of halo
+// on each side; after t steps the outermost t cells of each side are stale, so the
+// middle 32*K - 2*tb_steps cells are exact and are the only cells stored. Reads come from
+// one copy of the fields and writes go to the other (ping-pong), so neighbouring tiles
+// never see each other's writes within a pass.
+//
+// Two instantiations per (T, K): the interior kernel (every loaded cell is an interior
+// cell of its slab, outside any CPML) carries no boundary code; the edge kernel handles
+// cells outside the slab, the first-order Mur or PEC end cells and the CPML memories.
+#include "rketd_internal.cuh"
+
+namespace rketd {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Eq. 15, normalised by tau: amp ((t - t0)/tau) exp(-(t - t0)^2 / (2 tau^2)).
+__device__ __forceinline__ double pulse(double t, double t0, double tau, double amp) {
+  const double u = (t - t0) / tau;
+  return amp * u * exp(-0.5 * u * u);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ T pick(const T (&r)[K], int i) {
+  T v = T(0);
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q == i) v = r[q];
+  return v;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void put(T (&r)[K], int i, T v) {
+#pragma unroll
+  for (int q = 0; q < K; ++q)
+    if (q == i) r[q] = v;
+}
+
+// Four consecutive values at p (16-byte aligned for float, 32 for double).
+__device__ __forceinline__ void ld4(const float* p, float* r) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* r) {
+  const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  r[0] = q0.x; r[1] = q0.y; r[2] = q1.x; r[3] = q1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float* r) {
+  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* r) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
+}
+
+// K values of slab storage `base` at slab-local cells g0 .. g0+K-1; groups of four
+// outside [0, hi) read as zero (g0 and hi are multiples of 4).
+template <typename T, int K, bool MASK>
+__device__ __forceinline__ void load_row(const T* __restrict__ base, int64_t g0, int64_t hi, T (&r)[K]) {
+#pragma unroll
+  for (int v = 0; v < K / 4; ++v) {
+    const int64_t g = g0 + 4 * v;
+    if (!MASK || (g >= 0 && g < hi)) {
+      ld4(base + g, &r[4 * v]);
+    } else {
+      r[4 * v] = r[4 * v + 1] = r[4 * v + 2] = r[4 * v + 3] = T(0);
+    }
+  }
+}
+
+// Stores the slots whose tile-local index lies in [vlo, vhi).
+template <typename T, int K>
+__device__ __forceinline__ void store_row(T* __restrict__ base, int64_t g0, int li0, int vlo, int vhi,
+                                          const T (&r)[K]) {
+#pragma unroll
+  for (int v = 0; v < K / 4; ++v) {
+    const int li = li0 + 4 * v;
+    if (li >= vlo && li + 4 <= vhi) {
+      st4(base + g0 + 4 * v, &r[4 * v]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (li + q >= vlo && li + q < vhi) base[g0 + 4 * v + q] = r[4 * v + q];
+    }
+  }
+}
+
+template <typename T, int K, bool EDGE>
+__global__ void __launch_bounds__(128) k_tb(const StepArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (tid >= a.n_tiles) return;  // uniform per warp
+  const Tile tl = a.tiles[tid];
+  const int s = tl.slab;
+  const int64_t nz = a.nz[s];
+  const int64_t soff = a.soff[s];
+  const int64_t nzp = (nz + 31) & ~int64_t(31);  // storage extent of the slab
+  const int li0 = lane * K;
+  const int64_t g0 = tl.start + li0;  // slab-local cell of slot 0
+  const T S = a.S;
+
+  T e[K], h[K], jj[K], da[K], cb[K], cj[K], dj[K], bp[K], cc[K];
+  load_row<T, K, EDGE>(a.E_in + soff, g0, nzp, e);
+  load_row<T, K, EDGE>(a.H_in + soff, g0, nzp, h);
+  load_row<T, K, EDGE>(a.J_in + soff, g0, nzp, jj);
+  load_row<T, K, EDGE>(a.coef[kDa] + soff, g0, nzp, da);
+  load_row<T, K, EDGE>(a.coef[kCb] + soff, g0, nzp, cb);
+  load_row<T, K, EDGE>(a.coef[kCj] + soff, g0, nzp, cj);
+  load_row<T, K, EDGE>(a.coef[kDj] + soff, g0, nzp, dj);
+  load_row<T, K, EDGE>(a.coef[kBp] + soff, g0, nzp, bp);
+  load_row<T, K, EDGE>(a.coef[kCc] + soff, g0, nzp, cc);
+
+  // Edge-tile bookkeeping (bit i = slot i).
+  uint32_t mH = 0, mE = 0, mcH = 0, mcE = 0;
+  T pE[EDGE ? K : 1], pH[EDGE ? K : 1];
+  int i0 = -1, i1 = -1;  // slots of cells 0 and nz-1 in this lane
+  const int nc = a.ncpml;
+  const int64_t pbase = (int64_t)s * 2 * nc;
+  if (EDGE) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int64_t g = g0 + i;
+      const bool hasH = g >= 0 && g <= nz - 2;
+      const bool intE = g >= 1 && g <= nz - 2;
+      if (hasH) mH |= 1u << i;
+      if (intE) mE |= 1u << i;
+      pE[i] = T(0);
+      pH[i] = T(0);
+      if (a.bc == 1) {
+        if (intE && (g < nc || g > nz - 1 - nc)) {
+          mcE |= 1u << i;
+          pE[i] = a.psiE_in[pbase + (g < nc ? g : nc + (nz - 1 - g))];
+        }
+        if (hasH && (g < nc || g >= nz - 1 - nc)) {
+          mcH |= 1u << i;
+          pH[i] = a.psiH_in[pbase + (g < nc ? g : nc + (nz - 2 - g))];
+        }
+      }
+      if (g == 0) i0 = i;
+      if (g == nz - 1) i1 = i;
+    }
+  }
+
+  for (int t = 0; t < a.nsub; ++t) {
+    // ---- Eq. 14: H~_{k+1/2} -= S (E_{k+1} - E_k) (CPML: stretched difference + psi) ----
+    const T eR = __shfl_down_sync(kFull, e[0], 1);
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const T en = (i + 1 < K) ? e[i + 1] : eR;
+      const T dE = en - e[i];
+      if (!EDGE) {
+        h[i] = fma(-S, dE, h[i]);
+      } else if (mH & (1u << i)) {
+        if (mcH & (1u << i)) {
+          const int64_t g = g0 + i;
+          const int ih = (int)(g < nc ? g : nz - 2 - g);
+          const T b = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
+          pH[i] = fma(b, pH[i], c * dE);
+          h[i] = fma(-S, fma(dE, ki, pH[i]), h[i]);
+        } else {
+          h[i] = fma(-S, dE, h[i]);
+        }
+      }
+    }
+    // ---- Eqs. 13 + 11: E^{n+1} then J~^{n+1} ----
+    const T hL = __shfl_up_sync(kFull, h[K - 1], 1);
+    T e0o = T(0), e1o = T(0), eN1o = T(0), eN2o = T(0);
+    if (EDGE) {
+      const T eLo = __shfl_up_sync(kFull, e[K - 1], 1);
+      if (i0 >= 0) {
+        e0o = pick(e, i0);
+        e1o = (i0 + 1 < K) ? pick(e, i0 + 1) : eR;
+      }
+      if (i1 >= 0) {
+        eN1o = pick(e, i1);
+        eN2o = (i1 > 0) ? pick(e, i1 - 1) : eLo;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const T hp = i ? h[i - 1] : hL;
+      const T dH = h[i] - hp;
+      T curl = dH;
+      bool upd = true;
+      if (EDGE) {
+        upd = (mE >> i) & 1u;
+        if (mcE & (1u << i)) {
+          const int64_t g = g0 + i;
+          const int d = (int)(g < nc ? g : nz - 1 - g);
+          const T b = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
+          pE[i] = fma(b, pE[i], c * dH);
+          curl = fma(dH, ki, pE[i]);
+        }
+      }
+      if (upd) {
+        const T en = e[i];
+        T enew = fma(da[i], en, en);
+        enew = fma(-cb[i], curl, enew);
+        enew = fma(-cj[i], jj[i], enew);
+        T jn = fma(dj[i], jj[i], jj[i]);
+        jn = fma(bp[i], en, jn);
+        jn = fma(cc[i], enew, jn);
+        e[i] = enew;
+        jj[i] = jn;
+      }
+    }
+    // ---- Eq. 15 soft source at t = (n+1) dt ----
+    if (tl.src_local >= 0 && lane == tl.src_local / K) {
+      const int sl = tl.src_local % K;
+      const double sv = pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
+      put(e, sl, pick(e, sl) + (T)sv);
+    }
+    // ---- ends: first-order Mur or PEC ----
+    if (EDGE) {
+      const T eRn = __shfl_down_sync(kFull, e[0], 1);
+      const T eLn = __shfl_up_sync(kFull, e[K - 1], 1);
+      if (a.bc == 0) {
+        if (i0 >= 0) {
+          const T e1n = (i0 + 1 < K) ? pick(e, i0 + 1) : eRn;
+          put(e, i0, fma(a.qmur, e1n - e0o, e1o));
+        }
+        if (i1 >= 0) {
+          const T eN2n = (i1 > 0) ? pick(e, i1 - 1) : eLn;
+          put(e, i1, fma(a.qmur, eN2n - eN1o, eN2o));
+        }
+      } else {
+        if (i0 >= 0) put(e, i0, T(0));
+        if (i1 >= 0) put(e, i1, T(0));
+      }
+    }
+    // ---- probe samples (only the tile whose exact region holds the probe) ----
+    for (int p = 0; p < tl.probe_count; ++p) {
+      const TileProbe tp = a.tprobes[tl.probe_begin + p];
+      if (lane == tp.local / K)
+        a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick(e, tp.local % K);
+    }
+  }
+
+  store_row<T, K>(a.E_out + soff, g0, li0, tl.vlo, tl.vhi, e);
+  store_row<T, K>(a.H_out + soff, g0, li0, tl.vlo, tl.vhi, h);
+  store_row<T, K>(a.J_out + soff, g0, li0, tl.vlo, tl.vhi, jj);
+  if (EDGE && a.bc == 1) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int li = li0 + i;
+      if (li < tl.vlo || li >= tl.vhi) continue;
+      const int64_t g = g0 + i;
+      if (mcE & (1u << i)) a.psiE_out[pbase + (g < nc ? g : nc + (nz - 1 - g))] = pE[i];
+      if (mcH & (1u << i)) a.psiH_out[pbase + (g < nc ? g : nc + (nz - 2 - g))] = pH[i];
+    }
+  }
+}
+
+template <typename T, int K>
+cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st) {
+  const dim3 block(32 * wpb);
+  const dim3 grid((a.n_tiles + wpb - 1) / wpb);
+  if (edge)
+    k_tb<T, K, true><<<grid, block, 0, st>>>(a);
+  else
+    k_tb<T, K, false><<<grid, block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
+  switch (K) {
+    case 8: return launch_k<float, 8>(a, edge, wpb, st);
+    case 16: return launch_k<float, 16>(a, edge, wpb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
+  switch (K) {
+    case 4: return launch_k<double, 4>(a, edge, wpb, st);
+    case 8: return launch_k<double, 8>(a, edge, wpb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace rketd

@@ -1,0 +1,262 @@
+"""Python binding of librketd.so (include/rketd.h): argument marshalling only.
+
+Every numeric step runs in the library's CUDA kernels. The binding loads the
+in-tree library and raises if it is missing or if no CUDA device is usable; it
+has no fallback path. PyTorch supplies the CUDA stream (and device tensors where
+a call takes device pointers).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librketd.so")
+
+RKETD_F32, RKETD_F64 = 0, 1
+RKETD_BC_MUR1, RKETD_BC_CPML = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ECOURANT", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "EUNSUPPORTED",
+          7: "ENUMERIC", 8: "EIO"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class RketdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rketd {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid1D(ctypes.Structure):
+    _fields_ = [("dz", ctypes.c_double), ("dt", ctypes.c_double), ("prec", ctypes.c_int32),
+                ("bc", ctypes.c_int32), ("cpml_cells", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("cpml_m", ctypes.c_double), ("cpml_sigma_max", ctypes.c_double),
+                ("cpml_kappa_max", ctypes.c_double), ("cpml_alpha_max", ctypes.c_double)]
+
+
+class Pulse(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("t0", ctypes.c_double), ("amp", ctypes.c_double)]
+
+
+class Dft(ctypes.Structure):
+    _fields_ = [("n_probes", ctypes.c_int32), ("n_freq", ctypes.c_int32), ("freq_hz", _dp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("cells_per_lane", ctypes.c_int32), ("tb_steps", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("dft_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rketd_default_options": (None, [ctypes.POINTER(Options)]),
+    "rketd_create_batch_1d": (ctypes.c_int, [ctypes.c_int32, _i64p, ctypes.POINTER(Grid1D), _dp, _dp, _i64p,
+                                             ctypes.POINTER(Pulse), _i64p, ctypes.POINTER(Dft),
+                                             ctypes.POINTER(Options), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "rketd_create_1d": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Grid1D), _dp, _dp, ctypes.c_int64,
+                                       ctypes.POINTER(Pulse), _i64p, ctypes.POINTER(Dft), ctypes.POINTER(Options),
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "rketd_set_medium": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "rketd_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_step_index": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_get_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp, _dp, _dp]),
+    "rketd_get_spectra": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "rketd_get_spectra_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "rketd_rt": (ctypes.c_int, [_dp, _dp, _dp, _dp, ctypes.c_int32, _dp, _dp, _dp, _dp]),
+    "rketd_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "rketd_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "rketd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options)]),
+    "rketd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_last_error": (ctypes.c_char_p, []),
+    "rketd_version": (ctypes.c_char_p, []),
+}
+
+
+def exported_symbols() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """Loads librketd.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first (__graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(st: int):
+    if st != 0:
+        raise RketdError(st, lib().rketd_last_error().decode())
+
+
+def _arr(a, dtype=np.float64):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+def _ptr(a: np.ndarray, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def _default_stream():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the RKETD library runs only on the GPU")
+    return torch.cuda.current_stream().cuda_stream
+
+
+def cpml_params(dz: float, m: float = 3.0):
+    eta0 = np.sqrt(1.25663706212e-6 / 8.8541878128e-12)
+    return m, 0.8 * (m + 1) / (eta0 * dz), 1.0, 0.05
+
+
+class Context:
+    """One rketd_ctx: a batch of 1D slabs advanced together on one CUDA stream."""
+
+    def __init__(self, slabs, prec: str = "f64", options: Optional[dict] = None, stream=None):
+        if not isinstance(slabs, (list, tuple)):
+            slabs = [slabs]
+        L = lib()
+        s0 = slabs[0]
+        self.slabs = list(slabs)
+        self.n_slabs = len(slabs)
+        self.n_probes = len(s0.probes)
+        self.freq = _arr(s0.freq_hz)
+        g = Grid1D()
+        g.dz, g.dt = s0.dz, s0.dt
+        g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
+        g.bc = RKETD_BC_CPML if s0.bc == "cpml" else RKETD_BC_MUR1
+        g.cpml_cells = s0.cpml_cells if s0.bc == "cpml" else 0
+        g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = cpml_params(s0.dz)
+        self.prec = prec
+        p = Pulse(s0.src_tau, s0.src_t0, s0.src_amp)
+        d = Dft(self.n_probes, len(self.freq), _ptr(self.freq))
+        o = Options()
+        L.rketd_default_options(ctypes.byref(o))
+        for k, v in (options or {}).items():
+            setattr(o, k, v)
+        nz = _arr([s.nz for s in slabs], np.int64)
+        wp2 = _arr(np.concatenate([np.asarray(s.wp2, float) for s in slabs]))
+        nu = _arr(np.concatenate([np.asarray(s.nu, float) for s in slabs]))
+        src = _arr([s.src_cell for s in slabs], np.int64)
+        probes = _arr(np.concatenate([np.asarray(s.probes, np.int64) for s in slabs]) if self.n_probes
+                      else np.zeros(1), np.int64)
+        self.stream = _default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(L.rketd_create_batch_1d(self.n_slabs, _ptr(nz, _i64p), ctypes.byref(g), _ptr(wp2), _ptr(nu),
+                                       _ptr(src, _i64p), ctypes.byref(p), _ptr(probes, _i64p), ctypes.byref(d),
+                                       ctypes.byref(o), ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self.h = h
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rketd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def step(self, n: int):
+        _check(lib().rketd_step(self.h, int(n)))
+
+    def sync(self):
+        _check(lib().rketd_sync(self.h))
+
+    def reset(self):
+        _check(lib().rketd_reset(self.h))
+
+    @property
+    def step_index(self) -> int:
+        return lib().rketd_step_index(self.h)
+
+    def set_medium(self, wp2, nu):
+        """Host numpy arrays (copied H2D) or CUDA torch tensors (read on the device), FP64."""
+        if hasattr(wp2, "data_ptr"):
+            assert wp2.is_cuda and nu.is_cuda and wp2.dtype == nu.dtype
+            on_dev = 1
+            pw, pn = ctypes.c_void_p(wp2.data_ptr()), ctypes.c_void_p(nu.data_ptr())
+        elif isinstance(wp2, int):  # raw device or host pointers
+            on_dev = 1
+            pw, pn = ctypes.c_void_p(wp2), ctypes.c_void_p(nu)
+        else:
+            wp2 = _arr(wp2)
+            nu = _arr(nu)
+            self._keep = (wp2, nu)
+            on_dev = 0
+            pw, pn = ctypes.c_void_p(wp2.ctypes.data), ctypes.c_void_p(nu.ctypes.data)
+        _check(lib().rketd_set_medium(self.h, pw, pn, on_dev))
+
+    def set_medium_host_ptr(self, wp2_ptr: int, nu_ptr: int):
+        _check(lib().rketd_set_medium(self.h, ctypes.c_void_p(wp2_ptr), ctypes.c_void_p(nu_ptr), 0))
+
+    def fields(self, slab: int = 0):
+        nz = self.slabs[slab].nz
+        E, H, J = np.empty(nz), np.empty(nz - 1), np.empty(nz)
+        _check(lib().rketd_get_fields(self.h, slab, _ptr(E), _ptr(H), _ptr(J)))
+        return E, H, J
+
+    def spectra(self) -> np.ndarray:
+        n = self.n_slabs * self.n_probes * len(self.freq)
+        re, im = np.empty(n), np.empty(n)
+        _check(lib().rketd_get_spectra(self.h, _ptr(re), _ptr(im)))
+        return (re + 1j * im).reshape(self.n_slabs, self.n_probes, len(self.freq))
+
+    def spectra_device(self, re_ptr: int, im_ptr: int):
+        _check(lib().rketd_get_spectra_device(self.h, ctypes.c_void_p(re_ptr), ctypes.c_void_p(im_ptr)))
+
+    def save(self, path: str):
+        _check(lib().rketd_save_state(self.h, path.encode()))
+
+    def load(self, path: str):
+        _check(lib().rketd_load_state(self.h, path.encode()))
+
+    def autotune(self, passes: int = 8):
+        _check(lib().rketd_autotune(self.h, passes))
+
+    def options(self) -> dict:
+        o = Options()
+        _check(lib().rketd_get_options(self.h, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
+
+    @property
+    def launches(self) -> int:
+        return lib().rketd_launch_count(self.h)
+
+
+def rt(tot: np.ndarray, inc: np.ndarray):
+    """R, T from [2, n_freq] complex spectra (probe 0 reflection, probe 1 transmission)."""
+    n = tot.shape[-1]
+    tr, ti = _arr(tot.real), _arr(tot.imag)
+    ir, ii = _arr(inc.real), _arr(inc.imag)
+    Rr, Ri, Tr, Ti = (np.empty(n) for _ in range(4))
+    _check(lib().rketd_rt(_ptr(tr), _ptr(ti), _ptr(ir), _ptr(ii), n, _ptr(Rr), _ptr(Ri), _ptr(Tr), _ptr(Ti)))
+    return Rr + 1j * Ri, Tr + 1j * Ti

