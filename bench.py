@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""RKETD-FDTD throughput on one GB300: the long inhomogeneous 1D plasma slab.
+
+Workload (synthetic, seeded): Nz = 2^24 cells, dz = 1 um, Courant 0.5, 40000 leapfrog
+steps, Epstein density ramp wp0 = 2pi*50 GHz, L = 2 mm, with a 5% Gaussian ripple, nu
+uniform in [1e9, 5e10] 1/s, 32-cell CPML at both ends, Eq. 15 source, running DFT at two
+probes x 512 frequencies. One bench step = one whole run of that workload: the per-cell
+RKETD coefficient precompute from (wp2, nu), 40000 steps of Eqs. 14/13/11 with the
+source, CPML ends and DFT folds, and the spectra. Fields are FP32 (coefficients from
+FP64, compensated DFT); an FP64 run of the same workload is reported beside it.
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle (OpenMP, all
+host cores) on a bounded prefix of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RKETD-FDTD Gcell-updates/s, % HBM roofline; adjoint/forward time ratio"
+UNIT = "Gcell-updates/s"
+WORKLOAD = ("1D long inhomogeneous Drude slab: Nz=2^24, dz=1um, Courant 0.5, 40000 steps, Epstein wp^2 ramp "
+            "(wp0=2pi*50GHz, L=2mm, 5% seeded ripple), nu~U[1e9,5e10], CPML 32+32, 2 probes x 512 DFT freqs")
+B_ALG = {"f32": 32.0, "f64": 64.0}  # algorithmic bytes per cell-update: E,H,J read+write + wp2,nu read
+FLOPS_PER_CELL_UPDATE = 16.0  # Eq. 14: sub+fma; Eq. 13: sub+3 fma; Eq. 11: 3 fma (fma = 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nz", type=int, default=1 << 24)
+    ap.add_argument("--run-steps", type=int, default=40000)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps per CPU sample (0 = auto)")
+    ap.add_argument("--options", default="", help="library options, e.g. cells_per_lane=16,tb_steps=32")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured", p
+    except Exception:
+        return 6800.0, "fallback", {}
+
+
+def fp32_alu_peak_tflops(clock_mhz: float) -> float:
+    """FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops() -> float:
+    """FP64 FMA throughput measured on this machine's GB300 with an FMA-chain microbenchmark:
+    0.60 TFMA/s = 1.20 TFLOP/s (2 DFMA per clock per SM)."""
+    return 1.20
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.index is not None:
+            cmd += ["-i", str(self.index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        load = [x for x in sm if x > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_record(prec):
+    """Per-cell-update DRAM bytes of the interior tiled kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged (sha256 of step_tb.cu)."""
+    path = os.path.join(ROOT, "profiles", "tb_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "step_tb.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("step_tb_sha256") == sha and prec in rec:
+            return rec[prec]["dram_bytes_per_cell_update"], rec
+    except Exception:
+        pass
+    return None, None
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_baseline(slab, steps_per_sample: int, samples: int, warm: int = 0):
+    """Times the FP64 oracle (OpenMP build, all host cores) on prefixes of the workload."""
+    import oracle
+
+    oracle.build(omp=True)
+    cores = oracle.threads(omp=True)
+    times = []
+    for i in range(warm + samples):
+        t0 = time.perf_counter()
+        oracle.run1d(slab, steps=steps_per_sample, omp=True)
+        dt = time.perf_counter() - t0
+        if i >= warm:
+            times.append(dt)
+    cu = slab.nz * steps_per_sample * samples
+    return cu / sum(times) / 1e9, cores, times
+
+
+def run_reference(args):
+    rank, ws, local, dist = dist_init()
+    if rank != 0:
+        return
+    from paper_1709_00821_gb300 import workloads as wl
+
+    slab = wl.c2_epstein(nz=args.nz, steps=args.run_steps)
+    steps_per = args.cpu_steps or 60
+    val, cores, times = cpu_baseline(slab, steps_per, args.steps, warm=args.warmup)
+    sample = (f"{steps_per}-step prefix of the run (per bench step, incl. the oracle's per-call coefficient "
+              f"setup) on all {args.nz} cells, {args.steps} timed after {args.warmup} warm-up")
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "nz": args.nz, "steps_per_run": args.run_steps},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def parse_options(s):
+    out = {}
+    for kv in filter(None, s.split(",")):
+        k, v = kv.split("=")
+        out[k.strip()] = int(v)
+    return out
+
+
+def gpu_run(args, prec, steps, warmup, slab, wp2_d, nu_d, timing=True, opts=None):
+    """Timed whole runs with device-resident inputs; returns dict of measurements."""
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+
+    ctx = rk.Context(slab, prec, options=opts or None)
+    stream = torch.cuda.current_stream()
+    P = ctx.n_slabs * ctx.n_probes * len(ctx.freq)
+    xr = torch.empty(P, dtype=torch.float64, device="cuda")
+    xi = torch.empty(P, dtype=torch.float64, device="cuda")
+
+    def one_run():
+        ctx.set_medium(wp2_d, nu_d)
+        ctx.reset()
+        ctx.step(slab.steps)
+        ctx.spectra_device(xr.data_ptr(), xi.data_ptr())
+
+    for _ in range(warmup):
+        one_run()
+    ctx.sync()
+    torch.cuda.synchronize()
+    return ctx, one_run, (xr, xi)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+    from paper_1709_00821_gb300 import workloads as wl
+
+    rank, ws, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    dev_index = None
+    try:
+        props = torch.cuda.get_device_properties(local)
+        dev_index = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    except Exception:
+        dev_index = None
+    hbm_peak, peak_kind, peak_rec = peaks()
+    slab = wl.c2_epstein(nz=args.nz, steps=args.run_steps)
+    cells = slab.nz * slab.steps  # cell-updates per bench step
+    wp2_d = torch.from_numpy(slab.wp2).cuda()
+    nu_d = torch.from_numpy(slab.nu).cuda()
+    opts = parse_options(args.options)
+
+    # ---- FP32 headline: device-resident inputs ----
+    ctx, one_run, spec = gpu_run(args, "f32", args.steps, args.warmup, slab, wp2_d, nu_d, opts=opts)
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = ctx.launches
+    ctx.kernel_timing(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_index) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            one_run()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_launches, k_cells = ctx.get_kernel_timing()
+    ctx.kernel_timing(False)
+    launches = ctx.launches - launches0
+    ms_max = max_over_ranks(ms, dist)
+    value = ws * cells * args.steps / (ms_max / 1e3) / 1e9
+    opt_used = ctx.options()
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (interior tiled step)
+    avg_launch_s = k_ms / 1e3 / max(k_launches, 1)
+    cu_per_launch = k_cells / max(k_launches, 1)
+    kern_rate = cu_per_launch / avg_launch_s  # cell-updates/s inside the kernel
+    clock_for_peak = 2070.0
+    alu_peak = fp32_alu_peak_tflops(clock_for_peak)
+    alu_ach = FLOPS_PER_CELL_UPDATE * kern_rate / 1e12
+    bpc, trec = traffic_record("f32")
+    roofline = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+                "traffic": (bpc * cu_per_launch if bpc is not None else None),
+                "kernel": f"k_tb<float,K={opt_used['cells_per_lane']},interior> ({opt_used['tb_steps']} steps/launch)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts x max clock)",
+                "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                "cell_updates_per_launch": cu_per_launch, "avg_launch_ms": avg_launch_s * 1e3}
+    hbm_eff = {"bound": "hbm", "achieved": B_ALG["f32"] * kern_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "frac": B_ALG["f32"] * kern_rate / 1e9 / hbm_peak, "peak_kind": peak_kind,
+               "bytes_per_cell_update": B_ALG["f32"],
+               "whole_step_frac": B_ALG["f32"] * value / ws / hbm_peak,
+               "note": "algorithmic bytes x rate; temporal blocking moves fewer DRAM bytes than this"}
+    if bpc is not None:
+        hbm_eff["dram_bytes_per_cell_update"] = bpc
+        hbm_eff["dram_gbs"] = bpc * kern_rate / 1e9
+
+    # ---- e2e through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hw = torch.from_numpy(slab.wp2).pin_memory()
+        hn = torch.from_numpy(slab.nu).pin_memory()
+        nP = ctx.n_slabs * ctx.n_probes * len(ctx.freq)
+
+        def e2e_run():
+            ctx.set_medium_host_ptr(hw.data_ptr(), hn.data_ptr())
+            ctx.reset()
+            ctx.step(slab.steps)
+            return ctx.spectra()  # device->host, synchronises
+
+        e2e_run()
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_run()
+        t = time.perf_counter() - t0
+        t = max_over_ranks(t, dist)
+        e2e = {"value": ws * cells * args.steps / t / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * slab.nz,
+               "d2h_bytes_per_step": 2 * 8 * nP}
+    ctx.close()
+    del ctx
+
+    # ---- FP64 beside it ----
+    fp64 = None
+    if not args.no_fp64:
+        ctx64, run64, _ = gpu_run(args, "f64", 1, 1, slab, wp2_d, nu_d)
+        barrier(dist)
+        ctx64.kernel_timing(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run64()
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1), dist)
+        k64 = ctx64.get_kernel_timing()
+        o64 = ctx64.options()
+        ctx64.close()
+        v64 = ws * cells / (ms64 / 1e3) / 1e9
+        krate64 = (k64[2] / max(k64[1], 1)) / (k64[0] / 1e3 / max(k64[1], 1))
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1, "dtype": "f64",
+                "roofline": {"bound": "alu", "achieved": FLOPS_PER_CELL_UPDATE * krate64 / 1e12,
+                             "peak": fp64_alu_peak_tflops(), "unit": "TFLOP/s",
+                             "frac": FLOPS_PER_CELL_UPDATE * krate64 / 1e12 / fp64_alu_peak_tflops(),
+                             "kernel": f"k_tb<double,K={o64['cells_per_lane']},interior>",
+                             "peak_source": "measured FP64 FMA-chain throughput (0.60 TFMA/s)"},
+                "hbm_effective": {"achieved": B_ALG["f64"] * krate64 / 1e9, "peak": hbm_peak,
+                                  "frac": B_ALG["f64"] * krate64 / 1e9 / hbm_peak, "unit": "GB/s"}}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        steps_per = args.cpu_steps or 60
+        v, cores, times = cpu_baseline(slab, steps_per, 2, warm=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"2 x {steps_per}-step prefixes of the same workload on all {slab.nz} cells (FP64, "
+                         f"OpenMP build, per-call coefficient setup included), {sum(times):.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nz": slab.nz, "steps_per_run": slab.steps,
+                           "cell_updates_per_step": cells, "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (fields 2x192 MiB + coefficients 384 MiB FP32)",
+                           "variant": f"temporally blocked warp tiles, K={opt_used['cells_per_lane']}, "
+                                      f"{opt_used['tb_steps']} steps/pass, {opt_used['warps_per_block']} warps/CTA",
+                           "precision": "FP32 fields, FP64-derived delta coefficients, Kahan-FP32 DFT blocks into FP64"},
+                "roofline": roofline, "hbm_roofline_effective": hbm_eff, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks, "fp64": fp64, "cpu_baseline": cpu, "adjoint_forward_ratio": None}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

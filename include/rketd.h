@@ -95,15 +95,15 @@ typedef struct {
                            E+J kernel per step), 2 = temporally blocked warp tiles */
   int32_t cells_per_lane;  /* K for the tiled kernel: 8 or 16 (F32), 4 or 8 (F64); 0 = auto */
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
-  int32_t warps_per_block; /* 1..8; 0 = auto */
+  int32_t warps_per_block; /* warps per CTA of the tiled kernel, 1..4; 0 = auto */
   int32_t dft_block;    /* probe samples buffered between DFT folds (multiple of tb_steps); 0 = auto */
-  int32_t use_graphs;   /* 1 = replay captured CUDA graphs for whole DFT blocks */
+  int32_t use_graphs;   /* reserved, must be 0 */
   int32_t reserved[6];
 } rketd_options;
 
 typedef struct rketd_ctx rketd_ctx;
 
-/* Fills *opt with the defaults (auto variant, graphs on). */
+/* Fills *opt with the defaults (every field 0 = auto). */
 void rketd_default_options(rketd_options* opt);
 
 /*
@@ -178,6 +178,15 @@ rketd_status rketd_autotune(rketd_ctx* ctx, int32_t passes);
 
 /* Options in use (after auto selection). */
 rketd_status rketd_get_options(const rketd_ctx* ctx, rketd_options* opt);
+
+/* Enables (1) or disables (0) CUDA-event timing of every launch of the interior tiled
+ * step kernel (the kernel that carries almost all the work) on the context's stream, and
+ * clears the totals. Synchronises. */
+rketd_status rketd_kernel_timing(rketd_ctx* ctx, int32_t enable);
+
+/* Totals since rketd_kernel_timing: summed device time (ms), launches, and exact
+ * cell-updates done by those launches (halo recomputation not counted). Synchronises. */
+rketd_status rketd_get_kernel_timing(rketd_ctx* ctx, double* ms, int64_t* launches, double* cell_updates);
 
 /* Number of kernel launches this context has issued (graph replays count their nodes). */
 int64_t rketd_launch_count(const rketd_ctx* ctx);

@@ -98,7 +98,22 @@ struct rketd_ctx {
   int64_t step = 0;
   int64_t launches = 0;
 
+  // the edge-tile kernel runs on a side stream, overlapping the interior kernel
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+
+  // optional CUDA-event timing of the interior tiled kernel (the dominant kernel)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // pairs: start, stop
+  size_t ev_used = 0;
+  double t_ms = 0, t_cells = 0;
+  int64_t t_launches = 0;
+
   ~rketd_ctx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
     for (void* p : allocs) cudaFree(p);
     if (tiles_d) cudaFree(tiles_d);
     if (tprobes_d) cudaFree(tprobes_d);
@@ -138,45 +153,68 @@ rketd_status check_options(const rketd_options& o, int prec) {
 void fill_auto(rketd_options& o, int prec) {
   if (o.variant == 0) o.variant = 2;
   if (o.cells_per_lane == 0) o.cells_per_lane = prec == 1 ? 8 : 16;
-  if (o.tb_steps == 0) o.tb_steps = prec == 1 ? 16 : 32;
+  if (o.tb_steps == 0) o.tb_steps = prec == 1 ? 4 : 32;
   // a tile must keep at least 32 exact cells
   while (32 * o.cells_per_lane - 2 * o.tb_steps < 32 && o.tb_steps > 4) o.tb_steps -= 4;
-  if (o.warps_per_block == 0) o.warps_per_block = 4;
+  if (o.warps_per_block == 0) o.warps_per_block = 2;
   if (o.dft_block == 0) o.dft_block = 512;
   o.dft_block = (int32_t)round_up(o.dft_block, o.tb_steps);
 }
 
-// Builds the warp tiles for (K, T): per slab, tiles of W = 32K - 2T exact cells starting at
-// multiples of W, each loading T cells of halo on either side.
+// Cells per lane of the edge-tile kernel: narrow tiles keep the boundary code cheap.
+int edge_cells_per_lane(int T) { return 32 * 4 - 2 * T >= 32 ? 4 : 8; }
+
+// Builds the warp tiles for (K, T). Per slab, interior tiles of W = 32K - 2T exact cells
+// cover the middle: their loaded range (T cells of halo each side) stays inside
+// [max(1, ncpml), nz - 2 - ncpml], so the interior kernel needs no boundary code. Narrow
+// edge tiles (Ke cells per lane) cover the two ends, where the Mur/PEC cells, the CPML
+// and cells outside the slab live. Every cell is exact in exactly one tile.
 rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   const int L = 32 * K;
   const int W = L - 2 * T;
-  if (W < 4) return fail(RKETD_EINVAL, "tile of %d cells cannot hold %d steps of halo", L, T);
+  const int Ke = edge_cells_per_lane(T);
+  const int Le = 32 * Ke;
+  const int We = Le - 2 * T;
+  if (W < 4 || We < 4) return fail(RKETD_EINVAL, "tile of %d cells cannot hold %d steps of halo", L, T);
   const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
   std::vector<Tile> interior, edge;
   std::vector<TileProbe> tp_int, tp_edge;
+  auto add = [&](int s, int64_t vstart, int64_t vend, int Lt, bool is_edge) -> rketd_status {
+    Tile t{};
+    t.slab = s;
+    t.start = vstart - T;
+    t.vlo = T;
+    t.vhi = (int32_t)(T + (vend - vstart));
+    const int64_t sl = c->src[s] - t.start;
+    t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
+    std::vector<TileProbe>& tps = is_edge ? tp_edge : tp_int;
+    t.probe_begin = (int32_t)tps.size();
+    for (int p = 0; p < c->n_probes; ++p) {
+      const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
+      const int64_t loc = cell - t.start;
+      if (loc >= t.vlo && loc < t.vhi) tps.push_back({(int32_t)loc, s * c->n_probes + p});
+    }
+    t.probe_count = (int32_t)tps.size() - t.probe_begin;
+    if (t.probe_count > kMaxTileProbes) return fail(RKETD_EINVAL, "more than %d probes in one tile", kMaxTileProbes);
+    (is_edge ? edge : interior).push_back(t);
+    return RKETD_OK;
+  };
   for (int s = 0; s < c->n_slabs; ++s) {
     const int64_t nz = c->nz[s];
-    for (int64_t j = 0; j * W < nz; ++j) {
-      Tile t{};
-      t.slab = s;
-      t.start = j * W - T;
-      t.vlo = T;
-      t.vhi = (int32_t)std::min<int64_t>(T + W, nz - t.start);
-      const int64_t sl = c->src[s] - t.start;
-      t.src_local = (sl >= 0 && sl < L) ? (int32_t)sl : -1;
-      const bool is_edge = t.start < std::max<int64_t>(1, nc) || t.start + L - 1 > nz - 2 - nc;
-      std::vector<TileProbe>& tps = is_edge ? tp_edge : tp_int;
-      t.probe_begin = (int32_t)tps.size();
-      for (int p = 0; p < c->n_probes; ++p) {
-        const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
-        const int64_t loc = cell - t.start;
-        if (loc >= t.vlo && loc < t.vhi) tps.push_back({(int32_t)loc, s * c->n_probes + p});
-      }
-      t.probe_count = (int32_t)tps.size() - t.probe_begin;
-      if (t.probe_count > kMaxTileProbes) return fail(RKETD_EINVAL, "more than %d probes in one tile", kMaxTileProbes);
-      (is_edge ? edge : interior).push_back(t);
-    }
+    const int64_t lo_guard = std::max<int64_t>(1, nc);
+    const int64_t hi_guard = nz - 2 - nc;
+    int64_t a = round_up(lo_guard + T, 4);
+    int64_t n_int = 0;
+    if (a - T + L - 1 <= hi_guard) n_int = (hi_guard - (a - T + L - 1)) / W + 1;
+    if (n_int == 0) a = 0;
+    const int64_t b = a + n_int * W;
+    rketd_status st;
+    for (int64_t v = 0; v < a; v += We)
+      if ((st = add(s, v, std::min<int64_t>(v + We, a), Le, true))) return st;
+    for (int64_t j = 0; j < n_int; ++j)
+      if ((st = add(s, a + j * W, a + (j + 1) * W, L, false))) return st;
+    for (int64_t v = b; v < nz; v += We)
+      if ((st = add(s, v, std::min<int64_t>(v + We, nz), Le, true))) return st;
   }
   for (Tile& t : edge) t.probe_begin += (int32_t)tp_int.size();
   std::vector<Tile> all = interior;
@@ -247,6 +285,34 @@ rketd_status dft_block(rketd_ctx* c, int n, int64_t m0, double* Xr, double* Xi) 
   return RKETD_OK;
 }
 
+rketd_status harvest_timing(rketd_ctx* c) {
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    CK(cudaEventSynchronize(c->ev[i + 1]), "timing event");
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]), "timing event");
+    c->t_ms += ms;
+  }
+  c->ev_used = 0;
+  return RKETD_OK;
+}
+
+rketd_status timing_event(rketd_ctx* c, cudaEvent_t* out) {
+  if (c->ev_used == c->ev.size()) {
+    if (c->ev.size() >= 8192) {
+      rketd_status st = harvest_timing(c);
+      if (st) return st;
+    } else {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "timing event");
+        c->ev.push_back(e);
+      }
+    }
+  }
+  *out = c->ev[c->ev_used++];
+  return RKETD_OK;
+}
+
 template <typename T>
 rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
   const int B = c->opt.dft_block;
@@ -282,19 +348,40 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       const int nsub = (int)std::min<int64_t>({(int64_t)TS, nsteps, (int64_t)(B - pos)});
       StepArgs<T> a = make_args<T>(c, c->cur, 1 - c->cur);
       a.nsub = nsub;
-      a.tiles = c->tiles_d;
       a.tprobes = c->tprobes_d;
+      // Edge tiles first, on the high-priority side stream, so their few long-running warps
+      // start before the interior grid fills the GPU; joined back after the interior launch.
+      const bool forked = c->n_interior && c->n_edge;
+      if (forked) {
+        CK(cudaEventRecord(c->fork, c->stream), "fork");
+        CK(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
+      }
+      if (c->n_edge) {
+        a.tiles = c->tiles_d + c->n_interior;
+        a.n_tiles = c->n_edge;
+        CK(launch_tb<T>(a, edge_cells_per_lane(TS), true, 2, forked ? c->side : c->stream), "tiled step (edge)");
+        c->launches += 1;
+        if (forked) CK(cudaEventRecord(c->join, c->side), "join");
+      }
+      a.tiles = c->tiles_d;
       a.n_tiles = c->n_interior;
       if (a.n_tiles) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->timing) {
+          rketd_status st = timing_event(c, &e0);
+          if (!st) st = timing_event(c, &e1);
+          if (st) return st;
+          CK(cudaEventRecord(e0, c->stream), "timing event");
+        }
         CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "tiled step (interior)");
         c->launches += 1;
+        if (c->timing) {
+          CK(cudaEventRecord(e1, c->stream), "timing event");
+          c->t_launches += 1;
+          c->t_cells += (double)a.n_tiles * (32 * K - 2 * TS) * nsub;
+        }
       }
-      a.tiles = c->tiles_d + c->n_interior;
-      a.n_tiles = c->n_edge;
-      if (a.n_tiles) {
-        CK(launch_tb<T>(a, K, true, c->opt.warps_per_block, c->stream), "tiled step (edge)");
-        c->launches += 1;
-      }
+      if (forked) CK(cudaStreamWaitEvent(c->stream, c->join, 0), "join");
       c->cur = 1 - c->cur;
       c->step += nsub;
       nsteps -= nsub;
@@ -445,6 +532,12 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
     delete c;
     return s;
   };
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(cuda_fail(cudaGetLastError(), "side stream"));
   const size_t fb = c->esz * c->n_store;
   for (int b = 0; b < 2; ++b) {
     if ((st = c->alloc(&c->E[b], fb, "E"))) return cleanup(st);
@@ -795,6 +888,27 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
     }
   }
   return st;
+}
+
+rketd_status rketd_kernel_timing(rketd_ctx* c, int32_t enable) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  CK(cudaStreamSynchronize(c->stream), "timing sync");
+  c->ev_used = 0;
+  c->t_ms = 0;
+  c->t_cells = 0;
+  c->t_launches = 0;
+  c->timing = enable != 0;
+  return RKETD_OK;
+}
+
+rketd_status rketd_get_kernel_timing(rketd_ctx* c, double* ms, int64_t* launches, double* cell_updates) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  rketd_status st = harvest_timing(c);
+  if (st) return st;
+  if (ms) *ms = c->t_ms;
+  if (launches) *launches = c->t_launches;
+  if (cell_updates) *cell_updates = c->t_cells;
+  return RKETD_OK;
 }
 
 rketd_status rketd_get_options(const rketd_ctx* c, rketd_options* o) {

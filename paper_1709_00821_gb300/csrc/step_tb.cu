@@ -15,6 +15,11 @@
 // cells outside the slab, the first-order Mur or PEC end cells and the CPML memories.
 #include "rketd_internal.cuh"
 
+// Resident CTAs of 4 warps per SM the interior kernel is compiled for (register cap).
+#ifndef RKETD_TB_MINB
+#define RKETD_TB_MINB 3
+#endif
+
 namespace rketd {
 namespace {
 
@@ -93,7 +98,7 @@ __device__ __forceinline__ void store_row(T* __restrict__ base, int64_t g0, int 
 }
 
 template <typename T, int K, bool EDGE>
-__global__ void __launch_bounds__(128) k_tb(const StepArgs<T> a) {
+__global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const StepArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (tid >= a.n_tiles) return;  // uniform per warp
@@ -276,6 +281,7 @@ cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
+    case 4: return launch_k<float, 4>(a, edge, wpb, st);
     case 8: return launch_k<float, 8>(a, edge, wpb, st);
     case 16: return launch_k<float, 16>(a, edge, wpb, st);
     default: return cudaErrorInvalidValue;

@@ -77,6 +77,8 @@ _SIGS = {
     "rketd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options)]),
     "rketd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_get_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, _dp]),
     "rketd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
@@ -246,6 +248,15 @@ class Context:
         o = Options()
         _check(lib().rketd_get_options(self.h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
+
+    def kernel_timing(self, enable: bool = True):
+        _check(lib().rketd_kernel_timing(self.h, 1 if enable else 0))
+
+    def get_kernel_timing(self):
+        """(device ms, launches, cell-updates) of the interior tiled kernel since kernel_timing()."""
+        ms, n, cu = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().rketd_get_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(cu)))
+        return ms.value, n.value, cu.value
 
     @property
     def launches(self) -> int:
