@@ -82,6 +82,9 @@ struct StepArgs {
   int32_t total_probes;
 };
 
+// Sets the message rketd_last_error() returns on this thread (defined with the runtime).
+void set_error_message(const char* msg);
+
 // ---- launchers (defined in the .cu files) ----
 cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
                           const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,

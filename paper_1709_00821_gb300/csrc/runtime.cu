@@ -47,6 +47,8 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+void rketd::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 struct rketd_ctx {
   int32_t n_slabs = 0;
   int prec = 0;

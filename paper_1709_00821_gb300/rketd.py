@@ -79,6 +79,10 @@ _SIGS = {
     "rketd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "rketd_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_get_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, _dp]),
+    "rketd_advance_1d_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid1D), ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Pulse),
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "rketd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
@@ -271,3 +275,21 @@ def rt(tot: np.ndarray, inc: np.ndarray):
     Rr, Ri, Tr, Ti = (np.empty(n) for _ in range(4))
     _check(lib().rketd_rt(_ptr(tr), _ptr(ti), _ptr(ir), _ptr(ii), n, _ptr(Rr), _ptr(Ri), _ptr(Tr), _ptr(Ti)))
     return Rr + 1j * Ri, Tr + 1j * Ti
+
+
+def advance_1d_noalloc(slab, prec: str, wp2_dev: int, nu_dev: int, n0: int, nsteps: int, E_dev: int, H_dev: int,
+                       J_dev: int, stream=None):
+    """rketd_advance_1d_noalloc on caller-owned device arrays (raw device pointers, SI units).
+
+    For callers that must not allocate device memory: the library's fixed scratch array
+    holds the working state, so nothing is allocated here or in the library call.
+    """
+    g = Grid1D()
+    g.dz, g.dt = slab.dz, slab.dt
+    g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
+    g.bc = RKETD_BC_MUR1
+    p = Pulse(slab.src_tau, slab.src_t0, slab.src_amp)
+    st = _default_stream() if stream is None else stream
+    _check(lib().rketd_advance_1d_noalloc(ctypes.byref(g), slab.nz, ctypes.c_void_p(wp2_dev), ctypes.c_void_p(nu_dev),
+                                          slab.src_cell, ctypes.byref(p), n0, nsteps, ctypes.c_void_p(E_dev),
+                                          ctypes.c_void_p(H_dev), ctypes.c_void_p(J_dev), ctypes.c_void_p(st)))

@@ -1,0 +1,68 @@
+"""rketd_advance_1d_noalloc: the step entry point for callers that cannot allocate device memory.
+
+Some callers cannot call cudaMalloc: code being recorded into a CUDA stream capture,
+frameworks whose caching allocator owns the whole GPU, loops that cannot pay for the
+device-wide synchronisation of an allocation. The entry point keeps its working memory
+in a fixed array inside the library and only touches the caller's arrays. These tests
+check it against the context API (rketd_create_1d + rketd_step + rketd_get_fields) on
+two calls in a row, with the tolerances the other parity tests use.
+
+This file is named so that pytest collects it last.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1709_00821_gb300 import rketd as rk
+from paper_1709_00821_gb300 import workloads as wl
+
+
+def _scales(slab):
+    eta0 = math.sqrt(wl.MU0 / wl.EPS0)
+    return 1.0, eta0, slab.dt / wl.EPS0  # E, H and J into the same normalised units
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_noalloc_advance_matches_context_api_on_two_calls_in_a_row(prec, tol):
+    import torch
+
+    slab = wl.c1_plain_slab()
+    n1, n2 = 1500, 1337
+    with rk.Context(slab, prec) as ctx:
+        ctx.step(n1)
+        ref1 = ctx.fields(0)
+        ctx.step(n2)
+        ref2 = ctx.fields(0)
+
+    fdt = torch.float64 if prec == "f64" else torch.float32
+    wp2 = torch.tensor(slab.wp2, dtype=torch.float64, device="cuda")
+    nu = torch.tensor(slab.nu, dtype=torch.float64, device="cuda")
+    E = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    H = torch.zeros(slab.nz - 1, dtype=fdt, device="cuda")
+    J = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    ptrs = (E.data_ptr(), H.data_ptr(), J.data_ptr())
+
+    rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), 0, n1, *ptrs)
+    torch.cuda.synchronize()
+    got1 = [t.double().cpu().numpy() for t in (E, H, J)]
+    rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), n1, n2, *ptrs)
+    torch.cuda.synchronize()
+    got2 = [t.double().cpu().numpy() for t in (E, H, J)]
+
+    for got, ref in ((got1, ref1), (got2, ref2)):
+        scale = np.abs(ref[0]).max()
+        assert scale > 1e-3
+        for g, r, k in zip(got, ref, _scales(slab)):
+            assert np.abs(g - r).max() * k <= tol * scale
+
+
+def test_noalloc_rejects_slabs_beyond_the_fixed_capacity():
+    """Checked before any device work: runs without a GPU."""
+    slab = wl.c1_plain_slab(nz=131073, steps=1)
+    slab.src_cell, slab.probes = 100, []
+    with pytest.raises(rk.RketdError) as ei:
+        rk.advance_1d_noalloc(slab, "f64", 1, 1, 0, 1, 1, 1, 1, stream=0)
+    assert ei.value.status == 1
+    assert "131072" in str(ei.value)
