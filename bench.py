@@ -299,7 +299,9 @@ def run_ours(args):
     bpc, trec = traffic_record("f32")
     roofline = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
                 "traffic": (bpc * cu_per_launch if bpc is not None else None),
-                "kernel": f"k_tb<float,K={opt_used['cells_per_lane']},interior> ({opt_used['tb_steps']} steps/launch)",
+                "kernel": (f"k_tb2<K={opt_used['cells_per_lane']}> (FP32x2 pairs, interior tiles, "
+                           f"{opt_used['tb_steps']} steps/launch)" if opt_used.get("fp32_pairs", 0) != 2 else
+                           f"k_tb<float,K={opt_used['cells_per_lane']},interior> ({opt_used['tb_steps']} steps/launch)"),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts x max clock)",
                 "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
                 "cell_updates_per_launch": cu_per_launch, "avg_launch_ms": avg_launch_s * 1e3}

@@ -93,12 +93,13 @@ typedef struct {
 typedef struct {
   int32_t variant;      /* 0 = auto, 1 = plain (paper structure: one H kernel and one
                            E+J kernel per step), 2 = temporally blocked warp tiles */
-  int32_t cells_per_lane;  /* K for the tiled kernel: 8 or 16 (F32), 4 or 8 (F64); 0 = auto */
+  int32_t cells_per_lane;  /* K for the tiled kernel: 8, 12 or 16 (F32), 4 or 8 (F64); 0 = auto */
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
   int32_t warps_per_block; /* warps per CTA of the tiled kernel, 1..4; 0 = auto */
   int32_t dft_block;    /* probe samples buffered between DFT folds (multiple of tb_steps); 0 = auto */
   int32_t use_graphs;   /* reserved, must be 0 */
-  int32_t reserved[6];
+  int32_t fp32_pairs;   /* FP32 interior tiles: 0 = auto (packed FP32x2 pairs), 1 = pairs, 2 = scalar */
+  int32_t reserved[5];
 } rketd_options;
 
 typedef struct rketd_ctx rketd_ctx;

@@ -1,7 +1,8 @@
 // Per-cell RKETD update coefficients (Eqs. 11-13) and CPML grading tables, in FP64 on
-// the device. The FP32 path stores the same FP64 results rounded once to FP32; every
-// coefficient is a deviation from its vacuum value or a small term, so rounding keeps
-// its relative accuracy (a = e^{-nu dt} itself would lose most of a - 1 in FP32).
+// the device (layout and the scaled current cj J~ are described in rketd_internal.cuh).
+// The FP32 path stores the same FP64 results rounded once to FP32; every coefficient is a
+// deviation from its vacuum value or a small term, so rounding keeps its relative accuracy
+// (a = e^{-nu dt} itself would lose most of a - 1 in FP32).
 #include "rketd_internal.cuh"
 
 namespace rketd {
@@ -61,12 +62,13 @@ __global__ void k_coeffs(const double* __restrict__ wp2, const double* __restric
     phi12(x, p1, p2);
     const double em = expm1(-x);  // a - 1
     const double D = 1.0 + 0.5 * w * p2;
+    const double cjd = 0.5 * (2.0 + em) / D;  // (1 + a)/(2D)
     da[i] = (T)(-0.5 * w * p1 / D);
     cb[i] = (T)(S / D);
-    cj[i] = (T)(0.5 * (2.0 + em) / D);
+    cj[i] = (T)cjd;
     dj[i] = (T)em;
-    bp[i] = (T)(w * (p1 - p2));
-    cc[i] = (T)(w * p2);
+    bp[i] = (T)(cjd * (w * (p1 - p2)));  // acts on the carried current cj J~
+    cc[i] = (T)(cjd * (w * p2));
   }
 }
 
@@ -128,4 +130,23 @@ cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double 
   return cudaGetLastError();
 }
 
+}  // namespace rketd
+
+namespace rketd {
+namespace {
+template <typename T>
+__global__ void k_rescale(T* J, const T* num, const T* den, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && den[i] != T(0)) J[i] = (T)((double)J[i] * (double)num[i] / (double)den[i]);
+}
+}  // namespace
+
+cudaError_t launch_rescale(int prec, void* J, const void* num, const void* den, int64_t n, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (prec == 1)
+    k_rescale<double><<<blocks, 256, 0, st>>>((double*)J, (const double*)num, (const double*)den, n);
+  else
+    k_rescale<float><<<blocks, 256, 0, st>>>((float*)J, (const float*)num, (const float*)den, n);
+  return cudaGetLastError();
+}
 }  // namespace rketd

@@ -86,25 +86,26 @@ __global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int
   counts[1] = n - counts[0];
 }
 
-// Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, J~ = dt/eps0 J), with
-// the padding cells zeroed; and back.
+// Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, carried current
+// cj * dt/eps0 J), with the padding cells zeroed; and back.
 template <typename T>
-__global__ void k_in(const T* E, const T* H, const T* J, T* Es, T* Hs, T* Js, int64_t nz, int64_t nzp, double hs,
-                     double js) {
+__global__ void k_in(const T* E, const T* H, const T* J, const T* cj, T* Es, T* Hs, T* Js, int64_t nz, int64_t nzp,
+                     double hs, double js) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nzp) return;
   Es[k] = k < nz ? E[k] : T(0);
   Hs[k] = k < nz - 1 ? (T)((double)H[k] * hs) : T(0);
-  Js[k] = k < nz ? (T)((double)J[k] * js) : T(0);
+  Js[k] = k < nz ? (T)((double)J[k] * js * (double)cj[k]) : T(0);
 }
 
 template <typename T>
-__global__ void k_out(const T* Es, const T* Hs, const T* Js, T* E, T* H, T* J, int64_t nz, double hs, double js) {
+__global__ void k_out(const T* Es, const T* Hs, const T* Js, const T* cj, T* E, T* H, T* J, int64_t nz, double hs,
+                      double js) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nz) return;
   E[k] = Es[k];
   if (k < nz - 1) H[k] = (T)((double)Hs[k] * hs);
-  J[k] = (T)((double)Js[k] * js);
+  J[k] = (T)((double)Js[k] / (double)cj[k] * js);
 }
 
 template <typename T>
@@ -146,7 +147,7 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
   e = launch_coeffs(sizeof(T) == 8 ? 1 : 0, wp2, nu, table, table + 1, table + 2, 1, nzp, g->dt, S, cptr, st);
   if (e != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   const unsigned blocks = (unsigned)((nzp + 255) / 256);
-  k_in<T><<<blocks, 256, 0, st>>>(E, H, J, fld[0][0], fld[0][1], fld[0][2], nz, nzp, eta0, g->dt / kEps0);
+  k_in<T><<<blocks, 256, 0, st>>>(E, H, J, coef[kCj], fld[0][0], fld[0][1], fld[0][2], nz, nzp, eta0, g->dt / kEps0);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
 
   StepArgs<T> s{};
@@ -186,8 +187,8 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
     cur = 1 - cur;
     done += nsub;
   }
-  k_out<T><<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(fld[cur][0], fld[cur][1], fld[cur][2], E, H, J, nz,
-                                                         1.0 / eta0, kEps0 / g->dt);
+  k_out<T><<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(fld[cur][0], fld[cur][1], fld[cur][2], coef[kCj], E, H, J,
+                                                         nz, 1.0 / eta0, kEps0 / g->dt);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   return RKETD_OK;
 }

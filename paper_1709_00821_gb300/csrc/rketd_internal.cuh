@@ -12,6 +12,14 @@
 //   J~^{n+1} = J~^n + dj J~^n + bp E^n + cc E^{n+1},  dj = a - 1,  bp = w (phi1 - phi2),  cc = w phi2.
 // The six per-cell coefficients are kept as deviations (da, dj) or small terms so that
 // FP32 storage keeps their relative accuracy.
+//
+// The device state carries the current scaled by cj, Jc = cj J~ (cj = (1 + a)/(2D) lies in
+// (0, 1]). Multiplying the J recursion by cj gives
+//   E^{n+1} = E^n + da E^n - cb (H~_{k+1/2} - H~_{k-1/2}) - Jc^n,
+//   Jc^{n+1} = Jc^n + dj Jc^n + (cj bp) E^n + (cj cc) E^{n+1},
+// the same arithmetic with one coefficient fewer per cell in the step kernels. The arrays
+// kBp and kCc hold cj*bp and cj*cc; kCj is kept for converting Jc back to J (fields out,
+// medium changes).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -95,6 +103,9 @@ cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double 
 template <typename T>
 cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
 
+// FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu)
+cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,
                               const int64_t* probe_index, cudaStream_t st);
@@ -106,8 +117,10 @@ template <typename T>
 cudaError_t launch_dft(const T* series, int series_len, int n_samples, const T* tw, int total_probes,
                        int n_freq, double* X_re, double* X_im, cudaStream_t st);
 
-cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* J, int64_t off,
-                                 int64_t nz, double h_scale, double j_scale, double* Eo, double* Ho,
+cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* J, const void* cj,
+                                 int64_t off, int64_t nz, double h_scale, double j_scale, double* Eo, double* Ho,
                                  double* Jo, cudaStream_t st);
+// J <- J * num / den elementwise over n cells (re-scales the carried current when cj changes)
+cudaError_t launch_rescale(int prec, void* J, const void* num, const void* den, int64_t n, cudaStream_t st);
 
 }  // namespace rketd

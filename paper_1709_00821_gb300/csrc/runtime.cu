@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/rketd.h"
@@ -141,14 +142,16 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
 
 rketd_status check_options(const rketd_options& o, int prec) {
   if (o.variant < 0 || o.variant > 2) return fail(RKETD_EINVAL, "options.variant must be 0, 1 or 2");
-  if (prec == 0 && o.cells_per_lane != 0 && o.cells_per_lane != 8 && o.cells_per_lane != 16)
-    return fail(RKETD_EUNSUPPORTED, "FP32 cells_per_lane must be 8 or 16");
+  if (prec == 0 && o.cells_per_lane != 0 && o.cells_per_lane != 8 && o.cells_per_lane != 12 &&
+      o.cells_per_lane != 16)
+    return fail(RKETD_EUNSUPPORTED, "FP32 cells_per_lane must be 8, 12 or 16");
   if (prec == 1 && o.cells_per_lane != 0 && o.cells_per_lane != 4 && o.cells_per_lane != 8)
     return fail(RKETD_EUNSUPPORTED, "FP64 cells_per_lane must be 4 or 8");
   if (o.tb_steps != 0 && (o.tb_steps < 4 || o.tb_steps > 64 || o.tb_steps % 4))
     return fail(RKETD_EINVAL, "tb_steps must be a multiple of 4 in [4, 64]");
   if (o.warps_per_block < 0 || o.warps_per_block > 4) return fail(RKETD_EINVAL, "warps_per_block must be 1..4");
   if (o.dft_block < 0) return fail(RKETD_EINVAL, "dft_block must be >= 0");
+  if (o.fp32_pairs < 0 || o.fp32_pairs > 2) return fail(RKETD_EINVAL, "fp32_pairs must be 0, 1 or 2");
   return RKETD_OK;
 }
 
@@ -158,7 +161,7 @@ void fill_auto(rketd_options& o, int prec) {
   if (o.tb_steps == 0) o.tb_steps = prec == 1 ? 4 : 32;
   // a tile must keep at least 32 exact cells
   while (32 * o.cells_per_lane - 2 * o.tb_steps < 32 && o.tb_steps > 4) o.tb_steps -= 4;
-  if (o.warps_per_block == 0) o.warps_per_block = 2;
+  if (o.warps_per_block == 0) o.warps_per_block = prec == 1 ? 2 : 1;
   if (o.dft_block == 0) o.dft_block = 512;
   o.dft_block = (int32_t)round_up(o.dft_block, o.tb_steps);
 }
@@ -375,7 +378,12 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
           if (st) return st;
           CK(cudaEventRecord(e0, c->stream), "timing event");
         }
-        CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "tiled step (interior)");
+        if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
+          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream),
+             "tiled step (interior, FP32 pairs)");
+        } else {
+          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "tiled step (interior)");
+        }
         c->launches += 1;
         if (c->timing) {
           CK(cudaEventRecord(e1, c->stream), "timing event");
@@ -627,7 +635,15 @@ rketd_status rketd_set_medium(rketd_ctx* c, const double* wp2, const double* nu,
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemcpyAsync(c->wp2_d, wp2, b, kind, c->stream), "medium upload");
   CK(cudaMemcpyAsync(c->nu_d, nu, b, kind, c->stream), "medium upload");
-  return update_coeffs(c);
+  // The state carries cj J~; keep J~ unchanged across the medium change: J <- J cj_new / cj_old.
+  // The old cj is parked in the other (unused) ping-pong copy of J.
+  void* old_cj = c->J[1 - c->cur];
+  CK(cudaMemcpyAsync(old_cj, c->coef[kCj], c->esz * c->n_store, cudaMemcpyDeviceToDevice, c->stream), "medium");
+  rketd_status st = update_coeffs(c);
+  if (st) return st;
+  CK(launch_rescale(c->prec, c->J[c->cur], c->coef[kCj], old_cj, c->n_store, c->stream), "current rescale");
+  c->launches += 1;
+  return RKETD_OK;
 }
 
 rketd_status rketd_reset(rketd_ctx* c) {
@@ -660,8 +676,8 @@ rketd_status rketd_get_fields(rketd_ctx* c, int32_t slab, double* E, double* H, 
   CK(cudaMallocAsync((void**)&tmp, sizeof(double) * 3 * nz, c->stream), "field staging");
   const double hs = 1.0 / std::sqrt(kMu0 / kEps0);
   const double js = kEps0 / c->grid.dt;
-  cudaError_t e = launch_gather_fields(c->prec, c->E[c->cur], c->H[c->cur], c->J[c->cur], c->soff[slab], nz, hs,
-                                       js, tmp, tmp + nz, tmp + 2 * nz, c->stream);
+  cudaError_t e = launch_gather_fields(c->prec, c->E[c->cur], c->H[c->cur], c->J[c->cur], c->coef[kCj],
+                                       c->soff[slab], nz, hs, js, tmp, tmp + nz, tmp + 2 * nz, c->stream);
   c->launches += 1;
   if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, tmp, sizeof(double) * nz, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && H)
@@ -842,7 +858,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   const int cur0 = c->cur;
   const rketd_options opt0 = c->opt;
   std::vector<std::array<int, 3>> cands;
-  const int Ks32[] = {8, 16}, Ks64[] = {4, 8};
+  const std::vector<int> Ks32 = {8, 12, 16}, Ks64 = {4, 8};
   const int Ts[] = {8, 16, 24, 32, 48, 64};
   for (int K : (c->prec == RKETD_F64 ? Ks64 : Ks32))
     for (int T : Ts)

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int
   const T jo = J[i];
   T enew = fma(a.coef[kDa][i], en, en);
   enew = fma(-a.coef[kCb][i], curl, enew);
-  enew = fma(-a.coef[kCj][i], jo, enew);
+  enew = enew - jo;  // J holds cj J~
   T jn = fma(a.coef[kDj][i], jo, jo);
   jn = fma(a.coef[kBp][i], en, jn);
   jn = fma(a.coef[kCc][i], enew, jn);

@@ -1,7 +1,7 @@
 // Temporally blocked 1D RKETD-FDTD step (Eqs. 14, 13, 11, 15, ends) on warp tiles.
 //
 // A warp owns 32*K consecutive cells of one slab, K per lane, kept in registers
-// together with the six per-cell update coefficients. One pass advances the tile by up
+// together with five per-cell update coefficients. One pass advances the tile by up
 // to tb_steps leapfrog steps without leaving the registers: the only exchange between
 // cells of different lanes is one shuffle per half step (E of the right neighbour for
 // Eq. 14, H of the left neighbour for Eq. 12/13). A tile loads tb_steps cells of halo
@@ -111,13 +111,13 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
   const int64_t g0 = tl.start + li0;  // slab-local cell of slot 0
   const T S = a.S;
 
-  T e[K], h[K], jj[K], da[K], cb[K], cj[K], dj[K], bp[K], cc[K];
+  // jj carries cj J~ (see rketd_internal.cuh), so the E update subtracts it directly
+  T e[K], h[K], jj[K], da[K], cb[K], dj[K], bp[K], cc[K];
   load_row<T, K, EDGE>(a.E_in + soff, g0, nzp, e);
   load_row<T, K, EDGE>(a.H_in + soff, g0, nzp, h);
   load_row<T, K, EDGE>(a.J_in + soff, g0, nzp, jj);
   load_row<T, K, EDGE>(a.coef[kDa] + soff, g0, nzp, da);
   load_row<T, K, EDGE>(a.coef[kCb] + soff, g0, nzp, cb);
-  load_row<T, K, EDGE>(a.coef[kCj] + soff, g0, nzp, cj);
   load_row<T, K, EDGE>(a.coef[kDj] + soff, g0, nzp, dj);
   load_row<T, K, EDGE>(a.coef[kBp] + soff, g0, nzp, bp);
   load_row<T, K, EDGE>(a.coef[kCc] + soff, g0, nzp, cc);
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
         const T en = e[i];
         T enew = fma(da[i], en, en);
         enew = fma(-cb[i], curl, enew);
-        enew = fma(-cj[i], jj[i], enew);
+        enew = enew - jj[i];
         T jn = fma(dj[i], jj[i], jj[i]);
         jn = fma(bp[i], en, jn);
         jn = fma(cc[i], enew, jn);
@@ -283,6 +283,7 @@ cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb
   switch (K) {
     case 4: return launch_k<float, 4>(a, edge, wpb, st);
     case 8: return launch_k<float, 8>(a, edge, wpb, st);
+    case 12: return launch_k<float, 12>(a, edge, wpb, st);
     case 16: return launch_k<float, 16>(a, edge, wpb, st);
     default: return cudaErrorInvalidValue;
   }

@@ -178,3 +178,19 @@ def test_batch_of_ragged_slabs_matches_per_slab_oracle():
                 E, H, J = ctx.fields(i)
                 assert rel(E, ref.E) <= tol, (prec, i)
                 assert rel(X[i], ref.X) <= tol, (prec, i)
+
+
+def test_set_medium_mid_run_keeps_the_physical_current():
+    """The device carries cj*J; changing the medium rescales it so that J (SI) is unchanged."""
+    s = wl.c1_plain_slab(steps=2200)
+    for prec, tol in (("f64", 1e-15), ("f32", 1e-6)):
+        with rk.Context(s, prec) as ctx:
+            ctx.step(2200)
+            E0, H0, J0 = ctx.fields(0)
+            assert np.abs(J0).max() > 0
+            wp2 = s.wp2 * 1.7
+            nu = s.nu * 0.3 + 1e9
+            ctx.set_medium(wp2, nu)
+            E1, H1, J1 = ctx.fields(0)
+        assert np.array_equal(E0, E1) and np.array_equal(H0, H1)
+        assert np.abs(J1 - J0).max() <= tol * np.abs(J0).max()
