@@ -97,7 +97,8 @@ typedef struct {
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
   int32_t warps_per_block; /* warps per CTA of the tiled kernel, 1..4; 0 = auto */
   int32_t dft_block;    /* probe samples buffered between DFT folds (multiple of tb_steps); 0 = auto */
-  int32_t use_graphs;   /* reserved, must be 0 */
+  int32_t use_graphs;   /* 0 = auto (on), 1 = on, 2 = off: rketd_step calls that repeat an earlier
+                           call's start step, step count and buffer parity replay its CUDA graph */
   int32_t fp32_pairs;   /* FP32 interior tiles: 0 = auto (packed FP32x2 pairs), 1 = pairs, 2 = scalar */
   int32_t reserved[5];
 } rketd_options;

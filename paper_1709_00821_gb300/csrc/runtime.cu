@@ -105,6 +105,18 @@ struct rketd_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 
+  // captured whole rketd_step calls, keyed by (start step, steps, buffer parity)
+  struct GraphEntry {
+    int64_t s0, n;
+    int cur_in, cur_out;
+    int64_t launches;
+    int K, T;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap = nullptr;  // capture/replay stream, forked from and joined to `stream`
+  cudaEvent_t cap_in = nullptr, cap_out = nullptr;
+
   // optional CUDA-event timing of the interior tiled kernel (the dominant kernel)
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // pairs: start, stop
@@ -113,6 +125,10 @@ struct rketd_ctx {
   int64_t t_launches = 0;
 
   ~rketd_ctx() {
+    for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (cap_in) cudaEventDestroy(cap_in);
+    if (cap_out) cudaEventDestroy(cap_out);
+    if (cap) cudaStreamDestroy(cap);
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
@@ -152,6 +168,7 @@ rketd_status check_options(const rketd_options& o, int prec) {
   if (o.warps_per_block < 0 || o.warps_per_block > 4) return fail(RKETD_EINVAL, "warps_per_block must be 1..4");
   if (o.dft_block < 0) return fail(RKETD_EINVAL, "dft_block must be >= 0");
   if (o.fp32_pairs < 0 || o.fp32_pairs > 2) return fail(RKETD_EINVAL, "fp32_pairs must be 0, 1 or 2");
+  if (o.use_graphs < 0 || o.use_graphs > 2) return fail(RKETD_EINVAL, "use_graphs must be 0, 1 or 2");
   return RKETD_OK;
 }
 
@@ -226,6 +243,9 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   all.insert(all.end(), edge.begin(), edge.end());
   std::vector<TileProbe> tps = tp_int;
   tps.insert(tps.end(), tp_edge.begin(), tp_edge.end());
+  // captured graphs point at the old tile lists
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
   if (c->tiles_d) cudaFree(c->tiles_d);
   if (c->tprobes_d) cudaFree(c->tprobes_d);
   c->tiles_d = nullptr;
@@ -509,6 +529,66 @@ rketd_status update_coeffs(rketd_ctx* c) {
   return RKETD_OK;
 }
 
+// rketd_step through a CUDA graph: a call with the same start step, step count, buffer parity
+// and tile shape as an earlier one replays that call's captured launches (a whole run from a
+// reset, for example); otherwise the call is captured on the internal stream and kept (up to
+// 8 graphs). The internal stream is ordered after and before the context's stream by events,
+// so capture works whatever stream the context was given.
+rketd_status step_graph(rketd_ctx* c, int64_t nsteps) {
+  const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
+  if (c->tiles_K != K || c->tiles_T != TS) {
+    rketd_status st = plan_tiles(c, K, TS);
+    if (st) return st;
+  }
+  if (!c->cap) {
+    CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "graph stream");
+    CK(cudaEventCreateWithFlags(&c->cap_in, cudaEventDisableTiming), "graph event");
+    CK(cudaEventCreateWithFlags(&c->cap_out, cudaEventDisableTiming), "graph event");
+  }
+  CK(cudaEventRecord(c->cap_in, c->stream), "graph fork");
+  CK(cudaStreamWaitEvent(c->cap, c->cap_in, 0), "graph fork");
+  rketd_ctx::GraphEntry* hit = nullptr;
+  for (auto& g : c->graphs)
+    if (g.s0 == c->step && g.n == nsteps && g.cur_in == c->cur && g.K == K && g.T == TS) hit = &g;
+  if (!hit) {
+    cudaStream_t user = c->stream;
+    const int64_t s0 = c->step, l0 = c->launches;
+    const int cur0 = c->cur;
+    c->stream = c->cap;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+    rketd_status st = c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+    c->stream = user;
+    if (st || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (!st) st = cuda_fail(e, "graph capture");
+      return st;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    if (c->graphs.size() >= 8) {
+      cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back({s0, nsteps, cur0, c->cur, c->launches - l0, K, TS, exec});
+    hit = &c->graphs.back();
+    // step_impl advanced the host-side state while recording; the replay below does the work
+    c->step = s0;
+    c->cur = cur0;
+    c->launches = l0;
+  }
+  CK(cudaGraphLaunch(hit->exec, c->cap), "graph launch");
+  CK(cudaEventRecord(c->cap_out, c->cap), "graph join");
+  CK(cudaStreamWaitEvent(c->stream, c->cap_out, 0), "graph join");
+  c->step += nsteps;
+  c->cur = hit->cur_out;
+  c->launches += hit->launches;
+  return RKETD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -654,7 +734,10 @@ rketd_status rketd_reset(rketd_ctx* c) {
 rketd_status rketd_step(rketd_ctx* c, int64_t nsteps) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (nsteps < 0) return fail(RKETD_EINVAL, "nsteps < 0");
-  return c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
+  if (nsteps == 0) return RKETD_OK;
+  const bool graphs = c->opt.use_graphs != 2 && !c->timing && c->opt.variant == 2;
+  if (!graphs) return c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
+  return step_graph(c, nsteps);
 }
 
 rketd_status rketd_sync(rketd_ctx* c) {
@@ -872,6 +955,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   const int64_t nsteps = (int64_t)passes * 64;
   for (size_t i = 0; i < cands.size() && !st; ++i) {
     c->opt.variant = 2;
+    c->opt.use_graphs = 2;
     c->opt.cells_per_lane = cands[i][0];
     c->opt.tb_steps = cands[i][1];
     c->opt.warps_per_block = cands[i][2];
@@ -895,6 +979,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   if (e1) cudaEventDestroy(e1);
   // restore the state
   c->opt = st ? opt0 : best;
+  c->opt.use_graphs = opt0.use_graphs;
   c->step = step0;
   c->cur = cur0;
   void* dsts[8] = {c->E[c->cur], c->H[c->cur], c->J[c->cur], c->psiE[c->cur], c->psiH[c->cur], c->Xr, c->Xi, c->series};

@@ -194,3 +194,36 @@ def test_set_medium_mid_run_keeps_the_physical_current():
             E1, H1, J1 = ctx.fields(0)
         assert np.array_equal(E0, E1) and np.array_equal(H0, H1)
         assert np.abs(J1 - J0).max() <= tol * np.abs(J0).max()
+
+
+def test_graph_replay_is_bitwise_identical_to_direct_launches():
+    """The first call of a (start step, steps) pair is captured, later ones replay the graph."""
+    s = wl.c2_epstein(nz=20000, steps=1500, nfreq=32)
+    s.probes = [2032, 14032]
+    for prec in ("f32", "f64"):
+        direct = lib_run(s, prec, use_graphs=2)
+        with rk.Context(s, prec, options={"use_graphs": 1}) as ctx:
+            counts = []
+            for rep in range(3):
+                ctx.reset()
+                l0 = ctx.launches
+                ctx.step(1500)
+                counts.append(ctx.launches - l0)
+                X = ctx.spectra()[0]
+                E, H, J = ctx.fields(0)
+                for a, b in zip((X, E, H, J), direct):
+                    assert np.array_equal(a, b), (prec, rep)
+            assert counts[0] == counts[1] == counts[2] > 0
+
+
+def test_batch_plain_variant_matches_tiled_bitwise():
+    b = wl.c3_batch(subset=[5, 6, 7, 2000], steps=700)
+    outs = {}
+    for variant in (1, 2):
+        with rk.Context(b.slabs, "f32", options={"variant": variant}) as ctx:
+            ctx.step(b.steps)
+            outs[variant] = (ctx.spectra(), [ctx.fields(i) for i in range(len(b.slabs))])
+    assert np.array_equal(outs[1][0], outs[2][0])
+    for f1, f2 in zip(outs[1][1], outs[2][1]):
+        for a, c in zip(f1, f2):
+            assert np.array_equal(a, c)
