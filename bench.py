@@ -34,7 +34,10 @@ UNIT = "Gcell-updates/s"
 WORKLOAD = ("1D long inhomogeneous Drude slab: Nz=2^24, dz=1um, Courant 0.5, 40000 steps, Epstein wp^2 ramp "
             "(wp0=2pi*50GHz, L=2mm, 5% seeded ripple), nu~U[1e9,5e10], CPML 32+32, 2 probes x 512 DFT freqs")
 B_ALG = {"f32": 32.0, "f64": 64.0}  # algorithmic bytes per cell-update: E,H,J read+write + wp2,nu read
-FLOPS_PER_CELL_UPDATE = 16.0  # Eq. 14: sub+fma; Eq. 13: sub+3 fma; Eq. 11: 3 fma (fma = 2 flops)
+# FP32/FP64 arithmetic per cell-update: Eq. 14 sub + fma; Eq. 13 sub + 2 fma + sub (the carried
+# current cj J~ enters by a subtraction); Eq. 11 3 fma. Nine pipe operations, 15 flops (fma = 2).
+OPS_PER_CELL_UPDATE = 9.0
+FLOPS_PER_CELL_UPDATE = 15.0
 
 
 def parse():
@@ -65,15 +68,15 @@ def peaks():
         return 6800.0, "fallback", {}
 
 
-def fp32_alu_peak_tflops(clock_mhz: float) -> float:
-    """FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
-    return 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+def fp32_pipe_peak_tops(clock_mhz: float) -> float:
+    """FP32 pipe operations per second from unit counts: 152 SMs x 128 FP32 lanes x clock."""
+    return 152 * 128 * clock_mhz * 1e6 / 1e12
 
 
-def fp64_alu_peak_tflops() -> float:
-    """FP64 FMA throughput measured on this machine's GB300 with an FMA-chain microbenchmark:
-    0.60 TFMA/s = 1.20 TFLOP/s (2 DFMA per clock per SM)."""
-    return 1.20
+def fp64_pipe_peak_tops() -> float:
+    """FP64 pipe operations per second measured on this machine's GB300 with an FMA-chain
+    microbenchmark: 0.60 T DFMA/s (2 per clock per SM); DADD occupies the same pipe."""
+    return 0.60
 
 
 class ClockSampler:
@@ -132,14 +135,15 @@ class ClockSampler:
 
 
 def traffic_record(prec):
-    """Per-cell-update DRAM bytes of the interior tiled kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged (sha256 of step_tb.cu)."""
+    """Per-cell-update DRAM bytes of the interior tiled kernel from the committed ncu summary
+    (profiles/tb_kernel_traffic.json), valid only while that kernel's source is unchanged."""
     path = os.path.join(ROOT, "profiles", "tb_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "step_tb.cu")
+    src = os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "step_tb2.cu" if prec == "f32" else "step_tb.cu")
+    key = "step_tb2_sha256" if prec == "f32" else "step_tb_sha256"
     try:
         rec = json.load(open(path))
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("step_tb_sha256") == sha and prec in rec:
+        if rec.get(key) == sha and prec in rec:
             return rec[prec]["dram_bytes_per_cell_update"], rec
     except Exception:
         pass
@@ -369,16 +373,18 @@ def run_ours(args):
     cu_per_launch = k_cells / max(k_launches, 1)
     kern_rate = cu_per_launch / avg_launch_s  # cell-updates/s inside the kernel
     clock_for_peak = 2070.0
-    alu_peak = fp32_alu_peak_tflops(clock_for_peak)
-    alu_ach = FLOPS_PER_CELL_UPDATE * kern_rate / 1e12
+    alu_peak = fp32_pipe_peak_tops(clock_for_peak)
+    alu_ach = OPS_PER_CELL_UPDATE * kern_rate / 1e12
     bpc, trec = traffic_record("f32")
-    roofline = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+    roofline = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane-ops)",
+                "frac": alu_ach / alu_peak,
                 "traffic": (bpc * cu_per_launch if bpc is not None else None),
                 "kernel": (f"k_tb2<K={opt_used['cells_per_lane']}> (FP32x2 pairs, interior tiles, "
                            f"{opt_used['tb_steps']} steps/launch)" if opt_used.get("fp32_pairs", 0) != 2 else
                            f"k_tb<float,K={opt_used['cells_per_lane']},interior> ({opt_used['tb_steps']} steps/launch)"),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts x max clock)",
-                "flops_per_cell_update": FLOPS_PER_CELL_UPDATE,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)",
+                "ops_per_cell_update": OPS_PER_CELL_UPDATE,
+                "traffic_source": "ncu dram bytes per exact cell-update (profiles/tb_kernel_traffic.json) x launch",
                 "cell_updates_per_launch": cu_per_launch, "avg_launch_ms": avg_launch_s * 1e3}
     hbm_eff = {"bound": "hbm", "achieved": B_ALG["f32"] * kern_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
                "frac": B_ALG["f32"] * kern_rate / 1e9 / hbm_peak, "peak_kind": peak_kind,
@@ -434,11 +440,11 @@ def run_ours(args):
         v64 = ws * cells / (ms64 / 1e3) / 1e9
         krate64 = (k64[2] / max(k64[1], 1)) / (k64[0] / 1e3 / max(k64[1], 1))
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1, "dtype": "f64",
-                "roofline": {"bound": "alu", "achieved": FLOPS_PER_CELL_UPDATE * krate64 / 1e12,
-                             "peak": fp64_alu_peak_tflops(), "unit": "TFLOP/s",
-                             "frac": FLOPS_PER_CELL_UPDATE * krate64 / 1e12 / fp64_alu_peak_tflops(),
+                "roofline": {"bound": "alu", "achieved": OPS_PER_CELL_UPDATE * krate64 / 1e12,
+                             "peak": fp64_pipe_peak_tops(), "unit": "Tops/s (FP64 pipe ops)",
+                             "frac": OPS_PER_CELL_UPDATE * krate64 / 1e12 / fp64_pipe_peak_tops(),
                              "kernel": f"k_tb<double,K={o64['cells_per_lane']},interior>",
-                             "peak_source": "measured FP64 FMA-chain throughput (0.60 TFMA/s)"},
+                             "peak_source": "measured FP64 FMA-chain throughput (0.60 T DFMA/s)"},
                 "hbm_effective": {"achieved": B_ALG["f64"] * krate64 / 1e9, "peak": hbm_peak,
                                   "frac": B_ALG["f64"] * krate64 / 1e9 / hbm_peak, "unit": "GB/s"}}
 

@@ -73,6 +73,14 @@ def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
             L.or_phi2.argtypes = [ctypes.c_double]
             L.or_phi2.restype = ctypes.c_double
             L.or_threads.restype = ctypes.c_int
+            L.or_dphi1.argtypes = [ctypes.c_double]
+            L.or_dphi1.restype = ctypes.c_double
+            L.or_dphi2.argtypes = [ctypes.c_double]
+            L.or_dphi2.restype = ctypes.c_double
+            L.or_adjoint_step.argtypes = [ctypes.POINTER(OrGrid1D), dp, dp, dp, dp, dp]
+            L.or_adjoint_step.restype = ctypes.c_int
+            L.or_adjoint1d.argtypes = [ctypes.POINTER(OrGrid1D), dp, dp, ip, dp, ctypes.c_int64, dp, dp, dp, dp]
+            L.or_adjoint1d.restype = ctypes.c_int
             _LIBS[key] = L
         return _LIBS[key]
 
@@ -170,3 +178,56 @@ def reflection_transmission(X_tot: np.ndarray, X_inc: np.ndarray):
     R = (X_tot[0] - X_inc[0]) / X_inc[0]
     T = X_tot[1] / X_inc[1] if X_tot.shape[0] > 1 else None
     return R, T
+
+
+def dphi1(x: float) -> float:
+    return lib().or_dphi1(x)
+
+
+def dphi2(x: float) -> float:
+    return lib().or_dphi2(x)
+
+
+def adjoint_step(slab, lE, lH, lJ):
+    """One transposed step (Mur ends, no gradients): returns the adjoint before the step."""
+    g = make_grid(slab)
+    lE = np.ascontiguousarray(lE, float).copy()
+    lH = np.ascontiguousarray(np.concatenate([lH, [0.0]]), float)
+    lJ = np.ascontiguousarray(lJ, float).copy()
+    rc = lib().or_adjoint_step(ctypes.byref(g), _dp(np.ascontiguousarray(slab.wp2, float)),
+                               _dp(np.ascontiguousarray(slab.nu, float)), _dp(lE), _dp(lH), _dp(lJ))
+    if rc:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    return lE, lH[:-1], lJ
+
+
+def adjoint(slab, gX: np.ndarray, steps: Optional[int] = None):
+    """dL/d(wp2), dL/d(nu) per cell for a loss with dL/dX = gX ([n_probes, n_freq] complex:
+    real part dL/dRe X, imaginary part dL/dIm X) after `steps` steps from rest."""
+    g = make_grid(slab)
+    steps = slab.steps if steps is None else steps
+    gr = np.ascontiguousarray(np.real(gX).ravel(), float)
+    gi = np.ascontiguousarray(np.imag(gX).ravel(), float)
+    gw = np.zeros(slab.nz)
+    gn = np.zeros(slab.nz)
+    probes = np.ascontiguousarray(np.asarray(slab.probes, dtype=np.int64))
+    rc = lib().or_adjoint1d(ctypes.byref(g), _dp(np.ascontiguousarray(slab.wp2, float)),
+                            _dp(np.ascontiguousarray(slab.nu, float)),
+                            probes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            _dp(np.ascontiguousarray(slab.freq_hz, float)), steps, _dp(gr), _dp(gi), _dp(gw), _dp(gn))
+    if rc:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    return gw, gn
+
+
+def reflection_loss(X_tot, X_inc, R_target):
+    """L = sum_f (|R(f)| - |R_t(f)|)^2 with R = (X_R^tot - X_R^inc)/X_R^inc at probe 0, and
+    dL/dX (complex: dL/dRe X + j dL/dIm X) for every probe (zero except probe 0)."""
+    d = X_tot[0] - X_inc[0]
+    absr = np.abs(d) / np.abs(X_inc[0])
+    L = float(np.sum((absr - R_target) ** 2))
+    # d|d|/dRe d = Re d/|d|, d|d|/dIm d = Im d/|d|
+    coef = 2.0 * (absr - R_target) / (np.abs(X_inc[0]) * np.abs(d))
+    gX = np.zeros_like(X_tot)
+    gX[0] = coef * d.real + 1j * coef * d.imag
+    return L, gX

@@ -266,6 +266,217 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
   return 0;
 }
 
+
+/* ------------------------------------------------------------------------------------------
+ * Adjoint (reverse mode) of the Mur-terminated scheme, for gradients of a loss that depends on
+ * the running DFT at the probes. Plain form: the forward trajectory is stored whole (state
+ * before every step) and the steps are transposed one at a time in reverse order.
+ * ------------------------------------------------------------------------------------------ */
+
+/* d phi1/dx and d phi2/dx. For x < 1 the term-by-term derivatives of the Taylor series of
+ * or_phi1/or_phi2, sum_j (j+1)(-1)^(j+1) x^j/(j+2)! and sum_j (j+1)(-1)^(j+1) x^j/(j+3)!, are
+ * summed from the smallest term (40 terms); otherwise (a - phi1)/x and (phi1 - 2 phi2)/x. */
+double or_dphi1(double x) {
+  if (x < 1.0) {
+    double terms[40];
+    double fact = 2.0; /* (j+2)! */
+    double xp = 1.0;   /* x^j */
+    for (int j = 0; j < 40; ++j) {
+      terms[j] = (double)(j + 1) * xp / fact * ((j % 2 == 0) ? -1.0 : 1.0);
+      xp *= x;
+      fact *= (double)(j + 3);
+    }
+    double s = 0.0;
+    for (int j = 39; j >= 0; --j) s += terms[j];
+    return s;
+  }
+  return (exp(-x) - or_phi1(x)) / x;
+}
+
+double or_dphi2(double x) {
+  if (x < 1.0) {
+    double terms[40];
+    double fact = 6.0; /* (j+3)! */
+    double xp = 1.0;
+    for (int j = 0; j < 40; ++j) {
+      terms[j] = (double)(j + 1) * xp / fact * ((j % 2 == 0) ? -1.0 : 1.0);
+      xp *= x;
+      fact *= (double)(j + 4);
+    }
+    double s = 0.0;
+    for (int j = 39; j >= 0; --j) s += terms[j];
+    return s;
+  }
+  return (or_phi1(x) - 2.0 * or_phi2(x)) / x;
+}
+
+/* Per-cell constants of Eqs. 11 and 13 (as in or_run1d) and their derivatives with respect to
+ * wp2 (index 0) and nu (index 1):
+ *   a = e^{-nu dt}, b1 = eps0 wp2 dt phi1, b2 = eps0 wp2 dt phi2, D = 1 + h b2 (h = dt/(2 eps0)),
+ *   cEE = (1 - h (b1 - b2))/D, cEH = (dt/eps0)/D, cEJ = h (1 + a)/D. */
+typedef struct {
+  double a, b1, b2, cEE, cEH, cEJ;
+  double da[2], db1[2], db2[2], dcEE[2], dcEH[2], dcEJ[2];
+} or_cell;
+
+static void or_cell_consts(double wp2, double nu, double dt, or_cell* c) {
+  const double x = nu * dt;
+  const double h = dt / (2.0 * OR_EPS0);
+  const double p1 = or_phi1(x), p2 = or_phi2(x);
+  c->a = exp(-x);
+  c->b1 = OR_EPS0 * wp2 * dt * p1;
+  c->b2 = OR_EPS0 * wp2 * dt * p2;
+  const double D = 1.0 + dt / (2.0 * OR_EPS0) * c->b2;
+  c->cEE = (1.0 - dt / (2.0 * OR_EPS0) * (c->b1 - c->b2)) / D;
+  c->cEH = (dt / OR_EPS0) / D;
+  c->cEJ = (dt / (2.0 * OR_EPS0)) * (1.0 + c->a) / D;
+  c->da[0] = 0.0;
+  c->da[1] = -dt * c->a;
+  c->db1[0] = OR_EPS0 * dt * p1;
+  c->db1[1] = OR_EPS0 * wp2 * dt * dt * or_dphi1(x);
+  c->db2[0] = OR_EPS0 * dt * p2;
+  c->db2[1] = OR_EPS0 * wp2 * dt * dt * or_dphi2(x);
+  for (int q = 0; q < 2; ++q) {
+    const double dD = h * c->db2[q];
+    c->dcEE[q] = (-h * (c->db1[q] - c->db2[q]) - c->cEE * dD) / D;
+    c->dcEH[q] = -c->cEH * dD / D;
+    c->dcEJ[q] = (h * c->da[q] - c->cEJ * dD) / D;
+  }
+}
+
+/* One transposed step. On entry (lE, lH, lJ) is the adjoint of the state after step n
+ * (E^{n+1}, H^{n+1/2}, J^{n+1}); on exit the adjoint of the state before it. If the forward
+ * values (E^n, J^n, H^{n+1/2}, E^{n+1} before the source) are given, gW/gN accumulate
+ * lambda^{n+1} . d(step)/d(wp2_k) and d/d(nu_k) for every interior cell. Scratch: tmp[3 nz]. */
+static void or_adjoint_step_impl(const or_grid1d* g, const or_cell* cell, double* lE, double* lH, double* lJ,
+                                 const double* En, const double* Jn, const double* Hh, const double* Enew,
+                                 double* gW, double* gN, double* tmp) {
+  const int64_t nz = g->nz;
+  const double dt = g->dt, dz = g->dz;
+  const double S = dt / (sqrt(OR_MU0 * OR_EPS0) * dz);
+  const double q = (S - 1.0) / (S + 1.0);
+  double* lEpre = tmp;       /* adjoint of E^n */
+  double* lHpost = tmp + nz; /* adjoint of H^{n+1/2} (after the H update) */
+  for (int64_t k = 0; k < nz; ++k) lEpre[k] = 0.0;
+  for (int64_t k = 0; k < nz - 1; ++k) lHpost[k] = lH[k];
+  /* 5. Mur ends: E_0' = E_1 + q (E_1' - E_0), E_{N-1}' = E_{N-2} + q (E_{N-2}' - E_{N-1}). */
+  lE[1] += q * lE[0];
+  lEpre[1] += lE[0];
+  lEpre[0] += -q * lE[0];
+  lE[0] = 0.0;
+  lE[nz - 2] += q * lE[nz - 1];
+  lEpre[nz - 2] += lE[nz - 1];
+  lEpre[nz - 1] += -q * lE[nz - 1];
+  lE[nz - 1] = 0.0;
+  /* 4. the source is additive: nothing to transpose. */
+  /* 2-3. interior E (Eq. 13) and J (Eq. 11). */
+  for (int64_t k = 1; k < nz - 1; ++k) {
+    const or_cell* c = &cell[k];
+    const double lJp = lJ[k];
+    const double mu = lE[k] + c->b2 * lJp; /* adjoint of E^{n+1}_k through both outputs */
+    if (gW && En) {
+      const double dH = Hh[k] - Hh[k - 1];
+      for (int qq = 0; qq < 2; ++qq) {
+        const double dEn = c->dcEE[qq] * En[k] - c->dcEH[qq] * (dH / dz) - c->dcEJ[qq] * Jn[k];
+        const double dJn = c->da[qq] * Jn[k] + c->db1[qq] * En[k] + c->db2[qq] * (Enew[k] - En[k]);
+        const double gval = mu * dEn + lJp * dJn;
+        if (qq == 0) gW[k] += gval; else gN[k] += gval;
+      }
+    }
+    lEpre[k] += c->cEE * mu + (c->b1 - c->b2) * lJp;
+    lJ[k] = -c->cEJ * mu + c->a * lJp;
+    lHpost[k] += -c->cEH / dz * mu;
+    lHpost[k - 1] += c->cEH / dz * mu;
+  }
+  /* J at the two end cells is not updated: its adjoint passes through. */
+  /* 1. Eq. 14: H' = H - dt/(mu0 dz) (E_{k+1} - E_k). */
+  const double cH = dt / (OR_MU0 * dz);
+  for (int64_t k = 0; k < nz - 1; ++k) {
+    lEpre[k + 1] += -cH * lHpost[k];
+    lEpre[k] += cH * lHpost[k];
+    lH[k] = lHpost[k];
+  }
+  for (int64_t k = 0; k < nz; ++k) lE[k] = lEpre[k];
+}
+
+/* Transposed single step without gradients (for dot-product tests): (lE, lH, lJ) in place. */
+int or_adjoint_step(const or_grid1d* g, const double* wp2, const double* nu, double* lE, double* lH, double* lJ) {
+  if (g->bc != 0 || g->nz < 4) return -1;
+  or_cell* cell = (or_cell*)malloc(sizeof(or_cell) * g->nz);
+  double* tmp = (double*)malloc(sizeof(double) * 3 * g->nz);
+  for (int64_t k = 0; k < g->nz; ++k) or_cell_consts(wp2[k], nu[k], g->dt, &cell[k]);
+  or_adjoint_step_impl(g, cell, lE, lH, lJ, NULL, NULL, NULL, NULL, NULL, NULL, tmp);
+  free(cell);
+  free(tmp);
+  return 0;
+}
+
+/*
+ * Gradient of a loss L(X) of the probe spectra after n_steps steps from rest, with respect to
+ * wp2 and nu of every cell. gXr/gXi [n_probes*n_freq] are dL/dRe X and dL/dIm X. The forward
+ * run is or_run1d one step at a time (states stored); the seed of sample m at probe p is
+ * dL/dE_p^m = sum_f (gXr cos(2 pi f m dt) - gXi sin(2 pi f m dt)). Mur ends only.
+ * Outputs grad_wp2[nz], grad_nu[nz] (overwritten). Returns 0 or a negative code.
+ */
+int or_adjoint1d(const or_grid1d* g, const double* wp2, const double* nu, const int64_t* probe_cells,
+                 const double* freq_hz, int64_t n_steps, const double* gXr, const double* gXi, double* grad_wp2,
+                 double* grad_nu) {
+  int rc = or_check(g, probe_cells);
+  if (rc) return rc;
+  if (g->bc != 0) return -5;
+  const int64_t nz = g->nz;
+  const int64_t N = n_steps;
+  double* Et = (double*)calloc((size_t)(N + 1) * nz, sizeof(double));
+  double* Ht = (double*)calloc((size_t)(N + 1) * (nz - 1), sizeof(double));
+  double* Jt = (double*)calloc((size_t)(N + 1) * nz, sizeof(double));
+  double* psiE = (double*)calloc(nz, sizeof(double));
+  double* psiH = (double*)calloc(nz, sizeof(double));
+  double* xr = (double*)calloc((size_t)g->n_probes * g->n_freq + 1, sizeof(double));
+  double* xi = (double*)calloc((size_t)g->n_probes * g->n_freq + 1, sizeof(double));
+  double* E = (double*)calloc(nz, sizeof(double));
+  double* H = (double*)calloc(nz, sizeof(double));
+  double* J = (double*)calloc(nz, sizeof(double));
+  /* forward: state n stored before step n */
+  for (int64_t n = 0; n < N; ++n) {
+    memcpy(Et + n * nz, E, sizeof(double) * nz);
+    memcpy(Ht + n * (nz - 1), H, sizeof(double) * (nz - 1));
+    memcpy(Jt + n * nz, J, sizeof(double) * nz);
+    or_run1d(g, wp2, nu, probe_cells, freq_hz, n, 1, E, H, J, psiE, psiH, xr, xi, NULL);
+  }
+  memcpy(Et + N * nz, E, sizeof(double) * nz);
+  memcpy(Ht + N * (nz - 1), H, sizeof(double) * (nz - 1));
+  memcpy(Jt + N * nz, J, sizeof(double) * nz);
+  /* reverse */
+  or_cell* cell = (or_cell*)malloc(sizeof(or_cell) * nz);
+  for (int64_t k = 0; k < nz; ++k) or_cell_consts(wp2[k], nu[k], g->dt, &cell[k]);
+  double* lE = (double*)calloc(nz, sizeof(double));
+  double* lH = (double*)calloc(nz, sizeof(double));
+  double* lJ = (double*)calloc(nz, sizeof(double));
+  double* tmp = (double*)malloc(sizeof(double) * 3 * nz);
+  double* Enew = (double*)malloc(sizeof(double) * nz);
+  for (int64_t k = 0; k < nz; ++k) grad_wp2[k] = grad_nu[k] = 0.0;
+  for (int64_t n = N - 1; n >= 0; --n) {
+    const int64_t m = n + 1;
+    const double t = (double)m * g->dt;
+    for (int p = 0; p < g->n_probes; ++p) {
+      double seed = 0.0;
+      for (int f = 0; f < g->n_freq; ++f) {
+        const double ph = 2.0 * OR_PI * freq_hz[f] * t;
+        seed += gXr[p * g->n_freq + f] * cos(ph) - gXi[p * g->n_freq + f] * sin(ph);
+      }
+      lE[probe_cells[p]] += seed;
+    }
+    /* E^{n+1} before the source was added */
+    memcpy(Enew, Et + m * nz, sizeof(double) * nz);
+    Enew[g->src_cell] -= or_source(g, t);
+    or_adjoint_step_impl(g, cell, lE, lH, lJ, Et + n * nz, Jt + n * nz, Ht + m * (nz - 1), Enew, grad_wp2, grad_nu,
+                         tmp);
+  }
+  free(Et); free(Ht); free(Jt); free(psiE); free(psiH); free(xr); free(xi); free(E); free(H); free(J);
+  free(cell); free(lE); free(lH); free(lJ); free(tmp); free(Enew);
+  return 0;
+}
+
 /* Number of OpenMP threads this build uses (1 for the serial build). */
 int or_threads(void) {
 #ifdef _OPENMP
