@@ -168,6 +168,29 @@ rketd_status rketd_rt(const double* tot_re, const double* tot_im, const double* 
                       const double* inc_im, int32_t n_freq, double* R_re, double* R_im, double* T_re,
                       double* T_im);
 
+/* Resets the context and runs nsteps steps from rest (as rketd_reset + rketd_step), keeping
+ * a copy of the full state every ckpt_every steps for rketd_adjoint. First-order Mur ends
+ * and the tiled variant only (RKETD_EUNSUPPORTED otherwise). The spectra of the run are
+ * available as after rketd_step. */
+rketd_status rketd_forward_ckpt(rketd_ctx* ctx, int64_t nsteps, int32_t ckpt_every);
+
+/*
+ * Discrete adjoint of the last rketd_forward_ckpt run (the transpose of Eqs. 14, 13, 11 and
+ * the Mur ends, step by step in reverse): gradients of a loss L(X) of the probe spectra with
+ * respect to the plasma frequency squared and the collision frequency of every cell in
+ * [w_lo, w_hi) of every slab (the trainable window; 1 <= w_lo < w_hi <= nz - 1).
+ *   dL_dX_re/im   dL/dRe X and dL/dIm X, [n_slabs][n_probes][n_freq] FP64, host or device
+ *   grad_wp2/nu   device FP64 [total cells, concatenated as wp2], caller-owned; cells
+ *                 outside the window are set to 0
+ * Each checkpoint segment is recomputed forward while the window states are recorded, then
+ * transposed on the same tiles; the per-step products are summed per segment (FP32 sums for
+ * FP32 fields, added into FP64 totals) and taken to (wp2, nu) by the derivatives of the update
+ * coefficients in FP64. Leaves the fields in an intermediate state (rketd_reset before reuse).
+ * Async on the stream.
+ */
+rketd_status rketd_adjoint(rketd_ctx* ctx, const double* dL_dX_re, const double* dL_dX_im, int64_t w_lo,
+                           int64_t w_hi, double* grad_wp2, double* grad_nu);
+
 /* Saves / restores the full state (fields, CPML memories, DFT sums, step index) to a
  * versioned binary file. A run resumed from a saved state is bitwise identical to
  * an uninterrupted one with the same options. Synchronises. */

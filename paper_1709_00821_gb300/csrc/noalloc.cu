@@ -77,6 +77,8 @@ __global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int
     t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
     t.probe_begin = 0;
     t.probe_count = 0;
+    t.adj_begin = 0;
+    t.adj_count = 0;
     tiles[n++] = t;
   };
   for (int64_t j = 0; j < n_int; ++j) put(a + j * W, a + (j + 1) * W, L);

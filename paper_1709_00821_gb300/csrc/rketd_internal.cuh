@@ -42,8 +42,10 @@ struct Tile {
   int32_t src_local;    // tile-local index of the source cell, -1 if not loaded
   int64_t start;
   int32_t vlo, vhi;
-  int32_t probe_begin;  // into the tile-probe list
+  int32_t probe_begin;  // into the tile-probe list: probes in [vlo, vhi) (sampled here)
   int32_t probe_count;
+  int32_t adj_begin;    // into the tile-probe list: probes anywhere in the loaded range
+  int32_t adj_count;    // (the adjoint injects its seeds into every copy of a probe cell)
 };
 
 struct TileProbe {
@@ -88,6 +90,45 @@ struct StepArgs {
   const TileProbe* tprobes;
   int32_t n_tiles;
   int32_t total_probes;
+  // window recording (adjoint recompute): after each step the state (E, H, carried J) of cells
+  // [rec_c0, rec_c0 + rec_w) of every slab goes to rec[slab][slot][3][rec_w], slot = rec_pos + t
+  T* rec;
+  int64_t rec_c0;
+  int32_t rec_w;
+  int32_t rec_len;
+  int32_t rec_pos;
+};
+
+// The reverse (adjoint) step on the same tiles. lambda = (lE, lH, lJ) is the adjoint of
+// (E, H~, carried J); a pass takes the adjoint from after step n_hi - 1 back to before step
+// n_hi - nsub. seeds[slot][seed_len] holds dL/dE at probe `slot` for the sample that follows
+// step n (column n - seg_n0). Window cells [rec_c0, rec_c0 + rec_w) record, for each step,
+// mu = lE + cc lJ and lJ (both after the step) to rec[slab][n - seg_n0][2][rec_w].
+template <typename T>
+struct AdjArgs {
+  const T* lE_in;
+  const T* lH_in;
+  const T* lJ_in;
+  T* lE_out;
+  T* lH_out;
+  T* lJ_out;
+  const T* coef[kNumCoef];
+  const int64_t* soff;
+  const int64_t* nz;
+  T S;
+  T qmur;
+  int32_t nsub;
+  int64_t n_hi;
+  int64_t seg_n0;
+  const T* seeds;
+  int32_t seed_len;
+  const Tile* tiles;
+  const TileProbe* tprobes;
+  int32_t n_tiles;
+  T* rec;
+  int64_t rec_c0;
+  int32_t rec_w;
+  int32_t rec_len;
 };
 
 // Sets the message rketd_last_error() returns on this thread (defined with the runtime).
@@ -102,6 +143,30 @@ cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double 
 
 template <typename T>
 cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+
+// forward tiles that also record the window state (scalar kernel, template REC = true)
+template <typename T>
+cudaError_t launch_tb_rec(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+
+// adjoint pass over the tiles (adjoint.cu)
+template <typename T>
+cudaError_t launch_adj(const AdjArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+// seeds[slot][t] = sum_f (gXr cos - gXi sin)(2 pi f (m0 + t) dt) from a twiddle table tw[t][f]
+template <typename T>
+cudaError_t launch_seeds(const double* gXr, const double* gXi, const T* tw, int P, int nf, int n, T* seeds,
+                         int seed_len, cudaStream_t st);
+// g[5][slab][w] += per-window-cell sums over one segment of the recorded forward and adjoint values
+template <typename T>
+cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int rec_w, int L, int recF_len,
+                              double* g, cudaStream_t st);
+// chain rule: grad_wp2, grad_nu of window cells from g and d(coefficient)/d(wp2, nu)
+cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* nu, const int64_t* off,
+                              int n_slabs, int64_t w_lo, int w, double dt, double S, double* grad_wp2,
+                              double* grad_nu, cudaStream_t st);
+// copies the window cells of the current state into recF slot 0
+template <typename T>
+cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, int n_slabs, int64_t c0,
+                            int w, int rec_len, T* rec, cudaStream_t st);
 
 // FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu)
 cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st);

@@ -105,6 +105,20 @@ struct rketd_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 
+  // adjoint: checkpoints of the forward run and the reverse-sweep buffers
+  int64_t ckpt_steps = 0;  // steps of the checkpointed forward run (0 = none)
+  int32_t ckpt_every = 0;
+  void* ckpt = nullptr;    // [n_ckpt][3][n_store]
+  int64_t n_ckpt = 0;
+  void* lam[6] = {};       // adjoint E, H, J (two copies each)
+  void* recF = nullptr;
+  void* recA = nullptr;
+  void* seeds = nullptr;
+  void* tw_seed = nullptr;
+  double* gX = nullptr;    // [2][P*nf]
+  double* gacc = nullptr;  // [5][n_slabs][w]
+  int64_t rec_cap = 0;     // window width the record buffers were sized for
+
   // captured whole rketd_step calls, keyed by (start step, steps, buffer parity)
   struct GraphEntry {
     int64_t s0, n;
@@ -218,6 +232,14 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     }
     t.probe_count = (int32_t)tps.size() - t.probe_begin;
     if (t.probe_count > kMaxTileProbes) return fail(RKETD_EINVAL, "more than %d probes in one tile", kMaxTileProbes);
+    // probes anywhere in the loaded range (the adjoint seeds every copy of a probe cell)
+    t.adj_begin = (int32_t)tps.size();
+    for (int p = 0; p < c->n_probes; ++p) {
+      const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
+      const int64_t loc = cell - t.start;
+      if (loc >= 0 && loc < Lt) tps.push_back({(int32_t)loc, s * c->n_probes + p});
+    }
+    t.adj_count = (int32_t)tps.size() - t.adj_begin;
     (is_edge ? edge : interior).push_back(t);
     return RKETD_OK;
   };
@@ -238,7 +260,10 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     for (int64_t v = b; v < nz; v += We)
       if ((st = add(s, v, std::min<int64_t>(v + We, nz), Le, true))) return st;
   }
-  for (Tile& t : edge) t.probe_begin += (int32_t)tp_int.size();
+  for (Tile& t : edge) {
+    t.probe_begin += (int32_t)tp_int.size();
+    t.adj_begin += (int32_t)tp_int.size();
+  }
   std::vector<Tile> all = interior;
   all.insert(all.end(), edge.begin(), edge.end());
   std::vector<TileProbe> tps = tp_int;
@@ -991,6 +1016,198 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
     }
   }
   return st;
+}
+
+rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  if (nsteps < 1 || ckpt_every < 1) return fail(RKETD_EINVAL, "nsteps and ckpt_every must be >= 1");
+  if (c->grid.bc != RKETD_BC_MUR1) return fail(RKETD_EUNSUPPORTED, "the adjoint supports first-order Mur ends only");
+  if (c->opt.variant != 2) return fail(RKETD_EUNSUPPORTED, "the adjoint runs on the tiled variant");
+  const int64_t n_ckpt = (nsteps + ckpt_every - 1) / ckpt_every;
+  const size_t fb = c->esz * c->n_store;
+  if (n_ckpt != c->n_ckpt) {
+    if (c->ckpt) {
+      cudaFree(c->ckpt);
+      c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), c->ckpt));
+      c->ckpt = nullptr;
+    }
+    rketd_status st = c->alloc(&c->ckpt, 3 * fb * n_ckpt, "checkpoints");
+    if (st) return st;
+    c->n_ckpt = n_ckpt;
+  }
+  rketd_status st = zero_state(c);
+  if (st) return st;
+  for (int64_t j = 0; j < n_ckpt; ++j) {
+    char* dst = (char*)c->ckpt + 3 * fb * j;
+    CK(cudaMemcpyAsync(dst, c->E[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    CK(cudaMemcpyAsync(dst + fb, c->H[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    CK(cudaMemcpyAsync(dst + 2 * fb, c->J[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    st = rketd_step(c, std::min<int64_t>(ckpt_every, nsteps - j * ckpt_every));
+    if (st) return st;
+  }
+  c->ckpt_steps = nsteps;
+  c->ckpt_every = ckpt_every;
+  return RKETD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad_wp2, double* grad_nu) {
+  const int64_t N = c->ckpt_steps, C = c->ckpt_every;
+  const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps, Ke = edge_cells_per_lane(TS);
+  const int64_t rw = w_hi - w_lo + 1;  // recorded cells: window plus its left neighbour (for dH)
+  const size_t fb = c->esz * c->n_store;
+  const int P = c->total_probes, nf = c->n_freq;
+  if (c->tiles_K != K || c->tiles_T != TS) {
+    rketd_status st = plan_tiles(c, K, TS);
+    if (st) return st;
+  }
+  rketd_status st;
+  if (!c->lam[0])
+    for (int i = 0; i < 6; ++i)
+      if ((st = c->alloc(&c->lam[i], fb, "adjoint fields"))) return st;
+  if (rw > c->rec_cap) {
+    for (void** p : {&c->recF, &c->recA, &c->seeds, &c->tw_seed, (void**)&c->gacc}) {
+      if (*p) {
+        cudaFree(*p);
+        c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), *p));
+        *p = nullptr;
+      }
+    }
+    if ((st = c->alloc(&c->recF, c->esz * (size_t)c->n_slabs * (C + 1) * 3 * rw, "adjoint records"))) return st;
+    if ((st = c->alloc(&c->recA, c->esz * (size_t)c->n_slabs * C * 2 * rw, "adjoint records"))) return st;
+    if ((st = c->alloc(&c->seeds, c->esz * (size_t)std::max(P, 1) * C, "adjoint seeds"))) return st;
+    if ((st = c->alloc(&c->tw_seed, c->esz * 2 * (size_t)C * std::max(nf, 1), "adjoint twiddles"))) return st;
+    void* g;
+    if ((st = c->alloc(&g, sizeof(double) * 5 * (size_t)c->n_slabs * (rw - 1), "gradient sums"))) return st;
+    c->gacc = (double*)g;
+    c->rec_cap = rw;
+  }
+  for (int i = 0; i < 6; ++i) CK(cudaMemsetAsync(c->lam[i], 0, fb, c->stream), "adjoint init");
+  CK(cudaMemsetAsync(c->gacc, 0, sizeof(double) * 5 * (size_t)c->n_slabs * (rw - 1), c->stream), "adjoint init");
+  int lcur = 0;
+  const int64_t n_seg = (N + C - 1) / C;
+  for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
+    const int64_t n0 = seg * C;
+    const int L = (int)std::min<int64_t>(C, N - n0);
+    // restore the checkpoint and recompute the segment, recording the window
+    const char* src = (const char*)c->ckpt + 3 * fb * seg;
+    CK(cudaMemcpyAsync(c->E[0], src, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
+    CK(cudaMemcpyAsync(c->H[0], src + fb, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
+    CK(cudaMemcpyAsync(c->J[0], src + 2 * fb, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
+    c->cur = 0;
+    CK(launch_rec_init<T>((const T*)c->E[0], (const T*)c->H[0], (const T*)c->J[0], c->soff_d, c->n_slabs, w_lo - 1,
+                          (int)rw, L + 1, (T*)c->recF, c->stream),
+       "record init");
+    c->launches += 1;
+    for (int done = 0; done < L;) {
+      const int nsub = std::min(TS, L - done);
+      c->step = n0 + done;
+      StepArgs<T> a = make_args<T>(c, c->cur, 1 - c->cur);
+      a.nsub = nsub;
+      a.series = nullptr;
+      a.tprobes = c->tprobes_d;
+      a.rec = (T*)c->recF;
+      a.rec_c0 = w_lo - 1;
+      a.rec_w = (int)rw;
+      a.rec_len = L + 1;
+      a.rec_pos = done + 1;
+      a.tiles = c->tiles_d;
+      a.n_tiles = c->n_interior;
+      CK(launch_tb_rec<T>(a, K, false, c->opt.warps_per_block, c->stream), "recompute (interior)");
+      a.tiles = c->tiles_d + c->n_interior;
+      a.n_tiles = c->n_edge;
+      CK(launch_tb_rec<T>(a, Ke, true, 2, c->stream), "recompute (edge)");
+      c->launches += 2;
+      c->cur = 1 - c->cur;
+      done += nsub;
+    }
+    // loss seeds for the samples after steps n0 .. n0+L-1
+    if (P > 0) {
+      CK(launch_twiddles<T>(c->freq_d, nf, c->grid.dt, n0 + 1, L, (T*)c->tw_seed, c->stream), "seed twiddles");
+      CK(launch_seeds<T>(c->gX, c->gX + (size_t)P * nf, (const T*)c->tw_seed, P, nf, L, (T*)c->seeds, L, c->stream),
+         "seeds");
+      c->launches += 2;
+    }
+    // transposed passes from the end of the segment back to its start
+    for (int hi = L; hi > 0;) {
+      const int nsub = std::min(TS, hi);
+      AdjArgs<T> a{};
+      a.lE_in = (const T*)c->lam[3 * lcur];
+      a.lH_in = (const T*)c->lam[3 * lcur + 1];
+      a.lJ_in = (const T*)c->lam[3 * lcur + 2];
+      a.lE_out = (T*)c->lam[3 * (1 - lcur)];
+      a.lH_out = (T*)c->lam[3 * (1 - lcur) + 1];
+      a.lJ_out = (T*)c->lam[3 * (1 - lcur) + 2];
+      for (int k = 0; k < kNumCoef; ++k) a.coef[k] = (const T*)c->coef[k];
+      a.soff = c->soff_d;
+      a.nz = c->nz_d;
+      a.S = (T)c->S;
+      a.qmur = (T)c->qmur;
+      a.nsub = nsub;
+      a.n_hi = n0 + hi;
+      a.seg_n0 = n0;
+      a.seeds = (const T*)c->seeds;
+      a.seed_len = L;
+      a.tprobes = c->tprobes_d;
+      a.rec = (T*)c->recA;
+      a.rec_c0 = w_lo - 1;
+      a.rec_w = (int)rw;
+      a.rec_len = L;
+      a.tiles = c->tiles_d;
+      a.n_tiles = c->n_interior;
+      CK(launch_adj<T>(a, K, false, 2, c->stream), "adjoint (interior)");
+      a.tiles = c->tiles_d + c->n_interior;
+      a.n_tiles = c->n_edge;
+      CK(launch_adj<T>(a, Ke, true, 2, c->stream), "adjoint (edge)");
+      c->launches += 2;
+      lcur = 1 - lcur;
+      hi -= nsub;
+    }
+    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, L, L + 1, c->gacc, c->stream),
+       "gradient sums");
+    c->launches += 1;
+  }
+  CK(cudaMemsetAsync(grad_wp2, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
+  CK(cudaMemsetAsync(grad_nu, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
+  CK(launch_grad_chain(c->gacc, c->wp2_d, c->nu_d, c->off_d, c->n_slabs, w_lo, (int)(rw - 1), c->grid.dt, c->S,
+                       grad_wp2, grad_nu, c->stream),
+     "chain rule");
+  c->launches += 1;
+  c->step = -1;  // the fields hold a recomputed intermediate state
+  return RKETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rketd_status rketd_adjoint(rketd_ctx* c, const double* dL_dX_re, const double* dL_dX_im, int64_t w_lo, int64_t w_hi,
+                           double* grad_wp2, double* grad_nu) {
+  if (!c || !dL_dX_re || !dL_dX_im || !grad_wp2 || !grad_nu) return fail(RKETD_EINVAL, "NULL argument");
+  if (c->ckpt_steps < 1) return fail(RKETD_EINVAL, "no checkpointed forward run: call rketd_forward_ckpt first");
+  int64_t nz_min = c->nz[0];
+  for (int64_t v : c->nz) nz_min = std::min(nz_min, v);
+  if (w_lo < 1 || w_hi <= w_lo || w_hi > nz_min - 1)
+    return fail(RKETD_EINVAL, "window [%lld, %lld) must lie inside [1, nz - 1) of every slab", (long long)w_lo,
+                (long long)w_hi);
+  const int P = c->total_probes, nf = c->n_freq;
+  if (P > 0) {
+    if (!c->gX) {
+      void* p;
+      rketd_status st = c->alloc(&p, sizeof(double) * 2 * (size_t)P * nf, "loss gradient");
+      if (st) return st;
+      c->gX = (double*)p;
+    }
+    const size_t b = sizeof(double) * (size_t)P * nf;
+    CK(cudaMemcpyAsync(c->gX, dL_dX_re, b, cudaMemcpyDefault, c->stream), "loss gradient upload");
+    CK(cudaMemcpyAsync(c->gX + (size_t)P * nf, dL_dX_im, b, cudaMemcpyDefault, c->stream), "loss gradient upload");
+  }
+  return c->prec == RKETD_F64 ? adjoint_impl<double>(c, w_lo, w_hi, grad_wp2, grad_nu)
+                              : adjoint_impl<float>(c, w_lo, w_hi, grad_wp2, grad_nu);
 }
 
 rketd_status rketd_kernel_timing(rketd_ctx* c, int32_t enable) {

@@ -14,6 +14,7 @@
 // cell of its slab, outside any CPML) carries no boundary code; the edge kernel handles
 // cells outside the slab, the first-order Mur or PEC end cells and the CPML memories.
 #include "rketd_internal.cuh"
+#include "tile_common.cuh"
 
 // Resident CTAs of 4 warps per SM the interior kernel is compiled for (register cap).
 #ifndef RKETD_TB_MINB
@@ -23,81 +24,9 @@
 namespace rketd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using namespace tile;
 
-// Eq. 15, normalised by tau: amp ((t - t0)/tau) exp(-(t - t0)^2 / (2 tau^2)).
-__device__ __forceinline__ double pulse(double t, double t0, double tau, double amp) {
-  const double u = (t - t0) / tau;
-  return amp * u * exp(-0.5 * u * u);
-}
-
-template <typename T, int K>
-__device__ __forceinline__ T pick(const T (&r)[K], int i) {
-  T v = T(0);
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-    if (q == i) v = r[q];
-  return v;
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void put(T (&r)[K], int i, T v) {
-#pragma unroll
-  for (int q = 0; q < K; ++q)
-    if (q == i) r[q] = v;
-}
-
-// Four consecutive values at p (16-byte aligned for float, 32 for double).
-__device__ __forceinline__ void ld4(const float* p, float* r) {
-  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-  r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double* r) {
-  const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  r[0] = q0.x; r[1] = q0.y; r[2] = q1.x; r[3] = q1.y;
-}
-__device__ __forceinline__ void st4(float* p, const float* r) {
-  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
-}
-__device__ __forceinline__ void st4(double* p, const double* r) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(r[2], r[3]);
-}
-
-// K values of slab storage `base` at slab-local cells g0 .. g0+K-1; groups of four
-// outside [0, hi) read as zero (g0 and hi are multiples of 4).
-template <typename T, int K, bool MASK>
-__device__ __forceinline__ void load_row(const T* __restrict__ base, int64_t g0, int64_t hi, T (&r)[K]) {
-#pragma unroll
-  for (int v = 0; v < K / 4; ++v) {
-    const int64_t g = g0 + 4 * v;
-    if (!MASK || (g >= 0 && g < hi)) {
-      ld4(base + g, &r[4 * v]);
-    } else {
-      r[4 * v] = r[4 * v + 1] = r[4 * v + 2] = r[4 * v + 3] = T(0);
-    }
-  }
-}
-
-// Stores the slots whose tile-local index lies in [vlo, vhi).
-template <typename T, int K>
-__device__ __forceinline__ void store_row(T* __restrict__ base, int64_t g0, int li0, int vlo, int vhi,
-                                          const T (&r)[K]) {
-#pragma unroll
-  for (int v = 0; v < K / 4; ++v) {
-    const int li = li0 + 4 * v;
-    if (li >= vlo && li + 4 <= vhi) {
-      st4(base + g0 + 4 * v, &r[4 * v]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (li + q >= vlo && li + q < vhi) base[g0 + 4 * v + q] = r[4 * v + q];
-    }
-  }
-}
-
-template <typename T, int K, bool EDGE>
+template <typename T, int K, bool EDGE, bool REC>
 __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const StepArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -150,6 +79,17 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
       if (g == 0) i0 = i;
       if (g == nz - 1) i1 = i;
+    }
+  }
+
+  // window cells this lane records (exact cells only): bit i = slot i
+  uint32_t mrec = 0;
+  if (REC) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const int li = li0 + i;
+      const int64_t g = g0 + i;
+      if (li >= tl.vlo && li < tl.vhi && g >= a.rec_c0 && g < a.rec_c0 + a.rec_w) mrec |= 1u << i;
     }
   }
 
@@ -241,10 +181,25 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
     }
     // ---- probe samples (only the tile whose exact region holds the probe) ----
-    for (int p = 0; p < tl.probe_count; ++p) {
-      const TileProbe tp = a.tprobes[tl.probe_begin + p];
-      if (lane == tp.local / K)
-        a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick(e, tp.local % K);
+    if (a.series) {
+      for (int p = 0; p < tl.probe_count; ++p) {
+        const TileProbe tp = a.tprobes[tl.probe_begin + p];
+        if (lane == tp.local / K)
+          a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick(e, tp.local % K);
+      }
+    }
+    // ---- window recording for the adjoint ----
+    if (REC && mrec) {
+      T* r = a.rec + ((int64_t)s * a.rec_len + a.rec_pos + t) * 3 * a.rec_w;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        if (mrec & (1u << i)) {
+          const int64_t c = g0 + i - a.rec_c0;
+          r[c] = e[i];
+          r[a.rec_w + c] = h[i];
+          r[2 * a.rec_w + c] = jj[i];
+        }
+      }
     }
   }
 
@@ -263,14 +218,14 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
   }
 }
 
-template <typename T, int K>
+template <typename T, int K, bool REC = false>
 cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st) {
   const dim3 block(32 * wpb);
   const dim3 grid((a.n_tiles + wpb - 1) / wpb);
   if (edge)
-    k_tb<T, K, true><<<grid, block, 0, st>>>(a);
+    k_tb<T, K, true, REC><<<grid, block, 0, st>>>(a);
   else
-    k_tb<T, K, false><<<grid, block, 0, st>>>(a);
+    k_tb<T, K, false, REC><<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -296,6 +251,29 @@ cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int w
   switch (K) {
     case 4: return launch_k<double, 4>(a, edge, wpb, st);
     case 8: return launch_k<double, 8>(a, edge, wpb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_tb_rec<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
+  switch (K) {
+    case 4: return launch_k<float, 4, true>(a, edge, wpb, st);
+    case 8: return launch_k<float, 8, true>(a, edge, wpb, st);
+    case 16: return launch_k<float, 16, true>(a, edge, wpb, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_tb_rec<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
+  switch (K) {
+    case 4: return launch_k<double, 4, true>(a, edge, wpb, st);
+    case 8: return launch_k<double, 8, true>(a, edge, wpb, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
         const double sv = pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
         put2(e, src_slot, pick2(e, src_slot) + (float)sv);
       }
-      for (int q = 0; q < tl.probe_count; ++q) {
+      for (int q = 0; q < (a.series ? tl.probe_count : 0); ++q) {
         const TileProbe tp = a.tprobes[tl.probe_begin + q];
         if (lane == tp.local / K)
           a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick2(e, tp.local % K);

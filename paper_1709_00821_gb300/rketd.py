@@ -83,6 +83,9 @@ _SIGS = {
                                                 ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Pulse),
                                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p]),
+    "rketd_forward_ckpt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]),
+    "rketd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "rketd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
@@ -252,6 +255,28 @@ class Context:
         o = Options()
         _check(lib().rketd_get_options(self.h, ctypes.byref(o)))
         return {k: getattr(o, k) for k, _ in Options._fields_ if k != "reserved"}
+
+    def forward_ckpt(self, nsteps: int, every: int = 512):
+        """Reset, run nsteps from rest and keep a state checkpoint every `every` steps."""
+        _check(lib().rketd_forward_ckpt(self.h, int(nsteps), int(every)))
+
+    def adjoint(self, gX_re, gX_im, w_lo: int, w_hi: int, grad_wp2, grad_nu):
+        """Gradients (into device arrays grad_wp2/grad_nu, FP64, all cells) of a loss whose
+        derivatives with respect to the spectra are gX_re/gX_im ([slab, probe, freq], host
+        numpy or CUDA tensors)."""
+        keep = []
+
+        def ptr(a):
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            arr = _arr(a)
+            keep.append(arr)
+            return ctypes.c_void_p(arr.ctypes.data)
+
+        _check(lib().rketd_adjoint(self.h, ptr(gX_re), ptr(gX_im), int(w_lo), int(w_hi), ptr(grad_wp2),
+                                   ptr(grad_nu)))
+        if keep:
+            self.sync()
 
     def kernel_timing(self, enable: bool = True):
         _check(lib().rketd_kernel_timing(self.h, 1 if enable else 0))
