@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps per CPU sample (0 = auto)")
     ap.add_argument("--options", default="", help="library options, e.g. cells_per_lane=16,tb_steps=32")
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--adj-profiles", type=int, default=64)
     ap.add_argument("--batch-slabs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=20000)
     return ap.parse_args()
@@ -323,6 +325,61 @@ def measure_batch(args):
             "speedup_vs_slab_by_slab": ms_slab / ms, "speedup_vs_all_slabs_plain": ms_all / ms}
 
 
+def measure_adjoint(args):
+    """Adjoint workload: 64 profiles of 65536 cells, 30000 FP32 steps, trainable cells
+    [2048, 6144), loss = sum_f (|R(f)| - |R_t(f)|)^2 over 256 frequencies against the target
+    spectrum the FP64 oracle wrote to tests/golden/c4_target.txt. Times the checkpointed forward
+    (every 512 steps) and the adjoint (segment recompute + transposed sweep + gradients)."""
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+    from paper_1709_00821_gb300 import workloads as wl
+
+    tgt = np.loadtxt(os.path.join(ROOT, "tests", "golden", "c4_target.txt"))[:, 1]
+    profs = [wl.c4_profile(i) for i in range(args.adj_profiles)]
+    steps, every, win = profs[0].steps, 512, (2048, 6144)
+    # incident spectrum: the same line without plasma (every profile shares source and probe)
+    with rk.Context(profs[0].vacuum(), "f32") as cv:
+        cv.step(steps)
+        Xi = cv.spectra()[0, 0]
+    ctx = rk.Context(profs, "f32")
+    n = sum(p.nz for p in profs)
+    gw = torch.empty(n, dtype=torch.float64, device="cuda")
+    gn = torch.empty(n, dtype=torch.float64, device="cuda")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def once(timed):
+        e[0].record()
+        ctx.forward_ckpt(steps, every)
+        e[1].record()
+        X = ctx.spectra()[:, 0]
+        d = X - Xi[None]
+        absr = np.abs(d) / np.abs(Xi)[None]
+        loss = float(np.sum((absr - tgt[None]) ** 2))
+        coef = 2 * (absr - tgt[None]) / (np.abs(Xi)[None] * np.abs(d))
+        gX = np.zeros((len(profs), ctx.n_probes, len(ctx.freq)), complex)
+        gX[:, 0] = coef * d.real + 1j * coef * d.imag
+        gre = torch.from_numpy(np.ascontiguousarray(gX.real)).cuda()
+        gim = torch.from_numpy(np.ascontiguousarray(gX.imag)).cuda()
+        torch.cuda.synchronize()
+        e[2].record()
+        ctx.adjoint(gre, gim, win[0], win[1], gw, gn)
+        e[3].record()
+        torch.cuda.synchronize()
+        return loss, e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+
+    once(False)
+    loss, t_fwd, t_adj = once(True)
+    cu = n * steps
+    ctx.close()
+    return {"workload": f"{len(profs)} profiles x 65536 cells, {steps} steps, FP32, checkpoint every {every}, "
+                        f"window [{win[0]}, {win[1]}), 256 frequencies",
+            "forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
+            "forward_gcells": cu / (t_fwd / 1e3) / 1e9, "loss": loss,
+            "adjoint_includes": "segment recompute with window recording, seeds, transposed sweep, gradient sums, "
+                                "chain rule"}
+
+
 def run_ours(args):
     import torch
 
@@ -448,6 +505,11 @@ def run_ours(args):
                 "hbm_effective": {"achieved": B_ALG["f64"] * krate64 / 1e9, "peak": hbm_peak,
                                   "frac": B_ALG["f64"] * krate64 / 1e9 / hbm_peak, "unit": "GB/s"}}
 
+    # ---- adjoint (config 4) ----
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = measure_adjoint(args)
+
     # ---- ragged batch (config 3) ----
     batch = None
     if not args.no_batch:
@@ -473,8 +535,8 @@ def run_ours(args):
                                       f"{opt_used['tb_steps']} steps/pass, {opt_used['warps_per_block']} warps/CTA",
                            "precision": "FP32 fields, FP64-derived delta coefficients, Kahan-FP32 DFT blocks into FP64"},
                 "roofline": roofline, "hbm_roofline_effective": hbm_eff, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "batched": batch, "cpu_baseline": cpu,
-                "adjoint_forward_ratio": None}
+                "clocks": clocks, "fp64": fp64, "batched": batch, "adjoint": adjoint, "cpu_baseline": cpu,
+                "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -178,7 +178,7 @@ rketd_status rketd_forward_ckpt(rketd_ctx* ctx, int64_t nsteps, int32_t ckpt_eve
  * Discrete adjoint of the last rketd_forward_ckpt run (the transpose of Eqs. 14, 13, 11 and
  * the Mur ends, step by step in reverse): gradients of a loss L(X) of the probe spectra with
  * respect to the plasma frequency squared and the collision frequency of every cell in
- * [w_lo, w_hi) of every slab (the trainable window; 1 <= w_lo < w_hi <= nz - 1).
+ * [w_lo, w_hi) of every slab (the trainable window; 4 <= w_lo < w_hi <= nz - 1).
  *   dL_dX_re/im   dL/dRe X and dL/dIm X, [n_slabs][n_probes][n_freq] FP64, host or device
  *   grad_wp2/nu   device FP64 [total cells, concatenated as wp2], caller-owned; cells
  *                 outside the window are set to 0

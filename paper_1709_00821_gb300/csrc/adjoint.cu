@@ -103,14 +103,33 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : 2) k_adj(const AdjArgs<T> a) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const bool upd = !EDGE || ((mE >> i) & 1u);
-      const T m = upd ? fma(cc[i], lj[i], le[i]) : T(0);
-      mu[i] = m;
-      nu_[i] = cb[i] * m;
-      if (a.rec && (mrec & (1u << i))) {
-        T* r = a.rec + ((int64_t)s * a.rec_len + col) * 2 * a.rec_w + (g0 + i - a.rec_c0);
-        r[0] = m;
-        r[a.rec_w] = lj[i];
+      mu[i] = upd ? fma(cc[i], lj[i], le[i]) : T(0);
+    }
+    if (mrec) {  // record (mu, lJ) of the window cells, whole aligned groups as vectors
+      T* r = a.rec + ((int64_t)s * a.rec_len + col) * 2 * a.rec_w;
+#pragma unroll
+      for (int v = 0; v < K / 4; ++v) {
+        const uint32_t m4 = (mrec >> (4 * v)) & 0xFu;
+        const int64_t c = g0 + 4 * v - a.rec_c0;
+        if (m4 == 0xFu && (c & 3) == 0) {
+          st4(r + c, &mu[4 * v]);
+          st4(r + a.rec_w + c, &lj[4 * v]);
+        } else if (m4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (m4 & (1u << q)) {
+              r[c + q] = mu[4 * v + q];
+              r[a.rec_w + c + q] = lj[4 * v + q];
+            }
+          }
+        }
       }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const bool upd = !EDGE || ((mE >> i) & 1u);
+      const T m = mu[i];
+      nu_[i] = cb[i] * m;
       if (upd) {
         const T ljo = lj[i];
         lj[i] = fma(dj[i], ljo, ljo) - m;
@@ -157,6 +176,61 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : 2) k_adj(const AdjArgs<T> a) {
   store_row<T, K>(a.lJ_out + soff, g0, li0, tl.vlo, tl.vhi, lj);
 }
 
+// FP32 interior tiles off the window, two cells per packed FP32x2 register (halves A/B of each
+// lane's range, as in the forward k_tb2): every element is rounded as in k_adj.
+template <int K>
+__global__ void __launch_bounds__(128, 3) k_adj2(const AdjArgs<float> a) {
+  constexpr int P = K / 2;
+  const int lane = threadIdx.x & 31;
+  const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (tid >= a.n_tiles) return;
+  const Tile tl = a.tiles[tid];
+  const int64_t base = a.soff[tl.slab] + tl.start + lane * K;
+  const int li0 = lane * K;
+  f2 le[P], lh[P], lj[P], da[P], cb[P], dj[P], bp[P], cc[P];
+  load_pairs<K>(a.lE_in + base, le, false);
+  load_pairs<K>(a.lH_in + base, lh, false);
+  load_pairs<K>(a.lJ_in + base, lj, false);
+  load_pairs<K>(a.coef[kDa] + base, da, false);
+  load_pairs<K>(a.coef[kCb] + base, cb, false);
+  load_pairs<K>(a.coef[kDj] + base, dj, false);
+  load_pairs<K>(a.coef[kBp] + base, bp, false);
+  load_pairs<K>(a.coef[kCc] + base, cc, false);
+  const f2 S2 = pk(a.S, a.S);
+  for (int t = a.nsub - 1; t >= 0; --t) {
+    const int col = (int)(a.n_hi - a.nsub + t - a.seg_n0);
+    for (int p = 0; p < tl.adj_count; ++p) {
+      const TileProbe tp = a.tprobes[tl.adj_begin + p];
+      if (lane == tp.local / K) {
+        const int sl = tp.local % K;
+        put2(le, sl, pick2(le, sl) + a.seeds[(int64_t)tp.slot * a.seed_len + col]);
+      }
+    }
+    f2 nu[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const f2 m = fma2(cc[p], lj[p], le[p]);
+      const f2 ljo = lj[p];
+      lj[p] = sub2(fma2(dj[p], ljo, ljo), m);
+      le[p] = fma2(bp[p], ljo, fma2(da[p], m, m));
+      nu[p] = mul2(cb[p], m);
+    }
+    // lH'_k = (lH_k - nu_k) + nu_{k+1}; the cell after pair P-1 is (B[0], next lane's A[0])
+    const float nextA0 = __shfl_down_sync(kFull, lo_of(nu[0]), 1);
+    const f2 nuLast = pk(hi_of(nu[0]), nextA0);
+#pragma unroll
+    for (int p = 0; p < P; ++p) lh[p] = add2(sub2(lh[p], nu[p]), (p + 1 < P) ? nu[p + 1] : nuLast);
+    // lE_k += S (lH'_k - lH'_{k-1}); the cell before pair 0 is (previous lane's B[P-1], A[P-1])
+    const float prevB = __shfl_up_sync(kFull, hi_of(lh[P - 1]), 1);
+    const f2 lhFirst = pk(prevB, lo_of(lh[P - 1]));
+#pragma unroll
+    for (int p = 0; p < P; ++p) le[p] = fma2(S2, sub2(lh[p], p ? lh[p - 1] : lhFirst), le[p]);
+  }
+  store_pairs<K>(a.lE_out + base, li0, tl.vlo, tl.vhi, le);
+  store_pairs<K>(a.lH_out + base, li0, tl.vlo, tl.vhi, lh);
+  store_pairs<K>(a.lJ_out + base, li0, tl.vlo, tl.vhi, lj);
+}
+
 template <typename T, int K>
 cudaError_t launch_a(const AdjArgs<T>& a, bool edge, int wpb, cudaStream_t st) {
   const dim3 block(32 * wpb);
@@ -184,48 +258,58 @@ __global__ void k_seeds(const double* __restrict__ gXr, const double* __restrict
 }
 
 // recF[slab][j][3][w] holds the state after j steps of the segment (j = 0..L); recA[slab][t][2][w]
-// holds (mu, lJ) after step t. Window cell c (recorded index c + 1 for H's left neighbour).
+// holds (mu, lJ) after step t. Rows start 4 cells before the window: window cell c sits at index
+// c + 4, its left neighbour (needed for dH) at c + 3; w is a multiple of 4. Each thread sums four
+// window cells over the segment.
 template <typename T>
-__global__ void k_grad(const T* __restrict__ recF, const T* __restrict__ recA, int n_slabs, int w, int L,
+__global__ void k_grad(const T* __restrict__ recF, const T* __restrict__ recA, int n_slabs, int w, int nwin, int L,
                        int recF_len, double* __restrict__ g) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;  // 0 .. w-2 -> cell index c+1 of the record
+  const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);  // first of four window cells
   const int s = blockIdx.y;
-  if (c >= w - 1 || s >= n_slabs) return;
-  const int k = c + 1;
-  float sda = 0.f, scb = 0.f, sdj = 0.f, sbp = 0.f, scc = 0.f;  // FP32 partial sums of one segment
-  double dda = 0, dcb = 0, ddj = 0, dbp = 0, dcc = 0;
-  const bool f64 = sizeof(T) == 8;
+  if (c0 >= nwin || s >= n_slabs) return;
+  const int k = c0 + 4;
+  float fs[5][4] = {};
+  double ds[5][4] = {};
+  constexpr bool f64 = sizeof(T) == 8;
+#pragma unroll 2
   for (int t = 0; t < L; ++t) {
     const T* F0 = recF + ((int64_t)s * recF_len + t) * 3 * w;
     const T* F1 = F0 + 3 * w;
     const T* A = recA + ((int64_t)s * L + t) * 2 * w;
-    const T mu = A[k];
-    const T lj = A[w + k];
-    const T En = F0[k];
-    const T Jn = F0[2 * w + k];
-    const T dH = F1[w + k] - F1[w + k - 1];
-    const T E1 = F1[k];
-    if (f64) {
-      dda += (double)mu * (double)En;
-      dcb -= (double)mu * (double)dH;
-      ddj += (double)lj * (double)Jn;
-      dbp += (double)lj * (double)En;
-      dcc += (double)lj * (double)E1;
-    } else {
-      sda = fmaf((float)mu, (float)En, sda);
-      scb = fmaf(-(float)mu, (float)dH, scb);
-      sdj = fmaf((float)lj, (float)Jn, sdj);
-      sbp = fmaf((float)lj, (float)En, sbp);
-      scc = fmaf((float)lj, (float)E1, scc);
+    T mu[4], lj[4], En[4], Jn[4], H1[4], E1[4];
+    ld4(A + k, mu);
+    ld4(A + w + k, lj);
+    ld4(F0 + k, En);
+    ld4(F0 + 2 * w + k, Jn);
+    ld4(F1 + w + k, H1);
+    ld4(F1 + k, E1);
+    const T hprev = F1[w + k - 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T dH = H1[q] - (q ? H1[q - 1] : hprev);
+      if (f64) {
+        ds[0][q] += (double)mu[q] * (double)En[q];
+        ds[1][q] -= (double)mu[q] * (double)dH;
+        ds[2][q] += (double)lj[q] * (double)Jn[q];
+        ds[3][q] += (double)lj[q] * (double)En[q];
+        ds[4][q] += (double)lj[q] * (double)E1[q];
+      } else {
+        fs[0][q] = fmaf((float)mu[q], (float)En[q], fs[0][q]);
+        fs[1][q] = fmaf(-(float)mu[q], (float)dH, fs[1][q]);
+        fs[2][q] = fmaf((float)lj[q], (float)Jn[q], fs[2][q]);
+        fs[3][q] = fmaf((float)lj[q], (float)En[q], fs[3][q]);
+        fs[4][q] = fmaf((float)lj[q], (float)E1[q], fs[4][q]);
+      }
     }
   }
-  const int64_t wi = (int64_t)s * (w - 1) + c;
-  const int64_t stride = (int64_t)n_slabs * (w - 1);
-  g[wi] += f64 ? dda : (double)sda;
-  g[stride + wi] += f64 ? dcb : (double)scb;
-  g[2 * stride + wi] += f64 ? ddj : (double)sdj;
-  g[3 * stride + wi] += f64 ? dbp : (double)sbp;
-  g[4 * stride + wi] += f64 ? dcc : (double)scc;
+  const int64_t stride = (int64_t)n_slabs * nwin;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (c0 + q >= nwin) break;
+    const int64_t wi = (int64_t)s * nwin + c0 + q;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) g[m * stride + wi] += f64 ? ds[m][q] : (double)fs[m][q];
+  }
 }
 
 // phi1, phi2 and their x-derivatives: Horner sums of the Taylor series below x = 0.5 (degree
@@ -297,11 +381,11 @@ __global__ void k_chain(const double* __restrict__ g, const double* __restrict__
 
 template <typename T>
 __global__ void k_rec_init(const T* __restrict__ E, const T* __restrict__ H, const T* __restrict__ J,
-                           const int64_t* __restrict__ soff, int n_slabs, int64_t c0, int w, int rec_len,
-                           T* __restrict__ rec) {
+                           const int64_t* __restrict__ soff, const int64_t* __restrict__ nz, int n_slabs, int64_t c0,
+                           int w, int rec_len, T* __restrict__ rec) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
-  if (c >= w || s >= n_slabs) return;
+  if (c >= w || s >= n_slabs || c0 + c >= nz[s]) return;
   const int64_t i = soff[s] + c0 + c;
   T* r = rec + (int64_t)s * rec_len * 3 * w;
   r[c] = E[i];
@@ -320,6 +404,19 @@ cudaError_t launch_adj<float>(const AdjArgs<float>& a, int K, bool edge, int wpb
     case 16: return launch_a<float, 16>(a, edge, wpb, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_adj_pairs(const AdjArgs<float>& a, int K, int wpb, cudaStream_t st) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  const dim3 block(32 * wpb);
+  const dim3 grid((a.n_tiles + wpb - 1) / wpb);
+  switch (K) {
+    case 8: k_adj2<8><<<grid, block, 0, st>>>(a); break;
+    case 12: k_adj2<12><<<grid, block, 0, st>>>(a); break;
+    case 16: k_adj2<16><<<grid, block, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <>
@@ -345,13 +442,16 @@ template cudaError_t launch_seeds<double>(const double*, const double*, const do
                                           cudaStream_t);
 
 template <typename T>
-cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int w, int L, int recF_len, double* g,
-                              cudaStream_t st) {
-  k_grad<T><<<dim3((w - 1 + 127) / 128, n_slabs), 128, 0, st>>>(recF, recA, n_slabs, w, L, recF_len, g);
+cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int w, int nwin, int L, int recF_len,
+                              double* g, cudaStream_t st) {
+  const int threads = 64;
+  const int per = 4 * threads;
+  k_grad<T><<<dim3((nwin + per - 1) / per, n_slabs), threads, 0, st>>>(recF, recA, n_slabs, w, nwin, L, recF_len, g);
   return cudaGetLastError();
 }
-template cudaError_t launch_grad_accum<float>(const float*, const float*, int, int, int, int, double*, cudaStream_t);
-template cudaError_t launch_grad_accum<double>(const double*, const double*, int, int, int, int, double*,
+template cudaError_t launch_grad_accum<float>(const float*, const float*, int, int, int, int, int, double*,
+                                              cudaStream_t);
+template cudaError_t launch_grad_accum<double>(const double*, const double*, int, int, int, int, int, double*,
                                                cudaStream_t);
 
 cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* nu, const int64_t* off, int n_slabs,
@@ -361,14 +461,14 @@ cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* 
 }
 
 template <typename T>
-cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, int n_slabs, int64_t c0, int w,
-                            int rec_len, T* rec, cudaStream_t st) {
-  k_rec_init<T><<<dim3((w + 127) / 128, n_slabs), 128, 0, st>>>(E, H, J, soff, n_slabs, c0, w, rec_len, rec);
+cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, const int64_t* nz, int n_slabs,
+                            int64_t c0, int w, int rec_len, T* rec, cudaStream_t st) {
+  k_rec_init<T><<<dim3((w + 127) / 128, n_slabs), 128, 0, st>>>(E, H, J, soff, nz, n_slabs, c0, w, rec_len, rec);
   return cudaGetLastError();
 }
-template cudaError_t launch_rec_init<float>(const float*, const float*, const float*, const int64_t*, int, int64_t,
-                                            int, int, float*, cudaStream_t);
-template cudaError_t launch_rec_init<double>(const double*, const double*, const double*, const int64_t*, int,
-                                             int64_t, int, int, double*, cudaStream_t);
+template cudaError_t launch_rec_init<float>(const float*, const float*, const float*, const int64_t*, const int64_t*,
+                                            int, int64_t, int, int, float*, cudaStream_t);
+template cudaError_t launch_rec_init<double>(const double*, const double*, const double*, const int64_t*,
+                                             const int64_t*, int, int64_t, int, int, double*, cudaStream_t);
 
 }  // namespace rketd

@@ -151,13 +151,15 @@ cudaError_t launch_tb_rec(const StepArgs<T>& a, int K, bool edge, int warps_per_
 // adjoint pass over the tiles (adjoint.cu)
 template <typename T>
 cudaError_t launch_adj(const AdjArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+// adjoint pass, FP32 interior tiles off the window, packed FP32x2 pairs (no recording)
+cudaError_t launch_adj_pairs(const AdjArgs<float>& a, int K, int warps_per_block, cudaStream_t st);
 // seeds[slot][t] = sum_f (gXr cos - gXi sin)(2 pi f (m0 + t) dt) from a twiddle table tw[t][f]
 template <typename T>
 cudaError_t launch_seeds(const double* gXr, const double* gXi, const T* tw, int P, int nf, int n, T* seeds,
                          int seed_len, cudaStream_t st);
 // g[5][slab][w] += per-window-cell sums over one segment of the recorded forward and adjoint values
 template <typename T>
-cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int rec_w, int L, int recF_len,
+cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int rec_w, int nwin, int L, int recF_len,
                               double* g, cudaStream_t st);
 // chain rule: grad_wp2, grad_nu of window cells from g and d(coefficient)/d(wp2, nu)
 cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* nu, const int64_t* off,
@@ -165,8 +167,8 @@ cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* 
                               double* grad_nu, cudaStream_t st);
 // copies the window cells of the current state into recF slot 0
 template <typename T>
-cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, int n_slabs, int64_t c0,
-                            int w, int rec_len, T* rec, cudaStream_t st);
+cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, const int64_t* nz, int n_slabs,
+                            int64_t c0, int w, int rec_len, T* rec, cudaStream_t st);
 
 // FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu)
 cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st);

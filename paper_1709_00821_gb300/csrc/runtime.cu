@@ -93,6 +93,10 @@ struct rketd_ctx {
   int total_probes = 0;
 
   // tiles for the current (K, tb_steps)
+  std::vector<Tile> tiles_h;
+  Tile* adj_tiles_d = nullptr;  // [interior off-window][interior on-window][edge] for the adjoint
+  int adj_n_plain = 0, adj_n_win = 0;
+  int64_t adj_w_lo = -1, adj_w_hi = -1;
   Tile* tiles_d = nullptr;
   TileProbe* tprobes_d = nullptr;
   int n_interior = 0, n_edge = 0;
@@ -140,6 +144,7 @@ struct rketd_ctx {
 
   ~rketd_ctx() {
     for (GraphEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+    if (adj_tiles_d) cudaFree(adj_tiles_d);
     if (cap_in) cudaEventDestroy(cap_in);
     if (cap_out) cudaEventDestroy(cap_out);
     if (cap) cudaStreamDestroy(cap);
@@ -266,6 +271,8 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   }
   std::vector<Tile> all = interior;
   all.insert(all.end(), edge.begin(), edge.end());
+  c->tiles_h = all;
+  c->adj_w_lo = c->adj_w_hi = -1;  // the adjoint's tile order is rebuilt on next use
   std::vector<TileProbe> tps = tp_int;
   tps.insert(tps.end(), tp_edge.begin(), tp_edge.end());
   // captured graphs point at the old tile lists
@@ -1042,7 +1049,9 @@ rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every
     CK(cudaMemcpyAsync(dst, c->E[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
     CK(cudaMemcpyAsync(dst + fb, c->H[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
     CK(cudaMemcpyAsync(dst + 2 * fb, c->J[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-    st = rketd_step(c, std::min<int64_t>(ckpt_every, nsteps - j * ckpt_every));
+    // direct launches: every segment starts at a different step, so per-call graphs would not repeat
+    const int64_t n = std::min<int64_t>(ckpt_every, nsteps - j * ckpt_every);
+    st = c->prec == RKETD_F64 ? step_impl<double>(c, n) : step_impl<float>(c, n);
     if (st) return st;
   }
   c->ckpt_steps = nsteps;
@@ -1058,7 +1067,11 @@ template <typename T>
 rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad_wp2, double* grad_nu) {
   const int64_t N = c->ckpt_steps, C = c->ckpt_every;
   const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps, Ke = edge_cells_per_lane(TS);
-  const int64_t rw = w_hi - w_lo + 1;  // recorded cells: window plus its left neighbour (for dH)
+  // recorded rows start 4 cells before the window (its left neighbour, needed for dH, at index 3)
+  // and have a width that is a multiple of 4, so that whole aligned groups are stored as vectors
+  const int64_t nwin = w_hi - w_lo;
+  const int64_t rw = ((nwin + 4 + 3) / 4) * 4;
+  const int64_t r0 = w_lo - 4;
   const size_t fb = c->esz * c->n_store;
   const int P = c->total_probes, nf = c->n_freq;
   if (c->tiles_K != K || c->tiles_T != TS) {
@@ -1066,6 +1079,39 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     if (st) return st;
   }
   rketd_status st;
+  if (c->adj_w_lo != w_lo || c->adj_w_hi != w_hi || !c->adj_tiles_d) {
+    // interior tiles whose exact cells miss the recorded cells run the plain kernels
+    std::vector<Tile> plain, win;
+    for (int i = 0; i < c->n_interior; ++i) {
+      const Tile& t = c->tiles_h[i];
+      const int64_t v0 = t.start + t.vlo, v1 = t.start + t.vhi;
+      (v1 <= w_lo - 4 || v0 >= w_lo - 4 + ((w_hi - w_lo + 7) / 4) * 4 ? plain : win).push_back(t);
+    }
+    std::vector<Tile> order = plain;
+    order.insert(order.end(), win.begin(), win.end());
+    order.insert(order.end(), c->tiles_h.begin() + c->n_interior, c->tiles_h.end());
+    if (c->adj_tiles_d) cudaFree(c->adj_tiles_d);
+    c->adj_tiles_d = nullptr;
+    CK(cudaMalloc(&c->adj_tiles_d, sizeof(Tile) * std::max<size_t>(1, order.size())), "adjoint tiles");
+    CK(cudaMemcpy(c->adj_tiles_d, order.data(), sizeof(Tile) * order.size(), cudaMemcpyHostToDevice), "adjoint tiles");
+    c->adj_n_plain = (int)plain.size();
+    c->adj_n_win = (int)win.size();
+    c->adj_w_lo = w_lo;
+    c->adj_w_hi = w_hi;
+  }
+  const Tile* t_plain = c->adj_tiles_d;
+  const Tile* t_win = c->adj_tiles_d + c->adj_n_plain;
+  const Tile* t_edge = t_win + c->adj_n_win;
+  auto fork = [&]() -> rketd_status {
+    CK(cudaEventRecord(c->fork, c->stream), "fork");
+    CK(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
+    return RKETD_OK;
+  };
+  auto join = [&]() -> rketd_status {
+    CK(cudaEventRecord(c->join, c->side), "join");
+    CK(cudaStreamWaitEvent(c->stream, c->join, 0), "join");
+    return RKETD_OK;
+  };
   if (!c->lam[0])
     for (int i = 0; i < 6; ++i)
       if ((st = c->alloc(&c->lam[i], fb, "adjoint fields"))) return st;
@@ -1082,12 +1128,12 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     if ((st = c->alloc(&c->seeds, c->esz * (size_t)std::max(P, 1) * C, "adjoint seeds"))) return st;
     if ((st = c->alloc(&c->tw_seed, c->esz * 2 * (size_t)C * std::max(nf, 1), "adjoint twiddles"))) return st;
     void* g;
-    if ((st = c->alloc(&g, sizeof(double) * 5 * (size_t)c->n_slabs * (rw - 1), "gradient sums"))) return st;
+    if ((st = c->alloc(&g, sizeof(double) * 5 * (size_t)c->n_slabs * nwin, "gradient sums"))) return st;
     c->gacc = (double*)g;
     c->rec_cap = rw;
   }
   for (int i = 0; i < 6; ++i) CK(cudaMemsetAsync(c->lam[i], 0, fb, c->stream), "adjoint init");
-  CK(cudaMemsetAsync(c->gacc, 0, sizeof(double) * 5 * (size_t)c->n_slabs * (rw - 1), c->stream), "adjoint init");
+  CK(cudaMemsetAsync(c->gacc, 0, sizeof(double) * 5 * (size_t)c->n_slabs * nwin, c->stream), "adjoint init");
   int lcur = 0;
   const int64_t n_seg = (N + C - 1) / C;
   for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
@@ -1099,7 +1145,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     CK(cudaMemcpyAsync(c->H[0], src + fb, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
     CK(cudaMemcpyAsync(c->J[0], src + 2 * fb, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
     c->cur = 0;
-    CK(launch_rec_init<T>((const T*)c->E[0], (const T*)c->H[0], (const T*)c->J[0], c->soff_d, c->n_slabs, w_lo - 1,
+    CK(launch_rec_init<T>((const T*)c->E[0], (const T*)c->H[0], (const T*)c->J[0], c->soff_d, c->nz_d, c->n_slabs, r0,
                           (int)rw, L + 1, (T*)c->recF, c->stream),
        "record init");
     c->launches += 1;
@@ -1111,17 +1157,28 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.series = nullptr;
       a.tprobes = c->tprobes_d;
       a.rec = (T*)c->recF;
-      a.rec_c0 = w_lo - 1;
+      a.rec_c0 = r0;
       a.rec_w = (int)rw;
       a.rec_len = L + 1;
       a.rec_pos = done + 1;
-      a.tiles = c->tiles_d;
-      a.n_tiles = c->n_interior;
-      CK(launch_tb_rec<T>(a, K, false, c->opt.warps_per_block, c->stream), "recompute (interior)");
-      a.tiles = c->tiles_d + c->n_interior;
+      if ((st = fork())) return st;
+      // window and edge tiles (recording) on the side stream, the rest with the plain kernels
+      a.tiles = t_win;
+      a.n_tiles = c->adj_n_win;
+      CK(launch_tb_rec<T>(a, K, false, 2, c->side), "recompute (window)");
+      a.tiles = t_edge;
       a.n_tiles = c->n_edge;
-      CK(launch_tb_rec<T>(a, Ke, true, 2, c->stream), "recompute (edge)");
-      c->launches += 2;
+      CK(launch_tb_rec<T>(a, Ke, true, 2, c->side), "recompute (edge)");
+      a.tiles = t_plain;
+      a.n_tiles = c->adj_n_plain;
+      if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
+        CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream),
+           "recompute (interior)");
+      } else {
+        CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "recompute (interior)");
+      }
+      if ((st = join())) return st;
+      c->launches += 3;
       c->cur = 1 - c->cur;
       done += nsub;
     }
@@ -1154,26 +1211,38 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.seed_len = L;
       a.tprobes = c->tprobes_d;
       a.rec = (T*)c->recA;
-      a.rec_c0 = w_lo - 1;
+      a.rec_c0 = r0;
       a.rec_w = (int)rw;
       a.rec_len = L;
-      a.tiles = c->tiles_d;
-      a.n_tiles = c->n_interior;
-      CK(launch_adj<T>(a, K, false, 2, c->stream), "adjoint (interior)");
-      a.tiles = c->tiles_d + c->n_interior;
+      if ((st = fork())) return st;
+      a.tiles = t_win;
+      a.n_tiles = c->adj_n_win;
+      CK(launch_adj<T>(a, K, false, 2, c->side), "adjoint (window)");
+      a.tiles = t_edge;
       a.n_tiles = c->n_edge;
-      CK(launch_adj<T>(a, Ke, true, 2, c->stream), "adjoint (edge)");
-      c->launches += 2;
+      CK(launch_adj<T>(a, Ke, true, 2, c->side), "adjoint (edge)");
+      a.tiles = t_plain;
+      a.n_tiles = c->adj_n_plain;
+      a.rec = nullptr;
+      if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
+        CK(launch_adj_pairs(*reinterpret_cast<const AdjArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream),
+           "adjoint (interior, FP32 pairs)");
+      } else {
+        CK(launch_adj<T>(a, K, false, 2, c->stream), "adjoint (interior)");
+      }
+      if ((st = join())) return st;
+      c->launches += 3;
       lcur = 1 - lcur;
       hi -= nsub;
     }
-    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, L, L + 1, c->gacc, c->stream),
+    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, (int)nwin, L, L + 1, c->gacc,
+                            c->stream),
        "gradient sums");
     c->launches += 1;
   }
   CK(cudaMemsetAsync(grad_wp2, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
   CK(cudaMemsetAsync(grad_nu, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
-  CK(launch_grad_chain(c->gacc, c->wp2_d, c->nu_d, c->off_d, c->n_slabs, w_lo, (int)(rw - 1), c->grid.dt, c->S,
+  CK(launch_grad_chain(c->gacc, c->wp2_d, c->nu_d, c->off_d, c->n_slabs, w_lo, (int)nwin, c->grid.dt, c->S,
                        grad_wp2, grad_nu, c->stream),
      "chain rule");
   c->launches += 1;
@@ -1191,8 +1260,8 @@ rketd_status rketd_adjoint(rketd_ctx* c, const double* dL_dX_re, const double* d
   if (c->ckpt_steps < 1) return fail(RKETD_EINVAL, "no checkpointed forward run: call rketd_forward_ckpt first");
   int64_t nz_min = c->nz[0];
   for (int64_t v : c->nz) nz_min = std::min(nz_min, v);
-  if (w_lo < 1 || w_hi <= w_lo || w_hi > nz_min - 1)
-    return fail(RKETD_EINVAL, "window [%lld, %lld) must lie inside [1, nz - 1) of every slab", (long long)w_lo,
+  if (w_lo < 4 || w_hi <= w_lo || w_hi > nz_min - 1)
+    return fail(RKETD_EINVAL, "window [%lld, %lld) must lie inside [4, nz - 1) of every slab", (long long)w_lo,
                 (long long)w_hi);
   const int P = c->total_probes, nf = c->n_freq;
   if (P > 0) {

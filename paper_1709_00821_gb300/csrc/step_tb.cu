@@ -192,12 +192,22 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
     if (REC && mrec) {
       T* r = a.rec + ((int64_t)s * a.rec_len + a.rec_pos + t) * 3 * a.rec_w;
 #pragma unroll
-      for (int i = 0; i < K; ++i) {
-        if (mrec & (1u << i)) {
-          const int64_t c = g0 + i - a.rec_c0;
-          r[c] = e[i];
-          r[a.rec_w + c] = h[i];
-          r[2 * a.rec_w + c] = jj[i];
+      for (int v = 0; v < K / 4; ++v) {
+        const uint32_t m4 = (mrec >> (4 * v)) & 0xFu;
+        const int64_t c = g0 + 4 * v - a.rec_c0;
+        if (m4 == 0xFu && (c & 3) == 0) {  // whole aligned group: vector stores
+          st4(r + c, &e[4 * v]);
+          st4(r + a.rec_w + c, &h[4 * v]);
+          st4(r + 2 * a.rec_w + c, &jj[4 * v]);
+        } else if (m4) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (m4 & (1u << q)) {
+              r[c + q] = e[4 * v + q];
+              r[a.rec_w + c + q] = h[4 * v + q];
+              r[2 * a.rec_w + c + q] = jj[4 * v + q];
+            }
+          }
         }
       }
     }

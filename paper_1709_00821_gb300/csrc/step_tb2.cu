@@ -10,6 +10,7 @@
 // kernel (fma2 is two fused multiply-adds, sub2 two subtractions), so the fields are bitwise
 // identical to the plain and scalar tiled kernels.
 #include "rketd_internal.cuh"
+#include "tile_common.cuh"
 
 #ifndef RKETD_TB_MINB
 #define RKETD_TB_MINB 3
@@ -18,96 +19,7 @@
 namespace rketd {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-typedef unsigned long long f2;  // lo = cell of half A, hi = cell of half B
-
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float lo_of(f2 v) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
-  return l;
-}
-__device__ __forceinline__ float hi_of(f2 v) {
-  float l, h;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(v));
-  return h;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-__device__ __forceinline__ double pulse(double t, double t0, double tau, double amp) {
-  const double u = (t - t0) / tau;
-  return amp * u * exp(-0.5 * u * u);
-}
-
-// element `slot` (0..K-1) of a pair array
-template <int P>
-__device__ __forceinline__ float pick2(const f2 (&r)[P], int slot) {
-  const int p = slot < P ? slot : slot - P;
-  float v = 0.f;
-#pragma unroll
-  for (int q = 0; q < P; ++q)
-    if (q == p) v = slot < P ? lo_of(r[q]) : hi_of(r[q]);
-  return v;
-}
-template <int P>
-__device__ __forceinline__ void put2(f2 (&r)[P], int slot, float v) {
-  const int p = slot < P ? slot : slot - P;
-#pragma unroll
-  for (int q = 0; q < P; ++q)
-    if (q == p) r[q] = slot < P ? pk(v, hi_of(r[q])) : pk(lo_of(r[q]), v);
-}
-
-template <int K>
-__device__ __forceinline__ void load_pairs(const float* __restrict__ p, f2 (&r)[K / 2], bool negate) {
-  constexpr int P = K / 2;
-  float t[K];
-#pragma unroll
-  for (int v = 0; v < K / 4; ++v) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + v);
-    t[4 * v] = q.x;
-    t[4 * v + 1] = q.y;
-    t[4 * v + 2] = q.z;
-    t[4 * v + 3] = q.w;
-  }
-#pragma unroll
-  for (int q = 0; q < P; ++q) r[q] = negate ? pk(-t[q], -t[P + q]) : pk(t[q], t[P + q]);
-}
-
-template <int K>
-__device__ __forceinline__ void store_pairs(float* __restrict__ p, int li0, int vlo, int vhi, const f2 (&r)[K / 2]) {
-  constexpr int P = K / 2;
-  float t[K];
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    t[q] = lo_of(r[q]);
-    t[P + q] = hi_of(r[q]);
-  }
-#pragma unroll
-  for (int v = 0; v < K / 4; ++v) {
-    const int li = li0 + 4 * v;
-    if (li >= vlo && li + 4 <= vhi) {
-      reinterpret_cast<float4*>(p)[v] = make_float4(t[4 * v], t[4 * v + 1], t[4 * v + 2], t[4 * v + 3]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (li + q >= vlo && li + q < vhi) p[4 * v + q] = t[4 * v + q];
-    }
-  }
-}
-
+using namespace tile;
 template <int K>
 __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float> a) {
   constexpr int P = K / 2;

@@ -105,3 +105,21 @@ def test_autograd_function_drives_the_adjoint():
     w = slice(300, 400)
     assert np.abs(wp2.grad.cpu().numpy()[w] - gw_o[w]).max() <= 1e-9 * np.abs(gw_o).max()
     assert np.abs(nu.grad.cpu().numpy()[w] - gn_o[w]).max() <= 1e-9 * np.abs(gn_o).max()
+
+
+def test_unaligned_window_reaching_the_last_interior_cell():
+    """Window [301, 699): not 4-aligned, ends at nz - 1 (record rows pad past the slab end)."""
+    s, tgt = _problem(2, region=(301, 699))
+    inc, R_t, gX, gw_o, gn_o = _oracle_case(s, tgt)
+    X, gw, gn = _gpu_grad([s], "f64", gX[None], (301, 699), 512, s.steps)
+    w = slice(301, 699)
+    assert np.abs(gw[w] - gw_o[w]).max() <= 1e-9 * np.abs(gw_o).max()
+    assert np.abs(gn[w] - gn_o[w]).max() <= 1e-9 * np.abs(gn_o).max()
+
+
+def test_fp32_paired_adjoint_is_bitwise_equal_to_scalar(case):
+    s, (inc, R_t, gX, gw_o, gn_o) = case
+    a = _gpu_grad([s], "f32", gX[None], (300, 400), 512, s.steps)
+    b = _gpu_grad([s], "f32", gX[None], (300, 400), 512, s.steps, fp32_pairs=2)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
