@@ -17,7 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["rketd_oracle.c"]
+_SOURCES = ["rketd_oracle.c", "rketd_oracle3d.c"]
 _LOCK = threading.Lock()
 _LIBS = {}
 
@@ -58,6 +58,16 @@ class OrGrid1D(ctypes.Structure):
     ]
 
 
+class OrGrid3D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("d", ctypes.c_double),
+                ("dt", ctypes.c_double), ("periodic_xy", ctypes.c_int32), ("npml", ctypes.c_int32),
+                ("pml_m", ctypes.c_double), ("pml_sigma_max", ctypes.c_double), ("pml_kappa_max", ctypes.c_double),
+                ("pml_alpha_max", ctypes.c_double), ("tfsf", ctypes.c_int32), ("box", ctypes.c_int32 * 6),
+                ("sheet_k", ctypes.c_int32), ("src_tau", ctypes.c_double), ("src_t0", ctypes.c_double),
+                ("src_amp", ctypes.c_double), ("n_probes", ctypes.c_int32), ("n_freq", ctypes.c_int32),
+                ("inc_off", ctypes.c_int32), ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32)]
+
+
 def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
     key = (omp, mutant)
     with _LOCK:
@@ -81,6 +91,10 @@ def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
             L.or_adjoint_step.restype = ctypes.c_int
             L.or_adjoint1d.argtypes = [ctypes.POINTER(OrGrid1D), dp, dp, ip, dp, ctypes.c_int64, dp, dp, dp, dp]
             L.or_adjoint1d.restype = ctypes.c_int
+            L.or_run3d.argtypes = [ctypes.POINTER(OrGrid3D), ctypes.POINTER(ctypes.c_uint8), dp, dp, ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_int32), dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                   dp, dp, dp]
+            L.or_run3d.restype = ctypes.c_int
             _LIBS[key] = L
         return _LIBS[key]
 
@@ -231,3 +245,56 @@ def reflection_loss(X_tot, X_inc, R_target):
     gX = np.zeros_like(X_tot)
     gX[0] = coef * d.real + 1j * coef * d.imag
     return L, gX
+
+
+class State3D:
+    """3D oracle state: fields [9][N] (Ex, Ey, Ez, Hx, Hy, Hz, Jx, Jy, Jz), CPML memories
+    [12][N], incident line [2][L], DFT sums, step index."""
+
+    def __init__(self, prob):
+        N = prob.nx * prob.ny * prob.nz
+        self.fields = np.zeros((9, N))
+        self.psi = np.zeros((12, N))
+        self.inc = np.zeros((2, prob.inc_len))
+        self.X = np.zeros((len(prob.probes), len(prob.freq_hz)), dtype=np.complex128)
+        self.n = 0
+
+    def field(self, name, prob):
+        i = ["Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Jx", "Jy", "Jz"].index(name)
+        return self.fields[i].reshape(prob.nz, prob.ny, prob.nx)
+
+
+def run3d(prob, steps=None, state=None, series=False):
+    """Runs the 3D oracle on a workloads.Grid3D problem."""
+    L = lib()
+    steps = prob.steps if steps is None else steps
+    st = State3D(prob) if state is None else state
+    g = OrGrid3D()
+    g.nx, g.ny, g.nz, g.d, g.dt = prob.nx, prob.ny, prob.nz, prob.d, prob.dt
+    g.periodic_xy = 1 if prob.periodic_xy else 0
+    g.npml = prob.npml
+    g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = cpml_defaults(prob.d)
+    g.tfsf = 1 if prob.tfsf else 0
+    for q in range(6):
+        g.box[q] = prob.box[q]
+    g.sheet_k = prob.sheet_k
+    g.src_tau, g.src_t0, g.src_amp = prob.src_tau, prob.src_t0, prob.src_amp
+    g.n_probes, g.n_freq = len(prob.probes), len(prob.freq_hz)
+    g.inc_off, g.inc_len, g.inc_src = prob.inc_off, prob.inc_len, prob.inc_src
+    mat = np.ascontiguousarray(prob.mat, dtype=np.uint8)
+    mw = np.ascontiguousarray(prob.mat_wp2, float)
+    mn = np.ascontiguousarray(prob.mat_nu, float)
+    pr = np.ascontiguousarray(np.asarray(prob.probes, np.int32).ravel())
+    fr = np.ascontiguousarray(prob.freq_hz, float)
+    xr = np.ascontiguousarray(st.X.real.copy())
+    xi = np.ascontiguousarray(st.X.imag.copy())
+    ser = np.zeros((len(prob.probes), steps)) if series else None
+    rc = L.or_run3d(ctypes.byref(g), mat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(mw), _dp(mn), len(mw),
+                    pr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(fr), st.n, steps, _dp(st.fields),
+                    _dp(st.psi), _dp(st.inc), _dp(xr), _dp(xi),
+                    _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)())
+    if rc:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    st.X = xr + 1j * xi
+    st.n += steps
+    return st, ser

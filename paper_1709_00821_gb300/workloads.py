@@ -271,3 +271,61 @@ def c5_sphere(n: int = 512, steps: int = 4000, radius: Optional[float] = None, c
     freqs = 100e9 * np.arange(1, nfreq + 1, dtype=np.float64) / nfreq
     probes = [(c[0], c[1], lo - 4 if lo - 4 > cpml else lo - 1), (c[0], c[1], hi + 4 if hi + 4 < n - 1 - cpml else hi + 1)]
     return Sphere3D(n, d, dt, c, r, (2 * math.pi * 40e9) ** 2, 2e10, lo, hi, cpml, tau, 5 * tau, probes, freqs, steps)
+
+
+@dataclass
+class Grid3D:
+    """A 3D problem on an nx x ny x nz Yee grid (spacing d) with per-cell material indices."""
+
+    nx: int
+    ny: int
+    nz: int
+    d: float
+    dt: float
+    mat: np.ndarray  # uint8 [nz*ny*nx]: material of Ex, Ey, Ez of the cell in bits 0-1, 2-3, 4-5 (0 = vacuum)
+    mat_wp2: np.ndarray  # [n_mat], entry 0 = 0
+    mat_nu: np.ndarray
+    periodic_xy: bool
+    npml: int
+    tfsf: bool
+    box: tuple  # (i0, i1, j0, j1, k0, k1)
+    sheet_k: int
+    src_tau: float
+    src_t0: float
+    probes: List[tuple]
+    freq_hz: np.ndarray
+    steps: int
+    inc_off: int = 8
+    inc_len: int = 0
+    inc_src: int = 3
+    src_amp: float = 1.0
+
+    def __post_init__(self):
+        if not self.inc_len:
+            self.inc_len = self.nz + 2 * self.inc_off
+
+
+def sphere_materials(nx: int, ny: int, nz: int, center, radius: float, index: int) -> np.ndarray:
+    """Packed per-component material bytes for a sphere: Ex at (i+1/2, j, k), Ey at
+    (i, j+1/2, k), Ez at (i, j, k+1/2) take `index` when their own position is inside."""
+    k, j, i = np.meshgrid(np.arange(nz, dtype=float), np.arange(ny, dtype=float), np.arange(nx, dtype=float),
+                          indexing="ij")
+    cx, cy, cz = center
+    r2 = radius * radius
+    ex = (i + 0.5 - cx) ** 2 + (j - cy) ** 2 + (k - cz) ** 2 <= r2
+    ey = (i - cx) ** 2 + (j + 0.5 - cy) ** 2 + (k - cz) ** 2 <= r2
+    ez = (i - cx) ** 2 + (j - cy) ** 2 + (k + 0.5 - cz) ** 2 <= r2
+    return (ex * index + ey * (index << 2) + ez * (index << 4)).astype(np.uint8).ravel()
+
+
+def sphere_problem(n: int = 512, steps: int = 4000, radius: Optional[float] = None, npml: int = 16,
+                   nfreq: int = 200) -> Grid3D:
+    """Config of the 3D scale-up: Drude sphere (wp = 2pi*40 GHz, nu = 2e10) at the grid centre,
+    d = 100 um, Courant 0.5 (c dt/d), CPML on all faces, TF/SF box 24*n/512 cells in from every
+    face, Ex-polarised plane wave along +z (Eq. 15, tau = 15 dt), probes on the axis in the
+    scattered-field region before and after the box."""
+    sp = c5_sphere(n=n, steps=steps, radius=radius, cpml=npml, nfreq=nfreq)
+    mat = sphere_materials(n, n, n, sp.center, sp.radius, 1)
+    lo, hi = sp.tfsf_lo, sp.tfsf_hi
+    return Grid3D(n, n, n, sp.d, sp.dt, mat, np.array([0.0, sp.wp2]), np.array([0.0, sp.nu]), False, npml, True,
+                  (lo, hi, lo, hi, lo, hi), -1, sp.src_tau, sp.src_t0, sp.probes, sp.freq_hz, steps)
