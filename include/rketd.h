@@ -247,6 +247,74 @@ rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64_t nz, cons
 /* Releases the context and its device memory. NULL is accepted. */
 rketd_status rketd_destroy(rketd_ctx* ctx);
 
+/* ---------------------------------------------------------------------------------------
+ * 3D Yee RKETD-FDTD: the paper's stated generalisation of the 1D scheme to 2D/3D (Sec. IV.B
+ * closing remarks, Sec. V). Eqs. 14, 12, 11 and 13 applied component by component on a Yee
+ * grid of nx x ny x nz cells with cell size d; arrays are [k][j][i] (x fastest).
+ * Yee positions: Ex (i+1/2, j, k), Ey (i, j+1/2, k), Ez (i, j, k+1/2),
+ *                Hx (i, j+1/2, k+1/2), Hy (i+1/2, j, k+1/2), Hz (i+1/2, j+1/2, k).
+ * Boundaries: CPML of npml cells (grading as rketd_grid1d) on every face, backed by PEC
+ * walls, or periodic in x and y with CPML along z only. Sources: a total-field/scattered-
+ * field box fed by an auxiliary 1D vacuum line (Ex-polarised plane wave along +z, the Eq. 15
+ * pulse injected on that line, first-order Mur ends), and/or an Eq. 15 soft sheet source
+ * added to Ex on one z plane. Materials: each E component takes the Drude material at its own
+ * position; mat[cell] packs the material indices (0..3, 0 = vacuum) of Ex, Ey, Ez of that
+ * cell in bits 0-1, 2-3 and 4-5. Probes sample Ex; their running DFT is as rketd_dft.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t nx, ny, nz;    /* cells per axis, >= 4 (and room for the CPML: > 2 (npml + 2)) */
+  int32_t prec;          /* rketd_prec: F32 fields (FP64-derived coefficients) or F64 */
+  double d, dt;          /* cell size (m) and time step (s); c0 dt / d <= 1/sqrt(3) */
+  int32_t periodic_xy;   /* 1: periodic x and y, CPML along z only; 0: CPML on all faces */
+  int32_t npml;          /* CPML cells per face, >= 1 */
+  double pml_m, pml_sigma_max, pml_kappa_max, pml_alpha_max; /* as rketd_grid1d */
+  int32_t tfsf;          /* 1: TF/SF box active */
+  int32_t box[6];        /* i0, i1, j0, j1, k0, k1: the total-field region (outside the CPML) */
+  int32_t sheet_k;       /* >= 0: soft sheet source on Ex at this z plane; -1: none */
+  int32_t inc_off;       /* incident line index of plane k is k + inc_off (>= 2) */
+  int32_t inc_len;       /* incident line length, >= nz + 2 inc_off */
+  int32_t inc_src;       /* incident line source index, 1 <= inc_src < inc_off */
+  int32_t reserved0;
+} rketd_grid3d;
+
+typedef struct rketd_ctx3d rketd_ctx3d;
+
+/*
+ * Creates a 3D context and zeroes its state.
+ *   mat          host [nz][ny][nx] packed material bytes (copied)
+ *   n_mat        1..4 materials; mat_wp2/mat_nu [n_mat] (entry 0 must be vacuum: wp2 = 0)
+ *   pulse        Eq. 15 pulse of the incident line and of the sheet source
+ *   probes       host [n_probes][3] (i, j, k) of the Ex samples; dft as for the 1D calls
+ *   stream       cudaStream_t for all work of this context (NULL = legacy default stream)
+ * Memory: 9 field arrays of nx ny nz values, one material byte per cell, CPML memories only
+ * in the face slabs. Errors: RKETD_EINVAL, RKETD_ECOURANT, RKETD_ENOMEM, RKETD_ECUDA;
+ * *out is NULL on error.
+ */
+rketd_status rketd_create_3d(const rketd_grid3d* grid, const uint8_t* mat, int32_t n_mat, const double* mat_wp2,
+                             const double* mat_nu, const rketd_pulse* pulse, int32_t n_probes, const int32_t* probes,
+                             const rketd_dft* dft, void* stream, rketd_ctx3d** out);
+
+/* Zeroes fields, CPML memories, the incident line and the DFT sums; step index 0 (async). */
+rketd_status rketd_reset_3d(rketd_ctx3d* ctx);
+
+/* Queues nsteps steps: H (+CPML, TF/SF), incident H, E and J (+CPML, TF/SF, sheet),
+ * incident E, probe samples; the DFT is folded every 512 samples. Async. */
+rketd_status rketd_step_3d(rketd_ctx3d* ctx, int64_t nsteps);
+
+/* Copies one component to a host FP64 SI array [nz][ny][nx]: which = 0..8 for Ex, Ey, Ez,
+ * Hx, Hy, Hz, Jx, Jy, Jz. Synchronises. */
+rketd_status rketd_get_field_3d(rketd_ctx3d* ctx, int32_t which, double* out);
+
+/* Copies the DFT sums to host: re/im [n_probes][n_freq] (FP64), samples not yet folded
+ * included. Synchronises. */
+rketd_status rketd_get_spectra_3d(rketd_ctx3d* ctx, double* re, double* im);
+
+/* Number of kernel launches this context has issued. */
+int64_t rketd_launch_count_3d(const rketd_ctx3d* ctx);
+
+/* Releases the 3D context and its device memory. NULL is accepted. */
+rketd_status rketd_destroy_3d(rketd_ctx3d* ctx);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* rketd_last_error(void);
 

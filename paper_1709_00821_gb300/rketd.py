@@ -52,6 +52,15 @@ class Options(ctypes.Structure):
                 ("fp32_pairs", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class Grid3D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("d", ctypes.c_double), ("dt", ctypes.c_double), ("periodic_xy", ctypes.c_int32),
+                ("npml", ctypes.c_int32), ("pml_m", ctypes.c_double), ("pml_sigma_max", ctypes.c_double),
+                ("pml_kappa_max", ctypes.c_double), ("pml_alpha_max", ctypes.c_double), ("tfsf", ctypes.c_int32),
+                ("box", ctypes.c_int32 * 6), ("sheet_k", ctypes.c_int32), ("inc_off", ctypes.c_int32),
+                ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
 _LIB = None
 
 # name -> (restype, argtypes)
@@ -87,6 +96,15 @@ _SIGS = {
     "rketd_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "rketd_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_create_3d": (ctypes.c_int, [ctypes.POINTER(Grid3D), ctypes.c_void_p, ctypes.c_int32, _dp, _dp,
+                                       ctypes.POINTER(Pulse), ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Dft),
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "rketd_reset_3d": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_step_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "rketd_get_field_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
+    "rketd_get_spectra_3d": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
 }
@@ -318,3 +336,80 @@ def advance_1d_noalloc(slab, prec: str, wp2_dev: int, nu_dev: int, n0: int, nste
     _check(lib().rketd_advance_1d_noalloc(ctypes.byref(g), slab.nz, ctypes.c_void_p(wp2_dev), ctypes.c_void_p(nu_dev),
                                           slab.src_cell, ctypes.byref(p), n0, nsteps, ctypes.c_void_p(E_dev),
                                           ctypes.c_void_p(H_dev), ctypes.c_void_p(J_dev), ctypes.c_void_p(st)))
+
+
+FIELDS_3D = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Jx", "Jy", "Jz")
+
+
+class Context3D:
+    """One rketd_ctx3d: a 3D Yee RKETD problem (workloads.Grid3D) on one CUDA stream."""
+
+    def __init__(self, prob, prec: str = "f32", stream=None):
+        L = lib()
+        self.prob = prob
+        g = Grid3D()
+        g.nx, g.ny, g.nz = prob.nx, prob.ny, prob.nz
+        g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
+        g.d, g.dt = prob.d, prob.dt
+        g.periodic_xy = 1 if prob.periodic_xy else 0
+        g.npml = prob.npml
+        g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = cpml_params(prob.d)
+        g.tfsf = 1 if prob.tfsf else 0
+        for q in range(6):
+            g.box[q] = prob.box[q]
+        g.sheet_k = prob.sheet_k
+        g.inc_off, g.inc_len, g.inc_src = prob.inc_off, prob.inc_len, prob.inc_src
+        self.prec = prec
+        self.n_probes = len(prob.probes)
+        self.freq = _arr(prob.freq_hz)
+        mat = _arr(prob.mat, np.uint8)
+        mw, mn = _arr(prob.mat_wp2), _arr(prob.mat_nu)
+        pr = _arr(np.asarray(prob.probes, np.int32).reshape(-1) if self.n_probes else np.zeros(3), np.int32)
+        p = Pulse(prob.src_tau, prob.src_t0, prob.src_amp)
+        d = Dft(self.n_probes, len(self.freq), _ptr(self.freq))
+        self.stream = _default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(L.rketd_create_3d(ctypes.byref(g), ctypes.c_void_p(mat.ctypes.data), len(mw), _ptr(mw), _ptr(mn),
+                                 ctypes.byref(p), self.n_probes, ctypes.c_void_p(pr.ctypes.data), ctypes.byref(d),
+                                 ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rketd_destroy_3d(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n: int):
+        _check(lib().rketd_step_3d(self.h, int(n)))
+
+    def reset(self):
+        _check(lib().rketd_reset_3d(self.h))
+
+    def field(self, name: str) -> np.ndarray:
+        """One component as a host FP64 SI array [nz, ny, nx]."""
+        pb = self.prob
+        out = np.empty((pb.nz, pb.ny, pb.nx))
+        _check(lib().rketd_get_field_3d(self.h, FIELDS_3D.index(name), _ptr(out)))
+        return out
+
+    def spectra(self) -> np.ndarray:
+        n = self.n_probes * len(self.freq)
+        re, im = np.empty(max(n, 1)), np.empty(max(n, 1))
+        _check(lib().rketd_get_spectra_3d(self.h, _ptr(re), _ptr(im)))
+        return (re[:n] + 1j * im[:n]).reshape(self.n_probes, len(self.freq))
+
+    @property
+    def launches(self) -> int:
+        return lib().rketd_launch_count_3d(self.h)

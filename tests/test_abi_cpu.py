@@ -110,3 +110,82 @@ def test_rt_helper_reports_zero_incident_spectrum():
     with pytest.raises(rk.RketdError) as ei:
         rk.rt(tot, inc)
     assert ei.value.status == 7
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the ABI structs have the header's sizes and field offsets (gcc)."""
+    checks = {"rketd_grid1d": rk.Grid1D, "rketd_grid3d": rk.Grid3D, "rketd_options": rk.Options,
+              "rketd_pulse": rk.Pulse, "rketd_dft": rk.Dft}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for cname, py in checks.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for ln in out:
+        if not ln:
+            continue
+        cname, what, val = ln.split()
+        py = checks[cname]
+        expect = ctypes.sizeof(py) if what == "size" else getattr(py, what).offset
+        assert int(val) == expect, (cname, what)
+        seen += 1
+    assert seen == sum(len(p._fields_) + 1 for p in checks.values())
+
+
+def _create3d(prob, **over):
+    """Calls rketd_create_3d directly; validation fails before any CUDA call."""
+    L = rk.lib()
+    g = rk.Grid3D()
+    g.nx, g.ny, g.nz, g.prec = prob.nx, prob.ny, prob.nz, over.get("prec", 0)
+    g.d, g.dt = prob.d, over.get("dt", prob.dt)
+    g.periodic_xy, g.npml = int(prob.periodic_xy), prob.npml
+    g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = rk.cpml_params(prob.d)
+    g.tfsf = int(prob.tfsf)
+    for q in range(6):
+        g.box[q] = prob.box[q]
+    g.sheet_k, g.inc_off, g.inc_len, g.inc_src = prob.sheet_k, prob.inc_off, prob.inc_len, prob.inc_src
+    mat = np.ascontiguousarray(prob.mat, np.uint8)
+    mw = np.ascontiguousarray(over.get("wp2", prob.mat_wp2), float)
+    mn = np.ascontiguousarray(prob.mat_nu, float)
+    pr = np.ascontiguousarray(np.asarray(prob.probes, np.int32).reshape(-1))
+    fr = np.ascontiguousarray(prob.freq_hz, float)
+    p = rk.Pulse(prob.src_tau, prob.src_t0, prob.src_amp)
+    d = rk.Dft(len(prob.probes), len(fr), fr.ctypes.data_as(rk._dp))
+    h = ctypes.c_void_p()
+    st = L.rketd_create_3d(ctypes.byref(g), ctypes.c_void_p(mat.ctypes.data), len(mw), mw.ctypes.data_as(rk._dp),
+                           mn.ctypes.data_as(rk._dp), ctypes.byref(p), len(prob.probes),
+                           ctypes.c_void_p(pr.ctypes.data), ctypes.byref(d), None, ctypes.byref(h))
+    return st, L.rketd_last_error().decode(), h
+
+
+@pytest.mark.parametrize("case", ["courant", "box_in_cpml", "box_empty", "probe_out", "mat0_plasma", "npml_big",
+                                  "sheet_in_cpml", "inc_short"])
+def test_3d_invalid_inputs_are_rejected_before_any_device_work(case):
+    p = wl.sphere_problem(n=32, steps=10, radius=4.0, npml=4, nfreq=4)
+    over = {}
+    if case == "courant":
+        over["dt"] = 1.01 * p.d * math.sqrt(wl.MU0 * wl.EPS0) / math.sqrt(3.0)
+    elif case == "box_in_cpml":
+        p.box = (3, 20, 8, 20, 8, 20)
+    elif case == "box_empty":
+        p.box = (10, 10, 8, 20, 8, 20)
+    elif case == "probe_out":
+        p.probes = [(1, 2, 32)]
+    elif case == "mat0_plasma":
+        over["wp2"] = np.array([1e20, p.mat_wp2[1]])
+    elif case == "npml_big":
+        p.npml = 15
+    elif case == "sheet_in_cpml":
+        p.sheet_k = 2
+    elif case == "inc_short":
+        p.inc_len = p.nz
+    st, msg, h = _create3d(p, **over)
+    assert st == (2 if case == "courant" else 1), (st, msg)
+    assert msg and not h.value

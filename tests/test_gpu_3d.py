@@ -1,0 +1,164 @@
+"""GPU parity of the 3D Yee RKETD step against the 3D oracle (and, where the problem reduces
+to it, the 1D oracle). FP64: every field within 1e-11 of its group's peak; FP32: within
+2e-4 of the peak (single-precision rounding over a few hundred steps)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_00821_gb300 import rketd as rk
+from paper_1709_00821_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = {"E": ("Ex", "Ey", "Ez"), "H": ("Hx", "Hy", "Hz"), "J": ("Jx", "Jy", "Jz")}
+TOL = {"f64": 1e-11, "f32": 2e-4}
+
+
+def _compare(ctx, st, prob, prec, spectra=True):
+    worst = {}
+    for grp, names in GROUPS.items():
+        ref = {n: st.field(n, prob) for n in names}
+        peak = max(np.abs(r).max() for r in ref.values())
+        if peak == 0:
+            for n in names:
+                assert not np.any(ctx.field(n)), n
+            continue
+        for n in names:
+            err = np.abs(ctx.field(n) - ref[n]).max() / peak
+            worst[n] = err
+            assert err <= TOL[prec], (n, err)
+    if spectra and len(prob.probes):
+        X = ctx.spectra()
+        scale = np.abs(st.X).max()
+        assert scale > 0
+        err = np.abs(X - st.X).max() / scale
+        worst["X"] = err
+        assert err <= TOL[prec], ("X", err)
+    return worst
+
+
+def _sphere(n=37, steps=260):
+    p = wl.sphere_problem(n=n, steps=steps, radius=5.0, npml=6, nfreq=8)
+    p.box = (12, 24, 12, 24, 12, 24)
+    return p
+
+
+def _ragged():
+    """Odd sizes on every axis (x not a multiple of the 32-wide tile, y not of 8), an
+    off-centre sphere cut by the box, CPML of 5 cells, probes in both regions."""
+    nx, ny, nz = 37, 29, 45
+    d = 100e-6
+    dt = wl.dt_for_courant(d, 0.5)
+    m1 = wl.sphere_materials(nx, ny, nz, (17.3, 12.6, 23.9), 6.2, 1)
+    m2 = wl.sphere_materials(nx, ny, nz, (24.0, 19.0, 30.0), 3.1, 2)
+    assert not np.any((m1 != 0) & (m2 != 0))  # disjoint spheres: every 2-bit index stays 0, 1 or 2
+    mat = m1 | m2
+    freqs = 100e9 * np.arange(1, 9, dtype=float) / 8
+    return wl.Grid3D(nx, ny, nz, d, dt, mat, np.array([0.0, (2 * math.pi * 40e9) ** 2, (2 * math.pi * 25e9) ** 2]),
+                     np.array([0.0, 2e10, 7e10]), False, 5, True, (9, 27, 8, 21, 10, 35), -1, 15 * dt, 75 * dt,
+                     [(17, 12, 7), (20, 14, 38), (18, 13, 22)], freqs, 230)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sphere_tfsf_cpml_matches_the_3d_oracle(prec):
+    p = _sphere()
+    st, _ = oracle.run3d(p)
+    with rk.Context3D(p, prec) as ctx:
+        ctx.step(p.steps)
+        worst = _compare(ctx, st, p, prec)
+    print(prec, {k: f"{v:.2e}" for k, v in worst.items()})
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ragged_grid_two_materials_matches_the_3d_oracle(prec):
+    p = _ragged()
+    st, _ = oracle.run3d(p)
+    with rk.Context3D(p, prec) as ctx:
+        ctx.step(100)
+        ctx.step(p.steps - 100)  # split calls: the DFT fold and the step index carry over
+        worst = _compare(ctx, st, p, prec)
+    print(prec, {k: f"{v:.2e}" for k, v in worst.items()})
+
+
+def test_periodic_layered_slab_reduces_to_the_1d_oracle():
+    nx, ny, nz, steps = 4, 8, 260, 700
+    d = 75e-6
+    dt = wl.dt_for_courant(d, 0.5)
+    mat = np.zeros((nz, ny, nx), np.uint8)
+    mat[140:170] = 1 | (1 << 2) | (1 << 4)
+    freqs = 0.5e9 * np.arange(1, 41, dtype=float)
+    p = wl.Grid3D(nx, ny, nz, d, dt, mat.ravel(), np.array([0.0, (2 * math.pi * 28.7e9) ** 2]),
+                  np.array([0.0, 2e10]), True, 16, False, (0, 0, 0, 0, 0, 0), 60, 15 * dt, 75 * dt,
+                  [(1, 2, 40), (3, 5, 220)], freqs, steps)
+    s1 = wl.Slab1D(nz, d, dt, np.zeros(nz), np.zeros(nz), 60, 15 * dt, 75 * dt, [40, 220], freqs, "cpml", 16, steps)
+    s1.wp2[140:170] = p.mat_wp2[1]
+    s1.nu[140:170] = p.mat_nu[1]
+    st1, _ = oracle.run1d(s1)
+    with rk.Context3D(p, "f64") as ctx:
+        ctx.step(steps)
+        Ex, Hy, Jx = ctx.field("Ex"), ctx.field("Hy"), ctx.field("Jx")
+        X = ctx.spectra()
+        for n in ("Ey", "Ez", "Hx", "Hz", "Jy", "Jz"):
+            assert not np.any(ctx.field(n)), n
+    pe, ph = np.abs(st1.E).max(), np.abs(st1.H).max()
+    for j in range(ny):
+        for i in range(nx):
+            assert np.abs(Ex[:, j, i] - st1.E).max() <= 1e-11 * pe
+            assert np.abs(Hy[:-1, j, i] - st1.H).max() <= 1e-11 * ph
+            assert np.abs(Jx[:, j, i] - st1.J).max() <= 1e-11 * np.abs(st1.J).max()
+    assert np.abs(X - st1.X).max() <= 1e-11 * np.abs(st1.X).max()
+
+
+def test_sheet_source_on_a_closed_grid_matches_the_3d_oracle():
+    """CPML on all faces with the soft sheet source: the sheet covers the whole plane, the
+    PEC wall cells included, as in the oracle."""
+    p = _sphere(n=33, steps=150)
+    p.tfsf = False
+    p.sheet_k = 9
+    st, _ = oracle.run3d(p)
+    with rk.Context3D(p, "f64") as ctx:
+        ctx.step(p.steps)
+        _compare(ctx, st, p, "f64")
+
+
+def test_reset_reproduces_the_first_run_bitwise():
+    p = _ragged()
+    with rk.Context3D(p, "f32") as ctx:
+        ctx.step(120)
+        a = [ctx.field(n) for n in ("Ex", "Hy", "Jz")]
+        Xa = ctx.spectra()
+        ctx.reset()
+        ctx.step(120)
+        b = [ctx.field(n) for n in ("Ex", "Hy", "Jz")]
+        assert all(np.array_equal(u, v) for u, v in zip(a, b))
+        assert np.array_equal(Xa, ctx.spectra())
+        assert ctx.launches > 480
+
+
+def test_full_size_sphere_grid_total_field_is_the_incident_wave():
+    """512^3 FP32 as in the benchmark, 260 steps: the pulse is inside the TF/SF box but has
+    not reached the sphere (k >= 136), so the total field in the box equals the incident line,
+    which is the 1D oracle on a vacuum line of the same length, and the scattered-field region
+    holds only rounding. Checks every box face and the indexing at full size."""
+    p = wl.sphere_problem(n=512, steps=260)
+    steps = 260
+    line = wl.Slab1D(p.inc_len, p.d, p.dt, np.zeros(p.inc_len), np.zeros(p.inc_len), p.inc_src, p.src_tau,
+                     p.src_t0, [p.inc_off + 30], np.array([1e9]), "mur", 0, steps)
+    st1, _ = oracle.run1d(line)
+    inc = st1.E[np.arange(p.nz) + p.inc_off]
+    peak = np.abs(inc).max()
+    i0, i1, j0, j1, k0, k1 = p.box
+    assert np.abs(inc[k0 + 20:k1 + 1]).max() > 0.5 * peak  # the pulse is well inside the box
+    assert np.abs(inc[136:]).max() < 1e-6 * peak  # and has not reached the sphere
+    with rk.Context3D(p, "f32") as ctx:
+        ctx.step(steps)
+        Ex = ctx.field("Ex")
+        inside = Ex[k0:k1 + 1, j0:j1 + 1, i0:i1]
+        assert np.abs(inside - inc[k0:k1 + 1, None, None]).max() <= 2e-4 * peak
+        Ex[k0:k1 + 1, j0:j1 + 1, i0:i1] = 0.0
+        assert np.abs(Ex).max() <= 2e-5 * peak
+        del Ex, inside
+        for n in ("Ey", "Ez"):
+            assert np.abs(ctx.field(n)).max() <= 2e-5 * peak, n
