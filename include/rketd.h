@@ -274,7 +274,12 @@ typedef struct {
   int32_t inc_off;       /* incident line index of plane k is k + inc_off (>= 2) */
   int32_t inc_len;       /* incident line length, >= nz + 2 inc_off */
   int32_t inc_src;       /* incident line source index, 1 <= inc_src < inc_off */
-  int32_t reserved0;
+  int32_t variant;       /* 0 = auto (staged where it applies, else fused), 1 = plain (paper
+                            structure: an H kernel and an E+J kernel per step, fields in place),
+                            2 = fused (one kernel per step, step-n state in, step-n+1 state out:
+                            twice the E/H memory), 3 = staged (fused, with the step-n planes
+                            brought into shared memory by TMA copies; CPML on every face and
+                            nx a multiple of 16, else RKETD_EUNSUPPORTED) */
 } rketd_grid3d;
 
 typedef struct rketd_ctx3d rketd_ctx3d;
@@ -298,7 +303,8 @@ rketd_status rketd_create_3d(const rketd_grid3d* grid, const uint8_t* mat, int32
 rketd_status rketd_reset_3d(rketd_ctx3d* ctx);
 
 /* Queues nsteps steps: H (+CPML, TF/SF), incident H, E and J (+CPML, TF/SF, sheet),
- * incident E, probe samples; the DFT is folded every 512 samples. Async. */
+ * incident E, probe samples; the DFT is folded every 512 samples. Both variants give the
+ * same arithmetic, operation by operation. Async. */
 rketd_status rketd_step_3d(rketd_ctx3d* ctx, int64_t nsteps);
 
 /* Copies one component to a host FP64 SI array [nz][ny][nx]: which = 0..8 for Ex, Ey, Ez,
@@ -308,6 +314,14 @@ rketd_status rketd_get_field_3d(rketd_ctx3d* ctx, int32_t which, double* out);
 /* Copies the DFT sums to host: re/im [n_probes][n_freq] (FP64), samples not yet folded
  * included. Synchronises. */
 rketd_status rketd_get_spectra_3d(rketd_ctx3d* ctx, double* re, double* im);
+
+/* Waits for the context's stream; RKETD_ETIMEOUT if a bounded wait of the staged form gave
+ * up (its fields are then not valid). */
+rketd_status rketd_sync_3d(rketd_ctx3d* ctx);
+
+/* Sets the number of z planes (1..4096) one thread block advances per step (default 16).
+ * A tuning knob: results do not depend on it. */
+rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* ctx, int32_t k_chunk);
 
 /* Number of kernel launches this context has issued. */
 int64_t rketd_launch_count_3d(const rketd_ctx3d* ctx);

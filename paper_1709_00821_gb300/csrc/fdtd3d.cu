@@ -5,13 +5,24 @@
 // periodic x and y), a total-field/scattered-field box fed by a 1D line, a soft sheet
 // source and a running DFT of Ex at probe points.
 //
-// Streaming form: one H kernel and one E+J kernel per step. A thread owns an (i, j) column
-// and marches along k, so the z-neighbours of each update stay in registers; x- and
-// y-neighbours come from neighbouring threads through L1/L2. Arrays are [k][j][i].
-// Yee positions: Ex (i+1/2, j, k), Ey (i, j+1/2, k), Ez (i, j, k+1/2),
-//                Hx (i, j+1/2, k+1/2), Hy (i+1/2, j, k+1/2), Hz (i+1/2, j+1/2, k).
+// Arrays are [k][j][i] (x fastest). Yee positions:
+//   Ex (i+1/2, j, k), Ey (i, j+1/2, k), Ez (i, j, k+1/2),
+//   Hx (i, j+1/2, k+1/2), Hy (i+1/2, j, k+1/2), Hz (i+1/2, j+1/2, k).
 // Each E component takes the material at its own position: mat[c] packs the material
 // indices of Ex, Ey, Ez of cell c in bits 0-1, 2-3, 4-5 (0 = vacuum).
+//
+// Three forms of one step, doing the same operations on the same values:
+//  - plain: the paper's structure, an H kernel then an E+J kernel, fields updated in place;
+//  - staged (default where it applies): the fused step below fed from shared memory, whole
+//    planes of the step-n state brought in by the tensor memory accelerator (k3_staged);
+//  - fused: one kernel per step reading the step-n state (E, H, the H-side CPML
+//    memories, the incident line) and writing the step-n+1 state into a second set of
+//    buffers. A warp owns 32 consecutive i of one j row and a chunk of k; the new H of its
+//    own cells is stored and fed to the E update in registers: the i-1 neighbour comes from
+//    the next lane down (lane 0 recomputes it), the k-1 neighbour from the previous k, and
+//    the j-1 neighbour is recomputed from the step-n state (its owner may not have written
+//    it yet). E and H are each read once and written once per step.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,9 +38,7 @@ namespace rketd {
 namespace {
 
 constexpr int kMat = 4;
-// derivative axis of each CPML memory (order Ex/y, Ex/z, Ey/z, Ey/x, Ez/x, Ez/y, Hx/y, Hx/z,
-// Hy/z, Hy/x, Hz/x, Hz/y)
-constexpr int kPsiAxis[12] = {1, 2, 2, 0, 0, 1, 1, 2, 2, 0, 0, 1};
+constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T>
 struct Mat3 {
@@ -38,19 +47,28 @@ struct Mat3 {
 
 template <typename T>
 struct Args3 {
-  T *Ex, *Ey, *Ez, *Hx, *Hy, *Hz, *Jx, *Jy, *Jz;
+  // step-n state (read) and step-n+1 state (written); the plain kernels pass one set for both
+  const T *Ex, *Ey, *Ez, *Hx, *Hy, *Hz;
+  T *oEx, *oEy, *oEz, *oHx, *oHy, *oHz;
+  T *Jx, *Jy, *Jz;  // carried currents, updated in place
   const uint8_t* mat;
   Mat3<T> m;
-  int nx, ny, nz, per;
+  int nx, ny, nz, per, kc;
   T S, q;
-  // CPML: tables [axis][E/H][b, c, kinv, flag][nmax]; memories in compact zones of width Z
+  // CPML: tables [axis][E/H][b, c, 1/kappa, flag][nmax]; memories in compact face zones of
+  // width Z: x-derivative [k][j][Z], y-derivative [k][Z][i], z-derivative [Z][j][i]
   const T* tab;
   int nmax, np, Z;
-  T* psi[12];  // Ex/y, Ex/z, Ey/z, Ey/x, Ez/x, Ez/y, Hx/y, Hx/z, Hy/z, Hy/x, Hz/x, Hz/y
-  // TF/SF
+  T* psiE[6];        // Ex/y, Ex/z, Ey/z, Ey/x, Ez/x, Ez/y (in place)
+  const T* psiH[6];  // Hx/y, Hx/z, Hy/z, Hy/x, Hz/x, Hz/y (read)
+  T* opsiH[6];       // (written)
+  // TF/SF box and its 1D line (index k + inc_off)
   int tfsf, i0, i1, j0, j1, k0, k1;
-  T* Ei;
-  T* Hi;
+  const T* Ei;
+  const T* Hi;
+  T* oEi;
+  T* oHi;
+  int line_fresh;  // 1: Hi already holds H^{n+1/2} (plain form); 0: derive it from Ei, Hi
   int inc_len, inc_off, inc_src;
   // sources and probes
   int sheet_k;
@@ -66,12 +84,25 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int nx, int ny) {
   return ((int64_t)k * ny + j) * nx + i;
 }
 
-// compact CPML zone index of node n on an axis of N nodes (np layers): -1 outside
+// compact CPML zone of node n on an axis of N nodes with np layers (-1: outside)
 __device__ __forceinline__ int zone(int n, int N, int np) {
   if (np <= 0) return -1;
   if (n < np + 1) return n;
   if (n >= N - np - 1) return np + 1 + (n - (N - np - 1));
   return -1;
+}
+
+template <typename T>
+__device__ __forceinline__ int64_t zx_off(const Args3<T>& a, int j, int k, int z) {
+  return ((int64_t)k * a.ny + j) * a.Z + z;
+}
+template <typename T>
+__device__ __forceinline__ int64_t zy_off(const Args3<T>& a, int i, int k, int z) {
+  return ((int64_t)k * a.Z + z) * a.nx + i;
+}
+template <typename T>
+__device__ __forceinline__ int64_t zz_off(const Args3<T>& a, int i, int j, int z) {
+  return ((int64_t)z * a.ny + j) * a.nx + i;
 }
 
 template <typename T>
@@ -84,78 +115,134 @@ __device__ __forceinline__ double pulse3(double t, double t0, double tau, double
   return amp * u * exp(-0.5 * u * u);
 }
 
-// Stretched difference with CPML memory: psi = b psi + c dv; returns dv kinv + psi.
-template <typename T>
-__device__ __forceinline__ T stretch(const T* t, int nmax, int pos, T dv, T* psi) {
+// read of the step-n state: through the read-only cache when nothing in the kernel writes it
+template <bool RO, typename T>
+__device__ __forceinline__ T rd(const T* p) {
+  if constexpr (RO) return __ldg(p);
+  else return *p;
+}
+
+// CPML-stretched difference: psi' = b psi + c dv, result dv / kappa + psi'.
+// pout = nullptr: the new memory is not stored (a neighbour's value recomputed).
+template <bool RO, typename T>
+__device__ __forceinline__ T stretch(const T* t, int nmax, int pos, T dv, const T* pin, T* pout) {
   if (t[3 * nmax + pos] == T(0)) return dv;
-  const T p = fma(t[pos], *psi, t[nmax + pos] * dv);
-  *psi = p;
+  const T p = fma(t[pos], rd<RO>(pin), t[nmax + pos] * dv);
+  if (pout) *pout = p;
   return fma(dv, t[2 * nmax + pos], p);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k3_h(const Args3<T> a) {
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  if (blockIdx.z == 1) {  // the 1D incident line: H~ -= S (E_{m+1} - E_m)
-    if (blockIdx.x != 0 || blockIdx.y != 0 || !a.tfsf) return;
-    for (int m = threadIdx.y * blockDim.x + threadIdx.x; m < a.inc_len - 1; m += blockDim.x * blockDim.y)
-      a.Hi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
-    return;
+// New H components at one cell (Eq. 14 per component, CPML, TF/SF corrections with the
+// step-n incident E) from the values of the step-n E and H it depends on. Every form of the
+// step calls these, so all forms do the same operations on the same values.
+// own = false: the CPML memories are read but not stored (a neighbour's value recomputed).
+template <bool RO, typename T>
+__device__ __forceinline__ T hx_core(const Args3<T>& a, int i, int j, int k, T h, T ez_jp, T ez, T ey_kp, T ey,
+                                     bool own) {
+  const int jp = (j + 1 < a.ny) ? j + 1 : (a.per ? 0 : -1);
+  if (jp < 0 || k + 1 >= a.nz) return h;
+  T cy = ez_jp - ez;
+  T cz = ey_kp - ey;
+  const int zy = a.per ? -1 : zone(j, a.ny, a.np), zz = zone(k, a.nz, a.np);
+  if (zy >= 0) {
+    const int64_t o = zy_off(a, i, k, zy);
+    cy = stretch<RO>(tb(a, 1, 1), a.nmax, j, cy, a.psiH[0] + o, own ? a.opsiH[0] + o : nullptr);
   }
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= nx || j >= ny) return;
-  const int ip = (i + 1 < nx) ? i + 1 : (a.per ? 0 : -1);
-  const int jp = (j + 1 < ny) ? j + 1 : (a.per ? 0 : -1);
-  const int64_t nxy = (int64_t)nx * ny;
-  const T S = a.S;
-  const T* tx = tb(a, 0, 1);
-  const T* ty = tb(a, 1, 1);
-  const T* tz = tb(a, 2, 1);
-  const int zx = zone(i, nx, a.per ? 0 : a.np), zy = zone(j, ny, a.per ? 0 : a.np);
-  const bool in_i = a.tfsf && i >= a.i0 && i <= a.i1 - 1;
-  T ex = a.Ex[idx3(i, j, 0, nx, ny)], ey = a.Ey[idx3(i, j, 0, nx, ny)];
-  for (int k = 0; k < nz; ++k) {
-    const int64_t c = idx3(i, j, k, nx, ny);
-    const bool kn = k + 1 < nz;
-    const T exn = kn ? a.Ex[c + nxy] : T(0);
-    const T eyn = kn ? a.Ey[c + nxy] : T(0);
-    const T ez = a.Ez[c];
-    const int zz = zone(k, nz, a.np);
-    if (jp >= 0 && kn) {  // Hx
-      T cy = a.Ez[idx3(i, jp, k, nx, ny)] - ez;
-      T cz = eyn - ey;
-      if (zy >= 0) cy = stretch(ty, a.nmax, j, cy, &a.psi[6][((int64_t)k * a.Z + zy) * nx + i]);
-      if (zz >= 0) cz = stretch(tz, a.nmax, k, cz, &a.psi[7][((int64_t)zz * ny + j) * nx + i]);
-      a.Hx[c] = fma(-S, cy - cz, a.Hx[c]);
-    }
-    if (ip >= 0 && kn) {  // Hy
-      T cz = exn - ex;
-      T cx = a.Ez[idx3(ip, j, k, nx, ny)] - ez;
-      if (zz >= 0) cz = stretch(tz, a.nmax, k, cz, &a.psi[8][((int64_t)zz * ny + j) * nx + i]);
-      if (zx >= 0) cx = stretch(tx, a.nmax, i, cx, &a.psi[9][((int64_t)k * ny + j) * a.Z + zx]);
-      T h = fma(-S, cz - cx, a.Hy[c]);
-      if (in_i && j >= a.j0 && j <= a.j1) {
-        if (k == a.k0 - 1) h = fma(S, a.Ei[a.k0 + a.inc_off], h);
-        if (k == a.k1) h = fma(-S, a.Ei[a.k1 + a.inc_off], h);
-      }
-      a.Hy[c] = h;
-    }
-    if (ip >= 0 && jp >= 0) {  // Hz
-      T cx = a.Ey[idx3(ip, j, k, nx, ny)] - ey;
-      T cy = a.Ex[idx3(i, jp, k, nx, ny)] - ex;
-      if (zx >= 0) cx = stretch(tx, a.nmax, i, cx, &a.psi[10][((int64_t)k * ny + j) * a.Z + zx]);
-      if (zy >= 0) cy = stretch(ty, a.nmax, j, cy, &a.psi[11][((int64_t)k * a.Z + zy) * nx + i]);
-      T h = fma(-S, cx - cy, a.Hz[c]);
-      if (in_i && k >= a.k0 && k <= a.k1) {
-        if (j == a.j0 - 1) h = fma(-S, a.Ei[k + a.inc_off], h);
-        if (j == a.j1) h = fma(S, a.Ei[k + a.inc_off], h);
-      }
-      a.Hz[c] = h;
-    }
-    ex = exn;
-    ey = eyn;
+  if (zz >= 0) {
+    const int64_t o = zz_off(a, i, j, zz);
+    cz = stretch<RO>(tb(a, 2, 1), a.nmax, k, cz, a.psiH[1] + o, own ? a.opsiH[1] + o : nullptr);
   }
+  return fma(-a.S, cy - cz, h);
+}
+
+template <bool RO, typename T>
+__device__ __forceinline__ T hy_core(const Args3<T>& a, int i, int j, int k, T h, T ex_kp, T ex, T ez_ip, T ez,
+                                     bool own) {
+  const int ip = (i + 1 < a.nx) ? i + 1 : (a.per ? 0 : -1);
+  if (ip < 0 || k + 1 >= a.nz) return h;
+  T cz = ex_kp - ex;
+  T cx = ez_ip - ez;
+  const int zz = zone(k, a.nz, a.np), zx = a.per ? -1 : zone(i, a.nx, a.np);
+  if (zz >= 0) {
+    const int64_t o = zz_off(a, i, j, zz);
+    cz = stretch<RO>(tb(a, 2, 1), a.nmax, k, cz, a.psiH[2] + o, own ? a.opsiH[2] + o : nullptr);
+  }
+  if (zx >= 0) {
+    const int64_t o = zx_off(a, j, k, zx);
+    cx = stretch<RO>(tb(a, 0, 1), a.nmax, i, cx, a.psiH[3] + o, own ? a.opsiH[3] + o : nullptr);
+  }
+  T v = fma(-a.S, cz - cx, h);
+  if (a.tfsf && i >= a.i0 && i <= a.i1 - 1 && j >= a.j0 && j <= a.j1) {
+    if (k == a.k0 - 1) v = fma(a.S, rd<RO>(a.Ei + a.k0 + a.inc_off), v);
+    if (k == a.k1) v = fma(-a.S, rd<RO>(a.Ei + a.k1 + a.inc_off), v);
+  }
+  return v;
+}
+
+template <bool RO, typename T>
+__device__ __forceinline__ T hz_core(const Args3<T>& a, int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex,
+                                     bool own) {
+  const int ip = (i + 1 < a.nx) ? i + 1 : (a.per ? 0 : -1);
+  const int jp = (j + 1 < a.ny) ? j + 1 : (a.per ? 0 : -1);
+  if (ip < 0 || jp < 0) return h;
+  T cx = ey_ip - ey;
+  T cy = ex_jp - ex;
+  const int zx = a.per ? -1 : zone(i, a.nx, a.np), zy = a.per ? -1 : zone(j, a.ny, a.np);
+  if (zx >= 0) {
+    const int64_t o = zx_off(a, j, k, zx);
+    cx = stretch<RO>(tb(a, 0, 1), a.nmax, i, cx, a.psiH[4] + o, own ? a.opsiH[4] + o : nullptr);
+  }
+  if (zy >= 0) {
+    const int64_t o = zy_off(a, i, k, zy);
+    cy = stretch<RO>(tb(a, 1, 1), a.nmax, j, cy, a.psiH[5] + o, own ? a.opsiH[5] + o : nullptr);
+  }
+  T v = fma(-a.S, cx - cy, h);
+  if (a.tfsf && i >= a.i0 && i <= a.i1 - 1 && k >= a.k0 && k <= a.k1) {
+    if (j == a.j0 - 1) v = fma(-a.S, rd<RO>(a.Ei + k + a.inc_off), v);
+    if (j == a.j1) v = fma(a.S, rd<RO>(a.Ei + k + a.inc_off), v);
+  }
+  return v;
+}
+
+// the same from global memory (neighbours loaded only where the update is defined)
+template <bool RO, typename T>
+__device__ __forceinline__ T hx_new(const Args3<T>& a, int i, int j, int k, bool own) {
+  const int64_t c = idx3(i, j, k, a.nx, a.ny);
+  const T h = rd<RO>(a.Hx + c);
+  const int jp = (j + 1 < a.ny) ? j + 1 : (a.per ? 0 : -1);
+  if (jp < 0 || k + 1 >= a.nz) return h;
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+  return hx_core<RO>(a, i, j, k, h, rd<RO>(a.Ez + idx3(i, jp, k, a.nx, a.ny)), rd<RO>(a.Ez + c),
+                     rd<RO>(a.Ey + c + nxy), rd<RO>(a.Ey + c), own);
+}
+
+template <bool RO, typename T>
+__device__ __forceinline__ T hy_new(const Args3<T>& a, int i, int j, int k, bool own) {
+  const int64_t c = idx3(i, j, k, a.nx, a.ny);
+  const T h = rd<RO>(a.Hy + c);
+  const int ip = (i + 1 < a.nx) ? i + 1 : (a.per ? 0 : -1);
+  if (ip < 0 || k + 1 >= a.nz) return h;
+  const int64_t nxy = (int64_t)a.nx * a.ny;
+  return hy_core<RO>(a, i, j, k, h, rd<RO>(a.Ex + c + nxy), rd<RO>(a.Ex + c),
+                     rd<RO>(a.Ez + idx3(ip, j, k, a.nx, a.ny)), rd<RO>(a.Ez + c), own);
+}
+
+template <bool RO, typename T>
+__device__ __forceinline__ T hz_new(const Args3<T>& a, int i, int j, int k, bool own) {
+  const int64_t c = idx3(i, j, k, a.nx, a.ny);
+  const T h = rd<RO>(a.Hz + c);
+  const int ip = (i + 1 < a.nx) ? i + 1 : (a.per ? 0 : -1);
+  const int jp = (j + 1 < a.ny) ? j + 1 : (a.per ? 0 : -1);
+  if (ip < 0 || jp < 0) return h;
+  return hz_core<RO>(a, i, j, k, h, rd<RO>(a.Ey + idx3(ip, j, k, a.nx, a.ny)), rd<RO>(a.Ey + c),
+                     rd<RO>(a.Ex + idx3(i, jp, k, a.nx, a.ny)), rd<RO>(a.Ex + c), own);
+}
+
+// incident H~ at line index m, time n+1/2
+template <bool RO, typename T>
+__device__ __forceinline__ T hinc(const Args3<T>& a, int m) {
+  if (a.line_fresh) return a.Hi[m];
+  return fma(-a.S, rd<RO>(a.Ei + m + 1) - rd<RO>(a.Ei + m), rd<RO>(a.Hi + m));
 }
 
 // E' = E + da E + cb curl - Jc,  Jc' = Jc + dj Jc + bp E + cc E'  (material m of the component)
@@ -173,12 +260,116 @@ __device__ __forceinline__ T e_update(const Mat3<T>& M, int m, T e, T curl, T* J
   return en;
 }
 
+// E and J update of one cell (Eqs. 12, 11, 13 per component) from the new H of the cell and
+// of its i-1, j-1, k-1 neighbours; CPML, TF/SF corrections, sheet source. Returns the new Ex.
+template <bool RO, typename T>
+__device__ __forceinline__ T e_cell(const Args3<T>& a, int i, int j, int k, T ex, T ey, T ez, int mb, T hx, T hy,
+                                    T hz, T hx_jm, T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int64_t c = idx3(i, j, k, nx, ny);
+  const bool xin = a.per || (i > 0 && i < nx - 1);
+  const bool yin = a.per || (j > 0 && j < ny - 1);
+  const bool zin = k > 0 && k < nz - 1;
+  const int zx = a.per ? -1 : zone(i, nx, a.np), zy = a.per ? -1 : zone(j, ny, a.np), zz = zone(k, nz, a.np);
+  const T* tx = tb(a, 0, 0);
+  const T* ty = tb(a, 1, 0);
+  const T* tz = tb(a, 2, 0);
+  if ((a.per || i < nx - 1) && yin && zin) {
+    T cy = hz - hz_jm, cz = hy - hy_km;
+    if (zy >= 0) {
+      T* p = a.psiE[0] + zy_off(a, i, k, zy);
+      cy = stretch<false>(ty, a.nmax, j, cy, p, p);
+    }
+    if (zz >= 0) {
+      T* p = a.psiE[1] + zz_off(a, i, j, zz);
+      cz = stretch<false>(tz, a.nmax, k, cz, p, p);
+    }
+    ex = e_update(a.m, mb & 3, ex, cy - cz, a.Jx + c);
+    if (a.tfsf && i >= a.i0 && i <= a.i1 - 1 && j >= a.j0 && j <= a.j1) {
+      if (k == a.k0) ex = fma(a.S, hinc<RO>(a, a.k0 - 1 + a.inc_off), ex);
+      if (k == a.k1) ex = fma(-a.S, hinc<RO>(a, a.k1 + a.inc_off), ex);
+    }
+  }
+  if (k == a.sheet_k) ex = ex + srcv;  // the sheet covers the whole plane, walls included
+  a.oEx[c] = ex;
+  if ((a.per || j < ny - 1) && xin && zin) {
+    T cz = hx - hx_km, cx = hz - hz_im;
+    if (zz >= 0) {
+      T* p = a.psiE[2] + zz_off(a, i, j, zz);
+      cz = stretch<false>(tz, a.nmax, k, cz, p, p);
+    }
+    if (zx >= 0) {
+      T* p = a.psiE[3] + zx_off(a, j, k, zx);
+      cx = stretch<false>(tx, a.nmax, i, cx, p, p);
+    }
+    ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + c);
+  }
+  a.oEy[c] = ey;
+  if (k < nz - 1 && xin && yin) {
+    T cx = hy - hy_im, cy = hx - hx_jm;
+    if (zx >= 0) {
+      T* p = a.psiE[4] + zx_off(a, j, k, zx);
+      cx = stretch<false>(tx, a.nmax, i, cx, p, p);
+    }
+    if (zy >= 0) {
+      T* p = a.psiE[5] + zy_off(a, i, k, zy);
+      cy = stretch<false>(ty, a.nmax, j, cy, p, p);
+    }
+    ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + c);
+    if (a.tfsf && j >= a.j0 && j <= a.j1 && (i == a.i0 || i == a.i1) && k >= a.k0 && k <= a.k1 - 1)
+      ez = fma(i == a.i0 ? -a.S : a.S, hinc<RO>(a, k + a.inc_off), ez);
+  }
+  a.oEz[c] = ez;
+  return ex;
+}
+
+// probes of one (i, j) column inside [k_lo, k_hi): up to 4, as (k, probe index)
+template <typename T>
+__device__ __forceinline__ int column_probes(const Args3<T>& a, int i, int j, int k_lo, int k_hi, int* pk, int* ps) {
+  int n = 0;
+  for (int p = 0; p < a.n_probes && n < 4; ++p)
+    if (a.probes[3 * p] == i && a.probes[3 * p + 1] == j && a.probes[3 * p + 2] >= k_lo && a.probes[3 * p + 2] < k_hi) {
+      pk[n] = a.probes[3 * p + 2];
+      ps[n] = p;
+      ++n;
+    }
+  return n;
+}
+
+// ---------------------------------------------------------------------------------------
+// plain form: H kernel, then E+J kernel (in place); block z-slices cover k in chunks of a.kc
+// and, with TF/SF, one extra slice advances the incident line.
+template <typename T>
+__global__ void __launch_bounds__(256) k3_h(const Args3<T> a) {
+  const int nzc = (a.nz + a.kc - 1) / a.kc;
+  if ((int)blockIdx.z >= nzc) {  // incident line: H~ -= S (E_{m+1} - E_m)
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+    for (int m = threadIdx.y * blockDim.x + threadIdx.x; m < a.inc_len - 1; m += blockDim.x * blockDim.y)
+      a.oHi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
+    return;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= a.nx || j >= a.ny) return;
+  const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  for (int k = kb; k < ke; ++k) {
+    const int64_t c = idx3(i, j, k, a.nx, a.ny);
+    const T hx = hx_new<false>(a, i, j, k, true);
+    const T hy = hy_new<false>(a, i, j, k, true);
+    const T hz = hz_new<false>(a, i, j, k, true);
+    a.oHx[c] = hx;
+    a.oHy[c] = hy;
+    a.oHz[c] = hz;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k3_e(const Args3<T> a) {
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int nx = a.nx, ny = a.ny;
   const double t = (double)(a.n0 + 1) * a.dt;
-  if (blockIdx.z == 1) {  // 1D incident line: E update, soft source, first-order Mur ends
-    if (blockIdx.x != 0 || blockIdx.y != 0 || !a.tfsf) return;
+  const int nzc = (a.nz + a.kc - 1) / a.kc;
+  if ((int)blockIdx.z >= nzc) {  // incident line: E update, soft source, first-order Mur ends
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
     __shared__ T ends[4];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y, L = a.inc_len;
     if (tid == 0) {
@@ -188,12 +379,12 @@ __global__ void __launch_bounds__(256) k3_e(const Args3<T> a) {
       ends[3] = a.Ei[L - 1];
     }
     __syncthreads();
-    for (int m = 1 + tid; m < L - 1; m += nt) a.Ei[m] = fma(-a.S, a.Hi[m] - a.Hi[m - 1], a.Ei[m]);
+    for (int m = 1 + tid; m < L - 1; m += nt) a.oEi[m] = fma(-a.S, a.Hi[m] - a.Hi[m - 1], a.Ei[m]);
     __syncthreads();
     if (tid == 0) {
-      a.Ei[a.inc_src] = a.Ei[a.inc_src] + (T)pulse3(t, a.t0, a.tau, a.amp);
-      a.Ei[0] = fma(a.q, a.Ei[1] - ends[0], ends[1]);
-      a.Ei[L - 1] = fma(a.q, a.Ei[L - 2] - ends[3], ends[2]);
+      a.oEi[a.inc_src] = a.oEi[a.inc_src] + (T)pulse3(t, a.t0, a.tau, a.amp);
+      a.oEi[0] = fma(a.q, a.oEi[1] - ends[0], ends[1]);
+      a.oEi[L - 1] = fma(a.q, a.oEi[L - 2] - ends[3], ends[2]);
     }
     return;
   }
@@ -202,75 +393,570 @@ __global__ void __launch_bounds__(256) k3_e(const Args3<T> a) {
   if (i >= nx || j >= ny) return;
   const int im = (i > 0) ? i - 1 : (a.per ? nx - 1 : -1);
   const int jm = (j > 0) ? j - 1 : (a.per ? ny - 1 : -1);
-  const bool xin = a.per || (i > 0 && i < nx - 1);
-  const bool yin = a.per || (j > 0 && j < ny - 1);
-  const bool ex_x = a.per || i < nx - 1;
-  const bool ey_y = a.per || j < ny - 1;
-  const T* tx = tb(a, 0, 0);
-  const T* ty = tb(a, 1, 0);
-  const T* tz = tb(a, 2, 0);
-  const int zx = zone(i, nx, a.per ? 0 : a.np), zy = zone(j, ny, a.per ? 0 : a.np);
-  const bool tf_ex = a.tfsf && i >= a.i0 && i <= a.i1 - 1 && j >= a.j0 && j <= a.j1;
-  const bool tf_ez = a.tfsf && j >= a.j0 && j <= a.j1 && (i == a.i0 || i == a.i1);
   const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
-  // probes in this column
-  int pk[4], ps[4], npc = 0;
-  for (int p = 0; p < a.n_probes && npc < 4; ++p)
-    if (a.probes[3 * p] == i && a.probes[3 * p + 1] == j) {
-      pk[npc] = a.probes[3 * p + 2];
-      ps[npc] = p;
-      ++npc;
-    }
+  const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  int pk[4], ps[4];
+  const int npc = column_probes(a, i, j, kb, ke, pk, ps);
   T hx_km = T(0), hy_km = T(0);
-  for (int k = 0; k < nz; ++k) {
+  if (kb > 0) {
+    hx_km = a.Hx[idx3(i, j, kb - 1, nx, ny)];
+    hy_km = a.Hy[idx3(i, j, kb - 1, nx, ny)];
+  }
+  for (int k = kb; k < ke; ++k) {
     const int64_t c = idx3(i, j, k, nx, ny);
-    const bool zin = k > 0 && k < nz - 1;
     const T hx = a.Hx[c], hy = a.Hy[c], hz = a.Hz[c];
-    const int mb = a.mat[c];
-    const int zz = zone(k, nz, a.np);
-    T ex_out = T(0);
-    bool ex_written = false;
-    if (ex_x && yin && zin) {  // Ex
-      T cy = hz - a.Hz[idx3(i, jm, k, nx, ny)];
-      T cz = hy - hy_km;
-      if (zy >= 0) cy = stretch(ty, a.nmax, j, cy, &a.psi[0][((int64_t)k * a.Z + zy) * nx + i]);
-      if (zz >= 0) cz = stretch(tz, a.nmax, k, cz, &a.psi[1][((int64_t)zz * ny + j) * nx + i]);
-      T e = e_update(a.m, mb & 3, a.Ex[c], cy - cz, &a.Jx[c]);
-      if (tf_ex) {
-        if (k == a.k0) e = fma(a.S, a.Hi[a.k0 - 1 + a.inc_off], e);
-        if (k == a.k1) e = fma(-a.S, a.Hi[a.k1 + a.inc_off], e);
-      }
-      if (k == a.sheet_k) e = e + srcv;
-      a.Ex[c] = e;
-      ex_out = e;
-      ex_written = true;
-    } else if (k == a.sheet_k) {  // the sheet covers the whole plane, walls included
-      ex_out = a.Ex[c] + srcv;
-      a.Ex[c] = ex_out;
-      ex_written = true;
+    T hx_jm = T(0), hz_jm = T(0), hy_im = T(0), hz_im = T(0);
+    if (jm >= 0) {
+      hx_jm = a.Hx[idx3(i, jm, k, nx, ny)];
+      hz_jm = a.Hz[idx3(i, jm, k, nx, ny)];
     }
-    if (ey_y && xin && zin) {  // Ey
-      T cz = hx - hx_km;
-      T cx = hz - a.Hz[idx3(im, j, k, nx, ny)];
-      if (zz >= 0) cz = stretch(tz, a.nmax, k, cz, &a.psi[2][((int64_t)zz * ny + j) * nx + i]);
-      if (zx >= 0) cx = stretch(tx, a.nmax, i, cx, &a.psi[3][((int64_t)k * ny + j) * a.Z + zx]);
-      a.Ey[c] = e_update(a.m, (mb >> 2) & 3, a.Ey[c], cz - cx, &a.Jy[c]);
+    if (im >= 0) {
+      hy_im = a.Hy[idx3(im, j, k, nx, ny)];
+      hz_im = a.Hz[idx3(im, j, k, nx, ny)];
     }
-    if (k < nz - 1 && xin && yin) {  // Ez
-      T cx = hy - a.Hy[idx3(im, j, k, nx, ny)];
-      T cy = hx - a.Hx[idx3(i, jm, k, nx, ny)];
-      if (zx >= 0) cx = stretch(tx, a.nmax, i, cx, &a.psi[4][((int64_t)k * ny + j) * a.Z + zx]);
-      if (zy >= 0) cy = stretch(ty, a.nmax, j, cy, &a.psi[5][((int64_t)k * a.Z + zy) * nx + i]);
-      T e = e_update(a.m, (mb >> 4) & 3, a.Ez[c], cx - cy, &a.Jz[c]);
-      if (tf_ez && k >= a.k0 && k <= a.k1 - 1)
-        e = fma(i == a.i0 ? -a.S : a.S, a.Hi[k + a.inc_off], e);
-      a.Ez[c] = e;
-    }
+    const T ex = e_cell<false>(a, i, j, k, a.Ex[c], a.Ey[c], a.Ez[c], a.mat[c], hx, hy, hz, hx_jm, hz_jm, hy_im,
+                               hz_im, hx_km, hy_km, srcv);
     for (int q = 0; q < npc; ++q)
-      if (pk[q] == k)
-        a.series[(int64_t)ps[q] * a.series_len + a.series_pos] = ex_written ? ex_out : a.Ex[c];
+      if (pk[q] == k) a.series[(int64_t)ps[q] * a.series_len + a.series_pos] = ex;
     hx_km = hx;
     hy_km = hy;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// fused form: one kernel per step, step-n state in, step-n+1 state out. blockDim.x = 32.
+template <typename T>
+__global__ void __launch_bounds__(256) k3_fused(const Args3<T> a) {
+  const int nx = a.nx, ny = a.ny;
+  const double t = (double)(a.n0 + 1) * a.dt;
+  const int nzc = (a.nz + a.kc - 1) / a.kc;
+  if ((int)blockIdx.z >= nzc) {  // incident line, step n -> n+1 (H, then E, source, Mur ends)
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y, L = a.inc_len;
+    for (int m = tid; m < L - 1; m += nt) a.oHi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
+    if (tid == 0) a.oHi[L - 1] = a.Hi[L - 1];
+    __syncthreads();
+    for (int m = 1 + tid; m < L - 1; m += nt) a.oEi[m] = fma(-a.S, a.oHi[m] - a.oHi[m - 1], a.Ei[m]);
+    __syncthreads();
+    if (tid == 0) {
+      a.oEi[a.inc_src] = a.oEi[a.inc_src] + (T)pulse3(t, a.t0, a.tau, a.amp);
+      a.oEi[0] = fma(a.q, a.oEi[1] - a.Ei[0], a.Ei[1]);
+      a.oEi[L - 1] = fma(a.q, a.oEi[L - 2] - a.Ei[L - 1], a.Ei[L - 2]);
+    }
+    return;
+  }
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (j >= ny) return;  // whole warp
+  const bool act = i < nx;
+  const int im = (i > 0) ? i - 1 : (a.per ? nx - 1 : -1);
+  const int jm = (j > 0) ? j - 1 : (a.per ? ny - 1 : -1);
+  const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
+  const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  int pk[4], ps[4];
+  const int npc = act ? column_probes(a, i, j, kb, ke, pk, ps) : 0;
+  T hx_km = T(0), hy_km = T(0);
+  if (act && kb > 0) {
+    hx_km = hx_new<true>(a, i, j, kb - 1, false);
+    hy_km = hy_new<true>(a, i, j, kb - 1, false);
+  }
+  for (int k = kb; k < ke; ++k) {
+    T hx = T(0), hy = T(0), hz = T(0);
+    if (act) {
+      const int64_t c = idx3(i, j, k, nx, ny);
+      hx = hx_new<true>(a, i, j, k, true);
+      hy = hy_new<true>(a, i, j, k, true);
+      hz = hz_new<true>(a, i, j, k, true);
+      a.oHx[c] = hx;
+      a.oHy[c] = hy;
+      a.oHz[c] = hz;
+    }
+    T hy_im = __shfl_up_sync(kFull, hy, 1);
+    T hz_im = __shfl_up_sync(kFull, hz, 1);
+    if (!act) continue;
+    if (lane == 0 && im >= 0) {
+      hy_im = hy_new<true>(a, im, j, k, false);
+      hz_im = hz_new<true>(a, im, j, k, false);
+    }
+    T hx_jm = T(0), hz_jm = T(0);
+    if (jm >= 0) {
+      hx_jm = hx_new<true>(a, i, jm, k, false);
+      hz_jm = hz_new<true>(a, i, jm, k, false);
+    }
+    const int64_t c = idx3(i, j, k, nx, ny);
+    const T ex = e_cell<true>(a, i, j, k, __ldg(a.Ex + c), __ldg(a.Ey + c), __ldg(a.Ez + c), __ldg(a.mat + c), hx, hy,
+                              hz, hx_jm, hz_jm, hy_im, hz_im, hx_km, hy_km, srcv);
+    for (int q = 0; q < npc; ++q)
+      if (pk[q] == k) a.series[(int64_t)ps[q] * a.series_len + a.series_pos] = ex;
+    hx_km = hx;
+    hy_km = hy;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// staged form: the fused step with the step-n E, H and material planes brought into shared
+// memory by the tensor memory accelerator, kStages planes ahead, one mbarrier per stage.
+// Block = kTY compute warps (warp w owns row j0 + w, lane l owns column i0 + l) plus one
+// halo warp that issues the copies and computes the new H of the j0-1 row (Hx, Hz) and of
+// the i0-1 column (Hy, Hz) that the E update needs. Box of each E/H plane: x in
+// [i0-4, i0+36) (16-byte aligned start), y in [j0-1, j0+kTY+1); out-of-grid parts read 0.
+// Non-periodic grids with nx a multiple of 16.
+constexpr int kTY = 8;
+constexpr int kStages = 4;
+constexpr int kBW = 40;
+constexpr int kBH = kTY + 2;
+constexpr int kHW = 33;  // new-H tile row: i0-1 .. i0+31
+constexpr int kHH = kTY + 1;
+constexpr int kWaitLimit = 1 << 20;
+
+template <typename T>
+struct Stage3 {
+  static constexpr int box = ((kBW * kBH * (int)sizeof(T) + 127) / 128) * 128 / (int)sizeof(T);  // padded to 128 B
+  static constexpr int mat_bytes = 32 * kTY;
+  static constexpr int bytes = 6 * box * (int)sizeof(T) + mat_bytes;  // one plane of Ex..Hz + material
+  static constexpr int tx = 6 * kBW * kBH * (int)sizeof(T) + mat_bytes;  // bytes the copies deliver
+  static constexpr int hn = ((kHW * kHH + 31) / 32) * 32;
+  static constexpr int smem = kStages * bytes + 2 * 3 * hn * (int)sizeof(T) + kStages * 8;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity; false if it did not complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Per-column and per-plane facts of the general path of the staged form, worked out once
+// (per thread, per plane) instead of per update; the updates below then do exactly the
+// operations of hx_core .. e_cell for non-periodic grids.
+struct Col3 {
+  bool vi, vj;          // i+1 < nx, j+1 < ny
+  bool fxH, fyH;        // CPML memory active at x = i+1/2, y = j+1/2 (H positions)
+  bool fxE, fyE;        // CPML memory active at x = i, y = j (E positions)
+  bool ex_xy, ey_xy, ez_xy;  // E component updated, as far as x and y decide
+  bool tf_xy;           // i in [i0, i1-1] and j in [j0, j1] (TF/SF Hy and Ex faces)
+  bool tf_hz_i;         // i in [i0, i1-1]
+  int sg_hz;            // -1 at j = j0-1, +1 at j = j1, else 0 (Hz faces)
+  int sg_ez;            // -1 at i = i0, +1 at i = i1 when j in [j0, j1], else 0 (Ez faces)
+  int zx, zy;           // compact zone indices (valid where a flag is set)
+};
+
+template <typename T>
+__device__ __forceinline__ Col3 col3(const Args3<T>& a, int i, int j) {
+  Col3 c;
+  const int nx = a.nx, ny = a.ny;
+  c.vi = i + 1 < nx;
+  c.vj = j + 1 < ny;
+  c.zx = zone(i, nx, a.np);
+  c.zy = zone(j, ny, a.np);
+  const T* txH = tb(a, 0, 1);
+  const T* tyH = tb(a, 1, 1);
+  const T* txE = tb(a, 0, 0);
+  const T* tyE = tb(a, 1, 0);
+  c.fxH = c.zx >= 0 && txH[3 * a.nmax + i] != T(0);
+  c.fyH = c.zy >= 0 && tyH[3 * a.nmax + j] != T(0);
+  c.fxE = c.zx >= 0 && txE[3 * a.nmax + i] != T(0);
+  c.fyE = c.zy >= 0 && tyE[3 * a.nmax + j] != T(0);
+  const bool xin = i > 0 && i < nx - 1, yin = j > 0 && j < ny - 1;
+  c.ex_xy = i < nx - 1 && yin;
+  c.ey_xy = j < ny - 1 && xin;
+  c.ez_xy = xin && yin;
+  const bool ti = a.tfsf && i >= a.i0 && i <= a.i1 - 1;
+  c.tf_xy = ti && j >= a.j0 && j <= a.j1;
+  c.tf_hz_i = ti;
+  c.sg_hz = (j == a.j0 - 1) ? -1 : (j == a.j1 ? 1 : 0);
+  c.sg_ez = (a.tfsf && j >= a.j0 && j <= a.j1) ? (i == a.i0 ? -1 : (i == a.i1 ? 1 : 0)) : 0;
+  return c;
+}
+
+template <typename T>
+struct Plane3 {
+  bool vk, zin, zlast;  // z+1 < nz, 0 < z < nz-1, z < nz-1
+  bool fzH, fzE;        // CPML memory active at z+1/2 and at z
+  int zz;
+  int sg_hy;            // +1 at z = k0-1, -1 at z = k1 (Hy faces)
+  bool tf_hz;           // z in [k0, k1]
+  int sg_ex;            // +1 at z = k0, -1 at z = k1 (Ex faces)
+  bool tf_ez;           // z in [k0, k1-1]
+  T ei_hy, ei_hz;       // step-n incident E used by the Hy and Hz corrections of this plane
+  T hi_ex, hi_ez;       // step-n+1/2 incident H used by the Ex and Ez corrections
+  bool sheet;
+};
+
+template <typename T>
+__device__ __forceinline__ Plane3<T> plane3(const Args3<T>& a, int z) {
+  Plane3<T> p;
+  p.vk = z + 1 < a.nz;
+  p.zin = z > 0 && z < a.nz - 1;
+  p.zlast = z < a.nz - 1;
+  p.zz = zone(z, a.nz, a.np);
+  p.fzH = p.zz >= 0 && tb(a, 2, 1)[3 * a.nmax + z] != T(0);
+  p.fzE = p.zz >= 0 && tb(a, 2, 0)[3 * a.nmax + z] != T(0);
+  p.sg_hy = 0;
+  p.tf_hz = p.tf_ez = false;
+  p.sg_ex = 0;
+  p.ei_hy = p.ei_hz = p.hi_ex = p.hi_ez = T(0);
+  if (a.tfsf) {
+    if (z == a.k0 - 1) {
+      p.sg_hy = 1;
+      p.ei_hy = __ldg(a.Ei + a.k0 + a.inc_off);
+    } else if (z == a.k1) {
+      p.sg_hy = -1;
+      p.ei_hy = __ldg(a.Ei + a.k1 + a.inc_off);
+    }
+    p.tf_hz = z >= a.k0 && z <= a.k1;
+    if (p.tf_hz) p.ei_hz = __ldg(a.Ei + z + a.inc_off);
+    if (z == a.k0) {
+      p.sg_ex = 1;
+      p.hi_ex = hinc<true>(a, a.k0 - 1 + a.inc_off);
+    } else if (z == a.k1) {
+      p.sg_ex = -1;
+      p.hi_ex = hinc<true>(a, a.k1 + a.inc_off);
+    }
+    p.tf_ez = z >= a.k0 && z <= a.k1 - 1;
+    if (p.tf_ez) p.hi_ez = hinc<true>(a, z + a.inc_off);
+  }
+  p.sheet = z == a.sheet_k;
+  return p;
+}
+
+// CPML stretch where the memory is known to be active (stretch() without the flag test)
+template <typename T>
+__device__ __forceinline__ T stretch_on(const T* t, int nmax, int pos, T dv, const T* pin, T* pout) {
+  const T p = fma(t[pos], __ldg(pin), t[nmax + pos] * dv);
+  if (pout) *pout = p;
+  return fma(dv, t[2 * nmax + pos], p);
+}
+
+template <typename T>
+__device__ __forceinline__ T hx_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
+                                    T ez_jp, T ez, T ey_kp, T ey, bool own) {
+  if (!c.vj || !pl.vk) return h;
+  T cy = ez_jp - ez;
+  T cz = ey_kp - ey;
+  if (c.fyH) {
+    const int64_t o = zy_off(a, i, k, c.zy);
+    cy = stretch_on(tb(a, 1, 1), a.nmax, j, cy, a.psiH[0] + o, own ? a.opsiH[0] + o : nullptr);
+  }
+  if (pl.fzH) {
+    const int64_t o = zz_off(a, i, j, pl.zz);
+    cz = stretch_on(tb(a, 2, 1), a.nmax, k, cz, a.psiH[1] + o, own ? a.opsiH[1] + o : nullptr);
+  }
+  return fma(-a.S, cy - cz, h);
+}
+
+template <typename T>
+__device__ __forceinline__ T hy_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
+                                    T ex_kp, T ex, T ez_ip, T ez, bool own) {
+  if (!c.vi || !pl.vk) return h;
+  T cz = ex_kp - ex;
+  T cx = ez_ip - ez;
+  if (pl.fzH) {
+    const int64_t o = zz_off(a, i, j, pl.zz);
+    cz = stretch_on(tb(a, 2, 1), a.nmax, k, cz, a.psiH[2] + o, own ? a.opsiH[2] + o : nullptr);
+  }
+  if (c.fxH) {
+    const int64_t o = zx_off(a, j, k, c.zx);
+    cx = stretch_on(tb(a, 0, 1), a.nmax, i, cx, a.psiH[3] + o, own ? a.opsiH[3] + o : nullptr);
+  }
+  T v = fma(-a.S, cz - cx, h);
+  if (c.tf_xy && pl.sg_hy) v = fma(pl.sg_hy > 0 ? a.S : -a.S, pl.ei_hy, v);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T hz_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
+                                    T ey_ip, T ey, T ex_jp, T ex, bool own) {
+  if (!c.vi || !c.vj) return h;
+  T cx = ey_ip - ey;
+  T cy = ex_jp - ex;
+  if (c.fxH) {
+    const int64_t o = zx_off(a, j, k, c.zx);
+    cx = stretch_on(tb(a, 0, 1), a.nmax, i, cx, a.psiH[4] + o, own ? a.opsiH[4] + o : nullptr);
+  }
+  if (c.fyH) {
+    const int64_t o = zy_off(a, i, k, c.zy);
+    cy = stretch_on(tb(a, 1, 1), a.nmax, j, cy, a.psiH[5] + o, own ? a.opsiH[5] + o : nullptr);
+  }
+  T v = fma(-a.S, cx - cy, h);
+  if (c.tf_hz_i && c.sg_hz && pl.tf_hz) v = fma(c.sg_hz > 0 ? a.S : -a.S, pl.ei_hz, v);
+  return v;
+}
+
+// E and J of one cell (the operations of e_cell, for non-periodic grids); returns the new Ex
+template <typename T>
+__device__ __forceinline__ T e_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k,
+                                   int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy, T hz, T hx_jm, T hz_jm, T hy_im,
+                                   T hz_im, T hx_km, T hy_km, T srcv) {
+  if (c.ex_xy && pl.zin) {
+    T cy = hz - hz_jm, cz = hy - hy_km;
+    if (c.fyE) {
+      T* p = a.psiE[0] + zy_off(a, i, k, c.zy);
+      cy = stretch<false>(tb(a, 1, 0), a.nmax, j, cy, p, p);
+    }
+    if (pl.fzE) {
+      T* p = a.psiE[1] + zz_off(a, i, j, pl.zz);
+      cz = stretch<false>(tb(a, 2, 0), a.nmax, k, cz, p, p);
+    }
+    ex = e_update(a.m, mb & 3, ex, cy - cz, a.Jx + ci);
+    if (c.tf_xy && pl.sg_ex) ex = fma(pl.sg_ex > 0 ? a.S : -a.S, pl.hi_ex, ex);
+  }
+  if (pl.sheet) ex = ex + srcv;
+  a.oEx[ci] = ex;
+  if (c.ey_xy && pl.zin) {
+    T cz = hx - hx_km, cx = hz - hz_im;
+    if (pl.fzE) {
+      T* p = a.psiE[2] + zz_off(a, i, j, pl.zz);
+      cz = stretch<false>(tb(a, 2, 0), a.nmax, k, cz, p, p);
+    }
+    if (c.fxE) {
+      T* p = a.psiE[3] + zx_off(a, j, k, c.zx);
+      cx = stretch<false>(tb(a, 0, 0), a.nmax, i, cx, p, p);
+    }
+    ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + ci);
+  }
+  a.oEy[ci] = ey;
+  if (pl.zlast && c.ez_xy) {
+    T cx = hy - hy_im, cy = hx - hx_jm;
+    if (c.fxE) {
+      T* p = a.psiE[4] + zx_off(a, j, k, c.zx);
+      cx = stretch<false>(tb(a, 0, 0), a.nmax, i, cx, p, p);
+    }
+    if (c.fyE) {
+      T* p = a.psiE[5] + zy_off(a, i, k, c.zy);
+      cy = stretch<false>(tb(a, 1, 0), a.nmax, j, cy, p, p);
+    }
+    ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + ci);
+    if (c.sg_ez && pl.tf_ez) ez = fma(c.sg_ez < 0 ? -a.S : a.S, pl.hi_ez, ez);
+  }
+  a.oEz[ci] = ez;
+  return ex;
+}
+
+template <typename T>
+struct Maps3 {
+  CUtensorMap f[6];  // Ex, Ey, Ez, Hx, Hy, Hz of the step-n set
+  CUtensorMap mat;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp,
+                                                            int* err) {
+  using St = Stage3<T>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  const int nx = a.nx, ny = a.ny;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = w * 32 + lane, nt = 32 * (kTY + 1);
+  const double t = (double)(a.n0 + 1) * a.dt;
+  const int nzc = (a.nz + a.kc - 1) / a.kc;
+  if ((int)blockIdx.z >= nzc) {  // incident line, step n -> n+1 (as the fused form)
+    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+    const int L = a.inc_len;
+    for (int m = tid; m < L - 1; m += nt) a.oHi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
+    if (tid == 0) a.oHi[L - 1] = a.Hi[L - 1];
+    __syncthreads();
+    for (int m = 1 + tid; m < L - 1; m += nt) a.oEi[m] = fma(-a.S, a.oHi[m] - a.oHi[m - 1], a.Ei[m]);
+    __syncthreads();
+    if (tid == 0) {
+      a.oEi[a.inc_src] = a.oEi[a.inc_src] + (T)pulse3(t, a.t0, a.tau, a.amp);
+      a.oEi[0] = fma(a.q, a.oEi[1] - a.Ei[0], a.Ei[1]);
+      a.oEi[L - 1] = fma(a.q, a.oEi[L - 2] - a.Ei[L - 1], a.Ei[L - 2]);
+    }
+    return;
+  }
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kTY;
+  const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  const int NP = ke - kb + 2;  // planes kb-1 .. ke
+  T* hn = (T*)(sm + kStages * St::bytes);
+  uint64_t* bar = (uint64_t*)(sm + kStages * St::bytes + 2 * 3 * St::hn * sizeof(T));
+  auto plane = [&](int q) { return (const T*)(sm + (q % kStages) * St::bytes); };
+  const bool producer = (w == kTY && lane == 0);
+  auto issue = [&](int q) {
+    const int s = q % kStages;
+    unsigned char* dst = sm + s * St::bytes;
+    const int z = kb - 1 + q;
+    mbar_expect_tx(&bar[s], St::tx);
+    for (int f = 0; f < 6; ++f) tma_load3(dst + f * St::box * sizeof(T), &mp.f[f], i0 - 4, j0 - 1, z, &bar[s]);
+    tma_load3(dst + 6 * St::box * sizeof(T), &mp.mat, i0, j0, z, &bar[s]);
+  };
+  if (producer) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int issued = 0;  // planes whose copies the producer has issued
+  if (producer)
+    for (; issued < kStages && issued < NP; ++issued) issue(issued);
+  const int i = i0 + lane, j = j0 + w;
+  const bool act = w < kTY && i < nx && j < ny;
+  const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
+  int pk[4], ps[4];
+  const int npc = act ? column_probes(a, i, j, kb, ke, pk, ps) : 0;
+  constexpr int EX = 0, EY = St::box, EZ = 2 * St::box, HX = 3 * St::box, HY = 4 * St::box, HZ = 5 * St::box;
+  // Lean planes: where the whole tile with its halo is clear of the CPML, of the TF/SF faces
+  // and of the sheet, each update is the bare Eq. 14 / Eq. 13 / Eq. 11 arithmetic (the same
+  // operations the general path does there). Decided per block and plane, so uniformly.
+  const int np = a.np;
+  bool xy_lean = i0 - 1 >= np + 1 && i0 + 31 <= nx - np - 2 && j0 - 1 >= np + 1 && j0 + kTY - 1 <= ny - np - 2;
+  if (a.tfsf) {
+    if ((a.j0 - 1 >= j0 - 1 && a.j0 - 1 <= j0 + kTY - 1) || (a.j1 >= j0 - 1 && a.j1 <= j0 + kTY - 1)) xy_lean = false;
+    if ((a.i0 >= i0 && a.i0 <= i0 + 31) || (a.i1 >= i0 && a.i1 <= i0 + 31)) xy_lean = false;
+  }
+  const int64_t nxy = (int64_t)nx * ny;
+  const int64_t c0 = (int64_t)j * nx + i;
+  // column facts: compute warps for their own (i, j); the halo warp for its j0-1 row cell
+  // (cc) and, lanes < kTY, its i0-1 column cell (cc2)
+  const int ci_ = w < kTY ? min(i, nx - 1) : min(i0 + lane, nx - 1);
+  const int cj_ = w < kTY ? min(j, ny - 1) : max(j0 - 1, 0);
+  const Col3 cc = col3(a, ci_, cj_);
+  const Col3 cc2 = col3(a, max(i0 - 1, 0), min(j0 + (lane < kTY ? lane : 0), ny - 1));
+  T hx_km = T(0), hy_km = T(0);
+  bool fail = false, bad = false;  // fail: this thread's wait gave up; bad: some thread's did
+  for (int q = 0; q + 1 < NP; ++q) {
+    const int z = kb - 1 + q;
+    if (q == 0) fail |= !mbar_wait(&bar[0], 0);
+    fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1);
+    const T* P0 = plane(q);
+    const T* P1 = plane(q + 1);
+    T* H0 = hn + (q & 1) * 3 * St::hn;  // new Hx, Hy, Hz of plane z on the [i0-1, i0+32) x [j0-1, j0+kTY) tile
+    T hx = T(0), hy = T(0), hz = T(0);
+    const bool lean = xy_lean && z >= np + 1 && z <= a.nz - np - 2 && z != a.sheet_k &&
+                      !(a.tfsf && (z == a.k0 - 1 || z == a.k0 || z == a.k1));
+    if (lean && !fail) {
+      if (act) {
+        const int o = (w + 1) * kBW + lane + 4;
+        hx = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
+        hy = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
+        hz = fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
+        if (q > 0) {
+          const int64_t c = c0 + (int64_t)z * nxy;
+          a.oHx[c] = hx;
+          a.oHy[c] = hy;
+          a.oHz[c] = hz;
+          const int h = (w + 1) * kHW + lane + 1;
+          H0[h] = hx;
+          H0[St::hn + h] = hy;
+          H0[2 * St::hn + h] = hz;
+        }
+      } else if (w == kTY && q > 0) {
+        int o = lane + 4;  // row j0-1: Hx, Hz
+        H0[lane + 1] = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
+        H0[2 * St::hn + lane + 1] =
+            fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
+        if (lane < kTY) {  // column i0-1: Hy, Hz
+          o = (lane + 1) * kBW + 3;
+          const int h = (lane + 1) * kHW;
+          H0[St::hn + h] = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
+          H0[2 * St::hn + h] =
+              fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
+        }
+      }
+    } else if (z >= 0 && !fail) {
+      const Plane3<T> pl = plane3(a, z);
+      if (act) {
+        const int o = (w + 1) * kBW + lane + 4;
+        const bool own = q > 0;
+        hx = hx_gen(a, cc, pl, i, j, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o], P0[EY + o], own);
+        hy = hy_gen(a, cc, pl, i, j, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1], P0[EZ + o], own);
+        hz = hz_gen(a, cc, pl, i, j, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o], P0[EX + o + kBW], P0[EX + o], own);
+        if (own) {
+          const int64_t c = c0 + (int64_t)z * nxy;
+          a.oHx[c] = hx;
+          a.oHy[c] = hy;
+          a.oHz[c] = hz;
+          const int h = (w + 1) * kHW + lane + 1;
+          H0[h] = hx;
+          H0[St::hn + h] = hy;
+          H0[2 * St::hn + h] = hz;
+        }
+      } else if (w == kTY && q > 0) {
+        const int ih = i0 + lane, jh = j0 - 1;  // row j0-1: Hx, Hz
+        if (jh >= 0 && ih < nx) {
+          const int o = lane + 4;
+          H0[lane + 1] = hx_gen(a, cc, pl, ih, jh, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o],
+                                P0[EY + o], false);
+          H0[2 * St::hn + lane + 1] = hz_gen(a, cc, pl, ih, jh, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o],
+                                             P0[EX + o + kBW], P0[EX + o], false);
+        }
+        const int jc = j0 + lane;  // column i0-1: Hy, Hz
+        if (lane < kTY && i0 > 0 && jc < ny) {
+          const int o = (lane + 1) * kBW + 3;
+          const int h = (lane + 1) * kHW;
+          H0[St::hn + h] = hy_gen(a, cc2, pl, i0 - 1, jc, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1],
+                                  P0[EZ + o], false);
+          H0[2 * St::hn + h] = hz_gen(a, cc2, pl, i0 - 1, jc, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o],
+                                      P0[EX + o + kBW], P0[EX + o], false);
+        }
+      }
+    }
+    if (__syncthreads_or(fail)) {
+      bad = true;
+      break;
+    }
+    // every thread is past plane q-1: its stage takes plane q-1+kStages
+    if (producer && q >= 1 && issued < NP) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued);
+      ++issued;
+    }
+    if (act && z >= 0 && q > 0) {
+      const int o = (w + 1) * kBW + lane + 4;
+      const int h = (w + 1) * kHW + lane + 1;
+      const unsigned char* mt = sm + (q % kStages) * St::bytes + 6 * St::box * sizeof(T);
+      const int mb = mt[w * 32 + lane];
+      T ex;
+      if (lean) {
+        const int64_t c = c0 + (int64_t)z * nxy;
+        const T hx_jm = H0[h - kHW], hz_jm = H0[2 * St::hn + h - kHW];
+        const T hy_im = H0[St::hn + h - 1], hz_im = H0[2 * St::hn + h - 1];
+        ex = e_update(a.m, mb & 3, P0[EX + o], (hz - hz_jm) - (hy - hy_km), a.Jx + c);
+        a.oEx[c] = ex;
+        a.oEy[c] = e_update(a.m, (mb >> 2) & 3, P0[EY + o], (hx - hx_km) - (hz - hz_im), a.Jy + c);
+        a.oEz[c] = e_update(a.m, (mb >> 4) & 3, P0[EZ + o], (hy - hy_im) - (hx - hx_jm), a.Jz + c);
+      } else {
+        const Plane3<T> pl = plane3(a, z);
+        ex = e_gen(a, cc, pl, i, j, z, c0 + (int64_t)z * nxy, P0[EX + o], P0[EY + o], P0[EZ + o], mb, hx, hy, hz,
+                   H0[h - kHW], H0[2 * St::hn + h - kHW], H0[St::hn + h - 1], H0[2 * St::hn + h - 1], hx_km, hy_km,
+                   srcv);
+      }
+      for (int r = 0; r < npc; ++r)
+        if (pk[r] == z) a.series[(int64_t)ps[r] * a.series_len + a.series_pos] = ex;
+    }
+    hx_km = hx;
+    hy_km = hy;
+  }
+  if (bad && producer) {
+    // report, and let the copies still in flight land before the block's memory is released
+    atomicExch(err, 1);
+    for (int q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
+      mbar_wait(&bar[q % kStages], (q / kStages) & 1);
   }
 }
 
@@ -327,22 +1013,32 @@ __global__ void k3_gather(const T* src, int64_t n, double scale, const T* cj, co
 
 using namespace rketd;
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 struct rketd_ctx3d {
   rketd_grid3d g{};
-  int prec = 0;
+  int prec = 0, fused = 1, staged = 0, cur = 0, kc = 16;
+  Maps3<float> maps32[2];
+  Maps3<double> maps64[2];
+  int* err = nullptr;
   size_t esz = 4;
   int64_t N = 0;
   double S = 0;
   cudaStream_t stream = nullptr;
   std::vector<void*> allocs;
-  void* f[9] = {};
+  std::vector<std::pair<void*, size_t>> zeroed;  // every state buffer, cleared by reset
+  void* E[2][3] = {};
+  void* H[2][3] = {};
+  void* J[3] = {};
   uint8_t* mat = nullptr;
   void* tab = nullptr;
   int nmax = 0, Z = 0;
-  void* psi[12] = {};
-  size_t psi_bytes[12] = {};
-  void* Ei = nullptr;
-  void* Hi = nullptr;
+  void* psiE[6] = {};
+  void* psiH[2][6] = {};
+  void* Ei[2] = {};
+  void* Hi[2] = {};
   int* probes = nullptr;
   int n_probes = 0, n_freq = 0;
   double* freq = nullptr;
@@ -350,7 +1046,7 @@ struct rketd_ctx3d {
   void* tw = nullptr;
   double *Xr = nullptr, *Xi = nullptr, *Xtmp = nullptr;
   int dft_block = 512;
-  double coef[6][kMat] = {};  // da, cb, cj, dj, bp(cj-scaled), cc(cj-scaled) per material
+  double coef[6][kMat] = {};  // da, cb, cj, dj, bp (cj-scaled), cc (cj-scaled) per material
   void* cj_d = nullptr;
   int n_mat = 1;
   rketd_pulse pulse{};
@@ -359,18 +1055,24 @@ struct rketd_ctx3d {
   ~rketd_ctx3d() {
     for (void* p : allocs) cudaFree(p);
   }
-  bool alloc(void** p, size_t bytes) {
+  bool alloc(void** p, size_t bytes, bool state = false) {
     *p = nullptr;
-    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    if (!bytes) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
     allocs.push_back(*p);
+    if (state) zeroed.push_back({*p, bytes});
     return true;
   }
 };
 
 namespace {
+
+// derivative axis of each CPML memory, E side then H side (Ex/y, Ex/z, Ey/z, Ey/x, Ez/x, Ez/y;
+// Hx/y, Hx/z, Hy/z, Hy/x, Hz/x, Hz/y)
+constexpr int kPsiAxis[6] = {1, 2, 2, 0, 0, 1};
 
 rketd_status fail3(rketd_status st, const std::string& m) {
   set_error_message(m.c_str());
@@ -388,8 +1090,22 @@ rketd_status fail3(rketd_status st, const std::string& m) {
 template <typename T>
 Args3<T> args3(rketd_ctx3d* c) {
   Args3<T> a{};
-  T** F[9] = {&a.Ex, &a.Ey, &a.Ez, &a.Hx, &a.Hy, &a.Hz, &a.Jx, &a.Jy, &a.Jz};
-  for (int q = 0; q < 9; ++q) *F[q] = (T*)c->f[q];
+  const int in = c->cur, out = c->fused ? 1 - c->cur : c->cur;
+  a.Ex = (const T*)c->E[in][0];
+  a.Ey = (const T*)c->E[in][1];
+  a.Ez = (const T*)c->E[in][2];
+  a.Hx = (const T*)c->H[in][0];
+  a.Hy = (const T*)c->H[in][1];
+  a.Hz = (const T*)c->H[in][2];
+  a.oEx = (T*)c->E[out][0];
+  a.oEy = (T*)c->E[out][1];
+  a.oEz = (T*)c->E[out][2];
+  a.oHx = (T*)c->H[out][0];
+  a.oHy = (T*)c->H[out][1];
+  a.oHz = (T*)c->H[out][2];
+  a.Jx = (T*)c->J[0];
+  a.Jy = (T*)c->J[1];
+  a.Jz = (T*)c->J[2];
   a.mat = c->mat;
   for (int m = 0; m < kMat; ++m) {
     a.m.da[m] = (T)c->coef[0][m];
@@ -402,13 +1118,18 @@ Args3<T> args3(rketd_ctx3d* c) {
   a.ny = c->g.ny;
   a.nz = c->g.nz;
   a.per = c->g.periodic_xy;
+  a.kc = c->kc;
   a.S = (T)c->S;
   a.q = (T)((c->S - 1.0) / (c->S + 1.0));
   a.tab = (const T*)c->tab;
   a.nmax = c->nmax;
   a.np = c->g.npml;
   a.Z = c->Z;
-  for (int q = 0; q < 12; ++q) a.psi[q] = (T*)c->psi[q];
+  for (int q = 0; q < 6; ++q) {
+    a.psiE[q] = (T*)c->psiE[q];
+    a.psiH[q] = (const T*)c->psiH[in][q];
+    a.opsiH[q] = (T*)c->psiH[out][q];
+  }
   a.tfsf = c->g.tfsf;
   a.i0 = c->g.box[0];
   a.i1 = c->g.box[1];
@@ -416,8 +1137,10 @@ Args3<T> args3(rketd_ctx3d* c) {
   a.j1 = c->g.box[3];
   a.k0 = c->g.box[4];
   a.k1 = c->g.box[5];
-  a.Ei = (T*)c->Ei;
-  a.Hi = (T*)c->Hi;
+  a.Ei = (const T*)c->Ei[in];
+  a.Hi = (const T*)c->Hi[in];
+  a.oEi = (T*)c->Ei[out];
+  a.oHi = (T*)c->Hi[out];
   a.inc_len = c->g.inc_len;
   a.inc_off = c->g.inc_off;
   a.inc_src = c->g.inc_src;
@@ -446,15 +1169,87 @@ rketd_status fold3(rketd_ctx3d* c, int n, int64_t m0, double* Xr, double* Xi) {
 }
 
 template <typename T>
+const Maps3<T>& maps(const rketd_ctx3d* c, int set);
+template <>
+const Maps3<float>& maps<float>(const rketd_ctx3d* c, int set) {
+  return c->maps32[set];
+}
+template <>
+const Maps3<double>& maps<double>(const rketd_ctx3d* c, int set) {
+  return c->maps64[set];
+}
+
+// tensor maps of the staged form: a 3D box of kBW x kBH x 1 values of each field array and
+// 32 x kTY x 1 bytes of the material array, zero fill outside the grid
+template <typename T>
+rketd_status make_maps(rketd_ctx3d* c) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail3(RKETD_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = (EncodeTiledFn)fn;
+  }
+  const rketd_grid3d& g = c->g;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t fstr[2] = {(cuuint64_t)g.nx * sizeof(T), (cuuint64_t)g.nx * g.ny * sizeof(T)};
+  const cuuint64_t mstr[2] = {(cuuint64_t)g.nx, (cuuint64_t)g.nx * g.ny};
+  const cuuint32_t fbox[3] = {kBW, kBH, 1}, mbox[3] = {32, kTY, 1}, es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int set = 0; set < 2; ++set) {
+    Maps3<T>& m = const_cast<Maps3<T>&>(maps<T>(c, set));
+    void* arrs[6] = {c->E[set][0], c->E[set][1], c->E[set][2], c->H[set][0], c->H[set][1], c->H[set][2]};
+    for (int f = 0; f < 6; ++f)
+      if (encode(&m.f[f], dt, 3, arrs[f], dims, fstr, fbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail3(RKETD_ECUDA, "field tensor map");
+    if (encode(&m.mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, mstr, mbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail3(RKETD_ECUDA, "material tensor map");
+  }
+  CK3(cudaFuncSetAttribute(k3_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
+  return RKETD_OK;
+}
+
+// device-side status of the staged form (a bounded wait that gave up); synchronises
+rketd_status check3(rketd_ctx3d* c) {
+  CK3(cudaStreamSynchronize(c->stream), "3D step");
+  int e = 0;
+  CK3(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost), "3D status");
+  if (e) return fail3(RKETD_ETIMEOUT, "a staged-copy wait gave up; fields are not valid");
+  return RKETD_OK;
+}
+
+template <typename T>
 rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
-  const dim3 block(32, 8);
-  const dim3 grid((c->g.nx + 31) / 32, (c->g.ny + 7) / 8, c->g.tfsf ? 2 : 1);
+  const int ty = 8;
+  const unsigned nzc = (unsigned)((c->g.nz + c->kc - 1) / c->kc);
+  const dim3 block(32, ty);
+  const dim3 grid((c->g.nx + 31) / 32, (c->g.ny + ty - 1) / ty, nzc + (c->g.tfsf ? 1 : 0));
+  const dim3 sblock(32, kTY + 1);
+  const dim3 sgrid((c->g.nx + 31) / 32, (c->g.ny + kTY - 1) / kTY, nzc + (c->g.tfsf ? 1 : 0));
   for (int64_t s = 0; s < nsteps; ++s) {
     Args3<T> a = args3<T>(c);
-    k3_h<T><<<grid, block, 0, c->stream>>>(a);
-    k3_e<T><<<grid, block, 0, c->stream>>>(a);
+    if (c->staged) {
+      k3_staged<T><<<sgrid, sblock, Stage3<T>::smem, c->stream>>>(a, maps<T>(c, c->cur), c->err);
+      c->launches += 1;
+      c->cur = 1 - c->cur;
+    } else if (c->fused) {
+      k3_fused<T><<<grid, block, 0, c->stream>>>(a);
+      c->launches += 1;
+      c->cur = 1 - c->cur;
+    } else {
+      a.line_fresh = 1;
+      k3_h<T><<<grid, block, 0, c->stream>>>(a);
+      k3_e<T><<<grid, block, 0, c->stream>>>(a);
+      c->launches += 2;
+    }
     CK3(cudaGetLastError(), "3D step");
-    c->launches += 2;
     c->step += 1;
     if (c->step % c->dft_block == 0) {
       rketd_status st = fold3<T>(c, c->dft_block, c->step - c->dft_block + 1, c->Xr, c->Xi);
@@ -476,9 +1271,15 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
   *out = nullptr;
   if (!g || !mat || !mat_wp2 || !mat_nu || !pulse) return fail3(RKETD_EINVAL, "NULL argument");
   if (g->nx < 4 || g->ny < 4 || g->nz < 4) return fail3(RKETD_EINVAL, "grid must be at least 4 cells per axis");
+  if ((int64_t)g->nx * g->ny > (int64_t)1 << 31) return fail3(RKETD_EINVAL, "nx * ny must fit in 32 bits");
   if (!(g->d > 0) || !(g->dt > 0) || !std::isfinite(g->d) || !std::isfinite(g->dt))
     return fail3(RKETD_EINVAL, "d and dt must be finite and > 0");
   if (g->prec != RKETD_F32 && g->prec != RKETD_F64) return fail3(RKETD_EINVAL, "prec must be F32 or F64");
+  if (g->variant < 0 || g->variant > 3)
+    return fail3(RKETD_EINVAL, "variant must be 0 (auto), 1 (plain), 2 (fused) or 3 (staged)");
+  const bool can_stage = !g->periodic_xy && g->nx % 16 == 0;
+  if (g->variant == 3 && !can_stage)
+    return fail3(RKETD_EUNSUPPORTED, "the staged form needs CPML on every face and nx a multiple of 16");
   const double S = g->dt / (g->d * std::sqrt(kMu0 * kEps0));
   if (!(S <= 1.0 / std::sqrt(3.0))) return fail3(RKETD_ECOURANT, "3D Courant number c dt/d exceeds 1/sqrt(3)");
   if (n_mat < 1 || n_mat > kMat) return fail3(RKETD_EINVAL, "n_mat must be 1..4 (entry 0 is vacuum)");
@@ -507,6 +1308,12 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
     if (probes[3 * p] < 0 || probes[3 * p] >= g->nx || probes[3 * p + 1] < 0 || probes[3 * p + 1] >= g->ny ||
         probes[3 * p + 2] < 0 || probes[3 * p + 2] >= g->nz)
       return fail3(RKETD_EINVAL, "probe outside the grid");
+  // at most 4 probes per (i, j) column are sampled by one thread
+  for (int p = 0; p < n_probes; ++p) {
+    int same = 0;
+    for (int q = 0; q < n_probes; ++q) same += probes[3 * q] == probes[3 * p] && probes[3 * q + 1] == probes[3 * p + 1];
+    if (same > 4) return fail3(RKETD_EINVAL, "at most 4 probes may share an (i, j) column");
+  }
   rketd_ctx3d* c = new (std::nothrow) rketd_ctx3d();
   if (!c) return fail3(RKETD_ENOMEM, "host allocation");
   auto bad = [&](rketd_status s, const char* m) {
@@ -516,6 +1323,8 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
   c->g = *g;
   if (!(c->g.pml_sigma_max > 0)) c->g.pml_sigma_max = 0.8 * (g->pml_m + 1) / (std::sqrt(kMu0 / kEps0) * g->d);
   c->prec = g->prec;
+  c->fused = g->variant != 1;
+  c->staged = g->variant == 3 || (g->variant == 0 && can_stage);
   c->esz = g->prec == RKETD_F64 ? 8 : 4;
   c->N = (int64_t)g->nx * g->ny * g->nz;
   c->S = S;
@@ -524,15 +1333,16 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
   c->n_mat = n_mat;
   c->n_probes = n_probes;
   c->n_freq = n_probes ? nf : 0;
-  // per-material coefficients (the 1D formulas, FP64 on the host for at most four entries,
-  // then used as kernel arguments)
+  // per-material coefficients of the update (FP64 on the host for at most four materials,
+  // passed to the kernels as arguments)
   for (int m = 0; m < kMat; ++m) {
     const double w = m < n_mat ? mat_wp2[m] * g->dt * g->dt : 0.0;
     const double x = m < n_mat ? mat_nu[m] * g->dt : 0.0;
-    // phi1, phi2 by their Taylor series below 0.5, expm1 above
+    // phi1 = (1 - e^-x)/x and phi2 = (e^-x - 1 + x)/x^2: Taylor series below 0.5 (summed
+    // smallest term first), expm1 above
     double p1, p2;
     if (x < 0.5) {
-      double t1 = 1.0, t2 = 0.5, s1 = 0, s2 = 0;
+      double t1 = 1.0, t2 = 0.5;
       double terms1[24], terms2[24];
       for (int q = 0; q < 24; ++q) {
         terms1[q] = t1;
@@ -540,6 +1350,7 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
         t1 *= -x / (q + 2);
         t2 *= -x / (q + 3);
       }
+      double s1 = 0, s2 = 0;
       for (int q = 23; q >= 0; --q) {
         s1 += terms1[q];
         s2 += terms2[q];
@@ -562,28 +1373,47 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
     c->coef[5][m] = cj * (w * p2);
   }
   const size_t fb = c->esz * c->N;
-  for (int q = 0; q < 9; ++q)
-    if (!c->alloc(&c->f[q], fb)) return bad(RKETD_ENOMEM, "3D fields");
+  const int sets = c->fused ? 2 : 1;
+  for (int s = 0; s < sets; ++s)
+    for (int q = 0; q < 3; ++q)
+      if (!c->alloc(&c->E[s][q], fb, true) || !c->alloc(&c->H[s][q], fb, true)) return bad(RKETD_ENOMEM, "3D fields");
+  if (!c->fused)
+    for (int q = 0; q < 3; ++q) {
+      c->E[1][q] = c->E[0][q];
+      c->H[1][q] = c->H[0][q];
+    }
+  for (int q = 0; q < 3; ++q)
+    if (!c->alloc(&c->J[q], fb, true)) return bad(RKETD_ENOMEM, "3D currents");
   if (!c->alloc((void**)&c->mat, c->N)) return bad(RKETD_ENOMEM, "3D materials");
   c->nmax = std::max(g->nx, std::max(g->ny, g->nz));
   c->Z = 2 * (np + 1);
   if (!c->alloc(&c->tab, c->esz * 24 * c->nmax)) return bad(RKETD_ENOMEM, "CPML tables");
-  // compact zones: x-derivative memories [k][j][Z], y [k][Z][i], z [Z][j][i]
   const int64_t zsz[3] = {(int64_t)g->nz * g->ny * c->Z, (int64_t)g->nz * c->Z * g->nx,
                           (int64_t)c->Z * g->ny * g->nx};
-  for (int q = 0; q < 12; ++q) {
+  for (int q = 0; q < 6; ++q) {
     const int ax = kPsiAxis[q];
-    c->psi_bytes[q] = (ax < 2 && g->periodic_xy) ? 16 : c->esz * zsz[ax];
-    if (!c->alloc(&c->psi[q], c->psi_bytes[q])) return bad(RKETD_ENOMEM, "CPML memories");
+    const size_t bytes = (ax < 2 && g->periodic_xy) ? 16 : c->esz * zsz[ax];
+    if (!c->alloc(&c->psiE[q], bytes, true)) return bad(RKETD_ENOMEM, "CPML memories");
+    // H side: Hx/y, Hx/z, Hy/z, Hy/x, Hz/x, Hz/y have the axes of Ex/y, Ex/z, Ey/z, Ey/x, Ez/x, Ez/y
+    for (int s = 0; s < sets; ++s)
+      if (!c->alloc(&c->psiH[s][q], bytes, true)) return bad(RKETD_ENOMEM, "CPML memories");
+    if (!c->fused) c->psiH[1][q] = c->psiH[0][q];
   }
-  if (!c->alloc(&c->Ei, c->esz * std::max(1, g->inc_len)) || !c->alloc(&c->Hi, c->esz * std::max(1, g->inc_len)))
-    return bad(RKETD_ENOMEM, "incident line");
+  const size_t lb = c->esz * std::max(1, g->inc_len);
+  for (int s = 0; s < sets; ++s)
+    if (!c->alloc(&c->Ei[s], lb, true) || !c->alloc(&c->Hi[s], lb, true)) return bad(RKETD_ENOMEM, "incident line");
+  if (!c->fused) {
+    c->Ei[1] = c->Ei[0];
+    c->Hi[1] = c->Hi[0];
+  }
   if (!c->alloc(&c->cj_d, c->esz * kMat)) return bad(RKETD_ENOMEM, "coefficients");
+  if (!c->alloc((void**)&c->err, sizeof(int), true)) return bad(RKETD_ENOMEM, "status word");
   if (n_probes) {
     if (!c->alloc((void**)&c->probes, sizeof(int) * 3 * n_probes) || !c->alloc((void**)&c->freq, sizeof(double) * nf) ||
         !c->alloc(&c->series, c->esz * (size_t)n_probes * c->dft_block) ||
         !c->alloc(&c->tw, c->esz * 2 * (size_t)c->dft_block * nf) ||
-        !c->alloc((void**)&c->Xr, sizeof(double) * n_probes * nf) || !c->alloc((void**)&c->Xi, sizeof(double) * n_probes * nf) ||
+        !c->alloc((void**)&c->Xr, sizeof(double) * n_probes * nf, true) ||
+        !c->alloc((void**)&c->Xi, sizeof(double) * n_probes * nf, true) ||
         !c->alloc((void**)&c->Xtmp, sizeof(double) * 2 * n_probes * nf))
       return bad(RKETD_ENOMEM, "probes");
     if (cudaMemcpy(c->probes, probes, sizeof(int) * 3 * n_probes, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -600,16 +1430,23 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
     if (cudaMemcpy(c->cj_d, cj.data(), cj.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return bad(RKETD_ECUDA, "coefficient upload");
   }
-  const unsigned tb = (unsigned)((c->nmax + 127) / 128);
+  const unsigned tbk = (unsigned)((c->nmax + 127) / 128);
   if (c->prec == RKETD_F64)
-    k3_tables<double><<<tb, 128, 0, c->stream>>>(g->nx, g->ny, g->nz, np, g->periodic_xy, g->dt, g->pml_m,
-                                                 c->g.pml_sigma_max, g->pml_kappa_max, g->pml_alpha_max, c->nmax,
-                                                 (double*)c->tab);
+    k3_tables<double><<<tbk, 128, 0, c->stream>>>(g->nx, g->ny, g->nz, np, g->periodic_xy, g->dt, g->pml_m,
+                                                  c->g.pml_sigma_max, g->pml_kappa_max, g->pml_alpha_max, c->nmax,
+                                                  (double*)c->tab);
   else
-    k3_tables<float><<<tb, 128, 0, c->stream>>>(g->nx, g->ny, g->nz, np, g->periodic_xy, g->dt, g->pml_m,
-                                                c->g.pml_sigma_max, g->pml_kappa_max, g->pml_alpha_max, c->nmax,
-                                                (float*)c->tab);
+    k3_tables<float><<<tbk, 128, 0, c->stream>>>(g->nx, g->ny, g->nz, np, g->periodic_xy, g->dt, g->pml_m,
+                                                 c->g.pml_sigma_max, g->pml_kappa_max, g->pml_alpha_max, c->nmax,
+                                                 (float*)c->tab);
   c->launches += 1;
+  if (c->staged) {
+    rketd_status sm = c->prec == RKETD_F64 ? make_maps<double>(c) : make_maps<float>(c);
+    if (sm) {
+      delete c;
+      return sm;
+    }
+  }
   rketd_status st = rketd_reset_3d(c);
   if (st) {
     delete c;
@@ -622,16 +1459,9 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
 
 rketd_status rketd_reset_3d(rketd_ctx3d* c) {
   if (!c) return fail3(RKETD_EINVAL, "NULL context");
-  const size_t fb = c->esz * c->N;
-  for (int q = 0; q < 9; ++q) CK3(cudaMemsetAsync(c->f[q], 0, fb, c->stream), "reset");
-  for (int q = 0; q < 12; ++q) CK3(cudaMemsetAsync(c->psi[q], 0, c->psi_bytes[q], c->stream), "reset");
-  CK3(cudaMemsetAsync(c->Ei, 0, c->esz * std::max(1, c->g.inc_len), c->stream), "reset");
-  CK3(cudaMemsetAsync(c->Hi, 0, c->esz * std::max(1, c->g.inc_len), c->stream), "reset");
-  if (c->n_probes) {
-    CK3(cudaMemsetAsync(c->Xr, 0, sizeof(double) * c->n_probes * c->n_freq, c->stream), "reset");
-    CK3(cudaMemsetAsync(c->Xi, 0, sizeof(double) * c->n_probes * c->n_freq, c->stream), "reset");
-  }
+  for (auto& z : c->zeroed) CK3(cudaMemsetAsync(z.first, 0, z.second, c->stream), "reset");
   c->step = 0;
+  c->cur = 0;
   return RKETD_OK;
 }
 
@@ -643,6 +1473,7 @@ rketd_status rketd_step_3d(rketd_ctx3d* c, int64_t nsteps) {
 
 rketd_status rketd_get_field_3d(rketd_ctx3d* c, int32_t which, double* out) {
   if (!c || !out || which < 0 || which > 8) return fail3(RKETD_EINVAL, "invalid arguments");
+  const void* src = which < 3 ? c->E[c->cur][which] : (which < 6 ? c->H[c->cur][which - 3] : c->J[which - 6]);
   double* tmp;
   CK3(cudaMallocAsync((void**)&tmp, sizeof(double) * c->N, c->stream), "field staging");
   const double eta0 = std::sqrt(kMu0 / kEps0);
@@ -650,16 +1481,15 @@ rketd_status rketd_get_field_3d(rketd_ctx3d* c, int32_t which, double* out) {
   const int shift = which >= 6 ? 2 * (which - 6) : 0;
   const unsigned blocks = (unsigned)((c->N + 255) / 256);
   if (c->prec == RKETD_F64)
-    k3_gather<double><<<blocks, 256, 0, c->stream>>>((const double*)c->f[which], c->N, scale,
+    k3_gather<double><<<blocks, 256, 0, c->stream>>>((const double*)src, c->N, scale,
                                                      which >= 6 ? (const double*)c->cj_d : nullptr, c->mat, shift, tmp);
   else
-    k3_gather<float><<<blocks, 256, 0, c->stream>>>((const float*)c->f[which], c->N, scale,
+    k3_gather<float><<<blocks, 256, 0, c->stream>>>((const float*)src, c->N, scale,
                                                     which >= 6 ? (const float*)c->cj_d : nullptr, c->mat, shift, tmp);
   cudaError_t e = cudaMemcpyAsync(out, tmp, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream);
   cudaFreeAsync(tmp, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   CK3(e, "get_field_3d");
-  return RKETD_OK;
+  return check3(c);
 }
 
 rketd_status rketd_get_spectra_3d(rketd_ctx3d* c, double* re, double* im) {
@@ -676,7 +1506,17 @@ rketd_status rketd_get_spectra_3d(rketd_ctx3d* c, double* re, double* im) {
   }
   CK3(cudaMemcpyAsync(re, c->Xtmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
   CK3(cudaMemcpyAsync(im, c->Xtmp + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
-  CK3(cudaStreamSynchronize(c->stream), "spectra");
+  return check3(c);
+}
+
+rketd_status rketd_sync_3d(rketd_ctx3d* c) {
+  if (!c) return fail3(RKETD_EINVAL, "NULL context");
+  return check3(c);
+}
+
+rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* c, int32_t k_chunk) {
+  if (!c || k_chunk < 1 || k_chunk > 4096) return fail3(RKETD_EINVAL, "k_chunk must be 1..4096");
+  c->kc = k_chunk;
   return RKETD_OK;
 }
 

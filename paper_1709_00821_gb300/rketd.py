@@ -58,7 +58,7 @@ class Grid3D(ctypes.Structure):
                 ("npml", ctypes.c_int32), ("pml_m", ctypes.c_double), ("pml_sigma_max", ctypes.c_double),
                 ("pml_kappa_max", ctypes.c_double), ("pml_alpha_max", ctypes.c_double), ("tfsf", ctypes.c_int32),
                 ("box", ctypes.c_int32 * 6), ("sheet_k", ctypes.c_int32), ("inc_off", ctypes.c_int32),
-                ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
 _LIB = None
@@ -103,6 +103,8 @@ _SIGS = {
     "rketd_step_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "rketd_get_field_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
     "rketd_get_spectra_3d": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "rketd_kernel_chunk_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_sync_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
     "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
@@ -344,7 +346,9 @@ FIELDS_3D = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Jx", "Jy", "Jz")
 class Context3D:
     """One rketd_ctx3d: a 3D Yee RKETD problem (workloads.Grid3D) on one CUDA stream."""
 
-    def __init__(self, prob, prec: str = "f32", stream=None):
+    VARIANTS = {"auto": 0, "plain": 1, "fused": 2, "staged": 3}
+
+    def __init__(self, prob, prec: str = "f32", stream=None, variant: str = "auto", k_chunk: int = 0):
         L = lib()
         self.prob = prob
         g = Grid3D()
@@ -359,6 +363,7 @@ class Context3D:
             g.box[q] = prob.box[q]
         g.sheet_k = prob.sheet_k
         g.inc_off, g.inc_len, g.inc_src = prob.inc_off, prob.inc_len, prob.inc_src
+        g.variant = self.VARIANTS[variant]
         self.prec = prec
         self.n_probes = len(prob.probes)
         self.freq = _arr(prob.freq_hz)
@@ -373,6 +378,8 @@ class Context3D:
                                  ctypes.byref(p), self.n_probes, ctypes.c_void_p(pr.ctypes.data), ctypes.byref(d),
                                  ctypes.c_void_p(self.stream), ctypes.byref(h)))
         self.h = h
+        if k_chunk:
+            _check(L.rketd_kernel_chunk_3d(self.h, int(k_chunk)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -396,6 +403,9 @@ class Context3D:
 
     def reset(self):
         _check(lib().rketd_reset_3d(self.h))
+
+    def sync(self):
+        _check(lib().rketd_sync_3d(self.h))
 
     def field(self, name: str) -> np.ndarray:
         """One component as a host FP64 SI array [nz, ny, nx]."""

@@ -61,25 +61,106 @@ def _ragged():
                      [(17, 12, 7), (20, 14, 38), (18, 13, 22)], freqs, 230)
 
 
+def _ragged16():
+    """As _ragged with nx = 48, which the staged form takes (x a multiple of 16, not of the
+    32-wide tile), the sphere cut by the box and the CPML near the x faces."""
+    p = _ragged()
+    nx, ny, nz = 48, p.ny, p.nz
+    m1 = wl.sphere_materials(nx, ny, nz, (21.3, 12.6, 23.9), 6.2, 1)
+    m2 = wl.sphere_materials(nx, ny, nz, (33.0, 19.0, 30.0), 3.1, 2)
+    assert not np.any((m1 != 0) & (m2 != 0))
+    p.nx, p.mat = nx, m1 | m2
+    p.box = (9, 38, 8, 21, 10, 35)
+    p.probes = [(21, 12, 7), (40, 14, 38), (18, 13, 22), (31, 20, 30)]
+    return p
+
+
+def _lean():
+    """A grid whose middle tiles are clear of the CPML and of the TF/SF faces, so that the
+    staged form takes its lean path there, with plasma of both materials inside them."""
+    nx, ny, nz = 96, 40, 40
+    d = 100e-6
+    dt = wl.dt_for_courant(d, 0.5)
+    m1 = wl.sphere_materials(nx, ny, nz, (47.6, 20.3, 19.8), 8.3, 1)
+    m2 = wl.sphere_materials(nx, ny, nz, (70.2, 13.9, 26.1), 4.2, 2)
+    assert not np.any((m1 != 0) & (m2 != 0))
+    freqs = 100e9 * np.arange(1, 9, dtype=float) / 8
+    return wl.Grid3D(nx, ny, nz, d, dt, m1 | m2, np.array([0.0, (2 * math.pi * 40e9) ** 2, (2 * math.pi * 25e9) ** 2]),
+                     np.array([0.0, 2e10, 7e10]), False, 4, True, (8, 87, 6, 33, 7, 32), -1, 15 * dt, 75 * dt,
+                     [(48, 20, 5), (60, 25, 36), (50, 18, 20)], freqs, 200)
+
+
+@pytest.mark.parametrize("grid", ["ragged16", "lean"])
+@pytest.mark.parametrize("k_chunk", [0, 7, 45])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_sphere_tfsf_cpml_matches_the_3d_oracle(prec):
+def test_staged_form_matches_the_3d_oracle(prec, k_chunk, grid):
+    p = _ragged16() if grid == "ragged16" else _lean()
+    st, _ = oracle.run3d(p)
+    with rk.Context3D(p, prec, variant="staged", k_chunk=k_chunk) as ctx:
+        ctx.step(100)
+        ctx.step(p.steps - 100)
+        worst = _compare(ctx, st, p, prec)
+    print(prec, "staged", k_chunk, {k: f"{v:.2e}" for k, v in worst.items()})
+
+
+@pytest.mark.parametrize("grid", ["ragged16", "lean"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_staged_form_agrees_bitwise_with_the_plain_form(prec, grid):
+    p = _ragged16() if grid == "ragged16" else _lean()
+    out = []
+    for variant, kc in (("plain", 0), ("staged", 0), ("staged", 3), ("auto", 0)):
+        with rk.Context3D(p, prec, variant=variant, k_chunk=kc) as ctx:
+            ctx.step(151)
+            out.append(([ctx.field(n) for n in rk.FIELDS_3D], ctx.spectra()))
+    for f, X in out[1:]:
+        assert all(np.array_equal(u, v) for u, v in zip(out[0][0], f))
+        assert np.array_equal(out[0][1], X)
+
+
+def test_staged_form_is_refused_where_it_does_not_apply():
+    p = _ragged()  # nx = 37
+    with pytest.raises(rk.RketdError) as ei:
+        rk.Context3D(p, "f32", variant="staged")
+    assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("variant", ["plain", "fused"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sphere_tfsf_cpml_matches_the_3d_oracle(prec, variant):
     p = _sphere()
     st, _ = oracle.run3d(p)
-    with rk.Context3D(p, prec) as ctx:
+    with rk.Context3D(p, prec, variant=variant) as ctx:
         ctx.step(p.steps)
         worst = _compare(ctx, st, p, prec)
-    print(prec, {k: f"{v:.2e}" for k, v in worst.items()})
+    print(prec, variant, {k: f"{v:.2e}" for k, v in worst.items()})
 
 
+@pytest.mark.parametrize("variant,k_chunk", [("plain", 0), ("fused", 0), ("fused", 7), ("fused", 1)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_ragged_grid_two_materials_matches_the_3d_oracle(prec):
+def test_ragged_grid_two_materials_matches_the_3d_oracle(prec, variant, k_chunk):
     p = _ragged()
     st, _ = oracle.run3d(p)
-    with rk.Context3D(p, prec) as ctx:
+    with rk.Context3D(p, prec, variant=variant, k_chunk=k_chunk) as ctx:
         ctx.step(100)
         ctx.step(p.steps - 100)  # split calls: the DFT fold and the step index carry over
         worst = _compare(ctx, st, p, prec)
-    print(prec, {k: f"{v:.2e}" for k, v in worst.items()})
+    print(prec, variant, k_chunk, {k: f"{v:.2e}" for k, v in worst.items()})
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_plain_and_fused_forms_and_chunkings_agree_bitwise(prec):
+    """The two forms run the same operations in the same order on every value; the chunk of
+    z planes per block changes only which thread does them."""
+    p = _ragged()
+    p.probes = [(17, 12, 7), (20, 14, 38), (18, 13, 22), (18, 13, 23)]
+    out = []
+    for variant, kc in (("plain", 0), ("fused", 0), ("fused", 5), ("fused", 45)):
+        with rk.Context3D(p, prec, variant=variant, k_chunk=kc) as ctx:
+            ctx.step(177)
+            out.append(([ctx.field(n) for n in rk.FIELDS_3D], ctx.spectra()))
+    for f, X in out[1:]:
+        assert all(np.array_equal(u, v) for u, v in zip(out[0][0], f))
+        assert np.array_equal(out[0][1], X)
 
 
 def test_periodic_layered_slab_reduces_to_the_1d_oracle():
@@ -96,7 +177,7 @@ def test_periodic_layered_slab_reduces_to_the_1d_oracle():
     s1.wp2[140:170] = p.mat_wp2[1]
     s1.nu[140:170] = p.mat_nu[1]
     st1, _ = oracle.run1d(s1)
-    with rk.Context3D(p, "f64") as ctx:
+    with rk.Context3D(p, "f64", k_chunk=11) as ctx:
         ctx.step(steps)
         Ex, Hy, Jx = ctx.field("Ex"), ctx.field("Hy"), ctx.field("Jx")
         X = ctx.spectra()
@@ -111,14 +192,15 @@ def test_periodic_layered_slab_reduces_to_the_1d_oracle():
     assert np.abs(X - st1.X).max() <= 1e-11 * np.abs(st1.X).max()
 
 
-def test_sheet_source_on_a_closed_grid_matches_the_3d_oracle():
+@pytest.mark.parametrize("variant", ["plain", "fused"])
+def test_sheet_source_on_a_closed_grid_matches_the_3d_oracle(variant):
     """CPML on all faces with the soft sheet source: the sheet covers the whole plane, the
     PEC wall cells included, as in the oracle."""
     p = _sphere(n=33, steps=150)
     p.tfsf = False
     p.sheet_k = 9
     st, _ = oracle.run3d(p)
-    with rk.Context3D(p, "f64") as ctx:
+    with rk.Context3D(p, "f64", variant=variant) as ctx:
         ctx.step(p.steps)
         _compare(ctx, st, p, "f64")
 
@@ -134,7 +216,7 @@ def test_reset_reproduces_the_first_run_bitwise():
         b = [ctx.field(n) for n in ("Ex", "Hy", "Jz")]
         assert all(np.array_equal(u, v) for u, v in zip(a, b))
         assert np.array_equal(Xa, ctx.spectra())
-        assert ctx.launches > 480
+        assert ctx.launches >= 240  # one fused launch per step
 
 
 def test_full_size_sphere_grid_total_field_is_the_incident_wave():
