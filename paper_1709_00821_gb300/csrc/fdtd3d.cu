@@ -502,13 +502,42 @@ __global__ void __launch_bounds__(256) k3_fused(const Args3<T> a) {
 // the i0-1 column (Hy, Hz) that the E update needs. Box of each E/H plane: x in
 // [i0-4, i0+36) (16-byte aligned start), y in [j0-1, j0+kTY+1); out-of-grid parts read 0.
 // Non-periodic grids with nx a multiple of 16.
-constexpr int kTY = 8;
-constexpr int kStages = 4;
+#ifndef RKETD_3D_TY
+#define RKETD_3D_TY 8
+#endif
+#ifndef RKETD_3D_STAGES
+#define RKETD_3D_STAGES 4
+#endif
+#ifndef RKETD_3D_L2PROMO
+#define RKETD_3D_L2PROMO 2  // L2 promotion of the staged copies: 0 none, 1 64 B, 2 128 B, 3 256 B
+#endif
+#ifndef RKETD_3D_MINB
+#define RKETD_3D_MINB 0  // 0: resident blocks per SM that the shared memory allows (4 FP32, 2 FP64)
+#endif
+constexpr int kTY = RKETD_3D_TY;         // compute warps (rows) per block
+constexpr int kStages = RKETD_3D_STAGES;  // planes in the copy ring (>= 3)
+static_assert(kTY >= 1 && kTY <= 32 && kStages >= 3, "staged form shape");
 constexpr int kBW = 40;
 constexpr int kBH = kTY + 2;
 constexpr int kHW = 33;  // new-H tile row: i0-1 .. i0+31
 constexpr int kHH = kTY + 1;
 constexpr int kWaitLimit = 1 << 20;
+
+// Facts of one z plane for the staged form, written next to its stage by the thread that
+// issues the plane's copies and read by all threads once the stage's mbarrier completes.
+template <typename T>
+struct PlaneS {
+  T zb[2], zc[2], zk[2];  // z CPML coefficients at this plane: [0] H position z+1/2, [1] E position z
+  T ei_hy, ei_hz;         // step-n incident E for the Hy and Hz corrections
+  T hi_ex, hi_ez;         // step-n+1/2 incident H for the Ex and Ez corrections
+  int zz;                 // compact z zone
+  unsigned f;             // kP* flags
+};
+enum : unsigned {
+  kPVk = 1u, kPZin = 2u, kPZlast = 4u, kPFzH = 8u, kPFzE = 16u, kPTfHz = 32u, kPTfEz = 64u, kPSheet = 128u,
+  kPHyP = 256u, kPHyM = 512u, kPExP = 1024u, kPExM = 2048u, kPLean = 4096u
+};
+constexpr int kXN = 34;  // x coefficient entries of a tile: i0-1 .. i0+32
 
 template <typename T>
 struct Stage3 {
@@ -517,7 +546,14 @@ struct Stage3 {
   static constexpr int bytes = 6 * box * (int)sizeof(T) + mat_bytes;  // one plane of Ex..Hz + material
   static constexpr int tx = 6 * kBW * kBH * (int)sizeof(T) + mat_bytes;  // bytes the copies deliver
   static constexpr int hn = ((kHW * kHH + 31) / 32) * 32;
-  static constexpr int smem = kStages * bytes + 2 * 3 * hn * (int)sizeof(T) + kStages * 8;
+  static constexpr int off_hn = kStages * bytes;
+  static constexpr int off_bar = off_hn + 2 * 3 * hn * (int)sizeof(T);
+  static constexpr int off_pl = ((off_bar + kStages * 8 + 15) / 16) * 16;
+  static constexpr int pl_bytes = ((int)sizeof(PlaneS<T>) + 15) / 16 * 16;
+  static constexpr int off_xy = off_pl + kStages * pl_bytes;
+  // per-tile CPML coefficients, 8 values per x (kXN) and y (kTY+1) position:
+  // H: b, c, 1/kappa, flag; E: b, c, 1/kappa, flag
+  static constexpr int smem = off_xy + (kXN + kTY + 1) * 8 * (int)sizeof(T);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -553,19 +589,22 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
       : "memory");
 }
 
-// Per-column and per-plane facts of the general path of the staged form, worked out once
-// (per thread, per plane) instead of per update; the updates below then do exactly the
-// operations of hx_core .. e_cell for non-periodic grids.
+template <typename T>
+struct Maps3 {
+  CUtensorMap f[6];  // Ex, Ey, Ez, Hx, Hy, Hz of the step-n set
+  CUtensorMap mat;
+};
+
+// Per-cell facts of the staged form that depend on (i, j) only, worked out once per thread.
 struct Col3 {
-  bool vi, vj;          // i+1 < nx, j+1 < ny
-  bool fxH, fyH;        // CPML memory active at x = i+1/2, y = j+1/2 (H positions)
-  bool fxE, fyE;        // CPML memory active at x = i, y = j (E positions)
+  bool vi, vj;               // i+1 < nx, j+1 < ny
+  bool fxH, fyH, fxE, fyE;   // x / y CPML memory active (H positions i+1/2, j+1/2; E positions i, j)
   bool ex_xy, ey_xy, ez_xy;  // E component updated, as far as x and y decide
-  bool tf_xy;           // i in [i0, i1-1] and j in [j0, j1] (TF/SF Hy and Ex faces)
-  bool tf_hz_i;         // i in [i0, i1-1]
-  int sg_hz;            // -1 at j = j0-1, +1 at j = j1, else 0 (Hz faces)
-  int sg_ez;            // -1 at i = i0, +1 at i = i1 when j in [j0, j1], else 0 (Ez faces)
-  int zx, zy;           // compact zone indices (valid where a flag is set)
+  bool tf_xy;                // i in [i0, i1-1] and j in [j0, j1] (TF/SF Hy and Ex faces)
+  bool tf_hz_i;              // i in [i0, i1-1]
+  int sg_hz;                 // -1 at j = j0-1, +1 at j = j1, else 0 (Hz faces)
+  int sg_ez;                 // -1 at i = i0, +1 at i = i1 when j in [j0, j1], else 0 (Ez faces)
+  int zx, zy;                // compact zone indices
 };
 
 template <typename T>
@@ -576,14 +615,10 @@ __device__ __forceinline__ Col3 col3(const Args3<T>& a, int i, int j) {
   c.vj = j + 1 < ny;
   c.zx = zone(i, nx, a.np);
   c.zy = zone(j, ny, a.np);
-  const T* txH = tb(a, 0, 1);
-  const T* tyH = tb(a, 1, 1);
-  const T* txE = tb(a, 0, 0);
-  const T* tyE = tb(a, 1, 0);
-  c.fxH = c.zx >= 0 && txH[3 * a.nmax + i] != T(0);
-  c.fyH = c.zy >= 0 && tyH[3 * a.nmax + j] != T(0);
-  c.fxE = c.zx >= 0 && txE[3 * a.nmax + i] != T(0);
-  c.fyE = c.zy >= 0 && tyE[3 * a.nmax + j] != T(0);
+  c.fxH = c.zx >= 0 && tb(a, 0, 1)[3 * a.nmax + i] != T(0);
+  c.fyH = c.zy >= 0 && tb(a, 1, 1)[3 * a.nmax + j] != T(0);
+  c.fxE = c.zx >= 0 && tb(a, 0, 0)[3 * a.nmax + i] != T(0);
+  c.fyE = c.zy >= 0 && tb(a, 1, 0)[3 * a.nmax + j] != T(0);
   const bool xin = i > 0 && i < nx - 1, yin = j > 0 && j < ny - 1;
   c.ex_xy = i < nx - 1 && yin;
   c.ey_xy = j < ny - 1 && xin;
@@ -597,187 +632,221 @@ __device__ __forceinline__ Col3 col3(const Args3<T>& a, int i, int j) {
 }
 
 template <typename T>
-struct Plane3 {
-  bool vk, zin, zlast;  // z+1 < nz, 0 < z < nz-1, z < nz-1
-  bool fzH, fzE;        // CPML memory active at z+1/2 and at z
-  int zz;
-  int sg_hy;            // +1 at z = k0-1, -1 at z = k1 (Hy faces)
-  bool tf_hz;           // z in [k0, k1]
-  int sg_ex;            // +1 at z = k0, -1 at z = k1 (Ex faces)
-  bool tf_ez;           // z in [k0, k1-1]
-  T ei_hy, ei_hz;       // step-n incident E used by the Hy and Hz corrections of this plane
-  T hi_ex, hi_ez;       // step-n+1/2 incident H used by the Ex and Ez corrections
-  bool sheet;
-};
-
-template <typename T>
-__device__ __forceinline__ Plane3<T> plane3(const Args3<T>& a, int z) {
-  Plane3<T> p;
-  p.vk = z + 1 < a.nz;
-  p.zin = z > 0 && z < a.nz - 1;
-  p.zlast = z < a.nz - 1;
-  p.zz = zone(z, a.nz, a.np);
-  p.fzH = p.zz >= 0 && tb(a, 2, 1)[3 * a.nmax + z] != T(0);
-  p.fzE = p.zz >= 0 && tb(a, 2, 0)[3 * a.nmax + z] != T(0);
-  p.sg_hy = 0;
-  p.tf_hz = p.tf_ez = false;
-  p.sg_ex = 0;
-  p.ei_hy = p.ei_hz = p.hi_ex = p.hi_ez = T(0);
+__device__ __forceinline__ void plane_facts(const Args3<T>& a, int z, PlaneS<T>* p) {
+  unsigned f = 0;
+  p->zz = -1;
+  for (int h = 0; h < 2; ++h) p->zb[h] = p->zc[h] = p->zk[h] = T(0);
+  p->ei_hy = p->ei_hz = p->hi_ex = p->hi_ez = T(0);
+  if (z < 0 || z >= a.nz) {
+    p->f = 0;
+    return;
+  }
+  const int nz = a.nz, np = a.np;
+  if (z + 1 < nz) f |= kPVk;
+  if (z > 0 && z < nz - 1) f |= kPZin;
+  if (z < nz - 1) f |= kPZlast;
+  const int zz = zone(z, nz, np);
+  p->zz = zz;
+  if (zz >= 0)
+    for (int h = 0; h < 2; ++h) {
+      const T* t = tb(a, 2, h == 0 ? 1 : 0);
+      if (t[3 * a.nmax + z] != T(0)) {
+        f |= h == 0 ? kPFzH : kPFzE;
+        p->zb[h] = t[z];
+        p->zc[h] = t[a.nmax + z];
+        p->zk[h] = t[2 * a.nmax + z];
+      }
+    }
   if (a.tfsf) {
     if (z == a.k0 - 1) {
-      p.sg_hy = 1;
-      p.ei_hy = __ldg(a.Ei + a.k0 + a.inc_off);
+      f |= kPHyP;
+      p->ei_hy = a.Ei[a.k0 + a.inc_off];
     } else if (z == a.k1) {
-      p.sg_hy = -1;
-      p.ei_hy = __ldg(a.Ei + a.k1 + a.inc_off);
+      f |= kPHyM;
+      p->ei_hy = a.Ei[a.k1 + a.inc_off];
     }
-    p.tf_hz = z >= a.k0 && z <= a.k1;
-    if (p.tf_hz) p.ei_hz = __ldg(a.Ei + z + a.inc_off);
+    if (z >= a.k0 && z <= a.k1) {
+      f |= kPTfHz;
+      p->ei_hz = a.Ei[z + a.inc_off];
+    }
     if (z == a.k0) {
-      p.sg_ex = 1;
-      p.hi_ex = hinc<true>(a, a.k0 - 1 + a.inc_off);
+      f |= kPExP;
+      p->hi_ex = hinc<true>(a, a.k0 - 1 + a.inc_off);
     } else if (z == a.k1) {
-      p.sg_ex = -1;
-      p.hi_ex = hinc<true>(a, a.k1 + a.inc_off);
+      f |= kPExM;
+      p->hi_ex = hinc<true>(a, a.k1 + a.inc_off);
     }
-    p.tf_ez = z >= a.k0 && z <= a.k1 - 1;
-    if (p.tf_ez) p.hi_ez = hinc<true>(a, z + a.inc_off);
+    if (z >= a.k0 && z <= a.k1 - 1) {
+      f |= kPTfEz;
+      p->hi_ez = hinc<true>(a, z + a.inc_off);
+    }
   }
-  p.sheet = z == a.sheet_k;
-  return p;
+  if (z == a.sheet_k) f |= kPSheet;
+  if (z >= np + 1 && z <= nz - np - 2 && z != a.sheet_k && !(a.tfsf && (z == a.k0 - 1 || z == a.k0 || z == a.k1)))
+    f |= kPLean;
+  p->f = f;
 }
 
-// CPML stretch where the memory is known to be active (stretch() without the flag test)
+// CPML stretch with the coefficients given (stretch() once its flag is known to be set)
 template <typename T>
-__device__ __forceinline__ T stretch_on(const T* t, int nmax, int pos, T dv, const T* pin, T* pout) {
-  const T p = fma(t[pos], __ldg(pin), t[nmax + pos] * dv);
+__device__ __forceinline__ T stretch_c(T b, T cc, T ki, T dv, const T* pin, T* pout) {
+  const T p = fma(b, __ldg(pin), cc * dv);
   if (pout) *pout = p;
-  return fma(dv, t[2 * nmax + pos], p);
+  return fma(dv, ki, p);
 }
 
-template <typename T>
-__device__ __forceinline__ T hx_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
-                                    T ez_jp, T ez, T ey_kp, T ey, bool own) {
-  if (!c.vj || !pl.vk) return h;
+// The staged form's updates of one cell: the operations of hx_core .. e_cell for non-periodic
+// grids, with the per-cell facts (c), the x and y coefficient rows of the tile (X, Y: H b, c,
+// 1/kappa, flag, then E) and the plane's facts (p). INTERIOR: the cell is clear of the x/y
+// CPML and of the TF/SF x/y faces, so those terms are left out at compile time.
+template <bool INTERIOR, typename T>
+__device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneS<T>& p, int i, int j,
+                                  int k, T h, T ez_jp, T ez, T ey_kp, T ey, bool own) {
+  if (!(p.f & kPVk)) return h;
+  if constexpr (!INTERIOR)
+    if (!c.vj) return h;
   T cy = ez_jp - ez;
   T cz = ey_kp - ey;
-  if (c.fyH) {
-    const int64_t o = zy_off(a, i, k, c.zy);
-    cy = stretch_on(tb(a, 1, 1), a.nmax, j, cy, a.psiH[0] + o, own ? a.opsiH[0] + o : nullptr);
-  }
-  if (pl.fzH) {
-    const int64_t o = zz_off(a, i, j, pl.zz);
-    cz = stretch_on(tb(a, 2, 1), a.nmax, k, cz, a.psiH[1] + o, own ? a.opsiH[1] + o : nullptr);
+  if constexpr (!INTERIOR)
+    if (c.fyH) {
+      const int64_t o = zy_off(a, i, k, c.zy);
+      cy = stretch_c(Y[0], Y[1], Y[2], cy, a.psiH[0] + o, own ? a.opsiH[0] + o : nullptr);
+    }
+  if (p.f & kPFzH) {
+    const int64_t o = zz_off(a, i, j, p.zz);
+    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, a.psiH[1] + o, own ? a.opsiH[1] + o : nullptr);
   }
   return fma(-a.S, cy - cz, h);
 }
 
-template <typename T>
-__device__ __forceinline__ T hy_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
-                                    T ex_kp, T ex, T ez_ip, T ez, bool own) {
-  if (!c.vi || !pl.vk) return h;
+template <bool INTERIOR, typename T>
+__device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneS<T>& p, int i, int j,
+                                  int k, T h, T ex_kp, T ex, T ez_ip, T ez, bool own) {
+  if (!(p.f & kPVk)) return h;
+  if constexpr (!INTERIOR)
+    if (!c.vi) return h;
   T cz = ex_kp - ex;
   T cx = ez_ip - ez;
-  if (pl.fzH) {
-    const int64_t o = zz_off(a, i, j, pl.zz);
-    cz = stretch_on(tb(a, 2, 1), a.nmax, k, cz, a.psiH[2] + o, own ? a.opsiH[2] + o : nullptr);
+  if (p.f & kPFzH) {
+    const int64_t o = zz_off(a, i, j, p.zz);
+    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, a.psiH[2] + o, own ? a.opsiH[2] + o : nullptr);
   }
-  if (c.fxH) {
-    const int64_t o = zx_off(a, j, k, c.zx);
-    cx = stretch_on(tb(a, 0, 1), a.nmax, i, cx, a.psiH[3] + o, own ? a.opsiH[3] + o : nullptr);
-  }
-  T v = fma(-a.S, cz - cx, h);
-  if (c.tf_xy && pl.sg_hy) v = fma(pl.sg_hy > 0 ? a.S : -a.S, pl.ei_hy, v);
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T hz_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k, T h,
-                                    T ey_ip, T ey, T ex_jp, T ex, bool own) {
-  if (!c.vi || !c.vj) return h;
-  T cx = ey_ip - ey;
-  T cy = ex_jp - ex;
-  if (c.fxH) {
-    const int64_t o = zx_off(a, j, k, c.zx);
-    cx = stretch_on(tb(a, 0, 1), a.nmax, i, cx, a.psiH[4] + o, own ? a.opsiH[4] + o : nullptr);
-  }
-  if (c.fyH) {
-    const int64_t o = zy_off(a, i, k, c.zy);
-    cy = stretch_on(tb(a, 1, 1), a.nmax, j, cy, a.psiH[5] + o, own ? a.opsiH[5] + o : nullptr);
-  }
-  T v = fma(-a.S, cx - cy, h);
-  if (c.tf_hz_i && c.sg_hz && pl.tf_hz) v = fma(c.sg_hz > 0 ? a.S : -a.S, pl.ei_hz, v);
-  return v;
-}
-
-// E and J of one cell (the operations of e_cell, for non-periodic grids); returns the new Ex
-template <typename T>
-__device__ __forceinline__ T e_gen(const Args3<T>& a, const Col3& c, const Plane3<T>& pl, int i, int j, int k,
-                                   int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy, T hz, T hx_jm, T hz_jm, T hy_im,
-                                   T hz_im, T hx_km, T hy_km, T srcv) {
-  if (c.ex_xy && pl.zin) {
-    T cy = hz - hz_jm, cz = hy - hy_km;
-    if (c.fyE) {
-      T* p = a.psiE[0] + zy_off(a, i, k, c.zy);
-      cy = stretch<false>(tb(a, 1, 0), a.nmax, j, cy, p, p);
+  if constexpr (!INTERIOR)
+    if (c.fxH) {
+      const int64_t o = zx_off(a, j, k, c.zx);
+      cx = stretch_c(X[0], X[1], X[2], cx, a.psiH[3] + o, own ? a.opsiH[3] + o : nullptr);
     }
-    if (pl.fzE) {
-      T* p = a.psiE[1] + zz_off(a, i, j, pl.zz);
-      cz = stretch<false>(tb(a, 2, 0), a.nmax, k, cz, p, p);
+  T v = fma(-a.S, cz - cx, h);
+  if (c.tf_xy && (p.f & (kPHyP | kPHyM))) v = fma((p.f & kPHyP) ? a.S : -a.S, p.ei_hy, v);
+  return v;
+}
+
+template <bool INTERIOR, typename T>
+__device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
+                                  int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex, bool own) {
+  if constexpr (INTERIOR) {
+    return fma(-a.S, (ey_ip - ey) - (ex_jp - ex), h);
+  } else {
+    if (!c.vi || !c.vj) return h;
+    T cx = ey_ip - ey;
+    T cy = ex_jp - ex;
+    if (c.fxH) {
+      const int64_t o = zx_off(a, j, k, c.zx);
+      cx = stretch_c(X[0], X[1], X[2], cx, a.psiH[4] + o, own ? a.opsiH[4] + o : nullptr);
+    }
+    if (c.fyH) {
+      const int64_t o = zy_off(a, i, k, c.zy);
+      cy = stretch_c(Y[0], Y[1], Y[2], cy, a.psiH[5] + o, own ? a.opsiH[5] + o : nullptr);
+    }
+    T v = fma(-a.S, cx - cy, h);
+    if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) v = fma(c.sg_hz > 0 ? a.S : -a.S, p.ei_hz, v);
+    return v;
+  }
+}
+
+// E and J of one cell; returns the new Ex. The CPML memories of E are updated in place.
+template <bool INTERIOR, typename T>
+__device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p, int i,
+                                 int j, int k, int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy, T hz, T hx_jm,
+                                 T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
+  const bool zin = p.f & kPZin;
+  if (zin && (INTERIOR || c.ex_xy)) {
+    T cy = hz - hz_jm, cz = hy - hy_km;
+    if constexpr (!INTERIOR)
+      if (c.fyE) {
+        T* q = a.psiE[0] + zy_off(a, i, k, c.zy);
+        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, q, q);
+      }
+    if (p.f & kPFzE) {
+      T* q = a.psiE[1] + zz_off(a, i, j, p.zz);
+      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, q, q);
     }
     ex = e_update(a.m, mb & 3, ex, cy - cz, a.Jx + ci);
-    if (c.tf_xy && pl.sg_ex) ex = fma(pl.sg_ex > 0 ? a.S : -a.S, pl.hi_ex, ex);
+    if (c.tf_xy && (p.f & (kPExP | kPExM))) ex = fma((p.f & kPExP) ? a.S : -a.S, p.hi_ex, ex);
   }
-  if (pl.sheet) ex = ex + srcv;
+  if (p.f & kPSheet) ex = ex + srcv;
   a.oEx[ci] = ex;
-  if (c.ey_xy && pl.zin) {
+  if (zin && (INTERIOR || c.ey_xy)) {
     T cz = hx - hx_km, cx = hz - hz_im;
-    if (pl.fzE) {
-      T* p = a.psiE[2] + zz_off(a, i, j, pl.zz);
-      cz = stretch<false>(tb(a, 2, 0), a.nmax, k, cz, p, p);
+    if (p.f & kPFzE) {
+      T* q = a.psiE[2] + zz_off(a, i, j, p.zz);
+      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, q, q);
     }
-    if (c.fxE) {
-      T* p = a.psiE[3] + zx_off(a, j, k, c.zx);
-      cx = stretch<false>(tb(a, 0, 0), a.nmax, i, cx, p, p);
-    }
+    if constexpr (!INTERIOR)
+      if (c.fxE) {
+        T* q = a.psiE[3] + zx_off(a, j, k, c.zx);
+        cx = stretch_c<T>(X[4], X[5], X[6], cx, q, q);
+      }
     ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + ci);
   }
   a.oEy[ci] = ey;
-  if (pl.zlast && c.ez_xy) {
+  if ((p.f & kPZlast) && (INTERIOR || c.ez_xy)) {
     T cx = hy - hy_im, cy = hx - hx_jm;
-    if (c.fxE) {
-      T* p = a.psiE[4] + zx_off(a, j, k, c.zx);
-      cx = stretch<false>(tb(a, 0, 0), a.nmax, i, cx, p, p);
-    }
-    if (c.fyE) {
-      T* p = a.psiE[5] + zy_off(a, i, k, c.zy);
-      cy = stretch<false>(tb(a, 1, 0), a.nmax, j, cy, p, p);
+    if constexpr (!INTERIOR) {
+      if (c.fxE) {
+        T* q = a.psiE[4] + zx_off(a, j, k, c.zx);
+        cx = stretch_c<T>(X[4], X[5], X[6], cx, q, q);
+      }
+      if (c.fyE) {
+        T* q = a.psiE[5] + zy_off(a, i, k, c.zy);
+        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, q, q);
+      }
     }
     ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + ci);
-    if (c.sg_ez && pl.tf_ez) ez = fma(c.sg_ez < 0 ? -a.S : a.S, pl.hi_ez, ez);
+    if constexpr (!INTERIOR)
+      if (c.sg_ez && (p.f & kPTfEz)) ez = fma(c.sg_ez < 0 ? -a.S : a.S, p.hi_ez, ez);
   }
   a.oEz[ci] = ez;
   return ex;
 }
 
-template <typename T>
-struct Maps3 {
-  CUtensorMap f[6];  // Ex, Ey, Ez, Hx, Hy, Hz of the step-n set
-  CUtensorMap mat;
-};
+// Interior-column tile: the tile with its i0-1 / j0-1 halo clear of the x/y CPML and of the
+// TF/SF x and y faces (the host sorts tiles with the same test).
+__host__ __device__ __forceinline__ bool interior_tile(int i0, int j0, int nx, int ny, int np, int tfsf, const int* box) {
+  if (!(i0 - 1 >= np + 1 && i0 + 31 <= nx - np - 2 && j0 - 1 >= np + 1 && j0 + kTY - 1 <= ny - np - 2)) return false;
+  if (tfsf) {
+    const int jl = j0 - 1, jh = j0 + kTY - 1;
+    if ((box[2] - 1 >= jl && box[2] - 1 <= jh) || (box[3] >= jl && box[3] <= jh)) return false;
+    if ((box[0] >= i0 && box[0] <= i0 + 31) || (box[1] >= i0 && box[1] <= i0 + 31)) return false;
+  }
+  return true;
+}
 
-template <typename T>
-__global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp,
-                                                            int* err) {
+// One launch handles the tiles of one kind (INTERIOR or not), blockIdx.x indexing the tile
+// list and blockIdx.z the chunk of kc planes; with TF/SF the boundary launch carries one more
+// block (blockIdx.x == n_tiles, blockIdx.z == 0) that advances the incident line.
+template <typename T, bool INTERIOR>
+__global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? 4 : 2))
+    k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp, const int2* __restrict__ tiles, int n_tiles,
+              int* err) {
   using St = Stage3<T>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int nx = a.nx, ny = a.ny;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = w * 32 + lane, nt = 32 * (kTY + 1);
   const double t = (double)(a.n0 + 1) * a.dt;
-  const int nzc = (a.nz + a.kc - 1) / a.kc;
-  if ((int)blockIdx.z >= nzc) {  // incident line, step n -> n+1 (as the fused form)
-    if (blockIdx.x != 0 || blockIdx.y != 0) return;
+  if ((int)blockIdx.x >= n_tiles) {  // incident line, step n -> n+1 (as the fused form)
+    if (blockIdx.z != 0) return;
     const int L = a.inc_len;
     for (int m = tid; m < L - 1; m += nt) a.oHi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
     if (tid == 0) a.oHi[L - 1] = a.Hi[L - 1];
@@ -791,17 +860,22 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
     }
     return;
   }
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * kTY;
+  const int2 tile = tiles[blockIdx.x];
+  const int i0 = tile.x, j0 = tile.y;
   const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
   const int NP = ke - kb + 2;  // planes kb-1 .. ke
-  T* hn = (T*)(sm + kStages * St::bytes);
-  uint64_t* bar = (uint64_t*)(sm + kStages * St::bytes + 2 * 3 * St::hn * sizeof(T));
+  T* hn = (T*)(sm + St::off_hn);
+  uint64_t* bar = (uint64_t*)(sm + St::off_bar);
+  auto facts = [&](int q) -> PlaneS<T>* { return (PlaneS<T>*)(sm + St::off_pl + (q % kStages) * St::pl_bytes); };
+  T* xs = (T*)(sm + St::off_xy);  // [kXN][8]
+  T* ys = xs + kXN * 8;           // [kTY+1][8]
   auto plane = [&](int q) { return (const T*)(sm + (q % kStages) * St::bytes); };
   const bool producer = (w == kTY && lane == 0);
   auto issue = [&](int q) {
     const int s = q % kStages;
     unsigned char* dst = sm + s * St::bytes;
     const int z = kb - 1 + q;
+    plane_facts(a, z, facts(q));  // published to the consumers by the mbarrier arrival below
     mbar_expect_tx(&bar[s], St::tx);
     for (int f = 0; f < 6; ++f) tma_load3(dst + f * St::box * sizeof(T), &mp.f[f], i0 - 4, j0 - 1, z, &bar[s]);
     tma_load3(dst + 6 * St::box * sizeof(T), &mp.mat, i0, j0, z, &bar[s]);
@@ -809,6 +883,24 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
   if (producer) {
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if constexpr (!INTERIOR) {
+    // x coefficient rows for i0-1 .. i0+32 and y rows for j0-1 .. j0+kTY-1
+    for (int e = tid; e < kXN + kTY + 1; e += nt) {
+      const bool isx = e < kXN;
+      const int ax = isx ? 0 : 1;
+      const int n = isx ? i0 - 1 + e : j0 - 1 + (e - kXN);
+      const int N = isx ? nx : ny;
+      T* row = isx ? xs + 8 * e : ys + 8 * (e - kXN);
+      for (int h = 0; h < 2; ++h) {
+        const T* tt = tb(a, ax, h == 0 ? 1 : 0);
+        const bool in = n >= 0 && n < N;
+        row[4 * h + 0] = in ? tt[n] : T(0);
+        row[4 * h + 1] = in ? tt[a.nmax + n] : T(0);
+        row[4 * h + 2] = in ? tt[2 * a.nmax + n] : T(1);
+        row[4 * h + 3] = in ? tt[3 * a.nmax + n] : T(0);
+      }
+    }
   }
   __syncthreads();
   int issued = 0;  // planes whose copies the producer has issued
@@ -820,23 +912,16 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
   int pk[4], ps[4];
   const int npc = act ? column_probes(a, i, j, kb, ke, pk, ps) : 0;
   constexpr int EX = 0, EY = St::box, EZ = 2 * St::box, HX = 3 * St::box, HY = 4 * St::box, HZ = 5 * St::box;
-  // Lean planes: where the whole tile with its halo is clear of the CPML, of the TF/SF faces
-  // and of the sheet, each update is the bare Eq. 14 / Eq. 13 / Eq. 11 arithmetic (the same
-  // operations the general path does there). Decided per block and plane, so uniformly.
-  const int np = a.np;
-  bool xy_lean = i0 - 1 >= np + 1 && i0 + 31 <= nx - np - 2 && j0 - 1 >= np + 1 && j0 + kTY - 1 <= ny - np - 2;
-  if (a.tfsf) {
-    if ((a.j0 - 1 >= j0 - 1 && a.j0 - 1 <= j0 + kTY - 1) || (a.j1 >= j0 - 1 && a.j1 <= j0 + kTY - 1)) xy_lean = false;
-    if ((a.i0 >= i0 && a.i0 <= i0 + 31) || (a.i1 >= i0 && a.i1 <= i0 + 31)) xy_lean = false;
-  }
   const int64_t nxy = (int64_t)nx * ny;
   const int64_t c0 = (int64_t)j * nx + i;
-  // column facts: compute warps for their own (i, j); the halo warp for its j0-1 row cell
-  // (cc) and, lanes < kTY, its i0-1 column cell (cc2)
-  const int ci_ = w < kTY ? min(i, nx - 1) : min(i0 + lane, nx - 1);
-  const int cj_ = w < kTY ? min(j, ny - 1) : max(j0 - 1, 0);
-  const Col3 cc = col3(a, ci_, cj_);
+  // per-cell facts: own cell (compute warps) or j0-1 row cell (halo warp); i0-1 column cell
+  const Col3 cc = col3(a, w < kTY ? min(i, nx - 1) : min(i0 + lane, nx - 1), w < kTY ? min(j, ny - 1) : max(j0 - 1, 0));
   const Col3 cc2 = col3(a, max(i0 - 1, 0), min(j0 + (lane < kTY ? lane : 0), ny - 1));
+  // coefficient rows: own cell (x lane+1, y w+1); halo row cell (x lane+1, y 0); column cell (x 0, y lane+1)
+  const T* Xo = xs + 8 * (lane + 1);
+  const T* Yo = ys + 8 * (w < kTY ? w + 1 : 0);
+  const T* Xc = xs;
+  const T* Yc = ys + 8 * (lane < kTY ? lane + 1 : 0);
   T hx_km = T(0), hy_km = T(0);
   bool fail = false, bad = false;  // fail: this thread's wait gave up; bad: some thread's did
   for (int q = 0; q + 1 < NP; ++q) {
@@ -845,47 +930,27 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
     fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1);
     const T* P0 = plane(q);
     const T* P1 = plane(q + 1);
+    const PlaneS<T>& pf = *facts(q);
     T* H0 = hn + (q & 1) * 3 * St::hn;  // new Hx, Hy, Hz of plane z on the [i0-1, i0+32) x [j0-1, j0+kTY) tile
     T hx = T(0), hy = T(0), hz = T(0);
-    const bool lean = xy_lean && z >= np + 1 && z <= a.nz - np - 2 && z != a.sheet_k &&
-                      !(a.tfsf && (z == a.k0 - 1 || z == a.k0 || z == a.k1));
-    if (lean && !fail) {
+    // lean plane: interior-column tile and z clear of the z CPML, the TF/SF z faces and the
+    // sheet: the bare Eq. 14 / Eq. 13 / Eq. 11 arithmetic (decided uniformly per block)
+    const bool lean = INTERIOR && (pf.f & kPLean);
+    const bool own = q > 0;
+    if (z >= 0 && !fail) {
       if (act) {
         const int o = (w + 1) * kBW + lane + 4;
-        hx = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
-        hy = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
-        hz = fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
-        if (q > 0) {
-          const int64_t c = c0 + (int64_t)z * nxy;
-          a.oHx[c] = hx;
-          a.oHy[c] = hy;
-          a.oHz[c] = hz;
-          const int h = (w + 1) * kHW + lane + 1;
-          H0[h] = hx;
-          H0[St::hn + h] = hy;
-          H0[2 * St::hn + h] = hz;
+        if (lean) {
+          hx = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
+          hy = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
+        } else {
+          hx = hx_s<INTERIOR>(a, cc, Yo, pf, i, j, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o],
+                              P0[EY + o], own);
+          hy = hy_s<INTERIOR>(a, cc, Xo, pf, i, j, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1],
+                              P0[EZ + o], own);
         }
-      } else if (w == kTY && q > 0) {
-        int o = lane + 4;  // row j0-1: Hx, Hz
-        H0[lane + 1] = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
-        H0[2 * St::hn + lane + 1] =
-            fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
-        if (lane < kTY) {  // column i0-1: Hy, Hz
-          o = (lane + 1) * kBW + 3;
-          const int h = (lane + 1) * kHW;
-          H0[St::hn + h] = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
-          H0[2 * St::hn + h] =
-              fma(-a.S, (P0[EY + o + 1] - P0[EY + o]) - (P0[EX + o + kBW] - P0[EX + o]), P0[HZ + o]);
-        }
-      }
-    } else if (z >= 0 && !fail) {
-      const Plane3<T> pl = plane3(a, z);
-      if (act) {
-        const int o = (w + 1) * kBW + lane + 4;
-        const bool own = q > 0;
-        hx = hx_gen(a, cc, pl, i, j, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o], P0[EY + o], own);
-        hy = hy_gen(a, cc, pl, i, j, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1], P0[EZ + o], own);
-        hz = hz_gen(a, cc, pl, i, j, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o], P0[EX + o + kBW], P0[EX + o], own);
+        hz = hz_s<INTERIOR>(a, cc, Xo, Yo, pf, i, j, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o], P0[EX + o + kBW],
+                            P0[EX + o], own);
         if (own) {
           const int64_t c = c0 + (int64_t)z * nxy;
           a.oHx[c] = hx;
@@ -896,23 +961,24 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
           H0[St::hn + h] = hy;
           H0[2 * St::hn + h] = hz;
         }
-      } else if (w == kTY && q > 0) {
+      } else if (w == kTY && own) {
         const int ih = i0 + lane, jh = j0 - 1;  // row j0-1: Hx, Hz
+        const int jc = j0 + lane;               // column i0-1 (lanes < kTY): Hy, Hz
+        const int o = lane + 4, oc = (lane + 1) * kBW + 3, hc = (lane + 1) * kHW;
         if (jh >= 0 && ih < nx) {
-          const int o = lane + 4;
-          H0[lane + 1] = hx_gen(a, cc, pl, ih, jh, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o],
-                                P0[EY + o], false);
-          H0[2 * St::hn + lane + 1] = hz_gen(a, cc, pl, ih, jh, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o],
-                                             P0[EX + o + kBW], P0[EX + o], false);
+          H0[lane + 1] = lean ? fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o])
+                              : hx_s<INTERIOR>(a, cc, ys, pf, ih, jh, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o],
+                                               P1[EY + o], P0[EY + o], false);
+          H0[2 * St::hn + lane + 1] = hz_s<INTERIOR>(a, cc, Xo, ys, pf, ih, jh, z, P0[HZ + o], P0[EY + o + 1],
+                                                     P0[EY + o], P0[EX + o + kBW], P0[EX + o], false);
         }
-        const int jc = j0 + lane;  // column i0-1: Hy, Hz
         if (lane < kTY && i0 > 0 && jc < ny) {
-          const int o = (lane + 1) * kBW + 3;
-          const int h = (lane + 1) * kHW;
-          H0[St::hn + h] = hy_gen(a, cc2, pl, i0 - 1, jc, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1],
-                                  P0[EZ + o], false);
-          H0[2 * St::hn + h] = hz_gen(a, cc2, pl, i0 - 1, jc, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o],
-                                      P0[EX + o + kBW], P0[EX + o], false);
+          H0[St::hn + hc] = lean ? fma(-a.S, (P1[EX + oc] - P0[EX + oc]) - (P0[EZ + oc + 1] - P0[EZ + oc]),
+                                       P0[HY + oc])
+                                 : hy_s<INTERIOR>(a, cc2, Xc, pf, i0 - 1, jc, z, P0[HY + oc], P1[EX + oc],
+                                                  P0[EX + oc], P0[EZ + oc + 1], P0[EZ + oc], false);
+          H0[2 * St::hn + hc] = hz_s<INTERIOR>(a, cc2, Xc, Yc, pf, i0 - 1, jc, z, P0[HZ + oc], P0[EY + oc + 1],
+                                               P0[EY + oc], P0[EX + oc + kBW], P0[EX + oc], false);
         }
       }
     }
@@ -926,25 +992,23 @@ __global__ void __launch_bounds__(32 * (kTY + 1)) k3_staged(const Args3<T> a, co
       issue(issued);
       ++issued;
     }
-    if (act && z >= 0 && q > 0) {
+    if (act && z >= 0 && own) {
       const int o = (w + 1) * kBW + lane + 4;
       const int h = (w + 1) * kHW + lane + 1;
       const unsigned char* mt = sm + (q % kStages) * St::bytes + 6 * St::box * sizeof(T);
       const int mb = mt[w * 32 + lane];
+      const int64_t c = c0 + (int64_t)z * nxy;
+      const T hx_jm = H0[h - kHW], hz_jm = H0[2 * St::hn + h - kHW];
+      const T hy_im = H0[St::hn + h - 1], hz_im = H0[2 * St::hn + h - 1];
       T ex;
       if (lean) {
-        const int64_t c = c0 + (int64_t)z * nxy;
-        const T hx_jm = H0[h - kHW], hz_jm = H0[2 * St::hn + h - kHW];
-        const T hy_im = H0[St::hn + h - 1], hz_im = H0[2 * St::hn + h - 1];
         ex = e_update(a.m, mb & 3, P0[EX + o], (hz - hz_jm) - (hy - hy_km), a.Jx + c);
         a.oEx[c] = ex;
         a.oEy[c] = e_update(a.m, (mb >> 2) & 3, P0[EY + o], (hx - hx_km) - (hz - hz_im), a.Jy + c);
         a.oEz[c] = e_update(a.m, (mb >> 4) & 3, P0[EZ + o], (hy - hy_im) - (hx - hx_jm), a.Jz + c);
       } else {
-        const Plane3<T> pl = plane3(a, z);
-        ex = e_gen(a, cc, pl, i, j, z, c0 + (int64_t)z * nxy, P0[EX + o], P0[EY + o], P0[EZ + o], mb, hx, hy, hz,
-                   H0[h - kHW], H0[2 * St::hn + h - kHW], H0[St::hn + h - 1], H0[2 * St::hn + h - 1], hx_km, hy_km,
-                   srcv);
+        ex = e_s<INTERIOR>(a, cc, Xo, Yo, pf, i, j, z, c, P0[EX + o], P0[EY + o], P0[EZ + o], mb, hx, hy, hz, hx_jm,
+                           hz_jm, hy_im, hz_im, hx_km, hy_km, srcv);
       }
       for (int r = 0; r < npc; ++r)
         if (pk[r] == z) a.series[(int64_t)ps[r] * a.series_len + a.series_pos] = ex;
@@ -1023,6 +1087,11 @@ struct rketd_ctx3d {
   Maps3<float> maps32[2];
   Maps3<double> maps64[2];
   int* err = nullptr;
+  int2* tiles = nullptr;  // staged form: interior-column tiles, then the others
+  int n_inner = 0, n_outer = 0;
+  // the boundary-tile launch runs on a high-priority side stream, overlapping the interior one
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   size_t esz = 4;
   int64_t N = 0;
   double S = 0;
@@ -1054,6 +1123,9 @@ struct rketd_ctx3d {
   int64_t launches = 0;
   ~rketd_ctx3d() {
     for (void* p : allocs) cudaFree(p);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
   bool alloc(void** p, size_t bytes, bool state = false) {
     *p = nullptr;
@@ -1203,16 +1275,32 @@ rketd_status make_maps(rketd_ctx3d* c) {
     void* arrs[6] = {c->E[set][0], c->E[set][1], c->E[set][2], c->H[set][0], c->H[set][1], c->H[set][2]};
     for (int f = 0; f < 6; ++f)
       if (encode(&m.f[f], dt, 3, arrs[f], dims, fstr, fbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                 CU_TENSOR_MAP_SWIZZLE_NONE, (CUtensorMapL2promotion)RKETD_3D_L2PROMO,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return fail3(RKETD_ECUDA, "field tensor map");
     if (encode(&m.mat, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->mat, dims, mstr, mbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_SWIZZLE_NONE, (CUtensorMapL2promotion)RKETD_3D_L2PROMO,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail3(RKETD_ECUDA, "material tensor map");
   }
-  CK3(cudaFuncSetAttribute(k3_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+  CK3(cudaFuncSetAttribute(k3_staged<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
       "staged kernel shared memory");
+  CK3(cudaFuncSetAttribute(k3_staged<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
+  std::vector<int2> inner, outer;
+  for (int j0 = 0; j0 < g.ny; j0 += kTY)
+    for (int i0 = 0; i0 < g.nx; i0 += 32)
+      (interior_tile(i0, j0, g.nx, g.ny, g.npml, g.tfsf, g.box) ? inner : outer).push_back(make_int2(i0, j0));
+  c->n_inner = (int)inner.size();
+  c->n_outer = (int)outer.size();
+  inner.insert(inner.end(), outer.begin(), outer.end());
+  if (!c->alloc((void**)&c->tiles, sizeof(int2) * inner.size())) return fail3(RKETD_ENOMEM, "tile list");
+  CK3(cudaMemcpy(c->tiles, inner.data(), sizeof(int2) * inner.size(), cudaMemcpyHostToDevice), "tile list");
+  int prio_lo = 0, prio_hi = 0;
+  CK3(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "stream priorities");
+  CK3(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi), "side stream");
+  CK3(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "fork event");
+  CK3(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "join event");
   return RKETD_OK;
 }
 
@@ -1232,12 +1320,32 @@ rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
   const dim3 block(32, ty);
   const dim3 grid((c->g.nx + 31) / 32, (c->g.ny + ty - 1) / ty, nzc + (c->g.tfsf ? 1 : 0));
   const dim3 sblock(32, kTY + 1);
-  const dim3 sgrid((c->g.nx + 31) / 32, (c->g.ny + kTY - 1) / kTY, nzc + (c->g.tfsf ? 1 : 0));
+  const int line = c->g.tfsf ? 1 : 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     Args3<T> a = args3<T>(c);
     if (c->staged) {
-      k3_staged<T><<<sgrid, sblock, Stage3<T>::smem, c->stream>>>(a, maps<T>(c, c->cur), c->err);
-      c->launches += 1;
+      // boundary tiles (CPML, faces: more work per cell) first, on the high-priority side
+      // stream, so that they run alongside the interior tiles; joined back afterwards
+      const bool forked = c->n_inner && (c->n_outer + line);
+      if (forked) {
+        CK3(cudaEventRecord(c->fork, c->stream), "fork");
+        CK3(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
+      }
+      if (c->n_outer + line) {
+        k3_staged<T, false><<<dim3(c->n_outer + line, 1, nzc), sblock, Stage3<T>::smem,
+                              forked ? c->side : c->stream>>>(a, maps<T>(c, c->cur), c->tiles + c->n_inner,
+                                                              c->n_outer, c->err);
+        c->launches += 1;
+      }
+      if (c->n_inner) {
+        k3_staged<T, true><<<dim3(c->n_inner, 1, nzc), sblock, Stage3<T>::smem, c->stream>>>(
+            a, maps<T>(c, c->cur), c->tiles, c->n_inner, c->err);
+        c->launches += 1;
+      }
+      if (forked) {
+        CK3(cudaEventRecord(c->join, c->side), "join");
+        CK3(cudaStreamWaitEvent(c->stream, c->join, 0), "join");
+      }
       c->cur = 1 - c->cur;
     } else if (c->fused) {
       k3_fused<T><<<grid, block, 0, c->stream>>>(a);

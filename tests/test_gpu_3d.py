@@ -117,6 +117,20 @@ def test_staged_form_agrees_bitwise_with_the_plain_form(prec, grid):
         assert np.array_equal(out[0][1], X)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_staged_form_with_a_sheet_source_matches_the_3d_oracle(prec):
+    """The sheet plane crosses interior and boundary tiles; no TF/SF box."""
+    p = _lean()
+    p.tfsf = False
+    p.sheet_k = 12
+    p.steps = 150
+    st, _ = oracle.run3d(p)
+    with rk.Context3D(p, prec, variant="staged", k_chunk=9) as ctx:
+        ctx.step(p.steps)
+        worst = _compare(ctx, st, p, prec)
+    print(prec, "staged sheet", {k: f"{v:.2e}" for k, v in worst.items()})
+
+
 def test_staged_form_is_refused_where_it_does_not_apply():
     p = _ragged()  # nx = 37
     with pytest.raises(rk.RketdError) as ei:
