@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--adj-profiles", type=int, default=64)
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D sphere measurement")
+    ap.add_argument("--n3d", type=int, default=512)
+    ap.add_argument("--steps3d", type=int, default=4000)
     ap.add_argument("--batch-slabs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=20000)
     return ap.parse_args()
@@ -380,6 +383,59 @@ def measure_adjoint(args):
                                 "chain rule"}
 
 
+def bytes_3d(p, esz=4):
+    """Algorithmic DRAM bytes per cell-update of the 3D step: E and H read once and written
+    once (6 components), the material byte, the carried current read and written where the
+    component is plasma, and each CPML memory read and written where its grading is active
+    (2 npml positions per axis)."""
+    n = p.nx * p.ny * p.nz
+    m = np.asarray(p.mat)
+    plasma = int(np.count_nonzero(m & 3) + np.count_nonzero((m >> 2) & 3) + np.count_nonzero((m >> 4) & 3))
+    per_axis = {0: p.ny * p.nz, 1: p.nx * p.nz, 2: p.nx * p.ny}
+    axes = [1, 2, 2, 0, 0, 1] * 2  # derivative axis of the 12 memories (E side, then H side)
+    psi = sum(2 * p.npml * per_axis[ax] for ax in axes if not (p.periodic_xy and ax < 2))
+    total = 12 * esz * n + n + 2 * esz * plasma + 2 * esz * psi
+    return total / n, {"fields": 12 * esz, "material": 1, "current": 2 * esz * plasma / n, "cpml": 2 * esz * psi / n}
+
+
+def measure_3d(args, hbm_peak):
+    """3D scale-up: 512^3 Yee grid, Drude sphere of radius 120 cells, TF/SF plane wave, 16-cell
+    CPML on every face, 4000 FP32 steps, 2 probes x 200 frequencies; one run = reset, all steps
+    and the spectra read back, timed with CUDA events on the context's stream."""
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+    from paper_1709_00821_gb300 import workloads as wl
+
+    p = wl.sphere_problem(n=args.n3d, steps=args.steps3d)
+    cells = p.nx * p.ny * p.nz
+    bpc, parts = bytes_3d(p)
+    with rk.Context3D(p, "f32") as ctx:
+        ctx.step(20)
+        ctx.sync()
+        ctx.reset()
+        torch.cuda.synchronize()
+        l0 = ctx.launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(p.steps)
+        e1.record()
+        X = ctx.spectra()
+        ms = e0.elapsed_time(e1)
+        launches = ctx.launches - l0
+    rate = cells * p.steps / (ms / 1e3)
+    ach = bpc * rate / 1e9
+    return {"workload": f"{p.nx}^3 Yee grid, sphere r={args.n3d * 120 // 512} cells (wp=2pi*40 GHz, nu=2e10), "
+                        f"TF/SF plane wave, {p.npml}-cell CPML all faces, {p.steps} steps, FP32, "
+                        f"{len(p.probes)} probes x {len(p.freq_hz)} freqs",
+            "value": rate / 1e9, "unit": UNIT, "ms_per_step": ms / p.steps, "gpu_launches_per_run": launches,
+            "variant": "staged (TMA-fed fused H+E/J step; interior and boundary tile kernels)",
+            "spectra_finite": bool(np.all(np.isfinite(X))),
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                         "bytes_per_cell_update": bpc, "bytes_parts": parts,
+                         "traffic": None, "note": "whole step (both tile kernels run concurrently)"}}
+
+
 def run_ours(args):
     import torch
 
@@ -510,6 +566,11 @@ def run_ours(args):
     if not args.no_adjoint:
         adjoint = measure_adjoint(args)
 
+    # ---- 3D scale-up (config 5) ----
+    cfg3d = None
+    if not args.no_3d:
+        cfg3d = measure_3d(args, hbm_peak)
+
     # ---- ragged batch (config 3) ----
     batch = None
     if not args.no_batch:
@@ -535,7 +596,8 @@ def run_ours(args):
                                       f"{opt_used['tb_steps']} steps/pass, {opt_used['warps_per_block']} warps/CTA",
                            "precision": "FP32 fields, FP64-derived delta coefficients, Kahan-FP32 DFT blocks into FP64"},
                 "roofline": roofline, "hbm_roofline_effective": hbm_eff, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks, "fp64": fp64, "batched": batch, "adjoint": adjoint, "cpu_baseline": cpu,
+                "clocks": clocks, "fp64": fp64, "batched": batch, "adjoint": adjoint, "sphere_3d": cfg3d,
+                "cpu_baseline": cpu,
                 "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None}
         print(json.dumps(line), flush=True)
     if dist is not None:

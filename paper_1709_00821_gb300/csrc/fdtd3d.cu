@@ -1083,7 +1083,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 struct rketd_ctx3d {
   rketd_grid3d g{};
-  int prec = 0, fused = 1, staged = 0, cur = 0, kc = 16;
+  int prec = 0, fused = 1, staged = 0, cur = 0, kc = 32;
   Maps3<float> maps32[2];
   Maps3<double> maps64[2];
   int* err = nullptr;
