@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--adj-profiles", type=int, default=64)
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D sphere measurement")
+    ap.add_argument("--only-3d", action="store_true", help="run only the 3D sphere measurement (profiling)")
     ap.add_argument("--n3d", type=int, default=512)
     ap.add_argument("--steps3d", type=int, default=4000)
     ap.add_argument("--batch-slabs", type=int, default=4096)
@@ -398,6 +399,20 @@ def bytes_3d(p, esz=4):
     return total / n, {"fields": 12 * esz, "material": 1, "current": 2 * esz * plasma / n, "cpml": 2 * esz * psi / n}
 
 
+def traffic_record_3d(n):
+    """DRAM bytes per step of the 3D staged form from the committed ncu summary
+    (profiles/k3_staged_traffic.json), valid while fdtd3d.cu is unchanged and for its grid size."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k3_staged_traffic.json")))
+        sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "fdtd3d.cu"), "rb")
+                             .read()).hexdigest()
+        if rec.get("fdtd3d_sha256") == sha and rec.get("cells") == n ** 3:
+            return rec
+    except Exception:
+        pass
+    return None
+
+
 def measure_3d(args, hbm_peak):
     """3D scale-up: 512^3 Yee grid, Drude sphere of radius 120 cells, TF/SF plane wave, 16-cell
     CPML on every face, 4000 FP32 steps, 2 probes x 200 frequencies; one run = reset, all steps
@@ -425,6 +440,7 @@ def measure_3d(args, hbm_peak):
         launches = ctx.launches - l0
     rate = cells * p.steps / (ms / 1e3)
     ach = bpc * rate / 1e9
+    trec = traffic_record_3d(args.n3d)
     return {"workload": f"{p.nx}^3 Yee grid, sphere r={args.n3d * 120 // 512} cells (wp=2pi*40 GHz, nu=2e10), "
                         f"TF/SF plane wave, {p.npml}-cell CPML all faces, {p.steps} steps, FP32, "
                         f"{len(p.probes)} probes x {len(p.freq_hz)} freqs",
@@ -433,7 +449,11 @@ def measure_3d(args, hbm_peak):
             "spectra_finite": bool(np.all(np.isfinite(X))),
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "bytes_per_cell_update": bpc, "bytes_parts": parts,
-                         "traffic": None, "note": "whole step (both tile kernels run concurrently)"}}
+                         "traffic": trec["dram_bytes_per_step"] if trec else None,
+                         "traffic_per_cell_update": trec["dram_bytes_per_cell_update"] if trec else None,
+                         "traffic_source": "ncu dram bytes of both tile kernels per step "
+                                           "(profiles/k3_staged_traffic.json)",
+                         "note": "the unit is one step: two tile kernels run concurrently on two streams"}}
 
 
 def run_ours(args):
@@ -606,6 +626,12 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.only_3d:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_3d(args, peaks()[0])), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
