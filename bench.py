@@ -581,17 +581,17 @@ def run_ours(args):
                 "hbm_effective": {"achieved": B_ALG["f64"] * krate64 / 1e9, "peak": hbm_peak,
                                   "frac": B_ALG["f64"] * krate64 / 1e9 / hbm_peak, "unit": "GB/s"}}
 
-    # ---- adjoint (config 4) ----
+    # ---- adjoint: 64 trainable profiles of 65536 cells ----
     adjoint = None
     if not args.no_adjoint:
         adjoint = measure_adjoint(args)
 
-    # ---- 3D scale-up (config 5) ----
+    # ---- 3D scale-up: 512^3 plasma sphere ----
     cfg3d = None
     if not args.no_3d:
         cfg3d = measure_3d(args, hbm_peak)
 
-    # ---- ragged batch (config 3) ----
+    # ---- ragged batch: 4096 slabs ----
     batch = None
     if not args.no_batch:
         batch = measure_batch(args)
