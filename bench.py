@@ -441,12 +441,24 @@ def measure_3d(args, hbm_peak):
     rate = cells * p.steps / (ms / 1e3)
     ach = bpc * rate / 1e9
     trec = traffic_record_3d(args.n3d)
+    cpu = None
+    if not args.no_cpu:
+        # the 3D oracle (serial C, FP64) on a bounded sample: the same recipe on a 256^3 grid
+        import oracle
+
+        q = wl.sphere_problem(n=256, steps=3)
+        t0 = time.perf_counter()
+        oracle.run3d(q)
+        dt_cpu = time.perf_counter() - t0
+        cpu = {"value": q.nx * q.ny * q.nz * q.steps / dt_cpu / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the same sphere recipe on a 256^3 grid, 3 steps (serial FP64 3D oracle, allocation "
+                         f"included), {dt_cpu:.1f} s"}
     return {"workload": f"{p.nx}^3 Yee grid, sphere r={args.n3d * 120 // 512} cells (wp=2pi*40 GHz, nu=2e10), "
                         f"TF/SF plane wave, {p.npml}-cell CPML all faces, {p.steps} steps, FP32, "
                         f"{len(p.probes)} probes x {len(p.freq_hz)} freqs",
             "value": rate / 1e9, "unit": UNIT, "ms_per_step": ms / p.steps, "gpu_launches_per_run": launches,
             "variant": "staged (TMA-fed fused H+E/J step; interior and boundary tile kernels)",
-            "spectra_finite": bool(np.all(np.isfinite(X))),
+            "spectra_finite": bool(np.all(np.isfinite(X))), "cpu_baseline": cpu,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                          "bytes_per_cell_update": bpc, "bytes_parts": parts,
                          "traffic": trec["dram_bytes_per_step"] if trec else None,
