@@ -538,6 +538,9 @@ enum : unsigned {
   kPHyP = 256u, kPHyM = 512u, kPExP = 1024u, kPExM = 2048u, kPLean = 4096u
 };
 constexpr int kXN = 34;  // x coefficient entries of a tile: i0-1 .. i0+32
+// work kinds of the staged form: general (boundary tiles), interior tiles in the middle z range
+// (no CPML memory at all), interior tiles in the two z CPML slabs
+enum { kModeGen = 0, kModeMid = 1, kModeZc = 2 };
 
 template <typename T>
 struct Stage3 {
@@ -682,26 +685,73 @@ __device__ __forceinline__ void plane_facts(const Args3<T>& a, int z, PlaneS<T>*
     }
   }
   if (z == a.sheet_k) f |= kPSheet;
-  if (z >= np + 1 && z <= nz - np - 2 && z != a.sheet_k && !(a.tfsf && (z == a.k0 - 1 || z == a.k0 || z == a.k1)))
+  if (!(f & (kPFzH | kPFzE)) && (f & kPVk) && (f & kPZin) && z != a.sheet_k &&
+      !(a.tfsf && (z == a.k0 - 1 || z == a.k0 || z == a.k1)))
     f |= kPLean;
   p->f = f;
 }
 
-// CPML stretch with the coefficients given (stretch() once its flag is known to be set)
+// CPML stretch with the coefficients and the old memory value given (stretch() once its flag
+// is known to be set)
 template <typename T>
-__device__ __forceinline__ T stretch_c(T b, T cc, T ki, T dv, const T* pin, T* pout) {
-  const T p = fma(b, __ldg(pin), cc * dv);
+__device__ __forceinline__ T stretch_c(T b, T cc, T ki, T dv, T psi, T* pout) {
+  const T p = fma(b, psi, cc * dv);
   if (pout) *pout = p;
   return fma(dv, ki, p);
+}
+
+// The CPML memories one cell reads in one plane, loaded at the top of the plane's iteration so
+// that their latency overlaps the copy wait and the H phase: H side in the order of psiH, E side
+// in the order of psiE (slots that the cell does not use are left alone).
+template <typename T>
+struct Pre3 {
+  T h[6], e[6];
+};
+
+template <bool INTERIOR, bool ESIDE, typename T>
+__device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int i, int j, int z, int zz, unsigned hmask,
+                                          Pre3<T>& v) {
+  if (zz >= 0) {
+    const int64_t o = zz_off(a, i, j, zz);
+    if (hmask & 2u) v.h[1] = __ldg(a.psiH[1] + o);
+    if (hmask & 4u) v.h[2] = __ldg(a.psiH[2] + o);
+    if constexpr (ESIDE) {
+      if (hmask & 64u) {
+        v.e[1] = a.psiE[1][o];
+        v.e[2] = a.psiE[2][o];
+      }
+    }
+  }
+  if constexpr (!INTERIOR) {
+    if (c.zx >= 0) {
+      const int64_t o = zx_off(a, j, z, c.zx);
+      if (hmask & 8u) v.h[3] = __ldg(a.psiH[3] + o);
+      if (hmask & 16u) v.h[4] = __ldg(a.psiH[4] + o);
+      if constexpr (ESIDE) {
+        v.e[3] = a.psiE[3][o];
+        v.e[4] = a.psiE[4][o];
+      }
+    }
+    if (c.zy >= 0) {
+      const int64_t o = zy_off(a, i, z, c.zy);
+      if (hmask & 1u) v.h[0] = __ldg(a.psiH[0] + o);
+      if (hmask & 32u) v.h[5] = __ldg(a.psiH[5] + o);
+      if constexpr (ESIDE) {
+        v.e[0] = a.psiE[0][o];
+        v.e[5] = a.psiE[5][o];
+      }
+    }
+  }
 }
 
 // The staged form's updates of one cell: the operations of hx_core .. e_cell for non-periodic
 // grids, with the per-cell facts (c), the x and y coefficient rows of the tile (X, Y: H b, c,
 // 1/kappa, flag, then E) and the plane's facts (p). INTERIOR: the cell is clear of the x/y
 // CPML and of the TF/SF x/y faces, so those terms are left out at compile time.
-template <bool INTERIOR, typename T>
-__device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneS<T>& p, int i, int j,
-                                  int k, T h, T ez_jp, T ez, T ey_kp, T ey, bool own) {
+template <int MODE, typename T>
+__device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneS<T>& p, const Pre3<T>& v,
+                                  int i, int j, int k, T h, T ez_jp, T ez, T ey_kp, T ey, bool own) {
+  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
   if (!(p.f & kPVk)) return h;
   if constexpr (!INTERIOR)
     if (!c.vj) return h;
@@ -710,40 +760,42 @@ __device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, 
   if constexpr (!INTERIOR)
     if (c.fyH) {
       const int64_t o = zy_off(a, i, k, c.zy);
-      cy = stretch_c(Y[0], Y[1], Y[2], cy, a.psiH[0] + o, own ? a.opsiH[0] + o : nullptr);
+      cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[0], own ? a.opsiH[0] + o : nullptr);
     }
-  if (p.f & kPFzH) {
+  if (ZC && (p.f & kPFzH)) {
     const int64_t o = zz_off(a, i, j, p.zz);
-    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, a.psiH[1] + o, own ? a.opsiH[1] + o : nullptr);
+    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[1], own ? a.opsiH[1] + o : nullptr);
   }
   return fma(-a.S, cy - cz, h);
 }
 
-template <bool INTERIOR, typename T>
-__device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneS<T>& p, int i, int j,
-                                  int k, T h, T ex_kp, T ex, T ez_ip, T ez, bool own) {
+template <int MODE, typename T>
+__device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneS<T>& p, const Pre3<T>& v,
+                                  int i, int j, int k, T h, T ex_kp, T ex, T ez_ip, T ez, bool own) {
+  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
   if (!(p.f & kPVk)) return h;
   if constexpr (!INTERIOR)
     if (!c.vi) return h;
   T cz = ex_kp - ex;
   T cx = ez_ip - ez;
-  if (p.f & kPFzH) {
+  if (ZC && (p.f & kPFzH)) {
     const int64_t o = zz_off(a, i, j, p.zz);
-    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, a.psiH[2] + o, own ? a.opsiH[2] + o : nullptr);
+    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[2], own ? a.opsiH[2] + o : nullptr);
   }
   if constexpr (!INTERIOR)
     if (c.fxH) {
       const int64_t o = zx_off(a, j, k, c.zx);
-      cx = stretch_c(X[0], X[1], X[2], cx, a.psiH[3] + o, own ? a.opsiH[3] + o : nullptr);
+      cx = stretch_c(X[0], X[1], X[2], cx, v.h[3], own ? a.opsiH[3] + o : nullptr);
     }
-  T v = fma(-a.S, cz - cx, h);
-  if (c.tf_xy && (p.f & (kPHyP | kPHyM))) v = fma((p.f & kPHyP) ? a.S : -a.S, p.ei_hy, v);
-  return v;
+  T r = fma(-a.S, cz - cx, h);
+  if (c.tf_xy && (p.f & (kPHyP | kPHyM))) r = fma((p.f & kPHyP) ? a.S : -a.S, p.ei_hy, r);
+  return r;
 }
 
-template <bool INTERIOR, typename T>
+template <int MODE, typename T>
 __device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
-                                  int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex, bool own) {
+                                  const Pre3<T>& v, int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex, bool own) {
+  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
   if constexpr (INTERIOR) {
     return fma(-a.S, (ey_ip - ey) - (ex_jp - ex), h);
   } else {
@@ -752,34 +804,35 @@ __device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, 
     T cy = ex_jp - ex;
     if (c.fxH) {
       const int64_t o = zx_off(a, j, k, c.zx);
-      cx = stretch_c(X[0], X[1], X[2], cx, a.psiH[4] + o, own ? a.opsiH[4] + o : nullptr);
+      cx = stretch_c(X[0], X[1], X[2], cx, v.h[4], own ? a.opsiH[4] + o : nullptr);
     }
     if (c.fyH) {
       const int64_t o = zy_off(a, i, k, c.zy);
-      cy = stretch_c(Y[0], Y[1], Y[2], cy, a.psiH[5] + o, own ? a.opsiH[5] + o : nullptr);
+      cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[5], own ? a.opsiH[5] + o : nullptr);
     }
-    T v = fma(-a.S, cx - cy, h);
-    if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) v = fma(c.sg_hz > 0 ? a.S : -a.S, p.ei_hz, v);
-    return v;
+    T r = fma(-a.S, cx - cy, h);
+    if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) r = fma(c.sg_hz > 0 ? a.S : -a.S, p.ei_hz, r);
+    return r;
   }
 }
 
 // E and J of one cell; returns the new Ex. The CPML memories of E are updated in place.
-template <bool INTERIOR, typename T>
-__device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p, int i,
-                                 int j, int k, int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy, T hz, T hx_jm,
-                                 T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
+template <int MODE, typename T>
+__device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
+                                 const Pre3<T>& v, int i, int j, int k, int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy,
+                                 T hz, T hx_jm, T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
+  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
   const bool zin = p.f & kPZin;
   if (zin && (INTERIOR || c.ex_xy)) {
     T cy = hz - hz_jm, cz = hy - hy_km;
     if constexpr (!INTERIOR)
       if (c.fyE) {
         T* q = a.psiE[0] + zy_off(a, i, k, c.zy);
-        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, q, q);
+        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[0], q);
       }
-    if (p.f & kPFzE) {
+    if (ZC && (p.f & kPFzE)) {
       T* q = a.psiE[1] + zz_off(a, i, j, p.zz);
-      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, q, q);
+      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[1], q);
     }
     ex = e_update(a.m, mb & 3, ex, cy - cz, a.Jx + ci);
     if (c.tf_xy && (p.f & (kPExP | kPExM))) ex = fma((p.f & kPExP) ? a.S : -a.S, p.hi_ex, ex);
@@ -788,14 +841,14 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
   a.oEx[ci] = ex;
   if (zin && (INTERIOR || c.ey_xy)) {
     T cz = hx - hx_km, cx = hz - hz_im;
-    if (p.f & kPFzE) {
+    if (ZC && (p.f & kPFzE)) {
       T* q = a.psiE[2] + zz_off(a, i, j, p.zz);
-      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, q, q);
+      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[2], q);
     }
     if constexpr (!INTERIOR)
       if (c.fxE) {
         T* q = a.psiE[3] + zx_off(a, j, k, c.zx);
-        cx = stretch_c<T>(X[4], X[5], X[6], cx, q, q);
+        cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[3], q);
       }
     ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + ci);
   }
@@ -805,11 +858,11 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
     if constexpr (!INTERIOR) {
       if (c.fxE) {
         T* q = a.psiE[4] + zx_off(a, j, k, c.zx);
-        cx = stretch_c<T>(X[4], X[5], X[6], cx, q, q);
+        cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[4], q);
       }
       if (c.fyE) {
         T* q = a.psiE[5] + zy_off(a, i, k, c.zy);
-        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, q, q);
+        cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[5], q);
       }
     }
     ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + ci);
@@ -832,21 +885,23 @@ __host__ __device__ __forceinline__ bool interior_tile(int i0, int j0, int nx, i
   return true;
 }
 
-// One launch handles the tiles of one kind (INTERIOR or not), blockIdx.x indexing the tile
-// list and blockIdx.z the chunk of kc planes; with TF/SF the boundary launch carries one more
-// block (blockIdx.x == n_tiles, blockIdx.z == 0) that advances the incident line.
-template <typename T, bool INTERIOR>
+// One launch handles the work items of one kind: an item is a tile origin (i0, j0) and a range
+// of planes [kb, ke). MODE kModeGen: boundary tiles, general path. kModeMid: interior tiles in
+// the middle z range (lean planes, TF/SF z faces, sheet). kModeZc: interior tiles in the z CPML
+// slabs. With TF/SF the general launch carries one more block (blockIdx.x == n_items) that
+// advances the incident line.
+template <typename T, int MODE>
 __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? 4 : 2))
-    k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp, const int2* __restrict__ tiles, int n_tiles,
+    k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp, const int4* __restrict__ items, int n_items,
               int* err) {
+  constexpr bool INTERIOR = MODE != kModeGen;
   using St = Stage3<T>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int nx = a.nx, ny = a.ny;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = w * 32 + lane, nt = 32 * (kTY + 1);
   const double t = (double)(a.n0 + 1) * a.dt;
-  if ((int)blockIdx.x >= n_tiles) {  // incident line, step n -> n+1 (as the fused form)
-    if (blockIdx.z != 0) return;
+  if ((int)blockIdx.x >= n_items) {  // incident line, step n -> n+1 (as the fused form)
     const int L = a.inc_len;
     for (int m = tid; m < L - 1; m += nt) a.oHi[m] = fma(-a.S, a.Ei[m + 1] - a.Ei[m], a.Hi[m]);
     if (tid == 0) a.oHi[L - 1] = a.Hi[L - 1];
@@ -860,9 +915,9 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
     }
     return;
   }
-  const int2 tile = tiles[blockIdx.x];
-  const int i0 = tile.x, j0 = tile.y;
-  const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  const int4 item = items[blockIdx.x];
+  const int i0 = item.x, j0 = item.y;
+  const int kb = item.z, ke = item.w;
   const int NP = ke - kb + 2;  // planes kb-1 .. ke
   T* hn = (T*)(sm + St::off_hn);
   uint64_t* bar = (uint64_t*)(sm + St::off_bar);
@@ -875,7 +930,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
     const int s = q % kStages;
     unsigned char* dst = sm + s * St::bytes;
     const int z = kb - 1 + q;
-    plane_facts(a, z, facts(q));  // published to the consumers by the mbarrier arrival below
+    if constexpr (MODE != kModeMid) plane_facts(a, z, facts(q));  // published by the mbarrier arrival below
     mbar_expect_tx(&bar[s], St::tx);
     for (int f = 0; f < 6; ++f) tma_load3(dst + f * St::box * sizeof(T), &mp.f[f], i0 - 4, j0 - 1, z, &bar[s]);
     tma_load3(dst + 6 * St::box * sizeof(T), &mp.mat, i0, j0, z, &bar[s]);
@@ -926,6 +981,22 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
   bool fail = false, bad = false;  // fail: this thread's wait gave up; bad: some thread's did
   for (int q = 0; q + 1 < NP; ++q) {
     const int z = kb - 1 + q;
+    // CPML memories of this plane. Boundary tiles (most cells inside the CPML) issue the loads
+    // before the waits (own cell, or the halo cells); interior tiles, where only the z CPML
+    // planes need them, load them in their non-lean branch.
+    Pre3<T> pv, pc;
+    const int zz = z >= 0 ? zone(z, a.nz, a.np) : -1;
+    if constexpr (MODE != kModeMid) {
+      if (z >= 0) {
+        if (act)
+          prefetch3<INTERIOR, true>(a, cc, i, j, z, zz, 0x7fu, pv);
+        else if (w == kTY && q > 0) {
+          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<INTERIOR, false>(a, cc, i0 + lane, j0 - 1, z, zz, 0x33u, pv);
+          if (lane < kTY && i0 > 0 && j0 + lane < ny)
+            prefetch3<INTERIOR, false>(a, cc2, i0 - 1, j0 + lane, z, zz, 0x3cu, pc);
+        }
+      }
+    }
     if (q == 0) fail |= !mbar_wait(&bar[0], 0);
     fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1);
     const T* P0 = plane(q);
@@ -935,7 +1006,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
     T hx = T(0), hy = T(0), hz = T(0);
     // lean plane: interior-column tile and z clear of the z CPML, the TF/SF z faces and the
     // sheet: the bare Eq. 14 / Eq. 13 / Eq. 11 arithmetic (decided uniformly per block)
-    const bool lean = INTERIOR && (pf.f & kPLean);
+    constexpr bool lean = MODE == kModeMid;  // every plane of a middle item is a bare update
     const bool own = q > 0;
     if (z >= 0 && !fail) {
       if (act) {
@@ -944,12 +1015,12 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
           hx = fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o]);
           hy = fma(-a.S, (P1[EX + o] - P0[EX + o]) - (P0[EZ + o + 1] - P0[EZ + o]), P0[HY + o]);
         } else {
-          hx = hx_s<INTERIOR>(a, cc, Yo, pf, i, j, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o],
+          hx = hx_s<MODE>(a, cc, Yo, pf, pv, i, j, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o], P1[EY + o],
                               P0[EY + o], own);
-          hy = hy_s<INTERIOR>(a, cc, Xo, pf, i, j, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1],
+          hy = hy_s<MODE>(a, cc, Xo, pf, pv, i, j, z, P0[HY + o], P1[EX + o], P0[EX + o], P0[EZ + o + 1],
                               P0[EZ + o], own);
         }
-        hz = hz_s<INTERIOR>(a, cc, Xo, Yo, pf, i, j, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o], P0[EX + o + kBW],
+        hz = hz_s<MODE>(a, cc, Xo, Yo, pf, pv, i, j, z, P0[HZ + o], P0[EY + o + 1], P0[EY + o], P0[EX + o + kBW],
                             P0[EX + o], own);
         if (own) {
           const int64_t c = c0 + (int64_t)z * nxy;
@@ -967,17 +1038,17 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
         const int o = lane + 4, oc = (lane + 1) * kBW + 3, hc = (lane + 1) * kHW;
         if (jh >= 0 && ih < nx) {
           H0[lane + 1] = lean ? fma(-a.S, (P0[EZ + o + kBW] - P0[EZ + o]) - (P1[EY + o] - P0[EY + o]), P0[HX + o])
-                              : hx_s<INTERIOR>(a, cc, ys, pf, ih, jh, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o],
+                              : hx_s<MODE>(a, cc, ys, pf, pv, ih, jh, z, P0[HX + o], P0[EZ + o + kBW], P0[EZ + o],
                                                P1[EY + o], P0[EY + o], false);
-          H0[2 * St::hn + lane + 1] = hz_s<INTERIOR>(a, cc, Xo, ys, pf, ih, jh, z, P0[HZ + o], P0[EY + o + 1],
+          H0[2 * St::hn + lane + 1] = hz_s<MODE>(a, cc, Xo, ys, pf, pv, ih, jh, z, P0[HZ + o], P0[EY + o + 1],
                                                      P0[EY + o], P0[EX + o + kBW], P0[EX + o], false);
         }
         if (lane < kTY && i0 > 0 && jc < ny) {
           H0[St::hn + hc] = lean ? fma(-a.S, (P1[EX + oc] - P0[EX + oc]) - (P0[EZ + oc + 1] - P0[EZ + oc]),
                                        P0[HY + oc])
-                                 : hy_s<INTERIOR>(a, cc2, Xc, pf, i0 - 1, jc, z, P0[HY + oc], P1[EX + oc],
+                                 : hy_s<MODE>(a, cc2, Xc, pf, pc, i0 - 1, jc, z, P0[HY + oc], P1[EX + oc],
                                                   P0[EX + oc], P0[EZ + oc + 1], P0[EZ + oc], false);
-          H0[2 * St::hn + hc] = hz_s<INTERIOR>(a, cc2, Xc, Yc, pf, i0 - 1, jc, z, P0[HZ + oc], P0[EY + oc + 1],
+          H0[2 * St::hn + hc] = hz_s<MODE>(a, cc2, Xc, Yc, pf, pc, i0 - 1, jc, z, P0[HZ + oc], P0[EY + oc + 1],
                                                P0[EY + oc], P0[EX + oc + kBW], P0[EX + oc], false);
         }
       }
@@ -1007,7 +1078,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB 
         a.oEy[c] = e_update(a.m, (mb >> 2) & 3, P0[EY + o], (hx - hx_km) - (hz - hz_im), a.Jy + c);
         a.oEz[c] = e_update(a.m, (mb >> 4) & 3, P0[EZ + o], (hy - hy_im) - (hx - hx_jm), a.Jz + c);
       } else {
-        ex = e_s<INTERIOR>(a, cc, Xo, Yo, pf, i, j, z, c, P0[EX + o], P0[EY + o], P0[EZ + o], mb, hx, hy, hz, hx_jm,
+        ex = e_s<MODE>(a, cc, Xo, Yo, pf, pv, i, j, z, c, P0[EX + o], P0[EY + o], P0[EZ + o], mb, hx, hy, hz, hx_jm,
                            hz_jm, hy_im, hz_im, hx_km, hy_km, srcv);
       }
       for (int r = 0; r < npc; ++r)
@@ -1087,8 +1158,8 @@ struct rketd_ctx3d {
   Maps3<float> maps32[2];
   Maps3<double> maps64[2];
   int* err = nullptr;
-  int2* tiles = nullptr;  // staged form: interior-column tiles, then the others
-  int n_inner = 0, n_outer = 0;
+  int4* items = nullptr;  // staged form work items: middle, z-CPML, general (tile origin, plane range)
+  int n_mid = 0, n_zc = 0, n_gen = 0;
   // the boundary-tile launch runs on a high-priority side stream, overlapping the interior one
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -1251,6 +1322,70 @@ const Maps3<double>& maps<double>(const rketd_ctx3d* c, int set) {
   return c->maps64[set];
 }
 
+// Work items of the staged form for the current k chunk. Interior-column tiles split their z
+// range into the two z CPML slabs [0, np+1) and [nz-np-1, nz) plus one-plane items at the TF/SF
+// z faces and the sheet (kModeZc), and the rest of the middle, cut into chunks of kc planes
+// (kModeMid: every plane there is a bare update); the other tiles cover all planes in chunks of
+// kc (kModeGen).
+rketd_status plan_items3(rketd_ctx3d* c) {
+  const rketd_grid3d& g = c->g;
+  const int np = g.npml, nz = g.nz, kc = c->kc;
+  // chunk-major order: the tiles of one plane range are neighbours in the launch, so the halo
+  // rows that adjacent tiles share are read while still in L2
+  std::vector<int2> inner, outer;
+  for (int j0 = 0; j0 < g.ny; j0 += kTY)
+    for (int i0 = 0; i0 < g.nx; i0 += 32)
+      (interior_tile(i0, j0, g.nx, g.ny, np, g.tfsf, g.box) ? inner : outer).push_back(make_int2(i0, j0));
+  std::vector<int4> mid, zc, gen;
+  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, 0, np + 1));
+  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, nz - np - 1, nz));
+  // Planes of the middle range that need more than the bare update go to z-general items: the
+  // TF/SF z faces (Hy at k0-1 and k1, Ex at k0 and k1), the sheet, and the plane after each Hy
+  // face, because a middle item starting there would compute its first plane's k-1 neighbour
+  // (the corrected Hy of the face plane) without the correction. Consecutive ones form one item.
+  const int lo_all = np + 1, hi_all = nz - np - 1;
+  std::vector<int> special;
+  if (g.tfsf) special.insert(special.end(), {g.box[4] - 1, g.box[4], g.box[5], g.box[5] + 1});
+  if (g.sheet_k >= 0) special.push_back(g.sheet_k);
+  std::sort(special.begin(), special.end());
+  special.erase(std::unique(special.begin(), special.end()), special.end());
+  special.erase(std::remove_if(special.begin(), special.end(), [&](int z) { return z < lo_all || z >= hi_all; }),
+                special.end());
+  std::vector<std::pair<int, int>> runs;  // [start, end) of consecutive special planes
+  for (const int z : special) {
+    if (!runs.empty() && runs.back().second == z) runs.back().second = z + 1;
+    else runs.push_back({z, z + 1});
+  }
+  for (const auto& r : runs)
+    for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, r.first, r.second));
+  int lo = lo_all;
+  for (size_t ridx = 0; ridx <= runs.size(); ++ridx) {
+    const int hi = ridx < runs.size() ? runs[ridx].first : hi_all;
+    for (int kb = lo; kb < hi; kb += kc)
+      for (const int2 t : inner) mid.push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, hi)));
+    if (ridx < runs.size()) lo = runs[ridx].second;
+  }
+  for (int kb = 0; kb < nz; kb += kc)
+    for (const int2 t : outer) gen.push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, nz)));
+  c->n_mid = (int)mid.size();
+  c->n_zc = (int)zc.size();
+  c->n_gen = (int)gen.size();
+  std::vector<int4> all;
+  all.reserve(mid.size() + zc.size() + gen.size());
+  all.insert(all.end(), mid.begin(), mid.end());
+  all.insert(all.end(), zc.begin(), zc.end());
+  all.insert(all.end(), gen.begin(), gen.end());
+  if (c->items) {
+    cudaFree(c->items);
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void*)c->items), c->allocs.end());
+    c->items = nullptr;
+  }
+  if (!c->alloc((void**)&c->items, sizeof(int4) * std::max<size_t>(all.size(), 1)))
+    return fail3(RKETD_ENOMEM, "work items");
+  CK3(cudaMemcpy(c->items, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice), "work items");
+  return RKETD_OK;
+}
+
 // tensor maps of the staged form: a 3D box of kBW x kBH x 1 values of each field array and
 // 32 x kTY x 1 bytes of the material array, zero fill outside the grid
 template <typename T>
@@ -1283,19 +1418,14 @@ rketd_status make_maps(rketd_ctx3d* c) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail3(RKETD_ECUDA, "material tensor map");
   }
-  CK3(cudaFuncSetAttribute(k3_staged<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeGen>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
       "staged kernel shared memory");
-  CK3(cudaFuncSetAttribute(k3_staged<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeMid>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
       "staged kernel shared memory");
-  std::vector<int2> inner, outer;
-  for (int j0 = 0; j0 < g.ny; j0 += kTY)
-    for (int i0 = 0; i0 < g.nx; i0 += 32)
-      (interior_tile(i0, j0, g.nx, g.ny, g.npml, g.tfsf, g.box) ? inner : outer).push_back(make_int2(i0, j0));
-  c->n_inner = (int)inner.size();
-  c->n_outer = (int)outer.size();
-  inner.insert(inner.end(), outer.begin(), outer.end());
-  if (!c->alloc((void**)&c->tiles, sizeof(int2) * inner.size())) return fail3(RKETD_ENOMEM, "tile list");
-  CK3(cudaMemcpy(c->tiles, inner.data(), sizeof(int2) * inner.size(), cudaMemcpyHostToDevice), "tile list");
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeZc>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
+  rketd_status st = plan_items3(c);
+  if (st) return st;
   int prio_lo = 0, prio_hi = 0;
   CK3(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "stream priorities");
   CK3(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi), "side stream");
@@ -1326,20 +1456,24 @@ rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
     if (c->staged) {
       // boundary tiles (CPML, faces: more work per cell) first, on the high-priority side
       // stream, so that they run alongside the interior tiles; joined back afterwards
-      const bool forked = c->n_inner && (c->n_outer + line);
+      const bool forked = (c->n_mid + c->n_zc) && (c->n_gen + line);
       if (forked) {
         CK3(cudaEventRecord(c->fork, c->stream), "fork");
         CK3(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
       }
-      if (c->n_outer + line) {
-        k3_staged<T, false><<<dim3(c->n_outer + line, 1, nzc), sblock, Stage3<T>::smem,
-                              forked ? c->side : c->stream>>>(a, maps<T>(c, c->cur), c->tiles + c->n_inner,
-                                                              c->n_outer, c->err);
+      const Maps3<T>& mp = maps<T>(c, c->cur);
+      if (c->n_gen + line) {
+        k3_staged<T, kModeGen><<<c->n_gen + line, sblock, Stage3<T>::smem, forked ? c->side : c->stream>>>(
+            a, mp, c->items + c->n_mid + c->n_zc, c->n_gen, c->err);
         c->launches += 1;
       }
-      if (c->n_inner) {
-        k3_staged<T, true><<<dim3(c->n_inner, 1, nzc), sblock, Stage3<T>::smem, c->stream>>>(
-            a, maps<T>(c, c->cur), c->tiles, c->n_inner, c->err);
+      if (c->n_zc) {
+        k3_staged<T, kModeZc><<<c->n_zc, sblock, Stage3<T>::smem, c->stream>>>(a, mp, c->items + c->n_mid, c->n_zc,
+                                                                             c->err);
+        c->launches += 1;
+      }
+      if (c->n_mid) {
+        k3_staged<T, kModeMid><<<c->n_mid, sblock, Stage3<T>::smem, c->stream>>>(a, mp, c->items, c->n_mid, c->err);
         c->launches += 1;
       }
       if (forked) {
@@ -1625,6 +1759,10 @@ rketd_status rketd_sync_3d(rketd_ctx3d* c) {
 rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* c, int32_t k_chunk) {
   if (!c || k_chunk < 1 || k_chunk > 4096) return fail3(RKETD_EINVAL, "k_chunk must be 1..4096");
   c->kc = k_chunk;
+  if (c->staged) {
+    CK3(cudaStreamSynchronize(c->stream), "k chunk");
+    return plan_items3(c);
+  }
   return RKETD_OK;
 }
 
