@@ -890,8 +890,16 @@ __host__ __device__ __forceinline__ bool interior_tile(int i0, int j0, int nx, i
 // the middle z range (lean planes, TF/SF z faces, sheet). kModeZc: interior tiles in the z CPML
 // slabs. With TF/SF the general launch carries one more block (blockIdx.x == n_items) that
 // advances the incident line.
+// Resident blocks per SM the register budget is set for: the shared memory allows 4 (FP32) or
+// 2 (FP64); the general kind, which runs beside the others and needs more registers for its
+// CPML terms, is given 3 in FP32.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(32 * (kTY + 1), RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? 4 : 2))
+constexpr int staged_min_blocks() {
+  return RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? (MODE == kModeGen ? 3 : 4) : 2);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>()))
     k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp, const int4* __restrict__ items, int n_items,
               int* err) {
   constexpr bool INTERIOR = MODE != kModeGen;
