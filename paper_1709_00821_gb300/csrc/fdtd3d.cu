@@ -540,7 +540,17 @@ enum : unsigned {
 constexpr int kXN = 34;  // x coefficient entries of a tile: i0-1 .. i0+32
 // work kinds of the staged form: general (boundary tiles), interior tiles in the middle z range
 // (no CPML memory at all), interior tiles in the two z CPML slabs
-enum { kModeGen = 0, kModeMid = 1, kModeZc = 2 };
+enum { kModeGen = 0, kModeMid = 1, kModeZc = 2, kModeGenX = 3, kModeGenY = 4, kModeGenF = 5 };
+// what each kind of work item can meet: the x / y CPML with the x / y domain edges, the z CPML,
+// and the TF/SF x/y faces (kModeGen*: boundary tiles split by the CPML axes they reach; kModeGenF
+// tiles reach only TF/SF x/y faces)
+template <int MODE>
+struct Kind3 {
+  static constexpr bool interior = MODE == kModeMid || MODE == kModeZc;
+  static constexpr bool xc = MODE == kModeGen || MODE == kModeGenX;
+  static constexpr bool yc = MODE == kModeGen || MODE == kModeGenY;
+  static constexpr bool zc = MODE != kModeMid;
+};
 
 template <typename T>
 struct Stage3 {
@@ -708,7 +718,7 @@ struct Pre3 {
   T h[6], e[6];
 };
 
-template <bool INTERIOR, bool ESIDE, typename T>
+template <bool XC, bool YC, bool ESIDE, typename T>
 __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int i, int j, int z, int zz, unsigned hmask,
                                           Pre3<T>& v) {
   if (zz >= 0) {
@@ -722,7 +732,7 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
       }
     }
   }
-  if constexpr (!INTERIOR) {
+  if constexpr (XC) {
     if (c.zx >= 0) {
       const int64_t o = zx_off(a, j, z, c.zx);
       if (hmask & 8u) v.h[3] = __ldg(a.psiH[3] + o);
@@ -732,6 +742,8 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
         v.e[4] = a.psiE[4][o];
       }
     }
+  }
+  if constexpr (YC) {
     if (c.zy >= 0) {
       const int64_t o = zy_off(a, i, z, c.zy);
       if (hmask & 1u) v.h[0] = __ldg(a.psiH[0] + o);
@@ -746,23 +758,24 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
 
 // The staged form's updates of one cell: the operations of hx_core .. e_cell for non-periodic
 // grids, with the per-cell facts (c), the x and y coefficient rows of the tile (X, Y: H b, c,
-// 1/kappa, flag, then E) and the plane's facts (p). INTERIOR: the cell is clear of the x/y
-// CPML and of the TF/SF x/y faces, so those terms are left out at compile time.
+// 1/kappa, flag, then E) and the plane's facts (p). The kind of work item (Kind3) leaves out at
+// compile time the terms its cells cannot meet: the x or y CPML with the x or y domain edges, the
+// z CPML, the TF/SF x/y faces.
 template <int MODE, typename T>
 __device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneS<T>& p, const Pre3<T>& v,
                                   int i, int j, int k, T h, T ez_jp, T ez, T ey_kp, T ey, bool own) {
-  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
+  using K = Kind3<MODE>;
   if (!(p.f & kPVk)) return h;
-  if constexpr (!INTERIOR)
+  if constexpr (K::yc)
     if (!c.vj) return h;
   T cy = ez_jp - ez;
   T cz = ey_kp - ey;
-  if constexpr (!INTERIOR)
+  if constexpr (K::yc)
     if (c.fyH) {
       const int64_t o = zy_off(a, i, k, c.zy);
       cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[0], own ? a.opsiH[0] + o : nullptr);
     }
-  if (ZC && (p.f & kPFzH)) {
+  if (K::zc && (p.f & kPFzH)) {
     const int64_t o = zz_off(a, i, j, p.zz);
     cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[1], own ? a.opsiH[1] + o : nullptr);
   }
@@ -772,17 +785,17 @@ __device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, 
 template <int MODE, typename T>
 __device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneS<T>& p, const Pre3<T>& v,
                                   int i, int j, int k, T h, T ex_kp, T ex, T ez_ip, T ez, bool own) {
-  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
+  using K = Kind3<MODE>;
   if (!(p.f & kPVk)) return h;
-  if constexpr (!INTERIOR)
+  if constexpr (K::xc)
     if (!c.vi) return h;
   T cz = ex_kp - ex;
   T cx = ez_ip - ez;
-  if (ZC && (p.f & kPFzH)) {
+  if (K::zc && (p.f & kPFzH)) {
     const int64_t o = zz_off(a, i, j, p.zz);
     cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[2], own ? a.opsiH[2] + o : nullptr);
   }
-  if constexpr (!INTERIOR)
+  if constexpr (K::xc)
     if (c.fxH) {
       const int64_t o = zx_off(a, j, k, c.zx);
       cx = stretch_c(X[0], X[1], X[2], cx, v.h[3], own ? a.opsiH[3] + o : nullptr);
@@ -795,21 +808,26 @@ __device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, 
 template <int MODE, typename T>
 __device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
                                   const Pre3<T>& v, int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex, bool own) {
-  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
-  if constexpr (INTERIOR) {
+  using K = Kind3<MODE>;
+  if constexpr (K::interior) {
     return fma(-a.S, (ey_ip - ey) - (ex_jp - ex), h);
   } else {
-    if (!c.vi || !c.vj) return h;
+    if constexpr (K::xc)
+      if (!c.vi) return h;
+    if constexpr (K::yc)
+      if (!c.vj) return h;
     T cx = ey_ip - ey;
     T cy = ex_jp - ex;
-    if (c.fxH) {
-      const int64_t o = zx_off(a, j, k, c.zx);
-      cx = stretch_c(X[0], X[1], X[2], cx, v.h[4], own ? a.opsiH[4] + o : nullptr);
-    }
-    if (c.fyH) {
-      const int64_t o = zy_off(a, i, k, c.zy);
-      cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[5], own ? a.opsiH[5] + o : nullptr);
-    }
+    if constexpr (K::xc)
+      if (c.fxH) {
+        const int64_t o = zx_off(a, j, k, c.zx);
+        cx = stretch_c(X[0], X[1], X[2], cx, v.h[4], own ? a.opsiH[4] + o : nullptr);
+      }
+    if constexpr (K::yc)
+      if (c.fyH) {
+        const int64_t o = zy_off(a, i, k, c.zy);
+        cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[5], own ? a.opsiH[5] + o : nullptr);
+      }
     T r = fma(-a.S, cx - cy, h);
     if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) r = fma(c.sg_hz > 0 ? a.S : -a.S, p.ei_hz, r);
     return r;
@@ -821,16 +839,17 @@ template <int MODE, typename T>
 __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
                                  const Pre3<T>& v, int i, int j, int k, int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy,
                                  T hz, T hx_jm, T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
-  [[maybe_unused]] constexpr bool INTERIOR = MODE != kModeGen, ZC = MODE != kModeMid;
+  using K = Kind3<MODE>;
   const bool zin = p.f & kPZin;
-  if (zin && (INTERIOR || c.ex_xy)) {
+  constexpr bool edges = K::xc || K::yc;  // only then can x or y decide that a component is not updated
+  if (zin && (!edges || c.ex_xy)) {
     T cy = hz - hz_jm, cz = hy - hy_km;
-    if constexpr (!INTERIOR)
+    if constexpr (K::yc)
       if (c.fyE) {
         T* q = a.psiE[0] + zy_off(a, i, k, c.zy);
         cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[0], q);
       }
-    if (ZC && (p.f & kPFzE)) {
+    if (K::zc && (p.f & kPFzE)) {
       T* q = a.psiE[1] + zz_off(a, i, j, p.zz);
       cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[1], q);
     }
@@ -839,13 +858,13 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
   }
   if (p.f & kPSheet) ex = ex + srcv;
   a.oEx[ci] = ex;
-  if (zin && (INTERIOR || c.ey_xy)) {
+  if (zin && (!edges || c.ey_xy)) {
     T cz = hx - hx_km, cx = hz - hz_im;
-    if (ZC && (p.f & kPFzE)) {
+    if (K::zc && (p.f & kPFzE)) {
       T* q = a.psiE[2] + zz_off(a, i, j, p.zz);
       cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[2], q);
     }
-    if constexpr (!INTERIOR)
+    if constexpr (K::xc)
       if (c.fxE) {
         T* q = a.psiE[3] + zx_off(a, j, k, c.zx);
         cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[3], q);
@@ -853,20 +872,20 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
     ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + ci);
   }
   a.oEy[ci] = ey;
-  if ((p.f & kPZlast) && (INTERIOR || c.ez_xy)) {
+  if ((p.f & kPZlast) && (!edges || c.ez_xy)) {
     T cx = hy - hy_im, cy = hx - hx_jm;
-    if constexpr (!INTERIOR) {
+    if constexpr (K::xc)
       if (c.fxE) {
         T* q = a.psiE[4] + zx_off(a, j, k, c.zx);
         cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[4], q);
       }
+    if constexpr (K::yc)
       if (c.fyE) {
         T* q = a.psiE[5] + zy_off(a, i, k, c.zy);
         cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[5], q);
       }
-    }
     ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + ci);
-    if constexpr (!INTERIOR)
+    if constexpr (!K::interior)
       if (c.sg_ez && (p.f & kPTfEz)) ez = fma(c.sg_ez < 0 ? -a.S : a.S, p.hi_ez, ez);
   }
   a.oEz[ci] = ez;
@@ -886,23 +905,25 @@ __host__ __device__ __forceinline__ bool interior_tile(int i0, int j0, int nx, i
 }
 
 // One launch handles the work items of one kind: an item is a tile origin (i0, j0) and a range
-// of planes [kb, ke). MODE kModeGen: boundary tiles, general path. kModeMid: interior tiles in
-// the middle z range (lean planes, TF/SF z faces, sheet). kModeZc: interior tiles in the z CPML
-// slabs. With TF/SF the general launch carries one more block (blockIdx.x == n_items) that
-// advances the incident line.
+// of planes [kb, ke). kModeGen, kModeGenX, kModeGenY, kModeGenF: boundary tiles (reaching the x
+// and y CPML, the x CPML only, the y CPML only, only TF/SF x/y faces), general path. kModeMid:
+// interior tiles in the middle z range, bare updates. kModeZc: interior tiles in the z CPML slabs
+// and at the TF/SF z faces and the sheet. With TF/SF the kModeGen launch carries one more block
+// (blockIdx.x == n_items) that advances the incident line.
 // Resident blocks per SM the register budget is set for: the shared memory allows 4 (FP32) or
 // 2 (FP64); the general kind, which runs beside the others and needs more registers for its
 // CPML terms, is given 3 in FP32.
 template <typename T, int MODE>
 constexpr int staged_min_blocks() {
-  return RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? (MODE == kModeGen ? 3 : 4) : 2);
+  return RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? (Kind3<MODE>::interior ? 4 : 3) : 2);
 }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>()))
     k3_staged(const Args3<T> a, const __grid_constant__ Maps3<T> mp, const int4* __restrict__ items, int n_items,
               int* err) {
-  constexpr bool INTERIOR = MODE != kModeGen;
+  using K = Kind3<MODE>;
+  constexpr bool INTERIOR = K::interior;
   using St = Stage3<T>;
   extern __shared__ __align__(128) unsigned char sm[];
   const int nx = a.nx, ny = a.ny;
@@ -997,11 +1018,11 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     if constexpr (MODE != kModeMid) {
       if (z >= 0) {
         if (act)
-          prefetch3<INTERIOR, true>(a, cc, i, j, z, zz, 0x7fu, pv);
+          prefetch3<K::xc, K::yc, true>(a, cc, i, j, z, zz, 0x7fu, pv);
         else if (w == kTY && q > 0) {
-          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<INTERIOR, false>(a, cc, i0 + lane, j0 - 1, z, zz, 0x33u, pv);
+          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, false>(a, cc, i0 + lane, j0 - 1, z, zz, 0x33u, pv);
           if (lane < kTY && i0 > 0 && j0 + lane < ny)
-            prefetch3<INTERIOR, false>(a, cc2, i0 - 1, j0 + lane, z, zz, 0x3cu, pc);
+            prefetch3<K::xc, K::yc, false>(a, cc2, i0 - 1, j0 + lane, z, zz, 0x3cu, pc);
         }
       }
     }
@@ -1166,8 +1187,8 @@ struct rketd_ctx3d {
   Maps3<float> maps32[2];
   Maps3<double> maps64[2];
   int* err = nullptr;
-  int4* items = nullptr;  // staged form work items: middle, z-CPML, general (tile origin, plane range)
-  int n_mid = 0, n_zc = 0, n_gen = 0;
+  int4* items = nullptr;  // staged form work items (tile origin, plane range), by kind
+  int n_mid = 0, n_zc = 0, n_gen[4] = {};  // general kinds: x and y, x only, y only, faces only
   // the boundary-tile launch runs on a high-priority side stream, overlapping the interior one
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
@@ -1340,11 +1361,18 @@ rketd_status plan_items3(rketd_ctx3d* c) {
   const int np = g.npml, nz = g.nz, kc = c->kc;
   // chunk-major order: the tiles of one plane range are neighbours in the launch, so the halo
   // rows that adjacent tiles share are read while still in L2
-  std::vector<int2> inner, outer;
+  std::vector<int2> inner, outer[4];
+  const auto touches = [&](int lo, int hi, int N) { return lo <= np || hi >= N - np - 1; };  // CPML zone or edge
   for (int j0 = 0; j0 < g.ny; j0 += kTY)
-    for (int i0 = 0; i0 < g.nx; i0 += 32)
-      (interior_tile(i0, j0, g.nx, g.ny, np, g.tfsf, g.box) ? inner : outer).push_back(make_int2(i0, j0));
-  std::vector<int4> mid, zc, gen;
+    for (int i0 = 0; i0 < g.nx; i0 += 32) {
+      if (interior_tile(i0, j0, g.nx, g.ny, np, g.tfsf, g.box)) {
+        inner.push_back(make_int2(i0, j0));
+      } else {
+        const bool xc = touches(i0 - 1, i0 + 31, g.nx), yc = touches(j0 - 1, j0 + kTY - 1, g.ny);
+        outer[xc && yc ? 0 : (xc ? 1 : (yc ? 2 : 3))].push_back(make_int2(i0, j0));
+      }
+    }
+  std::vector<int4> mid, zc, gen[4];
   for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, 0, np + 1));
   for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, nz - np - 1, nz));
   // Planes of the middle range that need more than the bare update go to z-general items: the
@@ -1373,16 +1401,17 @@ rketd_status plan_items3(rketd_ctx3d* c) {
       for (const int2 t : inner) mid.push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, hi)));
     if (ridx < runs.size()) lo = runs[ridx].second;
   }
-  for (int kb = 0; kb < nz; kb += kc)
-    for (const int2 t : outer) gen.push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, nz)));
+  for (int kind = 0; kind < 4; ++kind)
+    for (int kb = 0; kb < nz; kb += kc)
+      for (const int2 t : outer[kind]) gen[kind].push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, nz)));
   c->n_mid = (int)mid.size();
   c->n_zc = (int)zc.size();
-  c->n_gen = (int)gen.size();
-  std::vector<int4> all;
-  all.reserve(mid.size() + zc.size() + gen.size());
-  all.insert(all.end(), mid.begin(), mid.end());
+  std::vector<int4> all(mid);
   all.insert(all.end(), zc.begin(), zc.end());
-  all.insert(all.end(), gen.begin(), gen.end());
+  for (int kind = 0; kind < 4; ++kind) {
+    c->n_gen[kind] = (int)gen[kind].size();
+    all.insert(all.end(), gen[kind].begin(), gen[kind].end());
+  }
   if (c->items) {
     cudaFree(c->items);
     c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void*)c->items), c->allocs.end());
@@ -1432,6 +1461,12 @@ rketd_status make_maps(rketd_ctx3d* c) {
       "staged kernel shared memory");
   CK3(cudaFuncSetAttribute(k3_staged<T, kModeZc>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
       "staged kernel shared memory");
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeGenX>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeGenY>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
+  CK3(cudaFuncSetAttribute(k3_staged<T, kModeGenF>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
+      "staged kernel shared memory");
   rketd_status st = plan_items3(c);
   if (st) return st;
   int prio_lo = 0, prio_hi = 0;
@@ -1464,15 +1499,32 @@ rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
     if (c->staged) {
       // boundary tiles (CPML, faces: more work per cell) first, on the high-priority side
       // stream, so that they run alongside the interior tiles; joined back afterwards
-      const bool forked = (c->n_mid + c->n_zc) && (c->n_gen + line);
+      const int n_gen_all = c->n_gen[0] + c->n_gen[1] + c->n_gen[2] + c->n_gen[3];
+      const bool forked = (c->n_mid + c->n_zc) && (n_gen_all + line);
       if (forked) {
         CK3(cudaEventRecord(c->fork, c->stream), "fork");
         CK3(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
       }
       const Maps3<T>& mp = maps<T>(c, c->cur);
-      if (c->n_gen + line) {
-        k3_staged<T, kModeGen><<<c->n_gen + line, sblock, Stage3<T>::smem, forked ? c->side : c->stream>>>(
-            a, mp, c->items + c->n_mid + c->n_zc, c->n_gen, c->err);
+      cudaStream_t gs = forked ? c->side : c->stream;
+      const int4* gi = c->items + c->n_mid + c->n_zc;
+      if (c->n_gen[0] + line) {  // the incident line rides with this launch
+        k3_staged<T, kModeGen><<<c->n_gen[0] + line, sblock, Stage3<T>::smem, gs>>>(a, mp, gi, c->n_gen[0], c->err);
+        c->launches += 1;
+      }
+      gi += c->n_gen[0];
+      if (c->n_gen[1]) {
+        k3_staged<T, kModeGenX><<<c->n_gen[1], sblock, Stage3<T>::smem, gs>>>(a, mp, gi, c->n_gen[1], c->err);
+        c->launches += 1;
+      }
+      gi += c->n_gen[1];
+      if (c->n_gen[2]) {
+        k3_staged<T, kModeGenY><<<c->n_gen[2], sblock, Stage3<T>::smem, gs>>>(a, mp, gi, c->n_gen[2], c->err);
+        c->launches += 1;
+      }
+      gi += c->n_gen[2];
+      if (c->n_gen[3]) {
+        k3_staged<T, kModeGenF><<<c->n_gen[3], sblock, Stage3<T>::smem, gs>>>(a, mp, gi, c->n_gen[3], c->err);
         c->launches += 1;
       }
       if (c->n_zc) {

@@ -90,11 +90,22 @@ def _lean():
                      [(48, 20, 5), (60, 25, 36), (50, 18, 20)], freqs, 200)
 
 
-@pytest.mark.parametrize("grid", ["ragged16", "lean"])
+def _faces():
+    """The lean grid with the TF/SF box's x face (i = 40) and y face (Hz at j = 16) crossing
+    tiles that are clear of the CPML, so those tiles take the faces-only boundary path."""
+    p = _lean()
+    p.box = (40, 87, 17, 33, 7, 32)
+    return p
+
+
+GRIDS3 = {"ragged16": _ragged16, "lean": _lean, "faces": _faces}
+
+
+@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces"])
 @pytest.mark.parametrize("k_chunk", [0, 7, 45])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_staged_form_matches_the_3d_oracle(prec, k_chunk, grid):
-    p = _ragged16() if grid == "ragged16" else _lean()
+    p = GRIDS3[grid]()
     st, _ = oracle.run3d(p)
     with rk.Context3D(p, prec, variant="staged", k_chunk=k_chunk) as ctx:
         ctx.step(100)
@@ -103,10 +114,10 @@ def test_staged_form_matches_the_3d_oracle(prec, k_chunk, grid):
     print(prec, "staged", k_chunk, {k: f"{v:.2e}" for k, v in worst.items()})
 
 
-@pytest.mark.parametrize("grid", ["ragged16", "lean"])
+@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_staged_form_agrees_bitwise_with_the_plain_form(prec, grid):
-    p = _ragged16() if grid == "ragged16" else _lean()
+    p = GRIDS3[grid]()
     out = []
     for variant, kc in (("plain", 0), ("staged", 0), ("staged", 3), ("auto", 0)):
         with rk.Context3D(p, prec, variant=variant, k_chunk=kc) as ctx:
