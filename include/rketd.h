@@ -319,7 +319,7 @@ rketd_status rketd_get_spectra_3d(rketd_ctx3d* ctx, double* re, double* im);
  * up (its fields are then not valid). */
 rketd_status rketd_sync_3d(rketd_ctx3d* ctx);
 
-/* Sets the number of z planes (1..4096) one thread block advances per step (default 32).
+/* Sets the number of z planes (1..4096) one thread block advances per step (default 64).
  * A tuning knob: results do not depend on it. */
 rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* ctx, int32_t k_chunk);
 

@@ -511,6 +511,9 @@ __global__ void __launch_bounds__(256) k3_fused(const Args3<T> a) {
 #ifndef RKETD_3D_L2PROMO
 #define RKETD_3D_L2PROMO 2  // L2 promotion of the staged copies: 0 none, 1 64 B, 2 128 B, 3 256 B
 #endif
+#ifndef RKETD_3D_KC_GEN
+#define RKETD_3D_KC_GEN 0  // planes per boundary-tile item; 0: the context's k chunk
+#endif
 #ifndef RKETD_3D_MINB
 #define RKETD_3D_MINB 0  // 0: resident blocks per SM that the shared memory allows (4 FP32, 2 FP64)
 #endif
@@ -1183,7 +1186,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 struct rketd_ctx3d {
   rketd_grid3d g{};
-  int prec = 0, fused = 1, staged = 0, cur = 0, kc = 32;
+  int prec = 0, fused = 1, staged = 0, cur = 0, kc = 64;
   Maps3<float> maps32[2];
   Maps3<double> maps64[2];
   int* err = nullptr;
@@ -1401,9 +1404,10 @@ rketd_status plan_items3(rketd_ctx3d* c) {
       for (const int2 t : inner) mid.push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, hi)));
     if (ridx < runs.size()) lo = runs[ridx].second;
   }
+  const int kcg = RKETD_3D_KC_GEN > 0 ? RKETD_3D_KC_GEN : kc;
   for (int kind = 0; kind < 4; ++kind)
-    for (int kb = 0; kb < nz; kb += kc)
-      for (const int2 t : outer[kind]) gen[kind].push_back(make_int4(t.x, t.y, kb, std::min(kb + kc, nz)));
+    for (int kb = 0; kb < nz; kb += kcg)
+      for (const int2 t : outer[kind]) gen[kind].push_back(make_int4(t.x, t.y, kb, std::min(kb + kcg, nz)));
   c->n_mid = (int)mid.size();
   c->n_zc = (int)zc.size();
   std::vector<int4> all(mid);
