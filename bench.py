@@ -271,6 +271,11 @@ def measure_batch(args):
     cells = b.total_cells
     cu = cells * b.steps
     ctx = rk.Context(b.slabs, "f32")
+    # tile shape (cells per lane, steps per pass, warps per block) picked by the library's
+    # autotuner on this batch (state saved and restored around the trials)
+    t_tune = time.perf_counter()
+    ctx.autotune(4)
+    t_tune = time.perf_counter() - t_tune
     P = ctx.n_slabs * ctx.n_probes * len(ctx.freq)
     xr = torch.empty(P, dtype=torch.float64, device="cuda")
     xi = torch.empty(P, dtype=torch.float64, device="cuda")
@@ -320,7 +325,8 @@ def measure_batch(args):
     return {"workload": f"{len(b.slabs)} slabs, {cells} cells, {b.steps} steps, FP32, Mur, 2 probes x 200 freqs",
             "value": cu / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_run": ms, "gpu_launches_per_run": launches,
             "graph": "one CUDA graph per run (captured on the first run)",
-            "variant": f"tiled K={opts['cells_per_lane']}, {opts['tb_steps']} steps/pass",
+            "variant": f"tiled K={opts['cells_per_lane']}, {opts['tb_steps']} steps/pass, "
+                       f"{opts['warps_per_block']} warps/CTA (rketd_autotune, {t_tune:.1f} s)",
             "plain_all_slabs_per_launch": {"value": cu / (ms_all / 1e3) / 1e9, "ms_per_run": ms_all,
                                            "measured": f"{pre}-step prefix, scaled to {b.steps}"},
             "plain_slab_by_slab": {"value": cu / (ms_slab / 1e3) / 1e9, "ms_per_run": ms_slab,

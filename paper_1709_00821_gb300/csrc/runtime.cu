@@ -977,7 +977,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   const int Ts[] = {8, 16, 24, 32, 48, 64};
   for (int K : (c->prec == RKETD_F64 ? Ks64 : Ks32))
     for (int T : Ts)
-      for (int w : {2, 4})
+      for (int w : {1, 2, 4})
         if (32 * K - 2 * T >= 64 && opt0.dft_block % T == 0) cands.push_back({K, T, w});
   float best_ms = 1e30f;
   rketd_options best = opt0;

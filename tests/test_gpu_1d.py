@@ -227,3 +227,26 @@ def test_batch_plain_variant_matches_tiled_bitwise():
     for f1, f2 in zip(outs[1][1], outs[2][1]):
         for a, c in zip(f1, f2):
             assert np.array_equal(a, c)
+
+
+def test_autotune_keeps_the_state_and_the_results_bitwise():
+    """rketd_autotune times tile shapes on the live context and restores its state: a run tuned
+    half-way ends bitwise equal to an untuned one (every tile shape computes the same values)."""
+    b = wl.c3_batch(subset=[0, 5, 17, 99], steps=700)
+    with rk.Context(b.slabs, "f32") as c1:
+        c1.step(300)
+        c1.autotune(2)
+        assert c1.step_index == 300
+        o = c1.options()
+        assert o["variant"] == 2 and o["cells_per_lane"] in (8, 12, 16) and o["warps_per_block"] in (1, 2, 4)
+        assert o["tb_steps"] in (8, 16, 24, 32, 48, 64)
+        c1.step(400)
+        X1 = c1.spectra()
+        F1 = [c1.fields(i) for i in range(len(b.slabs))]
+    with rk.Context(b.slabs, "f32") as c2:
+        c2.step(700)
+        X2 = c2.spectra()
+        F2 = [c2.fields(i) for i in range(len(b.slabs))]
+    assert np.array_equal(X1, X2)
+    for f1, f2 in zip(F1, F2):
+        assert all(np.array_equal(u, v) for u, v in zip(f1, f2))
