@@ -250,3 +250,22 @@ def test_autotune_keeps_the_state_and_the_results_bitwise():
     assert np.array_equal(X1, X2)
     for f1, f2 in zip(F1, F2):
         assert all(np.array_equal(u, v) for u, v in zip(f1, f2))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-4)])
+def test_collisionless_and_vacuum_cells_match_the_oracle(prec, tol):
+    """nu = 0 exactly in part of the plasma (phi1 -> 1, phi2 -> 1/2), wp2 = 0 cells inside it,
+    and a zero-step call that must change nothing."""
+    s = _random_slab(1537, 4242, steps=400)
+    s.nu[: s.nz // 2] = 0.0
+    s.wp2[700:720] = 0.0
+    ref, _ = oracle.run1d(s)
+    with rk.Context(s, prec) as ctx:
+        ctx.step(0)
+        assert ctx.step_index == 0 and not np.any(ctx.fields(0)[0])
+        ctx.step(s.steps)
+        ctx.step(0)
+        X = ctx.spectra()[0]
+        E, H, J = ctx.fields(0)
+    assert rel(E, ref.E) <= tol and rel(H, ref.H) <= tol and rel(J, ref.J) <= tol
+    assert rel(X, ref.X) <= tol

@@ -269,3 +269,20 @@ def test_full_size_sphere_grid_total_field_is_the_incident_wave():
         del Ex, inside
         for n in ("Ey", "Ez"):
             assert np.abs(ctx.field(n)).max() <= 2e-5 * peak, n
+
+
+def test_grid_without_probes_steps_and_returns_fields():
+    """No probes (no DFT buffers): the step, the fields and the (empty) spectra still work, and the
+    fields equal those of the same run with probes."""
+    p = _lean()
+    p.steps = 60
+    with rk.Context3D(p, "f32") as ref:
+        ref.step(p.steps)
+        ex_ref = ref.field("Ex")
+    q = _lean()
+    q.probes = []
+    with rk.Context3D(q, "f32") as ctx:
+        ctx.step(0)
+        ctx.step(p.steps)
+        assert np.array_equal(ctx.field("Ex"), ex_ref)
+        assert ctx.spectra().shape == (0, len(q.freq_hz))
