@@ -34,10 +34,10 @@ UNIT = "Gcell-updates/s"
 WORKLOAD = ("1D long inhomogeneous Drude slab: Nz=2^24, dz=1um, Courant 0.5, 40000 steps, Epstein wp^2 ramp "
             "(wp0=2pi*50GHz, L=2mm, 5% seeded ripple), nu~U[1e9,5e10], CPML 32+32, 2 probes x 512 DFT freqs")
 B_ALG = {"f32": 32.0, "f64": 64.0}  # algorithmic bytes per cell-update: E,H,J read+write + wp2,nu read
-# FP32/FP64 arithmetic per cell-update: Eq. 14 sub + fma; Eq. 13 sub + 2 fma + sub (the carried
-# current cj J~ enters by a subtraction); Eq. 11 3 fma. Nine pipe operations, 15 flops (fma = 2).
-OPS_PER_CELL_UPDATE = 9.0
-FLOPS_PER_CELL_UPDATE = 15.0
+# Arithmetic per cell-update with the folded current G = cj J~ - da E: Eq. 14 sub + fma; Eq. 13
+# sub + fma + sub; the G recursion (Eq. 11) mul + 2 fma + add (small terms summed before G is
+# added). Nine pipe operations in either precision (13 flops, fma = 2).
+OPS_PER_CELL_UPDATE = {"f32": 9.0, "f64": 9.0}
 
 
 def parse():
@@ -525,7 +525,7 @@ def run_ours(args):
     kern_rate = cu_per_launch / avg_launch_s  # cell-updates/s inside the kernel
     clock_for_peak = 2070.0
     alu_peak = fp32_pipe_peak_tops(clock_for_peak)
-    alu_ach = OPS_PER_CELL_UPDATE * kern_rate / 1e12
+    alu_ach = OPS_PER_CELL_UPDATE["f32"] * kern_rate / 1e12
     bpc, trec = traffic_record("f32")
     roofline = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s (FP32 lane-ops)",
                 "frac": alu_ach / alu_peak,
@@ -534,7 +534,7 @@ def run_ours(args):
                            f"{opt_used['tb_steps']} steps/launch)" if opt_used.get("fp32_pairs", 0) != 2 else
                            f"k_tb<float,K={opt_used['cells_per_lane']},interior> ({opt_used['tb_steps']} steps/launch)"),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (unit counts x max clock)",
-                "ops_per_cell_update": OPS_PER_CELL_UPDATE,
+                "ops_per_cell_update": OPS_PER_CELL_UPDATE["f32"],
                 "traffic_source": "ncu dram bytes per exact cell-update (profiles/tb_kernel_traffic.json) x launch",
                 "cell_updates_per_launch": cu_per_launch, "avg_launch_ms": avg_launch_s * 1e3}
     hbm_eff = {"bound": "hbm", "achieved": B_ALG["f32"] * kern_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -591,9 +591,9 @@ def run_ours(args):
         v64 = ws * cells / (ms64 / 1e3) / 1e9
         krate64 = (k64[2] / max(k64[1], 1)) / (k64[0] / 1e3 / max(k64[1], 1))
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": 1, "warmup": 1, "dtype": "f64",
-                "roofline": {"bound": "alu", "achieved": OPS_PER_CELL_UPDATE * krate64 / 1e12,
+                "roofline": {"bound": "alu", "achieved": OPS_PER_CELL_UPDATE["f64"] * krate64 / 1e12,
                              "peak": fp64_pipe_peak_tops(), "unit": "Tops/s (FP64 pipe ops)",
-                             "frac": OPS_PER_CELL_UPDATE * krate64 / 1e12 / fp64_pipe_peak_tops(),
+                             "frac": OPS_PER_CELL_UPDATE["f64"] * krate64 / 1e12 / fp64_pipe_peak_tops(),
                              "kernel": f"k_tb<double,K={o64['cells_per_lane']},interior>",
                              "peak_source": "measured FP64 FMA-chain throughput (0.60 T DFMA/s)"},
                 "hbm_effective": {"achieved": B_ALG["f64"] * krate64 / 1e9, "peak": hbm_peak,

@@ -1,21 +1,23 @@
 // Discrete adjoint of the tiled step, for gradients of a loss of the probe spectra with
 // respect to the per-cell plasma frequency squared and collision frequency.
 //
-// Device step (rketd_internal.cuh), per interior cell, with Jc = cj J~:
+// Device step (rketd_internal.cuh), per interior cell, with the folded current G = cj J~ - da E:
 //   H'_k = H_k - S (E_{k+1} - E_k)
-//   E'_k = E_k + da E_k - cb (H'_k - H'_{k-1}) - Jc_k,   Jc'_k = Jc_k + dj Jc_k + bp E_k + cc E'_k
-// then the source (additive) and the first-order Mur ends. Its transpose, from the adjoint
-// (lE, lH, lJ) of the state after the step, with mu_k = lE_k + cc_k lJ_k:
+//   E'_k = E_k - cb (H'_k - H'_{k-1}) - G_k,   G'_k = G_k + dj G_k + bq E_k + cq E'_k
+// then the source (E' += s, and G' -= da s at the source cell: both additive) and the
+// first-order Mur ends. Its transpose, from the adjoint (lE, lH, lJ) of (E, H~, G) after the
+// step, with mu_k = lE_k + cq_k lJ_k:
 //   Mur:      lE_1 += q lE_0, pre-step E_0 gets -q lE_0, pre-step E_1 gets lE_0, lE_0 = 0 (mirror)
-//   E and J:  lJ_k <- lJ_k + dj_k lJ_k - mu_k,  lE_k <- mu_k + da_k mu_k + bp_k lJ_k
+//   E and G:  lJ_k <- lJ_k + dj_k lJ_k - mu_k,  lE_k <- mu_k + bq_k lJ_k
 //   H:        lH'_k = lH_k - cb_k mu_k + cb_{k+1} mu_{k+1}
 //             lE_k += S (lH'_k - lH'_{k-1}),  lH_k <- lH'_k
 // The loss enters through the DFT: dL/dE_p^m = sum_f (dL/dRe X cos - dL/dIm X sin)(2 pi f m dt),
 // injected at the probe cells before each transposed step. Coefficient gradients per step:
-//   d/d(da) = mu E^n, d/d(cb) = -mu (H_k - H_{k-1})^{n+1/2}, d/d(dj) = lJ Jc^n,
-//   d/d(bp) = lJ E^n, d/d(cc) = lJ E^{n+1}  (lJ, mu after the step),
+//   d/d(cb) = -mu (H_k - H_{k-1})^{n+1/2}, d/d(dj) = lJ G^n, d/d(bq) = lJ E^n,
+//   d/d(cq) = lJ E'^{n+1} (before the source), and at the source cell d/d(da) = -s^{n+1} lJ
+//   (lJ, mu after the step),
 // summed over steps from values recorded at the window cells, then taken to (wp2, nu) by the
-// derivatives of the coefficients (FP64).
+// derivatives of the coefficients (FP64; bq and cq through da, dj and the paper's bp, cc).
 #include "rketd_internal.cuh"
 #include "tile_common.cuh"
 
@@ -38,15 +40,14 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : 2) k_adj(const AdjArgs<T> a) {
   const int64_t g0 = tl.start + li0;
   const T S = a.S;
 
-  T le[K], lh[K], lj[K], da[K], cb[K], dj[K], bp[K], cc[K];
+  T le[K], lh[K], lj[K], cb[K], dj[K], bq[K], cq[K];
   load_row<T, K, EDGE>(a.lE_in + soff, g0, nzp, le);
   load_row<T, K, EDGE>(a.lH_in + soff, g0, nzp, lh);
   load_row<T, K, EDGE>(a.lJ_in + soff, g0, nzp, lj);
-  load_row<T, K, EDGE>(a.coef[kDa] + soff, g0, nzp, da);
   load_row<T, K, EDGE>(a.coef[kCb] + soff, g0, nzp, cb);
   load_row<T, K, EDGE>(a.coef[kDj] + soff, g0, nzp, dj);
-  load_row<T, K, EDGE>(a.coef[kBp] + soff, g0, nzp, bp);
-  load_row<T, K, EDGE>(a.coef[kCc] + soff, g0, nzp, cc);
+  load_row<T, K, EDGE>(a.coef[kBq] + soff, g0, nzp, bq);
+  load_row<T, K, EDGE>(a.coef[kCq] + soff, g0, nzp, cq);
 
   uint32_t mH = 0, mE = 0, mrec = 0;
   int i0 = -1, i1 = -1;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : 2) k_adj(const AdjArgs<T> a) {
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const bool upd = !EDGE || ((mE >> i) & 1u);
-      mu[i] = upd ? fma(cc[i], lj[i], le[i]) : T(0);
+      mu[i] = upd ? fma(cq[i], lj[i], le[i]) : T(0);
     }
     if (mrec) {  // record (mu, lJ) of the window cells, whole aligned groups as vectors
       T* r = a.rec + ((int64_t)s * a.rec_len + col) * 2 * a.rec_w;
@@ -132,8 +133,10 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : 2) k_adj(const AdjArgs<T> a) {
       nu_[i] = cb[i] * m;
       if (upd) {
         const T ljo = lj[i];
-        lj[i] = fma(dj[i], ljo, ljo) - m;
-        le[i] = fma(bp[i], ljo, fma(da[i], m, m));
+        // the carried lJ is added last, as G in the forward step, so that dj lJ (a few ulp of
+        // it) is not rounded away on its own
+        lj[i] = ljo - fma(-dj[i], ljo, m);
+        le[i] = fma(bq[i], ljo, m);
       } else {
         le[i] = T(0);
       }
@@ -187,15 +190,14 @@ __global__ void __launch_bounds__(128, 3) k_adj2(const AdjArgs<float> a) {
   const Tile tl = a.tiles[tid];
   const int64_t base = a.soff[tl.slab] + tl.start + lane * K;
   const int li0 = lane * K;
-  f2 le[P], lh[P], lj[P], da[P], cb[P], dj[P], bp[P], cc[P];
+  f2 le[P], lh[P], lj[P], cb[P], ndj[P], bq[P], cq[P];
   load_pairs<K>(a.lE_in + base, le, false);
   load_pairs<K>(a.lH_in + base, lh, false);
   load_pairs<K>(a.lJ_in + base, lj, false);
-  load_pairs<K>(a.coef[kDa] + base, da, false);
   load_pairs<K>(a.coef[kCb] + base, cb, false);
-  load_pairs<K>(a.coef[kDj] + base, dj, false);
-  load_pairs<K>(a.coef[kBp] + base, bp, false);
-  load_pairs<K>(a.coef[kCc] + base, cc, false);
+  load_pairs<K>(a.coef[kDj] + base, ndj, true);
+  load_pairs<K>(a.coef[kBq] + base, bq, false);
+  load_pairs<K>(a.coef[kCq] + base, cq, false);
   const f2 S2 = pk(a.S, a.S);
   for (int t = a.nsub - 1; t >= 0; --t) {
     const int col = (int)(a.n_hi - a.nsub + t - a.seg_n0);
@@ -209,10 +211,10 @@ __global__ void __launch_bounds__(128, 3) k_adj2(const AdjArgs<float> a) {
     f2 nu[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-      const f2 m = fma2(cc[p], lj[p], le[p]);
+      const f2 m = fma2(cq[p], lj[p], le[p]);
       const f2 ljo = lj[p];
-      lj[p] = sub2(fma2(dj[p], ljo, ljo), m);
-      le[p] = fma2(bp[p], ljo, fma2(da[p], m, m));
+      lj[p] = sub2(ljo, fma2(ndj[p], ljo, m));
+      le[p] = fma2(bq[p], ljo, m);
       nu[p] = mul2(cb[p], m);
     }
     // lH'_k = (lH_k - nu_k) + nu_{k+1}; the cell after pair P-1 is (B[0], next lane's A[0])
@@ -257,17 +259,21 @@ __global__ void k_seeds(const double* __restrict__ gXr, const double* __restrict
   seeds[(int64_t)p * seed_len + t] = (T)acc;
 }
 
-// recF[slab][j][3][w] holds the state after j steps of the segment (j = 0..L); recA[slab][t][2][w]
-// holds (mu, lJ) after step t. Rows start 4 cells before the window: window cell c sits at index
-// c + 4, its left neighbour (needed for dH) at c + 3; w is a multiple of 4. Each thread sums four
-// window cells over the segment.
+// recF[slab][j][3][w] holds the state (E, H~, G) after j steps of the segment (j = 0..L);
+// recA[slab][t][2][w] holds (mu, lJ) after step t. Rows start 4 cells before the window: window
+// cell c sits at index c + 4, its left neighbour (needed for dH) at c + 3; w is a multiple of 4.
+// Each thread sums four window cells over the segment. g[0] collects the source cell's
+// d/d(da) (zero elsewhere), g[1..4] d/d(cb), d/d(dj), d/d(bq), d/d(cq).
 template <typename T>
 __global__ void k_grad(const T* __restrict__ recF, const T* __restrict__ recA, int n_slabs, int w, int nwin, int L,
-                       int recF_len, double* __restrict__ g) {
+                       int recF_len, GradSource src, double* __restrict__ g) {
   const int c0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);  // first of four window cells
   const int s = blockIdx.y;
   if (c0 >= nwin || s >= n_slabs) return;
   const int k = c0 + 4;
+  // slot of the source cell among this thread's four, -1 if none
+  const int64_t sc = src.cell[s] - src.w_lo - c0;
+  const int qs = (sc >= 0 && sc < 4 && c0 + sc < nwin) ? (int)sc : -1;
   float fs[5][4] = {};
   double ds[5][4] = {};
   constexpr bool f64 = sizeof(T) == 8;
@@ -276,29 +282,33 @@ __global__ void k_grad(const T* __restrict__ recF, const T* __restrict__ recA, i
     const T* F0 = recF + ((int64_t)s * recF_len + t) * 3 * w;
     const T* F1 = F0 + 3 * w;
     const T* A = recA + ((int64_t)s * L + t) * 2 * w;
-    T mu[4], lj[4], En[4], Jn[4], H1[4], E1[4];
+    T mu[4], lj[4], En[4], Gn[4], H1[4], E1[4];
     ld4(A + k, mu);
     ld4(A + w + k, lj);
     ld4(F0 + k, En);
-    ld4(F0 + 2 * w + k, Jn);
+    ld4(F0 + 2 * w + k, Gn);
     ld4(F1 + w + k, H1);
     ld4(F1 + k, E1);
     const T hprev = F1[w + k - 1];
+    // the source value this step added to E (and folded into G) at the source cell
+    const T sv = qs >= 0 ? (T)pulse((double)(src.n0 + t + 1) * src.dt, src.t0, src.tau, src.amp) : T(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T dH = H1[q] - (q ? H1[q - 1] : hprev);
+      const T s_q = q == qs ? sv : T(0);
+      const T E1p = E1[q] - s_q;  // E'^{n+1} before the source
       if (f64) {
-        ds[0][q] += (double)mu[q] * (double)En[q];
+        ds[0][q] -= (double)s_q * (double)lj[q];
         ds[1][q] -= (double)mu[q] * (double)dH;
-        ds[2][q] += (double)lj[q] * (double)Jn[q];
+        ds[2][q] += (double)lj[q] * (double)Gn[q];
         ds[3][q] += (double)lj[q] * (double)En[q];
-        ds[4][q] += (double)lj[q] * (double)E1[q];
+        ds[4][q] += (double)lj[q] * (double)E1p;
       } else {
-        fs[0][q] = fmaf((float)mu[q], (float)En[q], fs[0][q]);
+        fs[0][q] = fmaf(-(float)s_q, (float)lj[q], fs[0][q]);
         fs[1][q] = fmaf(-(float)mu[q], (float)dH, fs[1][q]);
-        fs[2][q] = fmaf((float)lj[q], (float)Jn[q], fs[2][q]);
+        fs[2][q] = fmaf((float)lj[q], (float)Gn[q], fs[2][q]);
         fs[3][q] = fmaf((float)lj[q], (float)En[q], fs[3][q]);
-        fs[4][q] = fmaf((float)lj[q], (float)E1[q], fs[4][q]);
+        fs[4][q] = fmaf((float)lj[q], (float)E1p, fs[4][q]);
       }
     }
   }
@@ -363,17 +373,24 @@ __global__ void k_chain(const double* __restrict__ g, const double* __restrict__
   const double dcj[2] = {-cj * dD[0] / D, -0.5 * a / D - cj * dD[1] / D};
   const double dP1[2] = {p1, W * d1};        // d(W phi1)
   const double dP2[2] = {p2, W * d2};        // d(W phi2)
-  double out[2];
+  // The sums are over the folded coefficients: bq = cj bp + da a and cq = cj cc - da (bp, cc
+  // as in Eq. 11), so d/d(da) gains a g_bq - g_cq and d/d(dj) gains da g_bq.
   const int64_t wi = (int64_t)s * w + c;
   const int64_t stride = (int64_t)n_slabs * w;
+  const double da = -0.5 * W * p1 / D;
+  const double g_da = g[wi] + a * g[3 * stride + wi] - g[4 * stride + wi];
+  const double g_cb = g[stride + wi];
+  const double g_dj = g[2 * stride + wi] + da * g[3 * stride + wi];
+  const double g_bp = g[3 * stride + wi];  // coefficient of cj bp
+  const double g_cc = g[4 * stride + wi];  // coefficient of cj cc
+  double out[2];
   for (int q = 0; q < 2; ++q) {
     const double dda = -0.5 * dP1[q] / D + 0.5 * W * p1 * dD[q] / (D * D);
     const double dcb = -S * dD[q] / (D * D);
     const double ddj = q == 0 ? 0.0 : -a;
-    const double dbp = dcj[q] * W * (p1 - p2) + cj * (dP1[q] - dP2[q]);
-    const double dcc = dcj[q] * W * p2 + cj * dP2[q];
-    out[q] = g[wi] * dda + g[stride + wi] * dcb + g[2 * stride + wi] * ddj + g[3 * stride + wi] * dbp +
-             g[4 * stride + wi] * dcc;
+    const double dbp = dcj[q] * W * (p1 - p2) + cj * (dP1[q] - dP2[q]);  // d(cj bp)
+    const double dcc = dcj[q] * W * p2 + cj * dP2[q];                    // d(cj cc)
+    out[q] = g_da * dda + g_cb * dcb + g_dj * ddj + g_bp * dbp + g_cc * dcc;
   }
   gw[cell] = out[0] * dt * dt;  // dW/dwp2 = dt^2
   gn[cell] = out[1] * dt;       // dx/dnu = dt
@@ -443,16 +460,17 @@ template cudaError_t launch_seeds<double>(const double*, const double*, const do
 
 template <typename T>
 cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int w, int nwin, int L, int recF_len,
-                              double* g, cudaStream_t st) {
+                              const GradSource& src, double* g, cudaStream_t st) {
   const int threads = 64;
   const int per = 4 * threads;
-  k_grad<T><<<dim3((nwin + per - 1) / per, n_slabs), threads, 0, st>>>(recF, recA, n_slabs, w, nwin, L, recF_len, g);
+  k_grad<T><<<dim3((nwin + per - 1) / per, n_slabs), threads, 0, st>>>(recF, recA, n_slabs, w, nwin, L, recF_len, src,
+                                                                        g);
   return cudaGetLastError();
 }
-template cudaError_t launch_grad_accum<float>(const float*, const float*, int, int, int, int, int, double*,
-                                              cudaStream_t);
-template cudaError_t launch_grad_accum<double>(const double*, const double*, int, int, int, int, int, double*,
-                                               cudaStream_t);
+template cudaError_t launch_grad_accum<float>(const float*, const float*, int, int, int, int, int, const GradSource&,
+                                              double*, cudaStream_t);
+template cudaError_t launch_grad_accum<double>(const double*, const double*, int, int, int, int, int,
+                                               const GradSource&, double*, cudaStream_t);
 
 cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* nu, const int64_t* off, int n_slabs,
                               int64_t w_lo, int w, double dt, double S, double* gw, double* gn, cudaStream_t st) {

@@ -1,5 +1,6 @@
 // Per-cell RKETD update coefficients (Eqs. 11-13) and CPML grading tables, in FP64 on
-// the device (layout and the scaled current cj J~ are described in rketd_internal.cuh).
+// the device (layout and the folded current G = cj J~ - da E are described in
+// rketd_internal.cuh).
 // The FP32 path stores the same FP64 results rounded once to FP32; every coefficient is a
 // deviation from its vacuum value or a small term, so rounding keeps its relative accuracy
 // (a = e^{-nu dt} itself would lose most of a - 1 in FP32).
@@ -9,32 +10,40 @@ namespace rketd {
 namespace {
 
 // phi1(x) = (1 - e^{-x})/x and phi2(x) = (e^{-x} - 1 + x)/x^2 (x = nu dt), the integrals that
-// take the exact solution Eq. 7 with F interpolated linearly over the step to Eq. 11.
-// Below x = 0.5 both are Taylor polynomials of degree 20 (coefficients (-1)^k/(k+1)! and
-// (-1)^k/(k+2)!) evaluated by Horner's rule; the first omitted term is below 1e-27.
-// From x = 0.5 up, expm1 keeps 1 - e^{-x} exact to rounding.
-__device__ void phi12(double x, double& p1, double& p2) {
+// take the exact solution Eq. 7 with F interpolated linearly over the step to Eq. 11, and
+// psi = phi1 - (1 + e^{-x}) phi2 of the folded current's bq.
+// Below x = 0.5 all are Taylor polynomials of degree 20 (coefficients (-1)^k/(k+1)!,
+// (-1)^k/(k+2)! and, for (phi1 - 2 phi2)/x, (-1)^(k+1) (k+1)/(k+3)!) evaluated by Horner's rule;
+// the first omitted term is below 1e-27. From x = 0.5 up, expm1 keeps 1 - e^{-x} exact to rounding.
+__device__ void phi12(double x, double& p1, double& p2, double& psi) {
   if (x < 0.5) {
-    double c1[21], c2[21];
+    // psi = phi1 - (1 + a) phi2 = (phi1 - 2 phi2) + x phi1 phi2 (1 + a = 2 - x phi1), where
+    // phi1 - 2 phi2 = x sum_{k>=1} (-1)^k k/(k+2)! x^{k-1}: no cancellation as x -> 0 (psi ~ x/3)
+    double c1[21], c2[21], c3[21];
     c1[0] = 1.0;
     c2[0] = 0.5;
+    c3[0] = -1.0 / 6.0;  // k = 1 term of the sum for phi1 - 2 phi2, divided by x
 #pragma unroll
     for (int k = 1; k <= 20; ++k) {
       c1[k] = -c1[k - 1] / (double)(k + 1);
       c2[k] = -c2[k - 1] / (double)(k + 2);
+      c3[k] = -c3[k - 1] * (double)(k + 1) / ((double)k * (double)(k + 3));
     }
-    double r1 = c1[20], r2 = c2[20];
+    double r1 = c1[20], r2 = c2[20], r3 = c3[20];
 #pragma unroll
     for (int k = 19; k >= 0; --k) {
       r1 = fma(r1, x, c1[k]);
       r2 = fma(r2, x, c2[k]);
+      r3 = fma(r3, x, c3[k]);
     }
     p1 = r1;
     p2 = r2;
+    psi = x * (r3 + r1 * r2);
   } else {
     const double em = expm1(-x);
     p1 = -em / x;
     p2 = (x + em) / (x * x);
+    psi = p1 - (2.0 + em) * p2;
   }
 }
 
@@ -43,7 +52,7 @@ __global__ void k_coeffs(const double* __restrict__ wp2, const double* __restric
                          const int64_t* __restrict__ soff, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ nz, int n_slabs, int64_t n_store, double dt,
                          double S, T* __restrict__ da, T* __restrict__ cb, T* __restrict__ cj,
-                         T* __restrict__ dj, T* __restrict__ bp, T* __restrict__ cc) {
+                         T* __restrict__ dj, T* __restrict__ bq, T* __restrict__ cq) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_store;
        i += (int64_t)gridDim.x * blockDim.x) {
     // slab owning storage cell i: last s with soff[s] <= i
@@ -58,17 +67,19 @@ __global__ void k_coeffs(const double* __restrict__ wp2, const double* __restric
       w = wp2[off[lo] + k] * dt * dt;
       x = nu[off[lo] + k] * dt;
     }
-    double p1, p2;
-    phi12(x, p1, p2);
+    double p1, p2, psi;
+    phi12(x, p1, p2, psi);
     const double em = expm1(-x);  // a - 1
     const double D = 1.0 + 0.5 * w * p2;
-    const double cjd = 0.5 * (2.0 + em) / D;  // (1 + a)/(2D)
-    da[i] = (T)(-0.5 * w * p1 / D);
+    const double h = 0.5 * w / D;
+    // End cells are set by the boundary condition, never by Eq. 12, and carry no current:
+    // da = 0 there makes G = cj J~ hold for them too (the step kernels do not read da).
+    da[i] = (k == 0 || k == nz[lo] - 1) ? T(0) : (T)(-h * p1);
     cb[i] = (T)(S / D);
-    cj[i] = (T)cjd;
+    cj[i] = (T)(0.5 * (2.0 + em) / D);  // (1 + a)/(2D)
     dj[i] = (T)em;
-    bp[i] = (T)(cjd * (w * (p1 - p2)));  // acts on the carried current cj J~
-    cc[i] = (T)(cjd * (w * p2));
+    bq[i] = (T)(h * psi);                     // cj bp + da a
+    cq[i] = (T)(h * (p1 + (2.0 + em) * p2));  // cj cc - da
   }
 }
 
@@ -88,11 +99,14 @@ __global__ void k_cpml(int n, double dt, double m, double smax, double kmax, dou
     const double sigma = smax * pm;
     const double kap = 1.0 + (kmax - 1.0) * pm;
     const double alpha = amax * (1.0 - rho);
-    const double b = exp(-(sigma / kap + alpha) * dt / kEps0);
+    // the memory's decay b = e^{-(sigma/kappa + alpha) dt / eps0} lies within 1e-5 of 1 near the
+    // inner interface: it is kept as db = b - 1 (expm1 in FP64), so that an FP32 copy keeps full
+    // relative accuracy, and the update reads psi' = psi + db psi + c dv
+    const double db = expm1(-(sigma / kap + alpha) * dt / kEps0);
     const double den = sigma * kap + kap * kap * alpha;
-    const double c = (sigma > 0.0 && den > 0.0) ? sigma * (b - 1.0) / den : 0.0;
+    const double c = (sigma > 0.0 && den > 0.0) ? sigma * db / den : 0.0;
     T* tab = which == 0 ? tabE : tabH;
-    tab[i] = (T)b;
+    tab[i] = (T)db;
     tab[count + i] = (T)c;
     tab[2 * count + i] = (T)(1.0 / kap);
   }
@@ -135,18 +149,27 @@ cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double 
 namespace rketd {
 namespace {
 template <typename T>
-__global__ void k_rescale(T* J, const T* num, const T* den, int64_t n) {
+__global__ void k_rescale(T* G, const T* E, const T* cj_new, const T* cj_old, const T* da_new, const T* da_old,
+                          int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n && den[i] != T(0)) J[i] = (T)((double)J[i] * (double)num[i] / (double)den[i]);
+  // cj_old = 0: no coefficients yet (the first medium of a new context, state all zero)
+  if (i >= n || cj_old[i] == T(0)) return;
+  // J~ = (G + da E)/cj is kept across the change; G' = cj' J~ - da' E
+  const double e = (double)E[i];
+  const double jt = ((double)G[i] + (double)da_old[i] * e) / (double)cj_old[i];
+  G[i] = (T)((double)cj_new[i] * jt - (double)da_new[i] * e);
 }
 }  // namespace
 
-cudaError_t launch_rescale(int prec, void* J, const void* num, const void* den, int64_t n, cudaStream_t st) {
+cudaError_t launch_rescale(int prec, void* G, const void* E, const void* cj_new, const void* cj_old,
+                           const void* da_new, const void* da_old, int64_t n, cudaStream_t st) {
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (prec == 1)
-    k_rescale<double><<<blocks, 256, 0, st>>>((double*)J, (const double*)num, (const double*)den, n);
+    k_rescale<double><<<blocks, 256, 0, st>>>((double*)G, (const double*)E, (const double*)cj_new,
+                                              (const double*)cj_old, (const double*)da_new, (const double*)da_old, n);
   else
-    k_rescale<float><<<blocks, 256, 0, st>>>((float*)J, (const float*)num, (const float*)den, n);
+    k_rescale<float><<<blocks, 256, 0, st>>>((float*)G, (const float*)E, (const float*)cj_new, (const float*)cj_old,
+                                             (const float*)da_new, (const float*)da_old, n);
   return cudaGetLastError();
 }
 }  // namespace rketd

@@ -66,16 +66,17 @@ __global__ void k_dft32(const float* __restrict__ series, int len, int n, const 
   }
 }
 
-// Device state to SI: E as is, H = H~/eta0, J = (cj J~)/cj * eps0/dt.
+// Device state to SI: E as is, H = H~/eta0, J = (G + da E)/cj * eps0/dt (G the folded current).
 template <typename T>
-__global__ void k_gather(const T* __restrict__ E, const T* __restrict__ H, const T* __restrict__ J,
-                         const T* __restrict__ cj, int64_t off, int64_t nz, double hs, double js, double* Eo,
-                         double* Ho, double* Jo) {
+__global__ void k_gather(const T* __restrict__ E, const T* __restrict__ H, const T* __restrict__ G,
+                         const T* __restrict__ cj, const T* __restrict__ da, int64_t off, int64_t nz, double hs,
+                         double js, double* Eo, double* Ho, double* Jo) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nz) return;
-  if (Eo) Eo[k] = (double)E[off + k];
+  const double e = (double)E[off + k];
+  if (Eo) Eo[k] = e;
   if (Ho && k < nz - 1) Ho[k] = (double)H[off + k] * hs;
-  if (Jo) Jo[k] = (double)J[off + k] / (double)cj[off + k] * js;
+  if (Jo) Jo[k] = ((double)G[off + k] + (double)da[off + k] * e) / (double)cj[off + k] * js;
 }
 
 }  // namespace
@@ -110,15 +111,16 @@ cudaError_t launch_dft<float>(const float* series, int len, int n, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* J, const void* cj, int64_t off,
-                                 int64_t nz, double hs, double js, double* Eo, double* Ho, double* Jo, cudaStream_t st) {
+cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* G, const void* cj,
+                                 const void* da, int64_t off, int64_t nz, double hs, double js, double* Eo, double* Ho,
+                                 double* Jo, cudaStream_t st) {
   const unsigned blocks = (unsigned)((nz + 255) / 256);
   if (prec == 1)
-    k_gather<double><<<blocks, 256, 0, st>>>((const double*)E, (const double*)H, (const double*)J,
-                                             (const double*)cj, off, nz, hs, js, Eo, Ho, Jo);
+    k_gather<double><<<blocks, 256, 0, st>>>((const double*)E, (const double*)H, (const double*)G, (const double*)cj,
+                                             (const double*)da, off, nz, hs, js, Eo, Ho, Jo);
   else
-    k_gather<float><<<blocks, 256, 0, st>>>((const float*)E, (const float*)H, (const float*)J, (const float*)cj,
-                                            off, nz, hs, js, Eo, Ho, Jo);
+    k_gather<float><<<blocks, 256, 0, st>>>((const float*)E, (const float*)H, (const float*)G, (const float*)cj,
+                                            (const float*)da, off, nz, hs, js, Eo, Ho, Jo);
   return cudaGetLastError();
 }
 

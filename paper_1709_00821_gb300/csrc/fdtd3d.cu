@@ -55,7 +55,7 @@ struct Args3 {
   Mat3<T> m;
   int nx, ny, nz, per, kc;
   T S, q;
-  // CPML: tables [axis][E/H][b, c, 1/kappa, flag][nmax]; memories in compact face zones of
+  // CPML: tables [axis][E/H][db = b - 1, c, 1/kappa, flag][nmax]; memories in compact face zones of
   // width Z: x-derivative [k][j][Z], y-derivative [k][Z][i], z-derivative [Z][j][i]
   const T* tab;
   int nmax, np, Z;
@@ -122,12 +122,14 @@ __device__ __forceinline__ T rd(const T* p) {
   else return *p;
 }
 
-// CPML-stretched difference: psi' = b psi + c dv, result dv / kappa + psi'.
+// CPML-stretched difference: psi' = psi + db psi + c dv (db = b - 1, kept as a deviation so that
+// an FP32 copy is accurate where b is within 1e-5 of 1), result dv / kappa + psi'.
 // pout = nullptr: the new memory is not stored (a neighbour's value recomputed).
 template <bool RO, typename T>
 __device__ __forceinline__ T stretch(const T* t, int nmax, int pos, T dv, const T* pin, T* pout) {
   if (t[3 * nmax + pos] == T(0)) return dv;
-  const T p = fma(t[pos], rd<RO>(pin), t[nmax + pos] * dv);
+  const T po = rd<RO>(pin);
+  const T p = fma(t[pos], po, fma(t[nmax + pos], dv, po));
   if (pout) *pout = p;
   return fma(dv, t[2 * nmax + pos], p);
 }
@@ -250,13 +252,9 @@ template <typename T>
 __device__ __forceinline__ T e_update(const Mat3<T>& M, int m, T e, T curl, T* J) {
   if (m == 0) return fma(M.cb[0], curl, e);
   const T jc = *J;
-  T en = fma(M.da[m], e, e);
-  en = fma(M.cb[m], curl, en);
-  en = en - jc;
-  T jn = fma(M.dj[m], jc, jc);
-  jn = fma(M.bp[m], e, jn);
-  jn = fma(M.cc[m], en, jn);
-  *J = jn;
+  // the small terms are summed before the carried E and J are added (see the 1D kernels)
+  const T en = e + fma(M.cb[m], curl, fma(M.da[m], e, -jc));
+  *J = fma(M.dj[m], jc, fma(M.bp[m], e, fma(M.cc[m], en, jc)));
   return en;
 }
 
@@ -530,7 +528,7 @@ constexpr int kWaitLimit = 1 << 20;
 // issues the plane's copies and read by all threads once the stage's mbarrier completes.
 template <typename T>
 struct PlaneS {
-  T zb[2], zc[2], zk[2];  // z CPML coefficients at this plane: [0] H position z+1/2, [1] E position z
+  T zb[2], zc[2], zk[2];  // z CPML coefficients (db, c, 1/kappa) at this plane: [0] H position z+1/2, [1] E position z
   T ei_hy, ei_hz;         // step-n incident E for the Hy and Hz corrections
   T hi_ex, hi_ez;         // step-n+1/2 incident H for the Ex and Ez corrections
   int zz;                 // compact z zone
@@ -568,7 +566,7 @@ struct Stage3 {
   static constexpr int pl_bytes = ((int)sizeof(PlaneS<T>) + 15) / 16 * 16;
   static constexpr int off_xy = off_pl + kStages * pl_bytes;
   // per-tile CPML coefficients, 8 values per x (kXN) and y (kTY+1) position:
-  // H: b, c, 1/kappa, flag; E: b, c, 1/kappa, flag
+  // H: db, c, 1/kappa, flag; E: db, c, 1/kappa, flag
   static constexpr int smem = off_xy + (kXN + kTY + 1) * 8 * (int)sizeof(T);
 };
 
@@ -704,11 +702,11 @@ __device__ __forceinline__ void plane_facts(const Args3<T>& a, int z, PlaneS<T>*
   p->f = f;
 }
 
-// CPML stretch with the coefficients and the old memory value given (stretch() once its flag
-// is known to be set)
+// CPML stretch with the coefficients (db = b - 1, c, 1/kappa) and the old memory value given
+// (stretch() once its flag is known to be set)
 template <typename T>
-__device__ __forceinline__ T stretch_c(T b, T cc, T ki, T dv, T psi, T* pout) {
-  const T p = fma(b, psi, cc * dv);
+__device__ __forceinline__ T stretch_c(T db, T cc, T ki, T dv, T psi, T* pout) {
+  const T p = fma(db, psi, fma(cc, dv, psi));
   if (pout) *pout = p;
   return fma(dv, ki, p);
 }
@@ -1127,7 +1125,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
   }
 }
 
-// CPML tables: [axis][E (integer positions) / H (half positions)][b, c, 1/kappa, flag][nmax]
+// CPML tables: [axis][E (integer positions) / H (half positions)][db = b - 1, c, 1/kappa, flag][nmax]
 template <typename T>
 __global__ void k3_tables(int nx, int ny, int nz, int np, int per, double dt, double m, double smax, double kmax,
                           double amax, int nmax, T* tab) {
@@ -1151,9 +1149,9 @@ __global__ void k3_tables(int nx, int ny, int nz, int np, int per, double dt, do
         const double sigma = smax * pm;
         const double kap = 1.0 + (kmax - 1.0) * pm;
         const double alpha = amax * (1.0 - rho);
-        b = exp(-(sigma / kap + alpha) * dt / kEps0);
+        b = expm1(-(sigma / kap + alpha) * dt / kEps0);  // stored as the deviation db = b - 1
         const double den = sigma * kap + kap * kap * alpha;
-        c = (sigma > 0.0 && den > 0.0) ? sigma * (b - 1.0) / den : 0.0;
+        c = (sigma > 0.0 && den > 0.0) ? sigma * b / den : 0.0;
         ki = 1.0 / kap;
         flag = 1;
       }

@@ -17,6 +17,7 @@
 // or different host threads) would race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -50,10 +51,11 @@ rketd_status nfail(rketd_status st, const char* msg) {
 }
 
 // Same tiling as the context path: edge tiles of Ke cells per lane over [0, a) and [b, nz),
-// interior tiles of K cells per lane over [a, b). One thread writes the whole list and the
-// slab table (soff = 0, off = 0, nz, src).
-__global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int K, int Ke, int T,
-                       int* counts) {
+// interior tiles of K cells per lane over [a, b), those with index in [j_src0, j_src1) (the ones
+// that load the source cell) last. One thread writes the whole list and the slab table
+// (soff = 0, off = 0, nz, src).
+__global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int K, int Ke, int T, int64_t j_src0,
+                       int64_t j_src1, int* counts) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   table[0] = 0;
   table[1] = 0;
@@ -81,33 +83,35 @@ __global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int
     t.adj_count = 0;
     tiles[n++] = t;
   };
-  for (int64_t j = 0; j < n_int; ++j) put(a + j * W, a + (j + 1) * W, L);
+  for (int64_t j = 0; j < n_int; ++j)
+    if (j < j_src0 || j >= j_src1) put(a + j * W, a + (j + 1) * W, L);
+  for (int64_t j = j_src0; j < j_src1; ++j) put(a + j * W, a + (j + 1) * W, L);
   counts[0] = n;
   for (int64_t v = 0; v < a; v += We) put(v, v + We < a ? v + We : a, Le);
   for (int64_t v = b; v < nz; v += We) put(v, v + We < nz ? v + We : nz, Le);
   counts[1] = n - counts[0];
 }
 
-// Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, carried current
-// cj * dt/eps0 J), with the padding cells zeroed; and back.
+// Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, folded current
+// G = cj (dt/eps0) J - da E), with the padding cells zeroed; and back.
 template <typename T>
-__global__ void k_in(const T* E, const T* H, const T* J, const T* cj, T* Es, T* Hs, T* Js, int64_t nz, int64_t nzp,
-                     double hs, double js) {
+__global__ void k_in(const T* E, const T* H, const T* J, const T* cj, const T* da, T* Es, T* Hs, T* Js, int64_t nz,
+                     int64_t nzp, double hs, double js) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nzp) return;
   Es[k] = k < nz ? E[k] : T(0);
   Hs[k] = k < nz - 1 ? (T)((double)H[k] * hs) : T(0);
-  Js[k] = k < nz ? (T)((double)J[k] * js * (double)cj[k]) : T(0);
+  Js[k] = k < nz ? (T)((double)J[k] * js * (double)cj[k] - (double)da[k] * (double)E[k]) : T(0);
 }
 
 template <typename T>
-__global__ void k_out(const T* Es, const T* Hs, const T* Js, const T* cj, T* E, T* H, T* J, int64_t nz, double hs,
-                      double js) {
+__global__ void k_out(const T* Es, const T* Hs, const T* Js, const T* cj, const T* da, T* E, T* H, T* J, int64_t nz,
+                      double hs, double js) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nz) return;
   E[k] = Es[k];
   if (k < nz - 1) H[k] = (T)((double)Hs[k] * hs);
-  J[k] = (T)((double)Js[k] / (double)cj[k] * js);
+  J[k] = (T)(((double)Js[k] + (double)da[k] * (double)Es[k]) / (double)cj[k] * js);
 }
 
 template <typename T>
@@ -138,10 +142,20 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
   if (n_int == 0) a = 0;
   const int64_t b = a + n_int * W;
   const int64_t n_edge = (a + We - 1) / We + (nz - b + We - 1) / We;
+  // interior tiles j whose loaded range [a + jW - TS, a + jW - TS + L) holds the source cell:
+  // d - L < jW <= d with d = src - a + TS
+  int64_t j_src0 = 0, j_src1 = 0;
+  const int64_t d = src - a + TS;
+  if (n_int && d >= 0) {
+    j_src0 = d - L + 1 > 0 ? (d - L + 1 + W - 1) / W : 0;
+    j_src1 = std::min<int64_t>(n_int, d / W + 1);
+    if (j_src1 < j_src0) j_src1 = j_src0;
+  }
+  const int64_t n_src = j_src1 - j_src0;
   if (n_int + n_edge > kNoallocMaxTiles) return nfail(RKETD_EINVAL, "noalloc: too many tiles");
 
   cudaError_t e;
-  k_plan<<<1, 32, 0, st>>>(tiles, table, nz, src, K, Ke, TS, counts);
+  k_plan<<<1, 32, 0, st>>>(tiles, table, nz, src, K, Ke, TS, j_src0, j_src1, counts);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   void* cptr[kNumCoef];
   for (int k = 0; k < kNumCoef; ++k) cptr[k] = coef[k];
@@ -149,7 +163,8 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
   e = launch_coeffs(sizeof(T) == 8 ? 1 : 0, wp2, nu, table, table + 1, table + 2, 1, nzp, g->dt, S, cptr, st);
   if (e != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   const unsigned blocks = (unsigned)((nzp + 255) / 256);
-  k_in<T><<<blocks, 256, 0, st>>>(E, H, J, coef[kCj], fld[0][0], fld[0][1], fld[0][2], nz, nzp, eta0, g->dt / kEps0);
+  k_in<T><<<blocks, 256, 0, st>>>(E, H, J, coef[kCj], coef[kDa], fld[0][0], fld[0][1], fld[0][2], nz, nzp, eta0,
+                                  g->dt / kEps0);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
 
   StepArgs<T> s{};
@@ -181,16 +196,22 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
     s.nsub = nsub;
     s.series_pos = 0;
     s.tiles = tiles;
-    s.n_tiles = (int)n_int;
-    if (n_int && (e = launch_tb<T>(s, K, false, 2, st)) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
+    s.n_tiles = (int)(n_int - n_src);
+    if (s.n_tiles && (e = launch_tb<T>(s, K, false, 2, st, false)) != cudaSuccess)
+      return nfail(RKETD_ECUDA, cudaGetErrorString(e));
+    s.tiles = tiles + (n_int - n_src);
+    s.n_tiles = (int)n_src;
+    if (n_src && (e = launch_tb<T>(s, K, false, 2, st, true)) != cudaSuccess)
+      return nfail(RKETD_ECUDA, cudaGetErrorString(e));
     s.tiles = tiles + n_int;
     s.n_tiles = (int)n_edge;
-    if (n_edge && (e = launch_tb<T>(s, Ke, true, 2, st)) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
+    if (n_edge && (e = launch_tb<T>(s, Ke, true, 2, st, true)) != cudaSuccess)
+      return nfail(RKETD_ECUDA, cudaGetErrorString(e));
     cur = 1 - cur;
     done += nsub;
   }
-  k_out<T><<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(fld[cur][0], fld[cur][1], fld[cur][2], coef[kCj], E, H, J,
-                                                         nz, 1.0 / eta0, kEps0 / g->dt);
+  k_out<T><<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(fld[cur][0], fld[cur][1], fld[cur][2], coef[kCj],
+                                                         coef[kDa], E, H, J, nz, 1.0 / eta0, kEps0 / g->dt);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   return RKETD_OK;
 }

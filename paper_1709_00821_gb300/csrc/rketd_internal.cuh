@@ -13,13 +13,19 @@
 // The six per-cell coefficients are kept as deviations (da, dj) or small terms so that
 // FP32 storage keeps their relative accuracy.
 //
-// The device state carries the current scaled by cj, Jc = cj J~ (cj = (1 + a)/(2D) lies in
-// (0, 1]). Multiplying the J recursion by cj gives
-//   E^{n+1} = E^n + da E^n - cb (H~_{k+1/2} - H~_{k-1/2}) - Jc^n,
-//   Jc^{n+1} = Jc^n + dj Jc^n + (cj bp) E^n + (cj cc) E^{n+1},
-// the same arithmetic with one coefficient fewer per cell in the step kernels. The arrays
-// kBp and kCc hold cj*bp and cj*cc; kCj is kept for converting Jc back to J (fields out,
-// medium changes).
+// The device state carries, in place of J~, the folded current
+//   G = cj J~ - da E        (cj = (1 + a)/(2D) in (0, 1]),
+// the part of the E update that does not depend on the new curl. Substituting it,
+//   E^{n+1} = E^n - (cb (H~_{k+1/2} - H~_{k-1/2}) + G^n),
+//   G^{n+1} = G^n + dj G^n + bq E^n + cq E^{n+1},
+//   bq = cj bp + da a = w (phi1 - (1 + a) phi2)/(2D),   cq = cj cc - da = w (phi1 + (1 + a) phi2)/(2D),
+// the same discrete map in exact arithmetic (expand G^{n+1} + da E^{n+1}). In finite precision it
+// matters: E and G are each rounded once per step at their own magnitude, after the small terms
+// have been summed, so that da E and dj G (down to 1e-7 of E and G on plasma slabs) are not
+// rounded away on their own every step; and E takes two operations instead of three. The soft
+// source adds s to E^{n+1} after G^{n+1} is formed, so the source cell also takes G -= da s.
+// kBq and kCq hold bq and cq; da and cj stay for converting G back to J (fields out, medium
+// changes, the no-allocation entry point) and for the adjoint's chain rule.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,7 +38,20 @@ constexpr double kMu0 = 1.25663706212e-6;
 constexpr int kMaxCells = 32;   // largest cells-per-lane instantiated
 constexpr int kMaxTileProbes = 8;
 
-enum CoefIndex { kDa = 0, kCb = 1, kCj = 2, kDj = 3, kBp = 4, kCc = 5, kNumCoef = 6 };
+enum CoefIndex { kDa = 0, kCb = 1, kCj = 2, kDj = 3, kBq = 4, kCq = 5, kNumCoef = 6 };
+
+// E and G update of one interior cell (the folded form above). The G update sums its three small
+// terms before adding G: G grows far beyond its per-step increment where the current has a large
+// low-frequency part, and adding the terms to G one at a time would round each of them against G
+// (in FP64 that alone moved the transmission spectrum of the 8000-step slab by 3e-12).
+template <typename T>
+__device__ __forceinline__ T fold_e(T e, T cb, T curl, T g) {
+  return e - fma(cb, curl, g);
+}
+template <typename T>
+__device__ __forceinline__ T fold_g(T g, T dj, T bq, T cq, T e, T enew) {
+  return g + fma(dj, g, fma(bq, e, cq * enew));
+}
 
 // One warp tile of the temporally blocked step: 32*K consecutive cells of one slab,
 // loaded from `start` (slab-local, may be negative); after a pass of up to tb_steps
@@ -90,7 +109,7 @@ struct StepArgs {
   const TileProbe* tprobes;
   int32_t n_tiles;
   int32_t total_probes;
-  // window recording (adjoint recompute): after each step the state (E, H, carried J) of cells
+  // window recording (adjoint recompute): after each step the state (E, H, G) of cells
   // [rec_c0, rec_c0 + rec_w) of every slab goes to rec[slab][slot][3][rec_w], slot = rec_pos + t
   T* rec;
   int64_t rec_c0;
@@ -100,10 +119,10 @@ struct StepArgs {
 };
 
 // The reverse (adjoint) step on the same tiles. lambda = (lE, lH, lJ) is the adjoint of
-// (E, H~, carried J); a pass takes the adjoint from after step n_hi - 1 back to before step
+// (E, H~, G); a pass takes the adjoint from after step n_hi - 1 back to before step
 // n_hi - nsub. seeds[slot][seed_len] holds dL/dE at probe `slot` for the sample that follows
 // step n (column n - seg_n0). Window cells [rec_c0, rec_c0 + rec_w) record, for each step,
-// mu = lE + cc lJ and lJ (both after the step) to rec[slab][n - seg_n0][2][rec_w].
+// mu = lE + cq lJ and lJ (both after the step) to rec[slab][n - seg_n0][2][rec_w].
 template <typename T>
 struct AdjArgs {
   const T* lE_in;
@@ -141,8 +160,10 @@ cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const i
 cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
                                double amax, void* cpmlE, void* cpmlH, cudaStream_t st);
 
+// Tiled step over a.tiles. Interior tiles (edge = false) whose loaded range holds their slab's
+// source cell need src = true; the others run a kernel without the source code.
 template <typename T>
-cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st);
+cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st, bool src);
 
 // forward tiles that also record the window state (scalar kernel, template REC = true)
 template <typename T>
@@ -157,10 +178,18 @@ cudaError_t launch_adj_pairs(const AdjArgs<float>& a, int K, int warps_per_block
 template <typename T>
 cudaError_t launch_seeds(const double* gXr, const double* gXi, const T* tw, int P, int nf, int n, T* seeds,
                          int seed_len, cudaStream_t st);
+// The source of each slab, for the gradient sums of one segment (steps n0 ..): slab-local
+// source cells, the window start and the pulse
+struct GradSource {
+  const int64_t* cell;
+  int64_t w_lo;
+  int64_t n0;
+  double dt, t0, tau, amp;
+};
 // g[5][slab][w] += per-window-cell sums over one segment of the recorded forward and adjoint values
 template <typename T>
 cudaError_t launch_grad_accum(const T* recF, const T* recA, int n_slabs, int rec_w, int nwin, int L, int recF_len,
-                              double* g, cudaStream_t st);
+                              const GradSource& src, double* g, cudaStream_t st);
 // chain rule: grad_wp2, grad_nu of window cells from g and d(coefficient)/d(wp2, nu)
 cudaError_t launch_grad_chain(const double* g, const double* wp2, const double* nu, const int64_t* off,
                               int n_slabs, int64_t w_lo, int w, double dt, double S, double* grad_wp2,
@@ -170,8 +199,8 @@ template <typename T>
 cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, const int64_t* nz, int n_slabs,
                             int64_t c0, int w, int rec_len, T* rec, cudaStream_t st);
 
-// FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu)
-cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st);
+// FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu); src as for launch_tb
+cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st, bool src);
 
 template <typename T>
 cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,
@@ -184,10 +213,13 @@ template <typename T>
 cudaError_t launch_dft(const T* series, int series_len, int n_samples, const T* tw, int total_probes,
                        int n_freq, double* X_re, double* X_im, cudaStream_t st);
 
-cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* J, const void* cj,
-                                 int64_t off, int64_t nz, double h_scale, double j_scale, double* Eo, double* Ho,
-                                 double* Jo, cudaStream_t st);
-// J <- J * num / den elementwise over n cells (re-scales the carried current when cj changes)
-cudaError_t launch_rescale(int prec, void* J, const void* num, const void* den, int64_t n, cudaStream_t st);
+// Device state of one slab to SI: E, H = H~ h_scale, J = (G + da E)/cj j_scale
+cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* G, const void* cj,
+                                 const void* da, int64_t off, int64_t nz, double h_scale, double j_scale, double* Eo,
+                                 double* Ho, double* Jo, cudaStream_t st);
+// Medium change: G <- cj_new (G + da_old E)/cj_old - da_new E elementwise over n cells, so that
+// J~ stays as it was while the coefficients change
+cudaError_t launch_rescale(int prec, void* G, const void* E, const void* cj_new, const void* cj_old,
+                           const void* da_new, const void* da_old, int64_t n, cudaStream_t st);
 
 }  // namespace rketd

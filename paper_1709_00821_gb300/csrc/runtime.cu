@@ -100,6 +100,7 @@ struct rketd_ctx {
   Tile* tiles_d = nullptr;
   TileProbe* tprobes_d = nullptr;
   int n_interior = 0, n_edge = 0;
+  int n_int_src = 0;  // the last n_int_src interior tiles hold a source cell in their loaded range
   int tiles_K = 0, tiles_T = 0;
 
   int64_t step = 0;
@@ -269,6 +270,10 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     t.probe_begin += (int32_t)tp_int.size();
     t.adj_begin += (int32_t)tp_int.size();
   }
+  // interior tiles that load a source cell go last: they run the kernel with the source code
+  std::stable_partition(interior.begin(), interior.end(), [](const Tile& t) { return t.src_local < 0; });
+  int n_int_src = 0;
+  for (const Tile& t : interior) n_int_src += t.src_local >= 0;
   std::vector<Tile> all = interior;
   all.insert(all.end(), edge.begin(), edge.end());
   c->tiles_h = all;
@@ -289,6 +294,7 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     CK(cudaMemcpy(c->tprobes_d, tps.data(), sizeof(TileProbe) * tps.size(), cudaMemcpyHostToDevice),
        "tile probe upload");
   c->n_interior = (int)interior.size();
+  c->n_int_src = n_int_src;
   c->n_edge = (int)edge.size();
   c->tiles_K = K;
   c->tiles_T = T;
@@ -407,8 +413,12 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       a.nsub = nsub;
       a.tprobes = c->tprobes_d;
       // Edge tiles first, on the high-priority side stream, so their few long-running warps
-      // start before the interior grid fills the GPU; joined back after the interior launch.
-      const bool forked = c->n_interior && c->n_edge;
+      // start before the interior grid fills the GPU, then the interior tiles that load a source
+      // cell; joined back after the main interior launch.
+      const bool fp32p = std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0;
+      const int n_main = c->n_interior - c->n_int_src;
+      const bool forked = n_main && (c->n_edge || c->n_int_src);
+      cudaStream_t side = forked ? c->side : c->stream;
       if (forked) {
         CK(cudaEventRecord(c->fork, c->stream), "fork");
         CK(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
@@ -416,12 +426,23 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       if (c->n_edge) {
         a.tiles = c->tiles_d + c->n_interior;
         a.n_tiles = c->n_edge;
-        CK(launch_tb<T>(a, edge_cells_per_lane(TS), true, 2, forked ? c->side : c->stream), "tiled step (edge)");
+        CK(launch_tb<T>(a, edge_cells_per_lane(TS), true, 2, side, true), "tiled step (edge)");
         c->launches += 1;
-        if (forked) CK(cudaEventRecord(c->join, c->side), "join");
       }
+      if (c->n_int_src) {
+        a.tiles = c->tiles_d + n_main;
+        a.n_tiles = c->n_int_src;
+        if (fp32p) {
+          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, side, true),
+             "tiled step (source tiles, FP32 pairs)");
+        } else {
+          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, side, true), "tiled step (source tiles)");
+        }
+        c->launches += 1;
+      }
+      if (forked) CK(cudaEventRecord(c->join, c->side), "join");
       a.tiles = c->tiles_d;
-      a.n_tiles = c->n_interior;
+      a.n_tiles = n_main;
       if (a.n_tiles) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (c->timing) {
@@ -430,11 +451,12 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
           if (st) return st;
           CK(cudaEventRecord(e0, c->stream), "timing event");
         }
-        if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
-          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream),
+        if (fp32p) {
+          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream,
+                             false),
              "tiled step (interior, FP32 pairs)");
         } else {
-          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "tiled step (interior)");
+          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream, false), "tiled step (interior)");
         }
         c->launches += 1;
         if (c->timing) {
@@ -747,13 +769,17 @@ rketd_status rketd_set_medium(rketd_ctx* c, const double* wp2, const double* nu,
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CK(cudaMemcpyAsync(c->wp2_d, wp2, b, kind, c->stream), "medium upload");
   CK(cudaMemcpyAsync(c->nu_d, nu, b, kind, c->stream), "medium upload");
-  // The state carries cj J~; keep J~ unchanged across the medium change: J <- J cj_new / cj_old.
-  // The old cj is parked in the other (unused) ping-pong copy of J.
+  // The state carries the folded current G = cj J~ - da E; J~ stays unchanged across the medium
+  // change. The old cj and da are parked in the other (unused) ping-pong copies of J and H.
   void* old_cj = c->J[1 - c->cur];
+  void* old_da = c->H[1 - c->cur];
   CK(cudaMemcpyAsync(old_cj, c->coef[kCj], c->esz * c->n_store, cudaMemcpyDeviceToDevice, c->stream), "medium");
+  CK(cudaMemcpyAsync(old_da, c->coef[kDa], c->esz * c->n_store, cudaMemcpyDeviceToDevice, c->stream), "medium");
   rketd_status st = update_coeffs(c);
   if (st) return st;
-  CK(launch_rescale(c->prec, c->J[c->cur], c->coef[kCj], old_cj, c->n_store, c->stream), "current rescale");
+  CK(launch_rescale(c->prec, c->J[c->cur], c->E[c->cur], c->coef[kCj], old_cj, c->coef[kDa], old_da, c->n_store,
+                    c->stream),
+     "current rescale");
   c->launches += 1;
   return RKETD_OK;
 }
@@ -792,7 +818,8 @@ rketd_status rketd_get_fields(rketd_ctx* c, int32_t slab, double* E, double* H, 
   const double hs = 1.0 / std::sqrt(kMu0 / kEps0);
   const double js = kEps0 / c->grid.dt;
   cudaError_t e = launch_gather_fields(c->prec, c->E[c->cur], c->H[c->cur], c->J[c->cur], c->coef[kCj],
-                                       c->soff[slab], nz, hs, js, tmp, tmp + nz, tmp + 2 * nz, c->stream);
+                                       c->coef[kDa], c->soff[slab], nz, hs, js, tmp, tmp + nz, tmp + 2 * nz,
+                                       c->stream);
   c->launches += 1;
   if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, tmp, sizeof(double) * nz, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && H)
@@ -857,6 +884,9 @@ rketd_status rketd_rt(const double* tr, const double* ti, const double* ir, cons
 
 namespace {
 
+// Version 2: the current is stored as the folded G = cj J~ - da E (version 1 held cj J~).
+constexpr int32_t kStateVersion = 2;
+
 struct StateHeader {
   char magic[8];
   int32_t version, prec, n_slabs, n_probes, n_freq, dft_block;
@@ -882,7 +912,7 @@ bool read_dev(FILE* f, void* dev, size_t bytes, cudaStream_t st) {
 StateHeader header_of(const rketd_ctx* c) {
   StateHeader h{};
   std::memcpy(h.magic, "RKETDST1", 8);
-  h.version = 1;
+  h.version = kStateVersion;
   h.prec = c->prec;
   h.n_slabs = c->n_slabs;
   h.n_probes = c->n_probes;
@@ -923,7 +953,7 @@ rketd_status rketd_load_state(rketd_ctx* c, const char* path) {
   if (!f) return fail(RKETD_EIO, "cannot open %s", path);
   StateHeader h{};
   const StateHeader want = header_of(c);
-  if (fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, want.magic, 8) || h.version != 1) {
+  if (fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, want.magic, 8) || h.version != kStateVersion) {
     fclose(f);
     return fail(RKETD_EIO, "%s is not an RKETD state file", path);
   }
@@ -1085,7 +1115,9 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     for (int i = 0; i < c->n_interior; ++i) {
       const Tile& t = c->tiles_h[i];
       const int64_t v0 = t.start + t.vlo, v1 = t.start + t.vhi;
-      (v1 <= w_lo - 4 || v0 >= w_lo - 4 + ((w_hi - w_lo + 7) / 4) * 4 ? plain : win).push_back(t);
+      // (tiles that load a source cell run the recording kernel, which has the source code)
+      (t.src_local < 0 && (v1 <= w_lo - 4 || v0 >= w_lo - 4 + ((w_hi - w_lo + 7) / 4) * 4) ? plain : win)
+          .push_back(t);
     }
     std::vector<Tile> order = plain;
     order.insert(order.end(), win.begin(), win.end());
@@ -1172,10 +1204,11 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.tiles = t_plain;
       a.n_tiles = c->adj_n_plain;
       if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
-        CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream),
+        CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, c->stream,
+                           false),
            "recompute (interior)");
       } else {
-        CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream), "recompute (interior)");
+        CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, c->stream, false), "recompute (interior)");
       }
       if ((st = join())) return st;
       c->launches += 3;
@@ -1235,8 +1268,9 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       lcur = 1 - lcur;
       hi -= nsub;
     }
-    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, (int)nwin, L, L + 1, c->gacc,
-                            c->stream),
+    const GradSource gs{c->src_d, w_lo, n0, c->grid.dt, c->pulse.t0, c->pulse.tau, c->pulse.amp};
+    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, (int)nwin, L, L + 1, gs,
+                            c->gacc, c->stream),
        "gradient sums");
     c->launches += 1;
   }

@@ -1,7 +1,7 @@
 // The paper's two-kernel structure (Sec. III): an H-update kernel then an E-update
 // kernel per time step, one cell per thread, fields in global memory. Here the E kernel
-// also advances J (Eq. 11 needs E^n and E^{n+1} of the same cell, so it stays in a
-// register), adds the Eq. 15 source and applies the end conditions; a third small kernel
+// also advances the current (Eq. 11 needs E^n and E^{n+1} of the same cell, so it stays in
+// a register), adds the Eq. 15 source and applies the end conditions; a third small kernel
 // copies the probe samples. This is the streaming form (one HBM pass per step) that the
 // temporally blocked kernel is measured against.
 #include "rketd_internal.cuh"
@@ -34,8 +34,9 @@ __global__ void __launch_bounds__(256) k_plain_h(const StepArgs<T> a, const int3
   if (a.bc == 1 && (k < nc || k >= nz - 1 - nc)) {
     const int ih = (int)(k < nc ? k : nz - 2 - k);
     const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 2 - k));
-    const T b = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
-    const T psi = fma(b, a.psiH_out[pi], c * dE);
+    const T db = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
+    const T po = a.psiH_out[pi];
+    const T psi = fma(db, po, fma(c, dE, po));
     a.psiH_out[pi] = psi;
     H[i] = fma(-a.S, fma(dE, ki, psi), H[i]);
   } else {
@@ -60,21 +61,23 @@ __global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int
   if (a.bc == 1 && (k < nc || k > nz - 1 - nc)) {
     const int d = (int)(k < nc ? k : nz - 1 - k);
     const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 1 - k));
-    const T b = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
-    const T psi = fma(b, a.psiE_out[pi], c * dH);
+    const T db = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
+    const T po = a.psiE_out[pi];
+    const T psi = fma(db, po, fma(c, dH, po));
     a.psiE_out[pi] = psi;
     curl = fma(dH, ki, psi);
   }
+  // J holds the folded current G (rketd_internal.cuh)
   const T en = E[i];
-  const T jo = J[i];
-  T enew = fma(a.coef[kDa][i], en, en);
-  enew = fma(-a.coef[kCb][i], curl, enew);
-  enew = enew - jo;  // J holds cj J~
-  T jn = fma(a.coef[kDj][i], jo, jo);
-  jn = fma(a.coef[kBp][i], en, jn);
-  jn = fma(a.coef[kCc][i], enew, jn);
-  J[i] = jn;
-  if (k == a.src[s]) enew += (T)pulse((double)(a.n0 + 1) * a.dt, a.t0, a.tau, a.amp);
+  const T go = J[i];
+  T enew = fold_e(en, a.coef[kCb][i], curl, go);
+  T gn = fold_g(go, a.coef[kDj][i], a.coef[kBq][i], a.coef[kCq][i], en, enew);
+  if (k == a.src[s]) {
+    const T sv = (T)pulse((double)(a.n0 + 1) * a.dt, a.t0, a.tau, a.amp);
+    enew += sv;
+    gn = fma(-a.coef[kDa][i], sv, gn);
+  }
+  J[i] = gn;
   // The thread of cell 1 owns cell 0 and the thread of cell nz-2 owns cell nz-1: Mur needs
   // E_1^n and E_1^{n+1}, which only this thread has (cells are updated in place).
   if (k == 1) {

@@ -1,7 +1,7 @@
 // Temporally blocked 1D RKETD-FDTD step (Eqs. 14, 13, 11, 15, ends) on warp tiles.
 //
 // A warp owns 32*K consecutive cells of one slab, K per lane, kept in registers
-// together with five per-cell update coefficients. One pass advances the tile by up
+// together with four per-cell update coefficients. One pass advances the tile by up
 // to tb_steps leapfrog steps without leaving the registers: the only exchange between
 // cells of different lanes is one shuffle per half step (E of the right neighbour for
 // Eq. 14, H of the left neighbour for Eq. 12/13). A tile loads tb_steps cells of halo
@@ -26,7 +26,9 @@ namespace {
 
 using namespace tile;
 
-template <typename T, int K, bool EDGE, bool REC>
+// SRC: the tiles may hold their slab's source cell (always so for edge tiles and the recording
+// recompute; the planner launches the few interior tiles that do apart from the rest).
+template <typename T, int K, bool EDGE, bool REC, bool SRC>
 __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const StepArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -40,16 +42,16 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
   const int64_t g0 = tl.start + li0;  // slab-local cell of slot 0
   const T S = a.S;
 
-  // jj carries cj J~ (see rketd_internal.cuh), so the E update subtracts it directly
-  T e[K], h[K], jj[K], da[K], cb[K], dj[K], bp[K], cc[K];
+  // jj carries the folded current G (rketd_internal.cuh): the E update subtracts it directly
+  T e[K], h[K], jj[K], cb[K], dj[K], bq[K], cq[K];
   load_row<T, K, EDGE>(a.E_in + soff, g0, nzp, e);
   load_row<T, K, EDGE>(a.H_in + soff, g0, nzp, h);
   load_row<T, K, EDGE>(a.J_in + soff, g0, nzp, jj);
-  load_row<T, K, EDGE>(a.coef[kDa] + soff, g0, nzp, da);
   load_row<T, K, EDGE>(a.coef[kCb] + soff, g0, nzp, cb);
   load_row<T, K, EDGE>(a.coef[kDj] + soff, g0, nzp, dj);
-  load_row<T, K, EDGE>(a.coef[kBp] + soff, g0, nzp, bp);
-  load_row<T, K, EDGE>(a.coef[kCc] + soff, g0, nzp, cc);
+  load_row<T, K, EDGE>(a.coef[kBq] + soff, g0, nzp, bq);
+  load_row<T, K, EDGE>(a.coef[kCq] + soff, g0, nzp, cq);
+  const bool has_src = SRC && tl.src_local >= 0 && lane == tl.src_local / K;
 
   // Edge-tile bookkeeping (bit i = slot i).
   uint32_t mH = 0, mE = 0, mcH = 0, mcE = 0;
@@ -106,8 +108,8 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
         if (mcH & (1u << i)) {
           const int64_t g = g0 + i;
           const int ih = (int)(g < nc ? g : nz - 2 - g);
-          const T b = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
-          pH[i] = fma(b, pH[i], c * dE);
+          const T db = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
+          pH[i] = fma(db, pH[i], fma(c, dE, pH[i]));
           h[i] = fma(-S, fma(dE, ki, pH[i]), h[i]);
         } else {
           h[i] = fma(-S, dE, h[i]);
@@ -139,28 +141,24 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
         if (mcE & (1u << i)) {
           const int64_t g = g0 + i;
           const int d = (int)(g < nc ? g : nz - 1 - g);
-          const T b = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
-          pE[i] = fma(b, pE[i], c * dH);
+          const T db = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
+          pE[i] = fma(db, pE[i], fma(c, dH, pE[i]));
           curl = fma(dH, ki, pE[i]);
         }
       }
       if (upd) {
         const T en = e[i];
-        T enew = fma(da[i], en, en);
-        enew = fma(-cb[i], curl, enew);
-        enew = enew - jj[i];
-        T jn = fma(dj[i], jj[i], jj[i]);
-        jn = fma(bp[i], en, jn);
-        jn = fma(cc[i], enew, jn);
+        const T enew = fold_e(en, cb[i], curl, jj[i]);
+        jj[i] = fold_g(jj[i], dj[i], bq[i], cq[i], en, enew);
         e[i] = enew;
-        jj[i] = jn;
       }
     }
-    // ---- Eq. 15 soft source at t = (n+1) dt ----
-    if (tl.src_local >= 0 && lane == tl.src_local / K) {
+    // ---- Eq. 15 soft source at t = (n+1) dt (and its fold into G) ----
+    if (SRC && has_src) {
       const int sl = tl.src_local % K;
-      const double sv = pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
-      put(e, sl, pick(e, sl) + (T)sv);
+      const T sv = (T)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
+      put(e, sl, pick(e, sl) + sv);
+      put(jj, sl, fma(-a.coef[kDa][soff + g0 + sl], sv, pick(jj, sl)));
     }
     // ---- ends: first-order Mur or PEC ----
     if (EDGE) {
@@ -229,38 +227,40 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
 }
 
 template <typename T, int K, bool REC = false>
-cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st) {
+cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st, bool src) {
   const dim3 block(32 * wpb);
   const dim3 grid((a.n_tiles + wpb - 1) / wpb);
   if (edge)
-    k_tb<T, K, true, REC><<<grid, block, 0, st>>>(a);
+    k_tb<T, K, true, REC, true><<<grid, block, 0, st>>>(a);
+  else if (REC || src)
+    k_tb<T, K, false, REC, true><<<grid, block, 0, st>>>(a);
   else
-    k_tb<T, K, false, REC><<<grid, block, 0, st>>>(a);
+    k_tb<T, K, false, false, false><<<grid, block, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <>
-cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st) {
+cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st, bool src) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<float, 4>(a, edge, wpb, st);
-    case 8: return launch_k<float, 8>(a, edge, wpb, st);
-    case 12: return launch_k<float, 12>(a, edge, wpb, st);
-    case 16: return launch_k<float, 16>(a, edge, wpb, st);
+    case 4: return launch_k<float, 4>(a, edge, wpb, st, src);
+    case 8: return launch_k<float, 8>(a, edge, wpb, st, src);
+    case 12: return launch_k<float, 12>(a, edge, wpb, st, src);
+    case 16: return launch_k<float, 16>(a, edge, wpb, st, src);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <>
-cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st) {
+cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st, bool src) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<double, 4>(a, edge, wpb, st);
-    case 8: return launch_k<double, 8>(a, edge, wpb, st);
+    case 4: return launch_k<double, 4>(a, edge, wpb, st, src);
+    case 8: return launch_k<double, 8>(a, edge, wpb, st, src);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -270,9 +270,9 @@ cudaError_t launch_tb_rec<float>(const StepArgs<float>& a, int K, bool edge, int
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<float, 4, true>(a, edge, wpb, st);
-    case 8: return launch_k<float, 8, true>(a, edge, wpb, st);
-    case 16: return launch_k<float, 16, true>(a, edge, wpb, st);
+    case 4: return launch_k<float, 4, true>(a, edge, wpb, st, true);
+    case 8: return launch_k<float, 8, true>(a, edge, wpb, st, true);
+    case 16: return launch_k<float, 16, true>(a, edge, wpb, st, true);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -282,8 +282,8 @@ cudaError_t launch_tb_rec<double>(const StepArgs<double>& a, int K, bool edge, i
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<double, 4, true>(a, edge, wpb, st);
-    case 8: return launch_k<double, 8, true>(a, edge, wpb, st);
+    case 4: return launch_k<double, 4, true>(a, edge, wpb, st, true);
+    case 8: return launch_k<double, 8, true>(a, edge, wpb, st, true);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -7,8 +7,9 @@
 // slots of the scalar kernel for the same FP32 work (the kernel is issue-bound: the FP32
 // pipe runs the pair in two cycles either way). Only the two pairs at the ends of a lane's
 // range need a repack per half step. Every element is rounded exactly as in the scalar
-// kernel (fma2 is two fused multiply-adds, sub2 two subtractions), so the fields are bitwise
-// identical to the plain and scalar tiled kernels.
+// kernel (fma2 is two fused multiply-adds, sub2 two subtractions, and so on), so the fields
+// are bitwise identical to the plain and scalar tiled kernels. The current is the folded
+// G of rketd_internal.cuh, updated as fold_e / fold_g do.
 #include "rketd_internal.cuh"
 #include "tile_common.cuh"
 
@@ -20,7 +21,9 @@ namespace rketd {
 namespace {
 
 using namespace tile;
-template <int K>
+// SRC: the tile list holds the tiles whose loaded range contains their slab's source cell
+// (the planner launches those few apart, so the main launch carries no source code).
+template <int K, bool SRC>
 __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float> a) {
   constexpr int P = K / 2;
   const int lane = threadIdx.x & 31;
@@ -31,19 +34,18 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
   const int64_t base = a.soff[s] + tl.start + lane * K;  // interior tile: every cell is in the slab
   const int li0 = lane * K;
 
-  f2 e[P], h[P], jj[P], da[P], ncb[P], dj[P], bp[P], cc[P];
+  f2 e[P], h[P], g[P], cb[P], dj[P], bq[P], cq[P];
   load_pairs<K>(a.E_in + base, e, false);
   load_pairs<K>(a.H_in + base, h, false);
-  load_pairs<K>(a.J_in + base, jj, false);  // carries cj J~
-  load_pairs<K>(a.coef[kDa] + base, da, false);
-  load_pairs<K>(a.coef[kCb] + base, ncb, true);
+  load_pairs<K>(a.J_in + base, g, false);
+  load_pairs<K>(a.coef[kCb] + base, cb, false);
   load_pairs<K>(a.coef[kDj] + base, dj, false);
-  load_pairs<K>(a.coef[kBp] + base, bp, false);
-  load_pairs<K>(a.coef[kCc] + base, cc, false);
+  load_pairs<K>(a.coef[kBq] + base, bq, false);
+  load_pairs<K>(a.coef[kCq] + base, cq, false);
   const f2 nS = pk(-a.S, -a.S);
-  const bool has_src = tl.src_local >= 0 && lane == tl.src_local / K;
+  const bool has_src = SRC && tl.src_local >= 0 && lane == tl.src_local / K;
   const int src_slot = tl.src_local % K;
-  const bool extras = tl.src_local >= 0 || tl.probe_count > 0;
+  const bool extras = (SRC && tl.src_local >= 0) || tl.probe_count > 0;
 
   for (int t = 0; t < a.nsub; ++t) {
     // Eq. 14 on pairs: the cell after pair p is pair p+1; after pair P-1 it is (B[0], next lane's A[0])
@@ -62,19 +64,15 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
       const f2 hp = p ? h[p - 1] : hFirst;
       const f2 dH = sub2(h[p], hp);
       const f2 en = e[p];
-      f2 enew = fma2(da[p], en, en);
-      enew = fma2(ncb[p], dH, enew);
-      enew = sub2(enew, jj[p]);
-      f2 jn = fma2(dj[p], jj[p], jj[p]);
-      jn = fma2(bp[p], en, jn);
-      jn = fma2(cc[p], enew, jn);
+      const f2 enew = sub2(en, fma2(cb[p], dH, g[p]));
+      g[p] = add2(g[p], fma2(dj[p], g[p], fma2(bq[p], en, mul2(cq[p], enew))));
       e[p] = enew;
-      jj[p] = jn;
     }
     if (extras) {
-      if (has_src) {
-        const double sv = pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
-        put2(e, src_slot, pick2(e, src_slot) + (float)sv);
+      if (SRC && has_src) {
+        const float sv = (float)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
+        put2(e, src_slot, pick2(e, src_slot) + sv);
+        put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
       }
       for (int q = 0; q < (a.series ? tl.probe_count : 0); ++q) {
         const TileProbe tp = a.tprobes[tl.probe_begin + q];
@@ -85,20 +83,20 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
   }
   store_pairs<K>(a.E_out + base, li0, tl.vlo, tl.vhi, e);
   store_pairs<K>(a.H_out + base, li0, tl.vlo, tl.vhi, h);
-  store_pairs<K>(a.J_out + base, li0, tl.vlo, tl.vhi, jj);
+  store_pairs<K>(a.J_out + base, li0, tl.vlo, tl.vhi, g);
 }
 
 }  // namespace
 
-cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int wpb, cudaStream_t st) {
+cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int wpb, cudaStream_t st, bool src) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   const dim3 block(32 * wpb);
   const dim3 grid((a.n_tiles + wpb - 1) / wpb);
   switch (K) {
-    case 8: k_tb2<8><<<grid, block, 0, st>>>(a); break;
-    case 12: k_tb2<12><<<grid, block, 0, st>>>(a); break;
-    case 16: k_tb2<16><<<grid, block, 0, st>>>(a); break;
+    case 8: src ? k_tb2<8, true><<<grid, block, 0, st>>>(a) : k_tb2<8, false><<<grid, block, 0, st>>>(a); break;
+    case 12: src ? k_tb2<12, true><<<grid, block, 0, st>>>(a) : k_tb2<12, false><<<grid, block, 0, st>>>(a); break;
+    case 16: src ? k_tb2<16, true><<<grid, block, 0, st>>>(a) : k_tb2<16, false><<<grid, block, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -181,7 +181,8 @@ def test_batch_of_ragged_slabs_matches_per_slab_oracle():
 
 
 def test_set_medium_mid_run_keeps_the_physical_current():
-    """The device carries cj*J; changing the medium rescales it so that J (SI) is unchanged."""
+    """The device carries the folded current G = cj J~ - da E; changing the medium re-folds it so that
+    J (SI) is unchanged."""
     s = wl.c1_plain_slab(steps=2200)
     for prec, tol in (("f64", 1e-15), ("f32", 1e-6)):
         with rk.Context(s, prec) as ctx:
