@@ -252,9 +252,10 @@ template <typename T>
 __device__ __forceinline__ T e_update(const Mat3<T>& M, int m, T e, T curl, T* J) {
   if (m == 0) return fma(M.cb[0], curl, e);
   const T jc = *J;
-  // the small terms are summed before the carried E and J are added (see the 1D kernels)
+  // the small terms are summed before the carried E and J are added, so that da E and dj J
+  // (a few ulp of E and J) are not rounded away on their own every step
   const T en = e + fma(M.cb[m], curl, fma(M.da[m], e, -jc));
-  *J = fma(M.dj[m], jc, fma(M.bp[m], e, fma(M.cc[m], en, jc)));
+  *J = jc + fma(M.cc[m], en, fma(M.bp[m], e, M.dj[m] * jc));
   return en;
 }
 

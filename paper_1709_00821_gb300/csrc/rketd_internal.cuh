@@ -43,14 +43,15 @@ enum CoefIndex { kDa = 0, kCb = 1, kCj = 2, kDj = 3, kBq = 4, kCq = 5, kNumCoef 
 // E and G update of one interior cell (the folded form above). The G update sums its three small
 // terms before adding G: G grows far beyond its per-step increment where the current has a large
 // low-frequency part, and adding the terms to G one at a time would round each of them against G
-// (in FP64 that alone moved the transmission spectrum of the 8000-step slab by 3e-12).
+// (in FP64 that alone moved the transmission spectrum of the 8000-step slab by 3e-12). The sum
+// starts from dj G and bq E, which do not wait for E', so only one fma and the add follow E'.
 template <typename T>
 __device__ __forceinline__ T fold_e(T e, T cb, T curl, T g) {
   return e - fma(cb, curl, g);
 }
 template <typename T>
 __device__ __forceinline__ T fold_g(T g, T dj, T bq, T cq, T e, T enew) {
-  return g + fma(dj, g, fma(bq, e, cq * enew));
+  return g + fma(cq, enew, fma(bq, e, dj * g));
 }
 
 // One warp tile of the temporally blocked step: 32*K consecutive cells of one slab,

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
       const f2 dH = sub2(h[p], hp);
       const f2 en = e[p];
       const f2 enew = sub2(en, fma2(cb[p], dH, g[p]));
-      g[p] = add2(g[p], fma2(dj[p], g[p], fma2(bq[p], en, mul2(cq[p], enew))));
+      g[p] = add2(g[p], fma2(cq[p], enew, fma2(bq[p], en, mul2(dj[p], g[p]))));
       e[p] = enew;
     }
     if (extras) {
