@@ -270,3 +270,38 @@ def test_collisionless_and_vacuum_cells_match_the_oracle(prec, tol):
         E, H, J = ctx.fields(0)
     assert rel(E, ref.E) <= tol and rel(H, ref.H) <= tol and rel(J, ref.J) <= tol
     assert rel(X, ref.X) <= tol
+
+
+def _plasma_line(nz, src, steps, probes):
+    """Mur-terminated line filled with collisional plasma, so that the source cell has da != 0
+    and the source's fold into the carried current is exercised."""
+    s = wl.c1_plain_slab(nz=nz, steps=steps)
+    s.wp2 = np.full(nz, (2 * np.pi * 30e9) ** 2)
+    s.nu = np.full(nz, 2e10)
+    s.src_cell = src
+    s.probes = probes
+    return s
+
+
+# Source cells at the first interior cell, at the exact-range boundary of two interior tiles and
+# inside the halo that two neighbouring tiles both load (default tiles: FP32 K = 16 with 32 steps
+# per pass, exact ranges [36 + 448 j, 484 + 448 j); FP64 K = 8 with 4 steps, [8 + 248 j, 256 + 248 j)).
+SRC_CASES = {"f32": [36, 37, 460, 483, 484, 515, 516, 1000], "f64": [8, 9, 252, 255, 256, 259, 260, 1000]}
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_source_cell_in_overlapping_tile_halos(prec):
+    """Interior tiles that load a source cell run a separate launch with the source code; every
+    placement gives the plain kernels' results bit for bit, and FP64 matches the oracle."""
+    for src in SRC_CASES[prec]:
+        s = _plasma_line(3000, src, 700, [src + 5, 2500])
+        tiled = lib_run(s, prec, variant=2)
+        plain = lib_run(s, prec, variant=1)
+        for a, b in zip(tiled, plain):
+            assert np.array_equal(a, b), (prec, src)
+        if prec == "f64":
+            tot, _ = oracle.run1d(s)
+            X, E, H, J = tiled
+            assert rel(X, tot.X) <= 1e-12, src
+            assert np.abs(E - tot.E).max() <= 1e-12 * np.abs(tot.E).max(), src
+            assert np.abs(J - tot.J).max() <= 1e-12 * np.abs(tot.J).max(), src

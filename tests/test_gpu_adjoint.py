@@ -62,6 +62,26 @@ def test_fp64_adjoint_matches_oracle_adjoint(case, every):
     assert not np.any(gw[:300]) and not np.any(gw[400:])
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("f32", 1e-3)])
+def test_adjoint_with_the_source_cell_inside_the_trainable_window(prec, tol):
+    """The plasma covers the source cell (da != 0 there) and the window contains it: the source
+    also folds into the carried current, which gives the source cell's gradient a term of its own."""
+    s, tgt = _problem(region=(60, 400))
+    assert s.wp2[s.src_cell] > 0
+    inc, R_t, gX, gw_o, gn_o = _oracle_case(s, tgt)
+    X, gw, gn = _gpu_grad([s], prec, gX[None], (80, 400), 512, s.steps)
+    w = slice(80, 400)
+    if prec == "f64":
+        assert np.abs(gw[w] - gw_o[w]).max() <= tol * np.abs(gw_o).max()
+        assert np.abs(gn[w] - gn_o[w]).max() <= tol * np.abs(gn_o).max()
+        k = s.src_cell
+        assert abs(gw[k] - gw_o[k]) <= 1e-9 * abs(gw_o[k]) + 1e-12 * np.abs(gw_o).max()
+    else:
+        assert np.linalg.norm(gw[w] - gw_o[w]) <= tol * np.linalg.norm(gw_o[w])
+        assert np.linalg.norm(gn[w] - gn_o[w]) <= tol * np.linalg.norm(gn_o[w])
+    assert not np.any(gw[:80]) and not np.any(gw[400:])
+
+
 def test_fp32_adjoint_within_1e3_of_oracle(case):
     s, (inc, R_t, gX, gw_o, gn_o) = case
     X, gw, gn = _gpu_grad([s], "f32", gX[None], (300, 400), 512, s.steps)

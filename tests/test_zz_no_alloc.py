@@ -23,12 +23,25 @@ def _scales(slab):
     return 1.0, eta0, slab.dt / wl.EPS0  # E, H and J into the same normalised units
 
 
+def _plasma_source(src):
+    """c1 line with plasma everywhere, so that the source cell folds into the carried current."""
+    slab = wl.c1_plain_slab()
+    slab.wp2 = np.full(slab.nz, (2 * math.pi * 30e9) ** 2)
+    slab.nu = np.full(slab.nz, 2e10)
+    slab.src_cell = src
+    return slab
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_noalloc_advance_matches_context_api_on_two_calls_in_a_row(prec, tol):
+@pytest.mark.parametrize("prec,tol,src", [("f64", 1e-12, None), ("f32", 1e-5, None),
+                                          ("f64", 1e-12, 255), ("f64", 1e-12, 8), ("f32", 1e-5, 460),
+                                          ("f32", 1e-5, 484), ("f32", 1e-5, 36)])
+def test_noalloc_advance_matches_context_api_on_two_calls_in_a_row(prec, tol, src):
+    """src None: the c1 slab (source in vacuum); otherwise a plasma line with the source cell where
+    two interior tiles load it (or at the first interior cell)."""
     import torch
 
-    slab = wl.c1_plain_slab()
+    slab = wl.c1_plain_slab() if src is None else _plasma_source(src)
     n1, n2 = 1500, 1337
     with rk.Context(slab, prec) as ctx:
         ctx.step(n1)
