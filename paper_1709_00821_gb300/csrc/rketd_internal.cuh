@@ -161,10 +161,10 @@ cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const i
 cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
                                double amax, void* cpmlE, void* cpmlH, cudaStream_t st);
 
-// Tiled step over a.tiles. Interior tiles (edge = false) whose loaded range holds their slab's
-// source cell need src = true; the others run a kernel without the source code.
+// Tiled step over a.tiles. Interior tiles (edge = false) that sample a probe or whose loaded range
+// holds their slab's source cell need xtra = true; the others run a kernel without that code.
 template <typename T>
-cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st, bool src);
+cudaError_t launch_tb(const StepArgs<T>& a, int K, bool edge, int warps_per_block, cudaStream_t st, bool xtra);
 
 // forward tiles that also record the window state (scalar kernel, template REC = true)
 template <typename T>
@@ -200,8 +200,8 @@ template <typename T>
 cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, const int64_t* nz, int n_slabs,
                             int64_t c0, int w, int rec_len, T* rec, cudaStream_t st);
 
-// FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu); src as for launch_tb
-cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st, bool src);
+// FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu); xtra as for launch_tb
+cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st, bool xtra);
 
 template <typename T>
 cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,

@@ -100,7 +100,7 @@ struct rketd_ctx {
   Tile* tiles_d = nullptr;
   TileProbe* tprobes_d = nullptr;
   int n_interior = 0, n_edge = 0;
-  int n_int_src = 0;  // the last n_int_src interior tiles hold a source cell in their loaded range
+  int n_int_xtra = 0;  // the last n_int_xtra interior tiles sample a probe or load a source cell
   int tiles_K = 0, tiles_T = 0;
 
   int64_t step = 0;
@@ -270,10 +270,12 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     t.probe_begin += (int32_t)tp_int.size();
     t.adj_begin += (int32_t)tp_int.size();
   }
-  // interior tiles that load a source cell go last: they run the kernel with the source code
-  std::stable_partition(interior.begin(), interior.end(), [](const Tile& t) { return t.src_local < 0; });
-  int n_int_src = 0;
-  for (const Tile& t : interior) n_int_src += t.src_local >= 0;
+  // interior tiles that sample a probe or load a source cell go last: they run the kernel with
+  // that code, the others a kernel without a per-step branch for it
+  auto plain_tile = [](const Tile& t) { return t.src_local < 0 && t.probe_count == 0; };
+  std::stable_partition(interior.begin(), interior.end(), plain_tile);
+  int n_int_xtra = 0;
+  for (const Tile& t : interior) n_int_xtra += !plain_tile(t);
   std::vector<Tile> all = interior;
   all.insert(all.end(), edge.begin(), edge.end());
   c->tiles_h = all;
@@ -294,7 +296,7 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     CK(cudaMemcpy(c->tprobes_d, tps.data(), sizeof(TileProbe) * tps.size(), cudaMemcpyHostToDevice),
        "tile probe upload");
   c->n_interior = (int)interior.size();
-  c->n_int_src = n_int_src;
+  c->n_int_xtra = n_int_xtra;
   c->n_edge = (int)edge.size();
   c->tiles_K = K;
   c->tiles_T = T;
@@ -413,11 +415,11 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       a.nsub = nsub;
       a.tprobes = c->tprobes_d;
       // Edge tiles first, on the high-priority side stream, so their few long-running warps
-      // start before the interior grid fills the GPU, then the interior tiles that load a source
-      // cell; joined back after the main interior launch.
+      // start before the interior grid fills the GPU, then the interior tiles with a probe or a
+      // source cell; joined back after the main interior launch.
       const bool fp32p = std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0;
-      const int n_main = c->n_interior - c->n_int_src;
-      const bool forked = n_main && (c->n_edge || c->n_int_src);
+      const int n_main = c->n_interior - c->n_int_xtra;
+      const bool forked = n_main && (c->n_edge || c->n_int_xtra);
       cudaStream_t side = forked ? c->side : c->stream;
       if (forked) {
         CK(cudaEventRecord(c->fork, c->stream), "fork");
@@ -429,14 +431,14 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
         CK(launch_tb<T>(a, edge_cells_per_lane(TS), true, 2, side, true), "tiled step (edge)");
         c->launches += 1;
       }
-      if (c->n_int_src) {
+      if (c->n_int_xtra) {
         a.tiles = c->tiles_d + n_main;
-        a.n_tiles = c->n_int_src;
+        a.n_tiles = c->n_int_xtra;
         if (fp32p) {
           CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, side, true),
-             "tiled step (source tiles, FP32 pairs)");
+             "tiled step (probe and source tiles, FP32 pairs)");
         } else {
-          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, side, true), "tiled step (source tiles)");
+          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, side, true), "tiled step (probe and source tiles)");
         }
         c->launches += 1;
       }

@@ -26,9 +26,10 @@ namespace {
 
 using namespace tile;
 
-// SRC: the tiles may hold their slab's source cell (always so for edge tiles and the recording
-// recompute; the planner launches the few interior tiles that do apart from the rest).
-template <typename T, int K, bool EDGE, bool REC, bool SRC>
+// XTRA: the tiles may sample a probe or hold their slab's source cell (always so for edge tiles
+// and the recording recompute; the planner launches the few interior tiles that do apart from the
+// rest, so that the main launch carries no per-step branch for them).
+template <typename T, int K, bool EDGE, bool REC, bool XTRA>
 __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const StepArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int tid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
   load_row<T, K, EDGE>(a.coef[kDj] + soff, g0, nzp, dj);
   load_row<T, K, EDGE>(a.coef[kBq] + soff, g0, nzp, bq);
   load_row<T, K, EDGE>(a.coef[kCq] + soff, g0, nzp, cq);
-  const bool has_src = SRC && tl.src_local >= 0 && lane == tl.src_local / K;
+  const bool has_src = XTRA && tl.src_local >= 0 && lane == tl.src_local / K;
 
   // Edge-tile bookkeeping (bit i = slot i).
   uint32_t mH = 0, mE = 0, mcH = 0, mcE = 0;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
     }
     // ---- Eq. 15 soft source at t = (n+1) dt (and its fold into G) ----
-    if (SRC && has_src) {
+    if (XTRA && has_src) {
       const int sl = tl.src_local % K;
       const T sv = (T)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
       put(e, sl, pick(e, sl) + sv);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
     }
     // ---- probe samples (only the tile whose exact region holds the probe) ----
-    if (a.series) {
+    if (XTRA && a.series) {
       for (int p = 0; p < tl.probe_count; ++p) {
         const TileProbe tp = a.tprobes[tl.probe_begin + p];
         if (lane == tp.local / K)
@@ -227,12 +228,12 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
 }
 
 template <typename T, int K, bool REC = false>
-cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st, bool src) {
+cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st, bool xtra) {
   const dim3 block(32 * wpb);
   const dim3 grid((a.n_tiles + wpb - 1) / wpb);
   if (edge)
     k_tb<T, K, true, REC, true><<<grid, block, 0, st>>>(a);
-  else if (REC || src)
+  else if (REC || xtra)
     k_tb<T, K, false, REC, true><<<grid, block, 0, st>>>(a);
   else
     k_tb<T, K, false, false, false><<<grid, block, 0, st>>>(a);
@@ -242,25 +243,25 @@ cudaError_t launch_k(const StepArgs<T>& a, bool edge, int wpb, cudaStream_t st, 
 }  // namespace
 
 template <>
-cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st, bool src) {
+cudaError_t launch_tb<float>(const StepArgs<float>& a, int K, bool edge, int wpb, cudaStream_t st, bool xtra) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<float, 4>(a, edge, wpb, st, src);
-    case 8: return launch_k<float, 8>(a, edge, wpb, st, src);
-    case 12: return launch_k<float, 12>(a, edge, wpb, st, src);
-    case 16: return launch_k<float, 16>(a, edge, wpb, st, src);
+    case 4: return launch_k<float, 4>(a, edge, wpb, st, xtra);
+    case 8: return launch_k<float, 8>(a, edge, wpb, st, xtra);
+    case 12: return launch_k<float, 12>(a, edge, wpb, st, xtra);
+    case 16: return launch_k<float, 16>(a, edge, wpb, st, xtra);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <>
-cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st, bool src) {
+cudaError_t launch_tb<double>(const StepArgs<double>& a, int K, bool edge, int wpb, cudaStream_t st, bool xtra) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   switch (K) {
-    case 4: return launch_k<double, 4>(a, edge, wpb, st, src);
-    case 8: return launch_k<double, 8>(a, edge, wpb, st, src);
+    case 4: return launch_k<double, 4>(a, edge, wpb, st, xtra);
+    case 8: return launch_k<double, 8>(a, edge, wpb, st, xtra);
     default: return cudaErrorInvalidValue;
   }
 }

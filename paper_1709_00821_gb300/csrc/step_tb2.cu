@@ -21,9 +21,10 @@ namespace rketd {
 namespace {
 
 using namespace tile;
-// SRC: the tile list holds the tiles whose loaded range contains their slab's source cell
-// (the planner launches those few apart, so the main launch carries no source code).
-template <int K, bool SRC>
+// XTRA: the tile list holds the tiles that sample a probe or whose loaded range contains their
+// slab's source cell (the planner launches those few apart, so that the main launch carries no
+// per-step branch for them).
+template <int K, bool XTRA>
 __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float> a) {
   constexpr int P = K / 2;
   const int lane = threadIdx.x & 31;
@@ -43,10 +44,10 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
   load_pairs<K>(a.coef[kBq] + base, bq, false);
   load_pairs<K>(a.coef[kCq] + base, cq, false);
   const f2 nS = pk(-a.S, -a.S);
-  const bool has_src = SRC && tl.src_local >= 0 && lane == tl.src_local / K;
+  const bool has_src = XTRA && tl.src_local >= 0 && lane == tl.src_local / K;
   const int src_slot = tl.src_local % K;
-  const bool extras = (SRC && tl.src_local >= 0) || tl.probe_count > 0;
 
+#pragma unroll 2
   for (int t = 0; t < a.nsub; ++t) {
     // Eq. 14 on pairs: the cell after pair p is pair p+1; after pair P-1 it is (B[0], next lane's A[0])
     const float nextA0 = __shfl_down_sync(kFull, lo_of(e[0]), 1);
@@ -68,8 +69,8 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
       g[p] = add2(g[p], fma2(cq[p], enew, fma2(bq[p], en, mul2(dj[p], g[p]))));
       e[p] = enew;
     }
-    if (extras) {
-      if (SRC && has_src) {
+    if constexpr (XTRA) {
+      if (has_src) {
         const float sv = (float)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
         put2(e, src_slot, pick2(e, src_slot) + sv);
         put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
@@ -88,15 +89,15 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
 
 }  // namespace
 
-cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int wpb, cudaStream_t st, bool src) {
+cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int wpb, cudaStream_t st, bool xtra) {
   if (a.n_tiles <= 0) return cudaSuccess;
   if (wpb < 1 || wpb > 4) return cudaErrorInvalidValue;
   const dim3 block(32 * wpb);
   const dim3 grid((a.n_tiles + wpb - 1) / wpb);
   switch (K) {
-    case 8: src ? k_tb2<8, true><<<grid, block, 0, st>>>(a) : k_tb2<8, false><<<grid, block, 0, st>>>(a); break;
-    case 12: src ? k_tb2<12, true><<<grid, block, 0, st>>>(a) : k_tb2<12, false><<<grid, block, 0, st>>>(a); break;
-    case 16: src ? k_tb2<16, true><<<grid, block, 0, st>>>(a) : k_tb2<16, false><<<grid, block, 0, st>>>(a); break;
+    case 8: xtra ? k_tb2<8, true><<<grid, block, 0, st>>>(a) : k_tb2<8, false><<<grid, block, 0, st>>>(a); break;
+    case 12: xtra ? k_tb2<12, true><<<grid, block, 0, st>>>(a) : k_tb2<12, false><<<grid, block, 0, st>>>(a); break;
+    case 16: xtra ? k_tb2<16, true><<<grid, block, 0, st>>>(a) : k_tb2<16, false><<<grid, block, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
