@@ -208,8 +208,9 @@ int edge_cells_per_lane(int T) { return 32 * 4 - 2 * T >= 32 ? 4 : 8; }
 
 // Builds the warp tiles for (K, T). Per slab, interior tiles of W = 32K - 2T exact cells
 // cover the middle: their loaded range (T cells of halo each side) stays inside
-// [max(1, ncpml), nz - 2 - ncpml], so the interior kernel needs no boundary code. Narrow
-// edge tiles (Ke cells per lane) cover the two ends, where the Mur/PEC cells, the CPML
+// [max(1, ncpml), nz - 2 - ncpml], so the interior kernel needs no boundary code; one more
+// interior tile, shifted left to end at that guard, takes the cells after the last whole one.
+// Narrow edge tiles (Ke cells per lane) cover the two ends, where the Mur/PEC cells, the CPML
 // and cells outside the slab live. Every cell is exact in exactly one tile.
 rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   const int L = 32 * K;
@@ -221,12 +222,13 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
   std::vector<Tile> interior, edge;
   std::vector<TileProbe> tp_int, tp_edge;
-  auto add = [&](int s, int64_t vstart, int64_t vend, int Lt, bool is_edge) -> rketd_status {
+  // a tile loading [start, start + Lt) and storing the exact cells [vstart, vend)
+  auto add_at = [&](int s, int64_t start, int64_t vstart, int64_t vend, int Lt, bool is_edge) -> rketd_status {
     Tile t{};
     t.slab = s;
-    t.start = vstart - T;
-    t.vlo = T;
-    t.vhi = (int32_t)(T + (vend - vstart));
+    t.start = start;
+    t.vlo = (int32_t)(vstart - start);
+    t.vhi = (int32_t)(vend - start);
     const int64_t sl = c->src[s] - t.start;
     t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
     std::vector<TileProbe>& tps = is_edge ? tp_edge : tp_int;
@@ -249,6 +251,9 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     (is_edge ? edge : interior).push_back(t);
     return RKETD_OK;
   };
+  auto add = [&](int s, int64_t vstart, int64_t vend, int Lt, bool is_edge) -> rketd_status {
+    return add_at(s, vstart - T, vstart, vend, Lt, is_edge);
+  };
   for (int s = 0; s < c->n_slabs; ++s) {
     const int64_t nz = c->nz[s];
     const int64_t lo_guard = std::max<int64_t>(1, nc);
@@ -257,12 +262,23 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     int64_t n_int = 0;
     if (a - T + L - 1 <= hi_guard) n_int = (hi_guard - (a - T + L - 1)) / W + 1;
     if (n_int == 0) a = 0;
-    const int64_t b = a + n_int * W;
+    int64_t b = a + n_int * W;
     rketd_status st;
     for (int64_t v = 0; v < a; v += We)
       if ((st = add(s, v, std::min<int64_t>(v + We, a), Le, true))) return st;
     for (int64_t j = 0; j < n_int; ++j)
       if ((st = add(s, a + j * W, a + (j + 1) * W, L, false))) return st;
+    // One more interior tile, shifted left as far as the guard needs (start a multiple of 4), takes
+    // over the cells after b that it holds exactly: the narrow edge tiles, several times dearer per
+    // cell, then only cover the last T + ncpml + a few cells.
+    if (n_int > 0) {
+      const int64_t st4 = ((hi_guard - L + 1) / 4) * 4;
+      const int64_t e_end = st4 + L - T;
+      if (st4 >= lo_guard && e_end > b) {
+        if ((st = add_at(s, st4, b, e_end, L, false))) return st;
+        b = e_end;
+      }
+    }
     for (int64_t v = b; v < nz; v += We)
       if ((st = add(s, v, std::min<int64_t>(v + We, nz), Le, true))) return st;
   }

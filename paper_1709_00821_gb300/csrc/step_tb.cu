@@ -53,6 +53,12 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
   load_row<T, K, EDGE>(a.coef[kBq] + soff, g0, nzp, bq);
   load_row<T, K, EDGE>(a.coef[kCq] + soff, g0, nzp, cq);
   const bool has_src = XTRA && tl.src_local >= 0 && lane == tl.src_local / K;
+  const LaneProbes lp = (XTRA && a.series)
+                            ? lane_probes(a.tprobes, tl.probe_begin, tl.probe_count, lane, K, a.series_len, a.series_pos)
+                            : LaneProbes{0, 0, 0, 0, 0};
+  const bool tile_src = XTRA && tl.src_local >= 0;  // warp-uniform
+  const PassSource<T> ps =
+      tile_src ? pass_source<T>(a.n0, a.nsub, a.dt, a.t0, a.tau, a.amp, lane) : PassSource<T>{T(0), T(0)};
 
   // Edge-tile bookkeeping (bit i = slot i).
   uint32_t mH = 0, mE = 0, mcH = 0, mcE = 0;
@@ -155,11 +161,13 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
     }
     // ---- Eq. 15 soft source at t = (n+1) dt (and its fold into G) ----
-    if (XTRA && has_src) {
-      const int sl = tl.src_local % K;
-      const T sv = (T)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
-      put(e, sl, pick(e, sl) + sv);
-      put(jj, sl, fma(-a.coef[kDa][soff + g0 + sl], sv, pick(jj, sl)));
+    if (tile_src) {
+      const T sv = source_at(ps, t);
+      if (has_src) {
+        const int sl = tl.src_local % K;
+        put(e, sl, pick(e, sl) + sv);
+        put(jj, sl, fma(-a.coef[kDa][soff + g0 + sl], sv, pick(jj, sl)));
+      }
     }
     // ---- ends: first-order Mur or PEC ----
     if (EDGE) {
@@ -180,11 +188,15 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       }
     }
     // ---- probe samples (only the tile whose exact region holds the probe) ----
-    if (XTRA && a.series) {
-      for (int p = 0; p < tl.probe_count; ++p) {
-        const TileProbe tp = a.tprobes[tl.probe_begin + p];
-        if (lane == tp.local / K)
-          a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick(e, tp.local % K);
+    if (XTRA && lp.n > 0) {
+      a.series[lp.o0 + t] = pick(e, lp.s0);
+      if (lp.n > 1) {
+        a.series[lp.o1 + t] = pick(e, lp.s1);
+        for (int p = 0, m = 0; lp.n > 2 && p < tl.probe_count; ++p) {
+          const TileProbe tp = a.tprobes[tl.probe_begin + p];
+          if (lane == tp.local / K && m++ >= 2)
+            a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick(e, tp.local % K);
+        }
       }
     }
     // ---- window recording for the adjoint ----

@@ -46,6 +46,12 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
   const f2 nS = pk(-a.S, -a.S);
   const bool has_src = XTRA && tl.src_local >= 0 && lane == tl.src_local / K;
   const int src_slot = tl.src_local % K;
+  const LaneProbes lp = (XTRA && a.series)
+                            ? lane_probes(a.tprobes, tl.probe_begin, tl.probe_count, lane, K, a.series_len, a.series_pos)
+                            : LaneProbes{0, 0, 0, 0, 0};
+  const bool tile_src = XTRA && tl.src_local >= 0;  // warp-uniform
+  const PassSource<float> ps = tile_src ? pass_source<float>(a.n0, a.nsub, a.dt, a.t0, a.tau, a.amp, lane)
+                                        : PassSource<float>{0.f, 0.f};
 
 #pragma unroll 2
   for (int t = 0; t < a.nsub; ++t) {
@@ -70,15 +76,23 @@ __global__ void __launch_bounds__(128, RKETD_TB_MINB) k_tb2(const StepArgs<float
       e[p] = enew;
     }
     if constexpr (XTRA) {
-      if (has_src) {
-        const float sv = (float)pulse((double)(a.n0 + t + 1) * a.dt, a.t0, a.tau, a.amp);
-        put2(e, src_slot, pick2(e, src_slot) + sv);
-        put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
+      if (tile_src) {
+        const float sv = source_at(ps, t);
+        if (has_src) {
+          put2(e, src_slot, pick2(e, src_slot) + sv);
+          put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
+        }
       }
-      for (int q = 0; q < (a.series ? tl.probe_count : 0); ++q) {
-        const TileProbe tp = a.tprobes[tl.probe_begin + q];
-        if (lane == tp.local / K)
-          a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick2(e, tp.local % K);
+      if (lp.n > 0) {
+        a.series[lp.o0 + t] = pick2(e, lp.s0);
+        if (lp.n > 1) {
+          a.series[lp.o1 + t] = pick2(e, lp.s1);
+          for (int q = 0, m = 0; lp.n > 2 && q < tl.probe_count; ++q) {
+            const TileProbe tp = a.tprobes[tl.probe_begin + q];
+            if (lane == tp.local / K && m++ >= 2)
+              a.series[(int64_t)tp.slot * a.series_len + a.series_pos + t] = pick2(e, tp.local % K);
+          }
+        }
       }
     }
   }

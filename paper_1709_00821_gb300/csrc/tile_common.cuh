@@ -16,6 +16,27 @@ __device__ __forceinline__ double pulse(double t, double t0, double tau, double 
   return amp * u * exp(-0.5 * u * u);
 }
 
+// The source values of one pass (steps n0 + 1 .. n0 + nsub, nsub <= 64), evaluated once per warp:
+// lane l holds steps n0 + 1 + l and n0 + 33 + l. One FP64 pulse per lane and pass instead of one
+// per step in the source lane (the FP64 pipe is narrow). Warp-uniform calls only.
+template <typename T>
+struct PassSource {
+  T v0, v1;
+};
+template <typename T>
+__device__ __forceinline__ PassSource<T> pass_source(int64_t n0, int nsub, double dt, double t0, double tau,
+                                                     double amp, int lane) {
+  PassSource<T> r{T(0), T(0)};
+  if (lane < nsub) r.v0 = (T)pulse((double)(n0 + 1 + lane) * dt, t0, tau, amp);
+  if (lane + 32 < nsub) r.v1 = (T)pulse((double)(n0 + 33 + lane) * dt, t0, tau, amp);
+  return r;
+}
+// value of step n0 + 1 + t, all lanes (t warp-uniform)
+template <typename T>
+__device__ __forceinline__ T source_at(const PassSource<T>& p, int t) {
+  return t < 32 ? __shfl_sync(kFull, p.v0, t) : __shfl_sync(kFull, p.v1, t - 32);
+}
+
 template <typename T, int K>
 __device__ __forceinline__ T pick(const T (&r)[K], int i) {
   T v = T(0);
@@ -30,6 +51,32 @@ __device__ __forceinline__ void put(T (&r)[K], int i, T v) {
 #pragma unroll
   for (int q = 0; q < K; ++q)
     if (q == i) r[q] = v;
+}
+
+// The probes one lane samples in a pass, gathered once before the time loop: the first two in
+// registers (slot among the lane's K cells, offset of the pass's first sample in the series
+// buffer); a lane with more (rare: probes closer than K cells) reads the rest from the list.
+struct LaneProbes {
+  int n, s0, s1;
+  int64_t o0, o1;
+};
+__device__ __forceinline__ LaneProbes lane_probes(const TileProbe* list, int begin, int count, int lane, int K,
+                                                  int series_len, int series_pos) {
+  LaneProbes r{0, 0, 0, 0, 0};
+  for (int q = 0; q < count; ++q) {
+    const TileProbe p = list[begin + q];
+    if (lane != p.local / K) continue;
+    const int64_t o = (int64_t)p.slot * series_len + series_pos;
+    if (r.n == 0) {
+      r.s0 = p.local % K;
+      r.o0 = o;
+    } else if (r.n == 1) {
+      r.s1 = p.local % K;
+      r.o1 = o;
+    }
+    ++r.n;
+  }
+  return r;
 }
 
 // Four consecutive values at p (16-byte aligned for float, 32 for double).
