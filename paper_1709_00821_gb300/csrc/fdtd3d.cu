@@ -392,8 +392,9 @@ __global__ void __launch_bounds__(256) k3_e(const Args3<T> a) {
   if (i >= nx || j >= ny) return;
   const int im = (i > 0) ? i - 1 : (a.per ? nx - 1 : -1);
   const int jm = (j > 0) ? j - 1 : (a.per ? ny - 1 : -1);
-  const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
   const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  // the sheet source's value, only where this column range holds the sheet (FP64 is narrow here)
+  const T srcv = (a.sheet_k >= kb && a.sheet_k < ke) ? (T)pulse3(t, a.t0, a.tau, a.amp) : T(0);
   int pk[4], ps[4];
   const int npc = column_probes(a, i, j, kb, ke, pk, ps);
   T hx_km = T(0), hy_km = T(0);
@@ -451,8 +452,9 @@ __global__ void __launch_bounds__(256) k3_fused(const Args3<T> a) {
   const bool act = i < nx;
   const int im = (i > 0) ? i - 1 : (a.per ? nx - 1 : -1);
   const int jm = (j > 0) ? j - 1 : (a.per ? ny - 1 : -1);
-  const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
   const int kb = blockIdx.z * a.kc, ke = min(a.nz, kb + a.kc);
+  // the sheet source's value, only where this column range holds the sheet (FP64 is narrow here)
+  const T srcv = (a.sheet_k >= kb && a.sheet_k < ke) ? (T)pulse3(t, a.t0, a.tau, a.amp) : T(0);
   int pk[4], ps[4];
   const int npc = act ? column_probes(a, i, j, kb, ke, pk, ps) : 0;
   T hx_km = T(0), hy_km = T(0);
@@ -994,7 +996,14 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     for (; issued < kStages && issued < NP; ++issued) issue(issued);
   const int i = i0 + lane, j = j0 + w;
   const bool act = w < kTY && i < nx && j < ny;
-  const T srcv = (T)pulse3(t, a.t0, a.tau, a.amp);
+  // the sheet source's value, only in items that hold the sheet plane (block-uniform): one FP64
+  // evaluation per warp, broadcast from lane 0 (the FP64 pipe is narrow on this part)
+  T srcv = T(0);
+  if (a.sheet_k >= kb && a.sheet_k < ke) {
+    double v = 0.0;
+    if (lane == 0) v = pulse3(t, a.t0, a.tau, a.amp);
+    srcv = (T)__shfl_sync(0xffffffffu, v, 0);
+  }
   int pk[4], ps[4];
   const int npc = act ? column_probes(a, i, j, kb, ke, pk, ps) : 0;
   constexpr int EX = 0, EY = St::box, EZ = 2 * St::box, HX = 3 * St::box, HY = 4 * St::box, HZ = 5 * St::box;
