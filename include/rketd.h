@@ -217,6 +217,28 @@ rketd_status rketd_get_kernel_timing(rketd_ctx* ctx, double* ms, int64_t* launch
 int64_t rketd_launch_count(const rketd_ctx* ctx);
 
 /*
+ * Host-only view of the 1D tile plan that rketd_step builds for a batch of slabs, with no
+ * device work (the library need not find a GPU). The paper has no counterpart: it lets tests
+ * and tools check the temporally blocked tiling without running it.
+ *   n_slabs, nz[n_slabs], src_cell[n_slabs], n_probes, probe_cell[n_slabs * n_probes]
+ *                   as for rketd_create_batch_1d (slab-local cells)
+ *   cpml_cells      CPML cells per end (0 for first-order Mur ends)
+ *   cells_per_lane  K, a multiple of 4 in [4, 32]; tb_steps: T, a multiple of 4 in [4, 64]
+ *   rows            caller-owned int64 array of cap rows of 8, written in launch order: slab, start
+ *                   (slab-local first loaded cell, may be negative for edge tiles), vlo, vhi (the
+ *                   exact cells stored are start + [vlo, vhi)), kind (0 interior tile, 1 interior
+ *                   tile that samples a probe or loads the source cell, 2 edge tile), src_local (the
+ *                   source cell minus start if loaded, else -1), probe_count (probes among the exact
+ *                   cells), loaded cells (32 K, or 32 Ke for edge tiles)
+ *   cap             rows available; n_tiles receives the tile count even when it exceeds cap
+ * Returns RKETD_EINVAL for NULL pointers, counts or shapes outside these ranges, cells outside
+ * their slab, or a tile too narrow for its halo.
+ */
+rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64_t* src_cell, int32_t n_probes,
+                                 const int64_t* probe_cell, int32_t cpml_cells, int32_t cells_per_lane,
+                                 int32_t tb_steps, int64_t* rows, int64_t cap, int64_t* n_tiles);
+
+/*
  * Advances one Mur-terminated 1D slab by nsteps steps without allocating any memory.
  * The paper has no counterpart: it exists for callers that must not allocate device
  * memory -- code recorded into a CUDA stream capture (allocation is illegal while

@@ -206,20 +206,28 @@ void fill_auto(rketd_options& o, int prec) {
 // Cells per lane of the edge-tile kernel: narrow tiles keep the boundary code cheap.
 int edge_cells_per_lane(int T) { return 32 * 4 - 2 * T >= 32 ? 4 : 8; }
 
-// Builds the warp tiles for (K, T). Per slab, interior tiles of W = 32K - 2T exact cells
-// cover the middle: their loaded range (T cells of halo each side) stays inside
+// The tile lists of one plan: interior tiles (those without a probe or a source cell first), then
+// edge tiles, in launch order; the tile-probe list they index.
+struct TilePlan {
+  std::vector<Tile> tiles;
+  std::vector<TileProbe> probes;
+  int n_interior = 0, n_int_xtra = 0, n_edge = 0;
+};
+
+// Builds the warp tiles for (K, T) on the host. Per slab, interior tiles of W = 32K - 2T exact
+// cells cover the middle: their loaded range (T cells of halo each side) stays inside
 // [max(1, ncpml), nz - 2 - ncpml], so the interior kernel needs no boundary code; one more
 // interior tile, shifted left to end at that guard, takes the cells after the last whole one.
 // Narrow edge tiles (Ke cells per lane) cover the two ends, where the Mur/PEC cells, the CPML
 // and cells outside the slab live. Every cell is exact in exactly one tile.
-rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
+rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* srcs, int n_probes,
+                             const int64_t* probe_cell, int64_t nc, int K, int T, TilePlan& out) {
   const int L = 32 * K;
   const int W = L - 2 * T;
   const int Ke = edge_cells_per_lane(T);
   const int Le = 32 * Ke;
   const int We = Le - 2 * T;
   if (W < 4 || We < 4) return fail(RKETD_EINVAL, "tile of %d cells cannot hold %d steps of halo", L, T);
-  const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
   std::vector<Tile> interior, edge;
   std::vector<TileProbe> tp_int, tp_edge;
   // a tile loading [start, start + Lt) and storing the exact cells [vstart, vend)
@@ -229,23 +237,23 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
     t.start = start;
     t.vlo = (int32_t)(vstart - start);
     t.vhi = (int32_t)(vend - start);
-    const int64_t sl = c->src[s] - t.start;
+    const int64_t sl = srcs[s] - t.start;
     t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
     std::vector<TileProbe>& tps = is_edge ? tp_edge : tp_int;
     t.probe_begin = (int32_t)tps.size();
-    for (int p = 0; p < c->n_probes; ++p) {
-      const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
+    for (int p = 0; p < n_probes; ++p) {
+      const int64_t cell = probe_cell[(size_t)s * n_probes + p];
       const int64_t loc = cell - t.start;
-      if (loc >= t.vlo && loc < t.vhi) tps.push_back({(int32_t)loc, s * c->n_probes + p});
+      if (loc >= t.vlo && loc < t.vhi) tps.push_back({(int32_t)loc, s * n_probes + p});
     }
     t.probe_count = (int32_t)tps.size() - t.probe_begin;
     if (t.probe_count > kMaxTileProbes) return fail(RKETD_EINVAL, "more than %d probes in one tile", kMaxTileProbes);
     // probes anywhere in the loaded range (the adjoint seeds every copy of a probe cell)
     t.adj_begin = (int32_t)tps.size();
-    for (int p = 0; p < c->n_probes; ++p) {
-      const int64_t cell = c->probe_cell[(size_t)s * c->n_probes + p];
+    for (int p = 0; p < n_probes; ++p) {
+      const int64_t cell = probe_cell[(size_t)s * n_probes + p];
       const int64_t loc = cell - t.start;
-      if (loc >= 0 && loc < Lt) tps.push_back({(int32_t)loc, s * c->n_probes + p});
+      if (loc >= 0 && loc < Lt) tps.push_back({(int32_t)loc, s * n_probes + p});
     }
     t.adj_count = (int32_t)tps.size() - t.adj_begin;
     (is_edge ? edge : interior).push_back(t);
@@ -254,8 +262,8 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   auto add = [&](int s, int64_t vstart, int64_t vend, int Lt, bool is_edge) -> rketd_status {
     return add_at(s, vstart - T, vstart, vend, Lt, is_edge);
   };
-  for (int s = 0; s < c->n_slabs; ++s) {
-    const int64_t nz = c->nz[s];
+  for (int s = 0; s < n_slabs; ++s) {
+    const int64_t nz = nzs[s];
     const int64_t lo_guard = std::max<int64_t>(1, nc);
     const int64_t hi_guard = nz - 2 - nc;
     int64_t a = round_up(lo_guard + T, 4);
@@ -290,14 +298,28 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   // that code, the others a kernel without a per-step branch for it
   auto plain_tile = [](const Tile& t) { return t.src_local < 0 && t.probe_count == 0; };
   std::stable_partition(interior.begin(), interior.end(), plain_tile);
-  int n_int_xtra = 0;
-  for (const Tile& t : interior) n_int_xtra += !plain_tile(t);
-  std::vector<Tile> all = interior;
-  all.insert(all.end(), edge.begin(), edge.end());
+  out.n_int_xtra = 0;
+  for (const Tile& t : interior) out.n_int_xtra += !plain_tile(t);
+  out.n_interior = (int)interior.size();
+  out.n_edge = (int)edge.size();
+  out.tiles = interior;
+  out.tiles.insert(out.tiles.end(), edge.begin(), edge.end());
+  out.probes = tp_int;
+  out.probes.insert(out.probes.end(), tp_edge.begin(), tp_edge.end());
+  return RKETD_OK;
+}
+
+// Plans the tiles for (K, T) and uploads the lists.
+rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
+  const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  TilePlan plan;
+  rketd_status st0 =
+      build_tile_plan(c->n_slabs, c->nz.data(), c->src.data(), c->n_probes, c->probe_cell.data(), nc, K, T, plan);
+  if (st0) return st0;
+  const std::vector<Tile>& all = plan.tiles;
+  const std::vector<TileProbe>& tps = plan.probes;
   c->tiles_h = all;
   c->adj_w_lo = c->adj_w_hi = -1;  // the adjoint's tile order is rebuilt on next use
-  std::vector<TileProbe> tps = tp_int;
-  tps.insert(tps.end(), tp_edge.begin(), tp_edge.end());
   // captured graphs point at the old tile lists
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   c->graphs.clear();
@@ -311,9 +333,9 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   if (!tps.empty())
     CK(cudaMemcpy(c->tprobes_d, tps.data(), sizeof(TileProbe) * tps.size(), cudaMemcpyHostToDevice),
        "tile probe upload");
-  c->n_interior = (int)interior.size();
-  c->n_int_xtra = n_int_xtra;
-  c->n_edge = (int)edge.size();
+  c->n_interior = plan.n_interior;
+  c->n_int_xtra = plan.n_int_xtra;
+  c->n_edge = plan.n_edge;
   c->tiles_K = K;
   c->tiles_T = T;
   return RKETD_OK;
@@ -1362,6 +1384,46 @@ rketd_status rketd_destroy(rketd_ctx* c) {
   if (!c) return RKETD_OK;
   cudaStreamSynchronize(c->stream);
   delete c;
+  return RKETD_OK;
+}
+
+rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64_t* src_cell, int32_t n_probes,
+                                 const int64_t* probe_cell, int32_t cpml_cells, int32_t cells_per_lane,
+                                 int32_t tb_steps, int64_t* rows, int64_t cap, int64_t* n_tiles) {
+  if (!nz || !src_cell || !n_tiles || (n_probes > 0 && !probe_cell) || (cap > 0 && !rows))
+    return fail(RKETD_EINVAL, "NULL argument");
+  if (n_slabs < 1 || n_probes < 0 || cpml_cells < 0 || cap < 0) return fail(RKETD_EINVAL, "bad count");
+  if (cells_per_lane < 4 || cells_per_lane > kMaxCells || cells_per_lane % 4)
+    return fail(RKETD_EINVAL, "cells_per_lane must be a multiple of 4 in [4, %d]", kMaxCells);
+  if (tb_steps < 4 || tb_steps > 64 || tb_steps % 4) return fail(RKETD_EINVAL, "tb_steps must be a multiple of 4 in [4, 64]");
+  for (int s = 0; s < n_slabs; ++s) {
+    if (nz[s] < 8) return fail(RKETD_EINVAL, "slab %d: nz must be >= 8", s);
+    if (src_cell[s] < 1 || src_cell[s] > nz[s] - 2) return fail(RKETD_EINVAL, "slab %d: source cell outside", s);
+    for (int p = 0; p < n_probes; ++p) {
+      const int64_t q = probe_cell[(size_t)s * n_probes + p];
+      if (q < 0 || q >= nz[s]) return fail(RKETD_EINVAL, "slab %d: probe %d outside", s, p);
+    }
+  }
+  TilePlan plan;
+  rketd_status st = build_tile_plan(n_slabs, nz, src_cell, n_probes, probe_cell, cpml_cells, cells_per_lane, tb_steps,
+                                    plan);
+  if (st) return st;
+  *n_tiles = (int64_t)plan.tiles.size();
+  const int64_t Lint = 32 * cells_per_lane, Ledge = 32 * edge_cells_per_lane(tb_steps);
+  for (int64_t i = 0; i < (int64_t)plan.tiles.size() && i < cap; ++i) {
+    const Tile& t = plan.tiles[i];
+    const bool is_edge = i >= plan.n_interior;
+    const int64_t kind = is_edge ? 2 : (i >= plan.n_interior - plan.n_int_xtra ? 1 : 0);
+    int64_t* r = rows + 8 * i;
+    r[0] = t.slab;
+    r[1] = t.start;
+    r[2] = t.vlo;
+    r[3] = t.vhi;
+    r[4] = kind;
+    r[5] = t.src_local;
+    r[6] = t.probe_count;
+    r[7] = is_edge ? Ledge : Lint;
+  }
   return RKETD_OK;
 }
 
