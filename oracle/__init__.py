@@ -264,9 +264,10 @@ class State3D:
         return self.fields[i].reshape(prob.nz, prob.ny, prob.nx)
 
 
-def run3d(prob, steps=None, state=None, series=False):
-    """Runs the 3D oracle on a workloads.Grid3D problem."""
-    L = lib()
+def run3d(prob, steps=None, state=None, series=False, mutant: int = 0):
+    """Runs the 3D oracle on a workloads.Grid3D problem (`mutant` > 0: a build with one planted
+    mistake, for the tests that check the pins reject it)."""
+    L = lib(mutant=mutant)
     steps = prob.steps if steps is None else steps
     st = State3D(prob) if state is None else state
     g = OrGrid3D()

@@ -16,6 +16,12 @@
  * One step: H update (+ TF/SF H corrections), 1D incident H, E and J update (+ TF/SF E
  * corrections, sheet source), 1D incident E, running DFT of Ex at the probes.
  * Only tests/ and bench.py's CPU legs load this file; it shares no code with the CUDA path.
+ *
+ * Pins (tests/test_oracle3d_pins.py): reduction to the 1D oracle along z for both polarisations,
+ * the exact lattice recurrence of a transverse Fourier mode (every x/y difference term), a cyclic
+ * rotation of the cube mapping the x/y-face CPML onto the z-face CPML bit for bit, the x/y-face
+ * CPML reflection against a domain with unreachable faces, and the TF/SF box in vacuum.
+ * OR_MUTANT 5-8 plant one mistake each (tests only) for the check that the pins reject them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -152,7 +158,12 @@ int or_run3d(const or_grid3d* g, const uint8_t* mat, const double* mat_wp2, cons
           const int kp = (k + 1 < nz) ? k + 1 : -1;
           /* Hx (i, j+1/2, k+1/2) */
           if (jp >= 0 && kp >= 0) {
+#if defined(OR_MUTANT) && OR_MUTANT == 6
+            /* planted mistake: Hx's y difference taken along x */
+            double dEz = Ez[IDX(ip >= 0 ? ip : i, j, k)] - Ez[c];
+#else
             double dEz = Ez[IDX(i, jp, k)] - Ez[c];
+#endif
             double dEy = Ey[IDX(i, j, kp)] - Ey[c];
             const double* ty = TB(1, 1, j);
             const double* tz = TB(2, 1, k);
@@ -166,7 +177,12 @@ int or_run3d(const or_grid3d* g, const uint8_t* mat, const double* mat_wp2, cons
             double dEx = Ex[IDX(i, j, kp)] - Ex[c];
             double dEz = Ez[IDX(ip, j, k)] - Ez[c];
             const double* tz = TB(2, 1, k);
+#if defined(OR_MUTANT) && OR_MUTANT == 7
+            /* planted mistake: Hy's x-face CPML graded at the E nodes */
+            const double* tx = TB(0, 0, i);
+#else
             const double* tx = TB(0, 1, i);
+#endif
             double cz = dEx / d, cx = dEz / d;
             if (tz[3] != 0.0) { P[8][c] = tz[0] * P[8][c] + tz[1] * cz; cz = dEx * tz[2] / d + P[8][c]; }
             if (tx[3] != 0.0) { P[9][c] = tx[0] * P[9][c] + tx[1] * cx; cx = dEz * tx[2] / d + P[9][c]; }
@@ -217,7 +233,12 @@ int or_run3d(const or_grid3d* g, const uint8_t* mat, const double* mat_wp2, cons
             const double* ty = TB(1, 0, j);
             const double* tz = TB(2, 0, k);
             double cy = dHz / d, cz = dHy / d;
+#if defined(OR_MUTANT) && OR_MUTANT == 8
+            /* planted mistake: Ex's y-face CPML memory driven with the wrong sign */
+            if (ty[3] != 0.0) { P[0][c] = ty[0] * P[0][c] - ty[1] * cy; cy = dHz * ty[2] / d + P[0][c]; }
+#else
             if (ty[3] != 0.0) { P[0][c] = ty[0] * P[0][c] + ty[1] * cy; cy = dHz * ty[2] / d + P[0][c]; }
+#endif
             if (tz[3] != 0.0) { P[1][c] = tz[0] * P[1][c] + tz[1] * cz; cz = dHy * tz[2] / d + P[1][c]; }
             double curl = cy - cz;
             double En = Ex[c];
@@ -234,7 +255,12 @@ int or_run3d(const or_grid3d* g, const uint8_t* mat, const double* mat_wp2, cons
             double cz = dHx / d, cx = dHz / d;
             if (tz[3] != 0.0) { P[2][c] = tz[0] * P[2][c] + tz[1] * cz; cz = dHx * tz[2] / d + P[2][c]; }
             if (tx[3] != 0.0) { P[3][c] = tx[0] * P[3][c] + tx[1] * cx; cx = dHz * tx[2] / d + P[3][c]; }
+#if defined(OR_MUTANT) && OR_MUTANT == 5
+            /* planted mistake: Ey's x term with the wrong sign */
+            double curl = cz + cx;
+#else
             double curl = cz - cx;
+#endif
             double En = Ey[c];
             double Enew = mEE[my] * En + mEH[my] * curl - mEJ[my] * Jy[c];
             Jy[c] = ma[my] * Jy[c] + mb1[my] * En + mb2[my] * (Enew - En);
