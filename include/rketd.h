@@ -241,26 +241,30 @@ rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64
 /*
  * Advances one Mur-terminated 1D slab by nsteps steps without allocating any memory.
  * The paper has no counterpart: it exists for callers that must not allocate device
- * memory -- code recorded into a CUDA stream capture (allocation is illegal while
- * capturing), a framework whose caching allocator owns the GPU, or a loop that cannot
- * afford the device-wide synchronisation of cudaMalloc/cudaFree. It runs the same tiled
- * kernels as rketd_step (default tile shapes, no probes or DFT) and keeps their working
- * memory (update coefficients, the two working copies of the fields, the tile list) in one
- * fixed array of about 12.7 MB that the library reserves on every GPU it is loaded on,
+ * memory -- a framework whose caching allocator owns the GPU and forbids allocations behind
+ * its back, or a loop that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * It runs the same tiled kernels as rketd_step (default tile shapes, no probes or DFT) and keeps
+ * their working memory (update coefficients, the two working copies of the fields, the tile list)
+ * in one fixed array of about 12.7 MB that the library reserves on every GPU it is loaded on,
  * from load until process exit.
  *   grid          dz, dt, prec (RKETD_F32 or RKETD_F64); bc must be RKETD_BC_MUR1
  *   nz            E nodes, 8 <= nz <= 131072 (larger is rejected with RKETD_EINVAL)
- *   wp2, nu       device FP64 arrays [nz] (rad^2/s^2, 1/s), read on the stream
+ *   wp2, nu       device FP64 arrays [nz] (rad^2/s^2, 1/s), read on the stream. They must be
+ *                 finite and >= 0: this call does not check them (they are never copied to the
+ *                 host), and a negative or non-finite value makes the fields grow or turn to NaN
  *   src_cell      1 <= src_cell <= nz-2; pulse as for rketd_create_1d
  *   n0            step index of the given fields (they hold E^n0, H^{n0-1/2}, J^n0)
  *   E, J          device arrays [nz], H [nz-1], SI, FP32 or FP64 as grid->prec; read and
  *                 overwritten in place with the state at step n0 + nsteps
  *   stream        cudaStream_t (NULL = legacy default stream)
  * The first call on each device looks up the device address of the fixed array (with that
- * device current); make that first call before any stream capture. Every call reuses the
- * same array, so calls whose GPU work overlaps (other streams, other host threads) race and
- * must be serialised by the caller. Async on the stream; errors from argument checks are
- * returned at once, device errors surface at the next synchronisation.
+ * device current) and keeps it for the life of the process; make that first call before any
+ * stream capture. A device reset (cudaDeviceReset, or destroying and recreating the primary
+ * context) while the library stays loaded leaves that address stale: do not use this entry
+ * point after one. Every call reuses the same array, so calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised by the caller. Async on the stream;
+ * errors from argument checks are returned at once, device errors surface at the next
+ * synchronisation.
  */
 rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64_t nz, const double* wp2, const double* nu,
                                       int64_t src_cell, const rketd_pulse* pulse, int64_t n0, int64_t nsteps,

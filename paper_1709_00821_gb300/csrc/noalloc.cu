@@ -1,14 +1,12 @@
 // rketd_advance_1d_noalloc: the temporally blocked single-slab step with all of its
 // working memory in one fixed device array, for callers that cannot allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not wanted -- for example
-// a host callback or a loop that is being recorded into a CUDA stream capture (allocation
-// calls are illegal while a stream is capturing), a framework whose caching allocator owns
-// the whole GPU and forbids allocations behind its back, or a real-time loop that cannot
-// afford the device-wide synchronisation that cudaMalloc/cudaFree imply. Such callers pass
-// their own input and output arrays; everything else the step needs (the per-cell update
-// coefficients, two working copies of the fields for the ping-pong passes, the tile list)
-// lives in g_noalloc_scratch below.
+// Who needs it: code that runs where cudaMalloc is not allowed or not wanted -- a framework
+// whose caching allocator owns the whole GPU and forbids allocations behind its back, or a
+// real-time loop that cannot afford the device-wide synchronisation that cudaMalloc/cudaFree
+// imply. Such callers pass their own input and output arrays; everything else the step needs
+// (the per-cell update coefficients, two working copies of the fields for the ping-pong passes,
+// the tile list) lives in g_noalloc_scratch below.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this library holds
 // it (kNoallocScratchBytes) until the process exits, whether or not the entry point is used.
@@ -50,24 +48,42 @@ rketd_status nfail(rketd_status st, const char* msg) {
   return st;
 }
 
-// Same tiling as the context path: edge tiles of Ke cells per lane over [0, a) and [b, nz),
-// interior tiles of K cells per lane over [a, b), those with index in [j_src0, j_src1) (the ones
-// that load the source cell) last. One thread writes the whole list and the slab table
-// (soff = 0, off = 0, nz, src).
-__global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int K, int Ke, int T, int64_t j_src0,
-                       int64_t j_src1, int* counts) {
+// The tiling of one slab: interior tiles of K cells per lane cover [a, b) (W = 32K - 2T exact cells
+// each, loaded range inside the guard cells [1, nz - 2]), narrow edge tiles of Ke cells per lane
+// cover [0, a) and [b, nz). Computed once on the host; k_plan writes the same tiles on the device.
+struct NoallocPlan {
+  int64_t a = 0, n_int = 0, b = 0, n_edge = 0;
+  int64_t j_src0 = 0, j_src1 = 0;  // interior tiles whose loaded range holds the source cell
+};
+
+NoallocPlan noalloc_plan(int64_t nz, int64_t src, int K, int Ke, int T) {
+  NoallocPlan p;
+  const int64_t L = 32 * K, W = L - 2 * T, We = 32 * Ke - 2 * T;
+  const int64_t hi_guard = nz - 2;
+  p.a = ((1 + T + 3) / 4) * 4;
+  if (p.a - T + L - 1 <= hi_guard) p.n_int = (hi_guard - (p.a - T + L - 1)) / W + 1;
+  if (p.n_int == 0) p.a = 0;
+  p.b = p.a + p.n_int * W;
+  p.n_edge = (p.a + We - 1) / We + (nz - p.b + We - 1) / We;
+  // tile j loads [a + jW - T, a + jW - T + L): it holds src when d - L < jW <= d, d = src - a + T
+  const int64_t d = src - p.a + T;
+  if (p.n_int && d >= 0) {
+    p.j_src0 = d - L + 1 > 0 ? (d - L + 1 + W - 1) / W : 0;
+    p.j_src1 = std::min<int64_t>(p.n_int, d / W + 1);
+    if (p.j_src1 < p.j_src0) p.j_src1 = p.j_src0;
+  }
+  return p;
+}
+
+// Writes the tile list of a NoallocPlan (interior tiles without the source first, then those with
+// it, then the edge tiles) and the slab table (soff = 0, off = 0, nz, src). One thread.
+__global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int K, int Ke, int T, NoallocPlan pl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   table[0] = 0;
   table[1] = 0;
   table[2] = nz;
   table[3] = src;
   const int L = 32 * K, W = L - 2 * T, Le = 32 * Ke, We = Le - 2 * T;
-  const int64_t lo_guard = 1, hi_guard = nz - 2;
-  int64_t a = ((lo_guard + T + 3) / 4) * 4;
-  int64_t n_int = 0;
-  if (a - T + L - 1 <= hi_guard) n_int = (hi_guard - (a - T + L - 1)) / W + 1;
-  if (n_int == 0) a = 0;
-  const int64_t b = a + n_int * W;
   int n = 0;
   auto put = [&](int64_t v0, int64_t v1, int Lt) {
     Tile t;
@@ -83,13 +99,11 @@ __global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int
     t.adj_count = 0;
     tiles[n++] = t;
   };
-  for (int64_t j = 0; j < n_int; ++j)
-    if (j < j_src0 || j >= j_src1) put(a + j * W, a + (j + 1) * W, L);
-  for (int64_t j = j_src0; j < j_src1; ++j) put(a + j * W, a + (j + 1) * W, L);
-  counts[0] = n;
-  for (int64_t v = 0; v < a; v += We) put(v, v + We < a ? v + We : a, Le);
-  for (int64_t v = b; v < nz; v += We) put(v, v + We < nz ? v + We : nz, Le);
-  counts[1] = n - counts[0];
+  for (int64_t j = 0; j < pl.n_int; ++j)
+    if (j < pl.j_src0 || j >= pl.j_src1) put(pl.a + j * W, pl.a + (j + 1) * W, L);
+  for (int64_t j = pl.j_src0; j < pl.j_src1; ++j) put(pl.a + j * W, pl.a + (j + 1) * W, L);
+  for (int64_t v = 0; v < pl.a; v += We) put(v, v + We < pl.a ? v + We : pl.a, Le);
+  for (int64_t v = pl.b; v < nz; v += We) put(v, v + We < nz ? v + We : nz, Le);
 }
 
 // Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, folded current
@@ -127,35 +141,18 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
     for (int f = 0; f < 3; ++f) fld[b][f] = (T*)(q + (size_t)(6 + 3 * b + f) * kNoallocPad * sizeof(double));
   Tile* tiles = (Tile*)(q + 12 * kNoallocPad * sizeof(double));
   int64_t* table = (int64_t*)(tiles + kNoallocMaxTiles);
-  int* counts = (int*)(table + 4);
 
   const int K = sizeof(T) == 8 ? 8 : 16;
   const int TS = sizeof(T) == 8 ? 4 : 32;
   const int Ke = 4;
   const double S = g->dt / (g->dz * std::sqrt(kMu0 * kEps0));
   const double eta0 = std::sqrt(kMu0 / kEps0);
-  // the tile count is fixed by nz, K, Ke and TS; compute it on the host with the same formula
-  const int L = 32 * K, W = L - 2 * TS, We = 32 * Ke - 2 * TS;
-  int64_t a = ((1 + TS + 3) / 4) * 4;
-  int64_t n_int = 0;
-  if (a - TS + L - 1 <= nz - 2) n_int = (nz - 2 - (a - TS + L - 1)) / W + 1;
-  if (n_int == 0) a = 0;
-  const int64_t b = a + n_int * W;
-  const int64_t n_edge = (a + We - 1) / We + (nz - b + We - 1) / We;
-  // interior tiles j whose loaded range [a + jW - TS, a + jW - TS + L) holds the source cell:
-  // d - L < jW <= d with d = src - a + TS
-  int64_t j_src0 = 0, j_src1 = 0;
-  const int64_t d = src - a + TS;
-  if (n_int && d >= 0) {
-    j_src0 = d - L + 1 > 0 ? (d - L + 1 + W - 1) / W : 0;
-    j_src1 = std::min<int64_t>(n_int, d / W + 1);
-    if (j_src1 < j_src0) j_src1 = j_src0;
-  }
-  const int64_t n_src = j_src1 - j_src0;
+  const NoallocPlan pl = noalloc_plan(nz, src, K, Ke, TS);
+  const int64_t n_int = pl.n_int, n_edge = pl.n_edge, n_src = pl.j_src1 - pl.j_src0;
   if (n_int + n_edge > kNoallocMaxTiles) return nfail(RKETD_EINVAL, "noalloc: too many tiles");
 
   cudaError_t e;
-  k_plan<<<1, 32, 0, st>>>(tiles, table, nz, src, K, Ke, TS, j_src0, j_src1, counts);
+  k_plan<<<1, 32, 0, st>>>(tiles, table, nz, src, K, Ke, TS, pl);
   if ((e = cudaGetLastError()) != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   void* cptr[kNumCoef];
   for (int k = 0; k < kNumCoef; ++k) cptr[k] = coef[k];

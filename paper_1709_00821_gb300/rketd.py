@@ -154,9 +154,9 @@ def _default_stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def cpml_params(dz: float, m: float = 3.0):
-    eta0 = np.sqrt(1.25663706212e-6 / 8.8541878128e-12)
-    return m, 0.8 * (m + 1) / (eta0 * dz), 1.0, 0.05
+# CPML grading passed to the library: m = 3, sigma_max <= 0 (the library then takes
+# 0.8 (m + 1)/(eta0 dz)), kappa_max = 1, alpha_max = 0.05 S/m.
+CPML_GRADING = (3.0, 0.0, 1.0, 0.05)
 
 
 class Context:
@@ -176,7 +176,7 @@ class Context:
         g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
         g.bc = RKETD_BC_CPML if s0.bc == "cpml" else RKETD_BC_MUR1
         g.cpml_cells = s0.cpml_cells if s0.bc == "cpml" else 0
-        g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = cpml_params(s0.dz)
+        g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = CPML_GRADING
         self.prec = prec
         p = Pulse(s0.src_tau, s0.src_t0, s0.src_amp)
         d = Dft(self.n_probes, len(self.freq), _ptr(self.freq))
@@ -376,7 +376,7 @@ class Context3D:
         g.d, g.dt = prob.d, prob.dt
         g.periodic_xy = 1 if prob.periodic_xy else 0
         g.npml = prob.npml
-        g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = cpml_params(prob.d)
+        g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = CPML_GRADING
         g.tfsf = 1 if prob.tfsf else 0
         for q in range(6):
             g.box[q] = prob.box[q]

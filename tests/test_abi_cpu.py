@@ -38,7 +38,7 @@ def _create(slab, prec="f64", **over):
     g.prec = 1 if prec == "f64" else 0
     g.bc = 1 if slab.bc == "cpml" else 0
     g.cpml_cells = slab.cpml_cells
-    g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = rk.cpml_params(slab.dz)
+    g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = rk.CPML_GRADING
     if "grid_prec" in over:
         g.prec = over["grid_prec"]
     if "dt" in over:
@@ -146,7 +146,7 @@ def _create3d(prob, **over):
     g.nx, g.ny, g.nz, g.prec = prob.nx, prob.ny, prob.nz, over.get("prec", 0)
     g.d, g.dt = prob.d, over.get("dt", prob.dt)
     g.periodic_xy, g.npml = int(prob.periodic_xy), prob.npml
-    g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = rk.cpml_params(prob.d)
+    g.pml_m, g.pml_sigma_max, g.pml_kappa_max, g.pml_alpha_max = rk.CPML_GRADING
     g.tfsf = int(prob.tfsf)
     for q in range(6):
         g.box[q] = prob.box[q]

@@ -286,3 +286,21 @@ def test_grid_without_probes_steps_and_returns_fields():
         ctx.step(p.steps)
         assert np.array_equal(ctx.field("Ex"), ex_ref)
         assert ctx.spectra().shape == (0, len(q.freq_hz))
+
+
+@pytest.fixture(scope="module")
+def sphere128():
+    """The benchmark's sphere recipe on a 128^3 grid (radius 30, TF/SF box 20..107, 16-cell CPML on
+    every face), 300 steps: the pulse crosses the whole sphere."""
+    p = wl.sphere_problem(n=128, steps=300, nfreq=16)
+    st, _ = oracle.run3d(p)
+    return p, st
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_staged_form_matches_the_3d_oracle_on_the_128_cube_sphere(sphere128, prec):
+    p, st = sphere128
+    with rk.Context3D(p, prec) as ctx:
+        ctx.step(p.steps)
+        worst = _compare(ctx, st, p, prec)
+    print(prec, "128^3", {k: f"{v:.2e}" for k, v in worst.items()})

@@ -75,6 +75,10 @@ def test_full_size_epstein_slab_matches_the_oracle_inside_the_light_cone(c2, pre
         assert eX <= 5e-12 and eE <= 5e-12
         assert errR <= 5e-12 * np.abs(Ro).max() and errT <= 5e-12 * np.abs(To).max()
     else:
+        # the spectra are within 1e-4 of their peak over the whole band; R and T are held on the
+        # 5% band only because they divide that error by the incident spectrum
+        assert np.abs(X - tot.X).max() <= 1e-4 * np.abs(tot.X).max()
+        assert np.abs(Xv - inc.X).max() <= 1e-4 * np.abs(inc.X).max()
         half = np.abs(inc.X[0]) >= 0.5 * np.abs(inc.X[0]).max()
         errR_half = np.abs(R - Ro)[half].max()
         print(f"FP32: R {errR:.2e}, T {errT:.2e} (absolute, {band.sum()} of {band.size} frequencies); "

@@ -1,8 +1,7 @@
 """rketd_advance_1d_noalloc: the step entry point for callers that cannot allocate device memory.
 
-Some callers cannot call cudaMalloc: code being recorded into a CUDA stream capture,
-frameworks whose caching allocator owns the whole GPU, loops that cannot pay for the
-device-wide synchronisation of an allocation. The entry point keeps its working memory
+Some callers cannot call cudaMalloc: frameworks whose caching allocator owns the whole GPU,
+loops that cannot pay for the device-wide synchronisation of an allocation. The entry point keeps its working memory
 in a fixed array inside the library and only touches the caller's arrays. These tests
 check it against the context API (rketd_create_1d + rketd_step + rketd_get_fields) on
 two calls in a row, with the tolerances the other parity tests use.
@@ -69,6 +68,40 @@ def test_noalloc_advance_matches_context_api_on_two_calls_in_a_row(prec, tol, sr
         assert scale > 1e-3
         for g, r, k in zip(got, ref, _scales(slab)):
             assert np.abs(g - r).max() * k <= tol * scale
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,nz", [("f32", 516), ("f32", 517), ("f32", 964), ("f32", 965), ("f32", 131072),
+                                     ("f64", 260), ("f64", 261), ("f64", 508), ("f64", 509), ("f64", 131072)])
+def test_noalloc_tiling_at_the_capacity_and_where_the_interior_tile_count_changes(prec, nz):
+    """nz values on both sides of each change of the interior tile count (FP32: K = 16, 32 steps per
+    pass, one more tile every 448 cells from 517; FP64: K = 8, 4 steps, every 248 from 261), and the
+    largest slab the fixed array holds."""
+    import torch
+
+    slab = wl.c1_plain_slab(nz=nz, steps=1)
+    slab.wp2 = np.full(nz, (2 * math.pi * 30e9) ** 2)
+    slab.nu = np.full(nz, 2e10)
+    slab.src_cell = nz // 3
+    slab.probes = []
+    n1 = 300
+    with rk.Context(slab, prec) as ctx:
+        ctx.step(n1)
+        ref = ctx.fields(0)
+    fdt = torch.float64 if prec == "f64" else torch.float32
+    wp2 = torch.tensor(slab.wp2, dtype=torch.float64, device="cuda")
+    nu = torch.tensor(slab.nu, dtype=torch.float64, device="cuda")
+    E = torch.zeros(nz, dtype=fdt, device="cuda")
+    H = torch.zeros(nz - 1, dtype=fdt, device="cuda")
+    J = torch.zeros(nz, dtype=fdt, device="cuda")
+    rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), 0, n1, E.data_ptr(), H.data_ptr(), J.data_ptr())
+    torch.cuda.synchronize()
+    got = [t.double().cpu().numpy() for t in (E, H, J)]
+    tol = 1e-12 if prec == "f64" else 1e-5
+    scale = np.abs(ref[0]).max()
+    assert scale > 1e-3
+    for g, r, k in zip(got, ref, _scales(slab)):
+        assert np.abs(g - r).max() * k <= tol * scale
 
 
 def test_noalloc_rejects_slabs_beyond_the_fixed_capacity():
