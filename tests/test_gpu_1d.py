@@ -342,7 +342,8 @@ def test_batch_of_32_slabs_at_the_full_20000_steps_matches_the_oracle(c3_full, p
     FP64: spectra within 1e-12 of their peak and fields within 1e-12 of the run's field scale (the
     pulse peak at the probes), R and T within 1e-12 of their peak where the incident spectrum holds
     at least 5% of its peak. FP32: R and T within 1e-4 absolute on that band, and the spectra
-    within 1e-4 of their peak over the whole band."""
+    within 1e-4 of their peak over the whole band. Where the transmission probe is out of the
+    pulse's reach within the run (6 of the 32 slabs), only R is compared."""
     b, tot, inc = c3_full
     with rk.Context(b.slabs, prec) as ctx:
         ctx.step(b.steps)
@@ -352,14 +353,29 @@ def test_batch_of_32_slabs_at_the_full_20000_steps_matches_the_oracle(c3_full, p
         ctx.step(b.steps)
         Xv = ctx.spectra()
     worst = {"X": 0.0, "E": 0.0, "R": 0.0, "T": 0.0}
+    n_dark = 0
     for i, s in enumerate(b.slabs):
         (st, ser), (si, _) = tot[i], inc[i]
         eX = max(np.abs(X[i] - st.X).max() / np.abs(st.X).max(), np.abs(Xv[i] - si.X).max() / np.abs(si.X).max())
-        R, T = rk.rt(X[i], Xv[i])
-        Ro, To = oracle.reflection_transmission(st.X, si.X)
+        # In the longest slabs the transmission probe (256 + w + 64 cells) lies beyond the distance the
+        # pulse travels in 20000 steps (half a cell per step at Courant 0.5): it sees at most the
+        # scheme's numerical precursor (zero or below 1e-60 of the reflection probe's spectrum), and
+        # only R is compared; the spectra comparison above covers both probes.
+        dark = np.abs(si.X[1]).max() < 1e-3 * np.abs(si.X[0]).max()
+        if dark:
+            n_dark += 1
+            assert s.probes[1] - s.src_cell > 0.5 * b.steps, i
+            tot_i, inc_i = X[i].copy(), Xv[i].copy()
+            tot_i[1] = inc_i[1] = Xv[i][0]  # R only (a stand-in transmission pair of T = 1)
+        else:
+            tot_i, inc_i = X[i], Xv[i]
+        R, T = rk.rt(tot_i, inc_i)
+        Ro = (st.X[0] - si.X[0]) / si.X[0]
+        To = T if dark else st.X[1] / si.X[1]
         band = np.abs(si.X[0]) >= 0.05 * np.abs(si.X[0]).max()
+        band_t = np.abs(si.X[1]) >= 0.05 * np.abs(si.X[1]).max() if not dark else band
         eR = np.abs(R - Ro)[band].max()
-        eT = np.abs(T - To)[band].max()
+        eT = np.abs(T - To)[band_t].max()
         if prec == "f64":
             peak = np.abs(ser).max()
             eE = np.abs(fields[i][0] - st.E).max() / peak
@@ -371,4 +387,5 @@ def test_batch_of_32_slabs_at_the_full_20000_steps_matches_the_oracle(c3_full, p
         worst["X"] = max(worst["X"], eX)
         worst["R"] = max(worst["R"], eR)
         worst["T"] = max(worst["T"], eT)
-    print(prec, {k: f"{v:.2e}" for k, v in worst.items()})
+    assert 0 < n_dark < len(b.slabs)
+    print(prec, {k: f"{v:.2e}" for k, v in worst.items()}, f"{n_dark} slabs with the T probe out of reach")
