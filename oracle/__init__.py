@@ -55,6 +55,7 @@ class OrGrid1D(ctypes.Structure):
         ("cpml_kappa_max", ctypes.c_double), ("cpml_alpha_max", ctypes.c_double),
         ("src_cell", ctypes.c_int64), ("src_tau", ctypes.c_double), ("src_t0", ctypes.c_double),
         ("src_amp", ctypes.c_double), ("n_probes", ctypes.c_int32), ("n_freq", ctypes.c_int32),
+        ("scheme", ctypes.c_int32),
     ]
 
 
@@ -76,7 +77,7 @@ def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int64)
             L.or_run1d.argtypes = [ctypes.POINTER(OrGrid1D), dp, dp, ip, dp, ctypes.c_int64, ctypes.c_int64,
-                                   dp, dp, dp, dp, dp, dp, dp, dp]
+                                   dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.or_run1d.restype = ctypes.c_int
             L.or_phi1.argtypes = [ctypes.c_double]
             L.or_phi1.restype = ctypes.c_double
@@ -121,6 +122,7 @@ def make_grid(slab, cpml=None) -> OrGrid1D:
     g.src_amp = slab.src_amp
     g.n_probes = len(slab.probes)
     g.n_freq = len(slab.freq_hz)
+    g.scheme = slab.scheme
     return g
 
 
@@ -139,6 +141,7 @@ class State1D:
         self.psiE = np.zeros(nz)
         self.psiH = np.zeros(nz - 1)
         self.X = np.zeros((len(slab.probes), len(slab.freq_hz)), dtype=np.complex128)
+        self.Eprev = np.zeros(nz)  # E^{n-1}, carried by the explicit second-order scheme (Eq. 10)
         self.n = 0
 
     def copy(self):
@@ -167,7 +170,8 @@ def run1d(slab, steps: Optional[int] = None, state: Optional[State1D] = None, se
     ser = np.zeros((len(slab.probes), steps)) if series else None
     rc = L.or_run1d(ctypes.byref(g), _dp(wp2), _dp(nu), probes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                     _dp(freqs), st.n, steps, _dp(st.E), _dp(st.H), _dp(st.J), _dp(st.psiE), _dp(st.psiH),
-                    _dp(xr), _dp(xi), _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)())
+                    _dp(xr), _dp(xi), _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)(),
+                    _dp(st.Eprev))
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     st.X = xr + 1j * xi

@@ -25,6 +25,10 @@
  *   6. running DFT of E^{n+1} at the probe cells.
  * Eq. 11 is used rather than Eq. 10: integrating the linear interpolant of F
  * between t_n and t_{n+1} against e^{nu tau} in Eq. 7 gives Eq. 11's terms.
+ * The grid's `scheme` also selects the paper's two other recursions for J (for the
+ * accuracy-order comparison): the first-order ETD of Eq. 9 and Eq. 10 read literally
+ * (F extrapolated from F_{n-1} and F_n, an explicit second-order ETD); both are explicit
+ * in J, and E^{n+1} then follows from Eq. 12 directly.
  *
  * Parity pins: see tests/test_oracle_pins.py (discrete transfer matrix,
  * continuous slab, wp = 0 reduction, nu = 0 energy balance, Courant limit,
@@ -51,6 +55,8 @@ typedef struct {
   int64_t src_cell;    /* soft source cell */
   double src_tau, src_t0, src_amp;
   int32_t n_probes, n_freq;
+  int32_t scheme;      /* current recursion: 0 = Eq. 11 (RKETD), 1 = Eq. 9 (first-order ETD),
+                          2 = Eq. 10 read literally (explicit second-order ETD) */
 } or_grid1d;
 
 /* phi1(x) = (1 - e^{-x})/x and phi2(x) = (e^{-x} - 1 + x)/x^2 with x = nu*dt: the two
@@ -115,6 +121,7 @@ static int or_check(const or_grid1d* g, const int64_t* probe_cells) {
   for (int p = 0; p < g->n_probes; ++p)
     if (probe_cells[p] < 0 || probe_cells[p] >= g->nz) return -3;
   if (g->bc == 1 && (g->cpml_cells < 1 || 2 * g->cpml_cells + 2 > g->nz)) return -4;
+  if (g->scheme < 0 || g->scheme > 2) return -6;
   return 0;
 }
 
@@ -126,13 +133,21 @@ static int or_check(const or_grid1d* g, const int64_t* probe_cells) {
  *   E[nz], J[nz], psiE[nz]; H[nz-1], psiH[nz-1]      (in/out)
  *   X_re/X_im[n_probes*n_freq]                        (in/out, accumulated)
  *   series[n_probes*n_steps] (may be NULL): E at each probe after each step.
+ *   Eprev[nz] (scheme 2 only, in/out): E^{n-1}, which Eq. 10's F_{n-1} needs; zero at rest.
  * Returns 0, or a negative code for invalid input (nothing is modified then).
+ *
+ * Schemes 1 and 2 (Eqs. 9 and 10) give J^{n+1} from values at steps n and n-1 only, so the step
+ * computes J^{n+1} first and then E^{n+1} from Eq. 12 as printed (no solve is needed):
+ *   Eq. 9:  J^{n+1} = e^{-nu dt} J^n + (1 - e^{-nu dt})/nu F_n,  F = eps0 wp^2 E;
+ *   Eq. 10: F taken as F_n + (tau/dt)(F_n - F_{n-1}) over the step in Eq. 7, which adds
+ *           (e^{-nu dt} - 1 + nu dt)/(nu^2 dt) (F_n - F_{n-1}) to the Eq. 9 value.
  */
 int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int64_t* probe_cells,
              const double* freq_hz, int64_t n_start, int64_t n_steps, double* E, double* H, double* J,
-             double* psiE, double* psiH, double* X_re, double* X_im, double* series) {
+             double* psiE, double* psiH, double* X_re, double* X_im, double* series, double* Eprev) {
   int rc = or_check(g, probe_cells);
   if (rc) return rc;
+  if (g->scheme == 2 && !Eprev) return -7;
   const int64_t nz = g->nz;
   const double dt = g->dt, dz = g->dz;
   /* Per-cell constants of Eqs. 11 and 13, evaluated once. */
@@ -221,6 +236,7 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
         curl = dH / dz;
       }
       double En = E[k];
+      if (g->scheme == 0) {
       double Enew = cEE[k] * En - cEH[k] * curl - cEJ[k] * J[k];
 #if defined(OR_MUTANT) && OR_MUTANT == 1
       /* planted mistake: Eq. 13 as printed (no 1/D on the curl and J terms) */
@@ -233,6 +249,22 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
       J[k] = a[k] * J[k] + b1[k] * En + b2[k] * (Enew - En);
 #endif
       E[k] = Enew;
+      } else {
+        /* Eq. 9 (b1 = eps0 wp^2 dt phi1 = eps0 wp^2 (1 - a)/nu), then Eq. 10's extra term */
+        double Jnew = a[k] * J[k] + b1[k] * En;
+        if (g->scheme == 2) {
+#if defined(OR_MUTANT) && OR_MUTANT == 9
+          /* planted mistake: F_{n-1} - F_n in place of F_n - F_{n-1} in Eq. 10 */
+          Jnew = Jnew + b2[k] * (Eprev[k] - En);
+#else
+          Jnew = Jnew + b2[k] * (En - Eprev[k]);
+#endif
+          Eprev[k] = En;
+        }
+        /* Eq. 12 with J^{n+1} and J^n */
+        E[k] = En - dt / OR_EPS0 * curl - dt / (2.0 * OR_EPS0) * (Jnew + J[k]);
+        J[k] = Jnew;
+      }
     }
     /* 4. Eq. 15 soft source at t = (n+1) dt. */
     E[g->src_cell] = E[g->src_cell] + or_source(g, (double)(n + 1) * dt);
@@ -401,7 +433,7 @@ static void or_adjoint_step_impl(const or_grid1d* g, const or_cell* cell, double
 
 /* Transposed single step without gradients (for dot-product tests): (lE, lH, lJ) in place. */
 int or_adjoint_step(const or_grid1d* g, const double* wp2, const double* nu, double* lE, double* lH, double* lJ) {
-  if (g->bc != 0 || g->nz < 4) return -1;
+  if (g->bc != 0 || g->scheme != 0 || g->nz < 4) return -1;
   or_cell* cell = (or_cell*)malloc(sizeof(or_cell) * g->nz);
   double* tmp = (double*)malloc(sizeof(double) * 3 * g->nz);
   for (int64_t k = 0; k < g->nz; ++k) or_cell_consts(wp2[k], nu[k], g->dt, &cell[k]);
@@ -423,7 +455,7 @@ int or_adjoint1d(const or_grid1d* g, const double* wp2, const double* nu, const 
                  double* grad_nu) {
   int rc = or_check(g, probe_cells);
   if (rc) return rc;
-  if (g->bc != 0) return -5;
+  if (g->bc != 0 || g->scheme != 0) return -5;
   const int64_t nz = g->nz;
   const int64_t N = n_steps;
   double* Et = (double*)calloc((size_t)(N + 1) * nz, sizeof(double));
@@ -441,7 +473,7 @@ int or_adjoint1d(const or_grid1d* g, const double* wp2, const double* nu, const 
     memcpy(Et + n * nz, E, sizeof(double) * nz);
     memcpy(Ht + n * (nz - 1), H, sizeof(double) * (nz - 1));
     memcpy(Jt + n * nz, J, sizeof(double) * nz);
-    or_run1d(g, wp2, nu, probe_cells, freq_hz, n, 1, E, H, J, psiE, psiH, xr, xi, NULL);
+    or_run1d(g, wp2, nu, probe_cells, freq_hz, n, 1, E, H, J, psiE, psiH, xr, xi, NULL, NULL);
   }
   memcpy(Et + N * nz, E, sizeof(double) * nz);
   memcpy(Ht + N * (nz - 1), H, sizeof(double) * (nz - 1));

@@ -84,12 +84,16 @@ class Slab1D:
     cpml_cells: int = 0
     steps: int = 0
     src_amp: float = 1.0
+    scheme: int = 0  # current recursion: SCHEME_RKETD (Eq. 11), SCHEME_ETD1 (Eq. 9), SCHEME_ETD2 (Eq. 10)
 
     def vacuum(self) -> "Slab1D":
         """Same grid, source and probes with the plasma removed (incident run)."""
         return Slab1D(self.nz, self.dz, self.dt, np.zeros(self.nz), np.zeros(self.nz), self.src_cell,
                       self.src_tau, self.src_t0, list(self.probes), self.freq_hz, self.bc, self.cpml_cells,
-                      self.steps, self.src_amp)
+                      self.steps, self.src_amp, self.scheme)
+
+
+SCHEME_RKETD, SCHEME_ETD1, SCHEME_ETD2 = 0, 1, 2
 
 
 def c1_plain_slab(nz: int = 2000, steps: int = 8000, slab=(800, 920), wp: float = 2 * math.pi * 28.7e9,

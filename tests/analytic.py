@@ -54,21 +54,37 @@ def _material_cache(wp2: np.ndarray, nu: np.ndarray, dt: float):
     return pairs
 
 
-def lattice_eps(theta: np.ndarray, w: float, a: float, p1: float, p2: float) -> np.ndarray:
-    """Discrete permittivity of one cell at normalised frequencies theta = w dt."""
+def current_response(z: np.ndarray, w: float, p1: float, p2: float, scheme: int = 0) -> np.ndarray:
+    """beta0 z + beta1 + beta2/z of a current recursion written (normalised, J~ = dt J/eps0) as
+    J~^{n+1} = a J~^n + beta0 E^{n+1} + beta1 E^n + beta2 E^{n-1}:
+      scheme 0, Eq. 11 (RKETD):          beta0 = w phi2, beta1 = w (phi1 - phi2), beta2 = 0;
+      scheme 1, Eq. 9 (first-order ETD): beta0 = 0,      beta1 = w phi1,          beta2 = 0;
+      scheme 2, Eq. 10 (explicit ETD2):  beta0 = 0,      beta1 = w (phi1 + phi2), beta2 = -w phi2."""
+    if scheme == 0:
+        return w * (p2 * z + (p1 - p2))
+    if scheme == 1:
+        return w * p1 + 0.0 * z
+    return w * (p1 + p2) - w * p2 / z
+
+
+def lattice_eps(theta: np.ndarray, w: float, a: float, p1: float, p2: float, scheme: int = 0) -> np.ndarray:
+    """Discrete permittivity of one cell at normalised frequencies theta = w dt.
+
+    With J~ = chi(z) E, chi = current_response/(z - a), Eq. 12's average (J~^{n+1} + J~^n)/2 adds
+    (z + 1) chi / 2 to (z - 1), so eps = 1 + cos(theta/2) chi / (2j sin(theta/2))."""
     z = np.exp(1j * theta)
     s = np.sin(theta / 2)
     c = np.cos(theta / 2)
-    return 1.0 + w * c * (p1 - p2 + p2 * z) / (2j * s * (z - a))
+    return 1.0 + c * current_response(z, w, p1, p2, scheme) / (2j * s * (z - a))
 
 
-def lattice_q(theta: np.ndarray, S: float, wp2: np.ndarray, nu: np.ndarray, dt: float) -> np.ndarray:
+def lattice_q(theta: np.ndarray, S: float, wp2: np.ndarray, nu: np.ndarray, dt: float, scheme: int = 0) -> np.ndarray:
     """q_k(theta) for every cell: shape [len(theta), nz]."""
     cache = _material_cache(wp2, nu, dt)
     s = np.sin(theta / 2)
     out = np.empty((len(theta), len(wp2)), dtype=np.complex128)
     keys = list(zip(wp2.tolist(), nu.tolist()))
-    epsd = {k: lattice_eps(theta, *v) for k, v in cache.items()}
+    epsd = {k: lattice_eps(theta, *v, scheme=scheme) for k, v in cache.items()}
     for i, k in enumerate(keys):
         out[:, i] = (2 * s / S) ** 2 * epsd[k]
     return out
@@ -79,7 +95,7 @@ def vacuum_K(theta: np.ndarray, S: float) -> np.ndarray:
     return np.arccos(1 - 2 * np.sin(theta / 2) ** 2 / S ** 2)
 
 
-def slab_rt_lattice(wp2, nu, dz, dt, freqs, p_r, p_t):
+def slab_rt_lattice(wp2, nu, dz, dt, freqs, p_r, p_t, scheme: int = 0):
     """R, T of the plasma region on the infinite lattice, referred to the probe cells.
 
     Start right of the slab with a purely transmitted wave e^{-jKk}, iterate
@@ -95,7 +111,7 @@ def slab_rt_lattice(wp2, nu, dz, dt, freqs, p_r, p_t):
     assert lo - 2 > p_r and hi + 2 < p_t
     K = vacuum_K(theta, S)
     sub = slice(lo - 2, hi + 3)
-    q = lattice_q(theta, S, wp2[sub], nu[sub], dt)  # cells lo-2 .. hi+2
+    q = lattice_q(theta, S, wp2[sub], nu[sub], dt, scheme)  # cells lo-2 .. hi+2
     n = hi - lo + 5
     Ek1 = np.exp(-1j * K * (hi + 2))  # E_{k+1}
     Ek = np.exp(-1j * K * (hi + 1))  # E_k
@@ -118,7 +134,7 @@ def slab_rt_lattice(wp2, nu, dz, dt, freqs, p_r, p_t):
     return R, T
 
 
-def domain_response(wp2, nu, dz, dt, freqs, src_cell, cells):
+def domain_response(wp2, nu, dz, dt, freqs, src_cell, cells, scheme: int = 0):
     """Steady-state phasors at `cells` of the finite lattice driven by a unit soft source.
 
     Rows: interior E_{k-1} + (q_k - 2) E_k + E_{k+1} = delta_{k, src}; first-order Mur at
@@ -131,7 +147,7 @@ def domain_response(wp2, nu, dz, dt, freqs, src_cell, cells):
     S = courant(dz, dt)
     qm = (S - 1) / (S + 1)
     theta = 2 * np.pi * np.asarray(freqs) * dt
-    qq = lattice_q(theta, S, wp2, nu, dt)
+    qq = lattice_q(theta, S, wp2, nu, dt, scheme)
     out = np.empty((len(theta), len(cells)), dtype=np.complex128)
     for i, th in enumerate(theta):
         z = np.exp(1j * th)
@@ -154,7 +170,8 @@ def domain_response(wp2, nu, dz, dt, freqs, src_cell, cells):
 def domain_rt(slab):
     """R and T the running DFT converges to for a Mur-terminated slab problem."""
     cells = slab.probes
-    tot = domain_response(slab.wp2, slab.nu, slab.dz, slab.dt, slab.freq_hz, slab.src_cell, cells)
+    tot = domain_response(slab.wp2, slab.nu, slab.dz, slab.dt, slab.freq_hz, slab.src_cell, cells,
+                          getattr(slab, "scheme", 0))
     inc = domain_response(np.zeros(slab.nz), np.zeros(slab.nz), slab.dz, slab.dt, slab.freq_hz,
                           slab.src_cell, cells)
     R = (tot[:, 0] - inc[:, 0]) / inc[:, 0]
