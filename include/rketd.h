@@ -50,6 +50,18 @@ typedef enum {
 
 typedef enum { RKETD_F32 = 0, RKETD_F64 = 1 } rketd_prec;
 typedef enum { RKETD_BC_MUR1 = 0, RKETD_BC_CPML = 1 } rketd_bc;
+/* Recursion for the plasma current over one step (Sec. II, from the exact solution Eq. 7):
+ *   RKETD_SCHEME_RKETD  Eq. 11: F = eps0 wp^2 E interpolated linearly between t_n and t_{n+1};
+ *                       Eq. 12 is then solved for E^{n+1} (Eq. 13). Second order. The default.
+ *   RKETD_SCHEME_ETD1   Eq. 9: F held at F_n over the step. First order. J^{n+1} is explicit and
+ *                       Eq. 12 gives E^{n+1} directly.
+ *   RKETD_SCHEME_ETD2   Eq. 10 read literally: F extrapolated from F_{n-1} and F_n over the step.
+ *                       Second order and explicit, but it needs E^{n-1}: the state carries one more
+ *                       array, and the step runs on the plain variant only (variant 0 selects it;
+ *                       the tiled variant returns RKETD_EUNSUPPORTED).
+ * The adjoint (rketd_forward_ckpt/rketd_adjoint) and the allocation-free entry point take
+ * RKETD_SCHEME_RKETD (and, for the latter, RKETD_SCHEME_ETD1) only. */
+typedef enum { RKETD_SCHEME_RKETD = 0, RKETD_SCHEME_ETD1 = 1, RKETD_SCHEME_ETD2 = 2 } rketd_scheme;
 
 /* Grid shared by every slab of a context. Courant number S = dt / (dz sqrt(mu0 eps0))
  * must satisfy 0 < S <= 1 (1D leapfrog stability); S is evaluated with
@@ -68,7 +80,7 @@ typedef struct {
   int32_t prec;          /* rketd_prec */
   int32_t bc;            /* rketd_bc */
   int32_t cpml_cells;
-  int32_t reserved0;
+  int32_t scheme;        /* rketd_scheme; 0 = Eq. 11 */
   double cpml_m, cpml_sigma_max, cpml_kappa_max, cpml_alpha_max;
 } rketd_grid1d;
 
@@ -247,7 +259,8 @@ rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64
  * their working memory (update coefficients, the two working copies of the fields, the tile list)
  * in one fixed array of about 12.7 MB that the library reserves on every GPU it is loaded on,
  * from load until process exit.
- *   grid          dz, dt, prec (RKETD_F32 or RKETD_F64); bc must be RKETD_BC_MUR1
+ *   grid          dz, dt, prec (RKETD_F32 or RKETD_F64); bc must be RKETD_BC_MUR1; scheme
+ *                 RKETD_SCHEME_RKETD or RKETD_SCHEME_ETD1 (RKETD_SCHEME_ETD2: RKETD_EUNSUPPORTED)
  *   nz            E nodes, 8 <= nz <= 131072 (larger is rejected with RKETD_EINVAL)
  *   wp2, nu       device FP64 arrays [nz] (rad^2/s^2, 1/s), read on the stream. They must be
  *                 finite and >= 0: this call does not check them (they are never copied to the

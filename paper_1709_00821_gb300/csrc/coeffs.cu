@@ -1,6 +1,6 @@
-// Per-cell RKETD update coefficients (Eqs. 11-13) and CPML grading tables, in FP64 on
-// the device (layout and the folded current G = cj J~ - da E are described in
-// rketd_internal.cuh).
+// Per-cell RKETD update coefficients (Eqs. 11-13, and the Eq. 9 / Eq. 10 recursions) and CPML
+// grading tables, in FP64 on the device (layout and the folded current G = cj J~ - da E are
+// described in rketd_internal.cuh).
 // The FP32 path stores the same FP64 results rounded once to FP32; every coefficient is a
 // deviation from its vacuum value or a small term, so rounding keeps its relative accuracy
 // (a = e^{-nu dt} itself would lose most of a - 1 in FP32).
@@ -47,12 +47,19 @@ __device__ void phi12(double x, double& p1, double& p2, double& psi) {
   }
 }
 
+// scheme 0 (Eq. 11, J~' = a J~ + w phi2 E' + w (phi1 - phi2) E): D = 1 + w phi2/2, the coefficients of
+// rketd_internal.cuh. scheme 1 (Eq. 9, J~' = a J~ + w phi1 E): explicit, D = 1, so da = -w phi1/2,
+// cb = S, cj = (1 + a)/2 and bq = cq = w phi1/2. scheme 2 (Eq. 10, J~' = a J~ + w (phi1 + phi2) E
+// - w phi2 E^{n-1}): D = 1, da = -w (phi1 + phi2)/2, bq = cq = w (phi1 + phi2)/2, and the E^{n-1}
+// term enters E' as +ep E^{n-1} and G' as +gp E^{n-1}, ep = w phi2/2, gp = -(1 + a) w phi2/2
+// (G' = cj J~' - da E' with G = cj J~ - da E, as for the other schemes).
 template <typename T>
 __global__ void k_coeffs(const double* __restrict__ wp2, const double* __restrict__ nu,
                          const int64_t* __restrict__ soff, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ nz, int n_slabs, int64_t n_store, double dt,
-                         double S, T* __restrict__ da, T* __restrict__ cb, T* __restrict__ cj,
-                         T* __restrict__ dj, T* __restrict__ bq, T* __restrict__ cq) {
+                         double S, int scheme, T* __restrict__ da, T* __restrict__ cb, T* __restrict__ cj,
+                         T* __restrict__ dj, T* __restrict__ bq, T* __restrict__ cq, T* __restrict__ ep,
+                         T* __restrict__ gp) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_store;
        i += (int64_t)gridDim.x * blockDim.x) {
     // slab owning storage cell i: last s with soff[s] <= i
@@ -70,16 +77,31 @@ __global__ void k_coeffs(const double* __restrict__ wp2, const double* __restric
     double p1, p2, psi;
     phi12(x, p1, p2, psi);
     const double em = expm1(-x);  // a - 1
-    const double D = 1.0 + 0.5 * w * p2;
-    const double h = 0.5 * w / D;
     // End cells are set by the boundary condition, never by Eq. 12, and carry no current:
     // da = 0 there makes G = cj J~ hold for them too (the step kernels do not read da).
-    da[i] = (k == 0 || k == nz[lo] - 1) ? T(0) : (T)(-h * p1);
-    cb[i] = (T)(S / D);
-    cj[i] = (T)(0.5 * (2.0 + em) / D);  // (1 + a)/(2D)
+    const bool end = k == 0 || k == nz[lo] - 1;
     dj[i] = (T)em;
-    bq[i] = (T)(h * psi);                     // cj bp + da a
-    cq[i] = (T)(h * (p1 + (2.0 + em) * p2));  // cj cc - da
+    if (scheme == 0) {
+      const double D = 1.0 + 0.5 * w * p2;
+      const double h = 0.5 * w / D;
+      da[i] = end ? T(0) : (T)(-h * p1);
+      cb[i] = (T)(S / D);
+      cj[i] = (T)(0.5 * (2.0 + em) / D);  // (1 + a)/(2D)
+      bq[i] = (T)(h * psi);                     // cj bp + da a
+      cq[i] = (T)(h * (p1 + (2.0 + em) * p2));  // cj cc - da
+    } else {
+      const double h = 0.5 * w;
+      const double f = scheme == 1 ? p1 : p1 + p2;  // the E^n weight of J~' is w f
+      da[i] = end ? T(0) : (T)(-h * f);
+      cb[i] = (T)S;
+      cj[i] = (T)(0.5 * (2.0 + em));
+      bq[i] = (T)(h * f);
+      cq[i] = (T)(h * f);
+      if (scheme == 2) {
+        ep[i] = end ? T(0) : (T)(h * p2);
+        gp[i] = end ? T(0) : (T)(-(2.0 + em) * h * p2);
+      }
+    }
   }
 }
 
@@ -116,19 +138,23 @@ __global__ void k_cpml(int n, double dt, double m, double smax, double kmax, dou
 
 cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
                           const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,
-                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st) {
+                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st, int scheme,
+                          void* const ext[2]) {
   const int threads = 256;
   int64_t blocks = (n_store + threads - 1) / threads;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
+  if (scheme < 0 || scheme > 2 || (scheme == 2 && (!ext || !ext[0] || !ext[1]))) return cudaErrorInvalidValue;
+  void* e0 = scheme == 2 ? ext[0] : nullptr;
+  void* e1 = scheme == 2 ? ext[1] : nullptr;
   if (prec == 1) {
     k_coeffs<double><<<(unsigned)blocks, threads, 0, st>>>(
-        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, (double*)coef[0], (double*)coef[1],
-        (double*)coef[2], (double*)coef[3], (double*)coef[4], (double*)coef[5]);
+        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, scheme, (double*)coef[0], (double*)coef[1],
+        (double*)coef[2], (double*)coef[3], (double*)coef[4], (double*)coef[5], (double*)e0, (double*)e1);
   } else {
     k_coeffs<float><<<(unsigned)blocks, threads, 0, st>>>(
-        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, (float*)coef[0], (float*)coef[1],
-        (float*)coef[2], (float*)coef[3], (float*)coef[4], (float*)coef[5]);
+        wp2, nu, soff, off, nz, n_slabs, n_store, dt, S, scheme, (float*)coef[0], (float*)coef[1],
+        (float*)coef[2], (float*)coef[3], (float*)coef[4], (float*)coef[5], (float*)e0, (float*)e1);
   }
   return cudaGetLastError();
 }

@@ -157,7 +157,8 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
   void* cptr[kNumCoef];
   for (int k = 0; k < kNumCoef; ++k) cptr[k] = coef[k];
   // table layout: soff[0] = 0, off[0] = 0, nz[0], src[0]
-  e = launch_coeffs(sizeof(T) == 8 ? 1 : 0, wp2, nu, table, table + 1, table + 2, 1, nzp, g->dt, S, cptr, st);
+  e = launch_coeffs(sizeof(T) == 8 ? 1 : 0, wp2, nu, table, table + 1, table + 2, 1, nzp, g->dt, S, cptr, st,
+                    g->scheme);
   if (e != cudaSuccess) return nfail(RKETD_ECUDA, cudaGetErrorString(e));
   const unsigned blocks = (unsigned)((nzp + 255) / 256);
   k_in<T><<<blocks, 256, 0, st>>>(E, H, J, coef[kCj], coef[kDa], fld[0][0], fld[0][1], fld[0][2], nz, nzp, eta0,
@@ -229,6 +230,9 @@ extern "C" rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64
     return nfail(RKETD_EINVAL, "noalloc: nz exceeds the fixed scratch capacity of 131072 cells");
   if (nsteps < 0 || n0 < 0) return nfail(RKETD_EINVAL, "noalloc: negative step count or index");
   if (grid->bc != RKETD_BC_MUR1) return nfail(RKETD_EUNSUPPORTED, "noalloc: only first-order Mur ends");
+  if (grid->scheme != RKETD_SCHEME_RKETD && grid->scheme != RKETD_SCHEME_ETD1)
+    return nfail(grid->scheme == RKETD_SCHEME_ETD2 ? RKETD_EUNSUPPORTED : RKETD_EINVAL,
+                 "noalloc: scheme must be RKETD (Eq. 11) or ETD1 (Eq. 9)");
   if (grid->prec != RKETD_F32 && grid->prec != RKETD_F64) return nfail(RKETD_EINVAL, "noalloc: bad precision");
   if (!(grid->dz > 0) || !(grid->dt > 0) || !std::isfinite(grid->dz) || !std::isfinite(grid->dt))
     return nfail(RKETD_EINVAL, "noalloc: dz and dt must be finite and > 0");

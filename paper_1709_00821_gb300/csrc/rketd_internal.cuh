@@ -86,6 +86,10 @@ struct StepArgs {
   const int64_t* soff;    // [n_slabs] storage offset of each slab
   const int64_t* nz;      // [n_slabs]
   const int64_t* src;     // [n_slabs] source cell
+  // Eq. 10 recursion only (plain kernels): E^{n-1} (updated in place) and its weights in E' and G'
+  T* Ep;
+  const T* ep;
+  const T* gp;
   // CPML (bc == 1): compact memories [n_slabs][2 ends][ncpml] for E and H nodes
   const T* psiE_in;
   const T* psiH_in;
@@ -155,9 +159,12 @@ struct AdjArgs {
 void set_error_message(const char* msg);
 
 // ---- launchers (defined in the .cu files) ----
+// scheme: 0 = Eq. 11, 1 = Eq. 9, 2 = Eq. 10 (then ext[0], ext[1] receive ep and gp, the weights of
+// E^{n-1} in the E and G updates; see coeffs.cu)
 cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
                           const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,
-                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st);
+                          double dt, double S, void* const coef[kNumCoef], cudaStream_t st, int scheme = 0,
+                          void* const ext[2] = nullptr);
 cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
                                double amax, void* cpmlE, void* cpmlH, cudaStream_t st);
 

@@ -71,6 +71,9 @@ struct rketd_ctx {
   void* J[2] = {nullptr, nullptr};
   int cur = 0;
   void* coef[kNumCoef] = {};
+  // Eq. 10 recursion only: E^{n-1} and its weights ep, gp in the E and G updates
+  void* Ep = nullptr;
+  void* ext[2] = {nullptr, nullptr};
   double* wp2_d = nullptr;
   double* nu_d = nullptr;
   int64_t* soff_d = nullptr;
@@ -354,6 +357,9 @@ StepArgs<T> make_args(rketd_ctx* c, int in, int out) {
   a.soff = c->soff_d;
   a.nz = c->nz_d;
   a.src = c->src_d;
+  a.Ep = (T*)c->Ep;
+  a.ep = (const T*)c->ext[0];
+  a.gp = (const T*)c->ext[1];
   a.psiE_in = (const T*)c->psiE[in];
   a.psiH_in = (const T*)c->psiH[in];
   a.psiE_out = (T*)c->psiE[out];
@@ -527,6 +533,8 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   if (!finite_pos(grid->dz) || !finite_pos(grid->dt)) return fail(RKETD_EINVAL, "dz and dt must be finite and > 0");
   if (grid->prec != RKETD_F32 && grid->prec != RKETD_F64) return fail(RKETD_EINVAL, "prec must be F32 or F64");
   if (grid->bc != RKETD_BC_MUR1 && grid->bc != RKETD_BC_CPML) return fail(RKETD_EINVAL, "bc must be MUR1 or CPML");
+  if (grid->scheme < RKETD_SCHEME_RKETD || grid->scheme > RKETD_SCHEME_ETD2)
+    return fail(RKETD_EINVAL, "scheme must be RKETD (Eq. 11), ETD1 (Eq. 9) or ETD2 (Eq. 10)");
   const double S = grid->dt / (grid->dz * std::sqrt(kMu0 * kEps0));
   if (!(S <= 1.0)) return fail(RKETD_ECOURANT, "Courant number c dt/dz = %.17g exceeds 1", S);
   if (!finite_pos(pulse->tau) || !std::isfinite(pulse->t0) || !std::isfinite(pulse->amp))
@@ -589,6 +597,12 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   if (opt) op = *opt;
   rketd_status st = check_options(op, c->prec);
   if (st) return st;
+  if (grid->scheme == RKETD_SCHEME_ETD2) {
+    // E^{n-1} is one more carried array: the plain (one step per launch) kernels carry it
+    if (op.variant == 2)
+      return fail(RKETD_EUNSUPPORTED, "the Eq. 10 recursion (ETD2) runs on the plain variant only");
+    op.variant = 1;
+  }
   fill_auto(op, c->prec);
   c->opt = op;
   return RKETD_OK;
@@ -605,6 +619,7 @@ rketd_status zero_state(rketd_ctx* c) {
       CK(cudaMemsetAsync(c->psiH[b], 0, c->esz * c->n_psi, c->stream), "memset psi");
     }
   }
+  if (c->Ep) CK(cudaMemsetAsync(c->Ep, 0, fb, c->stream), "memset E^{n-1}");
   if (c->total_probes) {
     const size_t xb = sizeof(double) * c->total_probes * c->n_freq;
     CK(cudaMemsetAsync(c->Xr, 0, xb, c->stream), "memset X");
@@ -617,7 +632,7 @@ rketd_status zero_state(rketd_ctx* c) {
 
 rketd_status update_coeffs(rketd_ctx* c) {
   CK(launch_coeffs(c->prec, c->wp2_d, c->nu_d, c->soff_d, c->off_d, c->nz_d, c->n_slabs, c->n_store, c->grid.dt,
-                   c->S, c->coef, c->stream),
+                   c->S, c->coef, c->stream, c->grid.scheme, c->ext),
      "coefficient kernel");
   c->launches += 1;
   return RKETD_OK;
@@ -730,6 +745,11 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
   }
   for (int k = 0; k < kNumCoef; ++k)
     if ((st = c->alloc(&c->coef[k], fb, "coefficients"))) return cleanup(st);
+  if (c->grid.scheme == RKETD_SCHEME_ETD2) {
+    if ((st = c->alloc(&c->Ep, fb, "E^{n-1}"))) return cleanup(st);
+    for (int k = 0; k < 2; ++k)
+      if ((st = c->alloc(&c->ext[k], fb, "coefficients"))) return cleanup(st);
+  }
   void* p;
   if ((st = c->alloc(&p, sizeof(double) * c->n_cells, "wp2"))) return cleanup(st);
   c->wp2_d = (double*)p;
@@ -783,6 +803,9 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
   // padding cells of the coefficient arrays must hold finite values: zero everything first
   for (int k = 0; k < kNumCoef; ++k)
     if (cudaMemsetAsync(c->coef[k], 0, fb, c->stream) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "memset"));
+  for (int k = 0; k < 2; ++k)
+    if (c->ext[k] && cudaMemsetAsync(c->ext[k], 0, fb, c->stream) != cudaSuccess)
+      return cleanup(cuda_fail(cudaGetLastError(), "memset"));
   if (nc) {
     cudaError_t e = launch_cpml_tables(c->prec, nc, c->grid.dt, c->grid.cpml_m, c->grid.cpml_sigma_max,
                                        c->grid.cpml_kappa_max, c->grid.cpml_alpha_max, c->cpmlE, c->cpmlH,
@@ -925,12 +948,14 @@ rketd_status rketd_rt(const double* tr, const double* ti, const double* ir, cons
 namespace {
 
 // Version 2: the current is stored as the folded G = cj J~ - da E (version 1 held cj J~).
-constexpr int32_t kStateVersion = 2;
+// Version 3: the header names the current recursion; the Eq. 10 recursion adds E^{n-1}.
+constexpr int32_t kStateVersion = 3;
 
 struct StateHeader {
   char magic[8];
   int32_t version, prec, n_slabs, n_probes, n_freq, dft_block;
   int64_t n_store, n_psi, step;
+  int32_t scheme, pad;
 };
 
 bool write_dev(FILE* f, const void* dev, size_t bytes, cudaStream_t st) {
@@ -961,6 +986,7 @@ StateHeader header_of(const rketd_ctx* c) {
   h.n_store = c->n_store;
   h.n_psi = c->n_psi;
   h.step = c->step;
+  h.scheme = c->grid.scheme;
   return h;
 }
 
@@ -981,7 +1007,8 @@ rketd_status rketd_save_state(rketd_ctx* c, const char* path) {
             write_dev(f, c->H[c->cur], fb, c->stream) && write_dev(f, c->J[c->cur], fb, c->stream) &&
             (!pb || (write_dev(f, c->psiE[c->cur], pb, c->stream) && write_dev(f, c->psiH[c->cur], pb, c->stream))) &&
             (!xb || (write_dev(f, c->Xr, xb, c->stream) && write_dev(f, c->Xi, xb, c->stream) &&
-                     write_dev(f, c->series, sb, c->stream)));
+                     write_dev(f, c->series, sb, c->stream))) &&
+            (!c->Ep || write_dev(f, c->Ep, fb, c->stream));
   ok = (fclose(f) == 0) && ok;
   if (!ok) return fail(RKETD_EIO, "writing %s failed", path);
   return RKETD_OK;
@@ -998,7 +1025,8 @@ rketd_status rketd_load_state(rketd_ctx* c, const char* path) {
     return fail(RKETD_EIO, "%s is not an RKETD state file", path);
   }
   if (h.prec != want.prec || h.n_slabs != want.n_slabs || h.n_probes != want.n_probes || h.n_freq != want.n_freq ||
-      h.dft_block != want.dft_block || h.n_store != want.n_store || h.n_psi != want.n_psi || h.step < 0) {
+      h.dft_block != want.dft_block || h.n_store != want.n_store || h.n_psi != want.n_psi || h.step < 0 ||
+      h.scheme != want.scheme) {
     fclose(f);
     return fail(RKETD_EINVAL, "%s was saved from a context of a different shape", path);
   }
@@ -1011,7 +1039,8 @@ rketd_status rketd_load_state(rketd_ctx* c, const char* path) {
             read_dev(f, c->J[0], fb, c->stream) &&
             (!pb || (read_dev(f, c->psiE[0], pb, c->stream) && read_dev(f, c->psiH[0], pb, c->stream))) &&
             (!xb || (read_dev(f, c->Xr, xb, c->stream) && read_dev(f, c->Xi, xb, c->stream) &&
-                     read_dev(f, c->series, sb, c->stream)));
+                     read_dev(f, c->series, sb, c->stream))) &&
+            (!c->Ep || read_dev(f, c->Ep, fb, c->stream));
   fclose(f);
   if (!ok) return fail(RKETD_EIO, "reading %s failed", path);
   c->step = h.step;
@@ -1021,6 +1050,8 @@ rketd_status rketd_load_state(rketd_ctx* c, const char* path) {
 rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (passes < 1) return fail(RKETD_EINVAL, "passes must be >= 1");
+  if (c->grid.scheme == RKETD_SCHEME_ETD2)
+    return fail(RKETD_EUNSUPPORTED, "the autotuner times the tiled variant, which the Eq. 10 recursion does not run on");
   CK(cudaStreamSynchronize(c->stream), "autotune sync");
   // save the state
   const size_t fb = c->esz * c->n_store, pb = c->esz * c->n_psi;
@@ -1099,6 +1130,8 @@ rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (nsteps < 1 || ckpt_every < 1) return fail(RKETD_EINVAL, "nsteps and ckpt_every must be >= 1");
   if (c->grid.bc != RKETD_BC_MUR1) return fail(RKETD_EUNSUPPORTED, "the adjoint supports first-order Mur ends only");
+  if (c->grid.scheme != RKETD_SCHEME_RKETD)
+    return fail(RKETD_EUNSUPPORTED, "the adjoint differentiates the Eq. 11 recursion only");
   if (c->opt.variant != 2) return fail(RKETD_EUNSUPPORTED, "the adjoint runs on the tiled variant");
   const int64_t n_ckpt = (nsteps + ckpt_every - 1) / ckpt_every;
   const size_t fb = c->esz * c->n_store;

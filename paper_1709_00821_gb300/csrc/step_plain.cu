@@ -3,7 +3,8 @@
 // also advances the current (Eq. 11 needs E^n and E^{n+1} of the same cell, so it stays in
 // a register), adds the Eq. 15 source and applies the end conditions; a third small kernel
 // copies the probe samples. This is the streaming form (one HBM pass per step) that the
-// temporally blocked kernel is measured against.
+// temporally blocked kernel is measured against, and the form that runs the Eq. 10 recursion
+// (whose E^{n-1} is one more array, updated in place).
 #include "rketd_internal.cuh"
 
 namespace rketd {
@@ -70,8 +71,17 @@ __global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int
   // J holds the folded current G (rketd_internal.cuh)
   const T en = E[i];
   const T go = J[i];
-  T enew = fold_e(en, a.coef[kCb][i], curl, go);
-  T gn = fold_g(go, a.coef[kDj][i], a.coef[kBq][i], a.coef[kCq][i], en, enew);
+  T enew, gn;
+  if (a.Ep == nullptr) {
+    enew = fold_e(en, a.coef[kCb][i], curl, go);
+    gn = fold_g(go, a.coef[kDj][i], a.coef[kBq][i], a.coef[kCq][i], en, enew);
+  } else {
+    // Eq. 10 read literally: E^{n-1} enters both updates (its small terms summed first, as above)
+    const T pv = a.Ep[i];
+    enew = en - fma(a.coef[kCb][i], curl, fma(-a.ep[i], pv, go));
+    gn = go + fma(a.gp[i], pv, fma(a.coef[kCq][i], enew, fma(a.coef[kBq][i], en, a.coef[kDj][i] * go)));
+    a.Ep[i] = en;
+  }
   if (k == a.src[s]) {
     const T sv = (T)pulse((double)(a.n0 + 1) * a.dt, a.t0, a.tau, a.amp);
     enew += sv;

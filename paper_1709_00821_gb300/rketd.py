@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "librketd.so")
 
 RKETD_F32, RKETD_F64 = 0, 1
 RKETD_BC_MUR1, RKETD_BC_CPML = 0, 1
+RKETD_SCHEME_RKETD, RKETD_SCHEME_ETD1, RKETD_SCHEME_ETD2 = 0, 1, 2  # Eq. 11, Eq. 9, Eq. 10
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECOURANT", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "EUNSUPPORTED",
           7: "ENUMERIC", 8: "EIO"}
 
@@ -33,7 +34,7 @@ class RketdError(RuntimeError):
 
 class Grid1D(ctypes.Structure):
     _fields_ = [("dz", ctypes.c_double), ("dt", ctypes.c_double), ("prec", ctypes.c_int32),
-                ("bc", ctypes.c_int32), ("cpml_cells", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("bc", ctypes.c_int32), ("cpml_cells", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("cpml_m", ctypes.c_double), ("cpml_sigma_max", ctypes.c_double),
                 ("cpml_kappa_max", ctypes.c_double), ("cpml_alpha_max", ctypes.c_double)]
 
@@ -177,6 +178,7 @@ class Context:
         g.bc = RKETD_BC_CPML if s0.bc == "cpml" else RKETD_BC_MUR1
         g.cpml_cells = s0.cpml_cells if s0.bc == "cpml" else 0
         g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = CPML_GRADING
+        g.scheme = getattr(s0, "scheme", RKETD_SCHEME_RKETD)
         self.prec = prec
         p = Pulse(s0.src_tau, s0.src_t0, s0.src_amp)
         d = Dft(self.n_probes, len(self.freq), _ptr(self.freq))
@@ -335,6 +337,7 @@ def advance_1d_noalloc(slab, prec: str, wp2_dev: int, nu_dev: int, n0: int, nste
     g.dz, g.dt = slab.dz, slab.dt
     g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
     g.bc = RKETD_BC_MUR1
+    g.scheme = getattr(slab, "scheme", RKETD_SCHEME_RKETD)
     p = Pulse(slab.src_tau, slab.src_t0, slab.src_amp)
     st = _default_stream() if stream is None else stream
     _check(lib().rketd_advance_1d_noalloc(ctypes.byref(g), slab.nz, ctypes.c_void_p(wp2_dev), ctypes.c_void_p(nu_dev),

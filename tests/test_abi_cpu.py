@@ -43,6 +43,13 @@ def _create(slab, prec="f64", **over):
         g.prec = over["grid_prec"]
     if "dt" in over:
         g.dt = over["dt"]
+    if "scheme" in over:
+        g.scheme = over["scheme"]
+    opt = None
+    if "variant" in over:
+        opt = rk.Options()
+        L.rketd_default_options(ctypes.byref(opt))
+        opt.variant = over["variant"]
     p = rk.Pulse(slab.src_tau, slab.src_t0, slab.src_amp)
     freq = np.ascontiguousarray(slab.freq_hz, float)
     d = rk.Dft(len(slab.probes), len(freq), freq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -52,7 +59,7 @@ def _create(slab, prec="f64", **over):
     h = ctypes.c_void_p()
     st = L.rketd_create_1d(slab.nz, ctypes.byref(g), wp2.ctypes.data_as(rk._dp), nu.ctypes.data_as(rk._dp),
                            over.get("src", slab.src_cell), ctypes.byref(p), probes.ctypes.data_as(rk._i64p),
-                           ctypes.byref(d), None, None, ctypes.byref(h))
+                           ctypes.byref(d), ctypes.byref(opt) if opt is not None else None, None, ctypes.byref(h))
     return st, L.rketd_last_error().decode(), h
 
 
@@ -91,6 +98,17 @@ def test_invalid_inputs_are_rejected_before_any_device_work(case):
         over["grid_prec"] = 7
     st, msg, h = _create(s, **over)
     assert st == 1, (st, msg)
+    assert msg and not h.value
+
+
+@pytest.mark.parametrize("scheme,variant,status", [(3, 0, 1), (-1, 0, 1), (2, 2, 6)])
+def test_current_recursion_choices_are_validated_before_any_device_work(scheme, variant, status):
+    """An unknown recursion is EINVAL; the Eq. 10 recursion asked of the tiled variant, which does
+    not carry E^{n-1}, is EUNSUPPORTED."""
+    s = wl.c1_plain_slab(nz=64, steps=1)
+    s.src_cell, s.probes = 8, [10, 50]
+    st, msg, h = _create(s, scheme=scheme, variant=variant)
+    assert st == status, (st, msg)
     assert msg and not h.value
 
 

@@ -104,6 +104,33 @@ def test_noalloc_tiling_at_the_capacity_and_where_the_interior_tile_count_change
         assert np.abs(g - r).max() * k <= tol * scale
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_noalloc_runs_the_first_order_recursion_like_the_context_api(prec, tol):
+    """The Eq. 9 recursion is a change of coefficients only, which this entry point also takes."""
+    import torch
+
+    slab = _plasma_source(460)
+    slab.scheme = rk.RKETD_SCHEME_ETD1
+    n1 = 900
+    with rk.Context(slab, prec) as ctx:
+        ctx.step(n1)
+        ref = ctx.fields(0)
+    fdt = torch.float64 if prec == "f64" else torch.float32
+    wp2 = torch.tensor(slab.wp2, dtype=torch.float64, device="cuda")
+    nu = torch.tensor(slab.nu, dtype=torch.float64, device="cuda")
+    E = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    H = torch.zeros(slab.nz - 1, dtype=fdt, device="cuda")
+    J = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), 0, n1, E.data_ptr(), H.data_ptr(), J.data_ptr())
+    torch.cuda.synchronize()
+    got = [t.double().cpu().numpy() for t in (E, H, J)]
+    scale = np.abs(ref[0]).max()
+    assert scale > 1e-3
+    for g, r, k in zip(got, ref, _scales(slab)):
+        assert np.abs(g - r).max() * k <= tol * scale
+
+
 def test_noalloc_rejects_slabs_beyond_the_fixed_capacity():
     """Checked before any device work: runs without a GPU."""
     slab = wl.c1_plain_slab(nz=131073, steps=1)
