@@ -23,8 +23,9 @@ def _with(slab, scheme):
 
 
 def _run(slab, prec, steps=None, **opts):
+    first = slab[0] if isinstance(slab, list) else slab
     with rk.Context(slab, prec, options=opts or None) as ctx:
-        ctx.step(slab.steps if steps is None else steps)
+        ctx.step(first.steps if steps is None else steps)
         X = ctx.spectra()
         fields = [ctx.fields(i) for i in range(ctx.n_slabs)]
         used = ctx.options()
