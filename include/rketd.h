@@ -103,8 +103,13 @@ typedef struct {
 /* Execution options. Zero-initialise and set what you need; rketd_default_options()
  * fills the defaults. */
 typedef struct {
-  int32_t variant;      /* 0 = auto, 1 = plain (paper structure: one H kernel and one
-                           E+J kernel per step), 2 = temporally blocked warp tiles */
+  int32_t variant;      /* 0 = auto (resident where it applies, else tiled; plain for the Eq. 10
+                           recursion), 1 = plain (paper structure: one H kernel and one E+J kernel per
+                           step), 2 = temporally blocked warp tiles, 3 = resident: a single
+                           Mur-terminated slab held in the registers of one thread-block cluster (up
+                           to 16 CTAs) for a whole DFT block of steps per launch, for slabs of up to
+                           8192 (FP64) or 32768 (FP32) cells; RKETD_EUNSUPPORTED where it does not
+                           apply. The checkpointed forward run and the adjoint use the tiled kernels. */
   int32_t cells_per_lane;  /* K for the tiled kernel: 8, 12 or 16 (F32), 4 or 8 (F64); 0 = auto */
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
   int32_t warps_per_block; /* warps per CTA of the tiled kernel, 1..4; 0 = auto */
@@ -112,7 +117,10 @@ typedef struct {
   int32_t use_graphs;   /* 0 = auto (on), 1 = on, 2 = off: rketd_step calls that repeat an earlier
                            call's start step, step count and buffer parity replay its CUDA graph */
   int32_t fp32_pairs;   /* FP32 interior tiles: 0 = auto (packed FP32x2 pairs), 1 = pairs, 2 = scalar */
-  int32_t reserved[5];
+  int32_t res_ctas;     /* resident variant: CTAs of the cluster, 1..16; 0 = auto */
+  int32_t res_threads;  /* resident variant: threads per CTA, a multiple of 32, <= 1024 (FP32) or 256
+                           (FP64); 0 = auto */
+  int32_t reserved[3];
 } rketd_options;
 
 typedef struct rketd_ctx rketd_ctx;

@@ -207,6 +207,14 @@ template <typename T>
 cudaError_t launch_rec_init(const T* E, const T* H, const T* J, const int64_t* soff, const int64_t* nz, int n_slabs,
                             int64_t c0, int w, int rec_len, T* rec, cudaStream_t st);
 
+// Resident step (step_resident.cu): a single slab held by one cluster of `ctas` CTAs of `threads`
+// threads, K cells per thread, pl cells of left padding; a.nsub steps in one launch, first-order Mur
+// ends; a.tprobes lists the probes as (slab cell, probe index). query_only: *max_clusters receives how
+// many such clusters can be resident at once (0: the shape cannot run), nothing is launched.
+template <typename T>
+cudaError_t launch_resident(const StepArgs<T>& a, int K, int ctas, int threads, int pl, cudaStream_t st,
+                            bool query_only, int* max_clusters);
+
 // FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu); xtra as for launch_tb
 cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st, bool xtra);
 
@@ -219,7 +227,9 @@ cudaError_t launch_twiddles(const double* freq, int n_freq, double dt, int64_t m
                             T* tw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_dft(const T* series, int series_len, int n_samples, const T* tw, int total_probes,
-                       int n_freq, double* X_re, double* X_im, cudaStream_t st);
+                       int n_freq, double* X_re, double* X_im, cudaStream_t st, const double* rot = nullptr);
+// rot[f] = exp(-j 2 pi f m0 dt), FP64 [n_freq][2]
+cudaError_t launch_dft_rotation(const double* freq, int n_freq, double dt, int64_t m0, double* rot, cudaStream_t st);
 
 // Device state of one slab to SI: E, H = H~ h_scale, J = (G + da E)/cj j_scale
 cudaError_t launch_gather_fields(int prec, const void* E, const void* H, const void* G, const void* cj,

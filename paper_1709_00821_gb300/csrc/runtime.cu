@@ -63,6 +63,7 @@ struct rketd_ctx {
   double S = 0, qmur = 0;
   cudaStream_t stream = nullptr;
   rketd_options opt{};
+  bool auto_variant = false;  // variant 0 was asked for: resident where it applies, else tiled
 
   // device memory
   std::vector<void*> allocs;
@@ -93,6 +94,7 @@ struct rketd_ctx {
   double* Xr = nullptr;
   double* Xi = nullptr;
   double* Xtmp = nullptr;  // [2][P*nf] for spectra with pending samples
+  double* rot = nullptr;   // [nf][2] exp(-j 2 pi f m0 dt) of the fold being added
   int total_probes = 0;
 
   // tiles for the current (K, tb_steps)
@@ -105,6 +107,11 @@ struct rketd_ctx {
   int n_interior = 0, n_edge = 0;
   int n_int_xtra = 0;  // the last n_int_xtra interior tiles sample a probe or load a source cell
   int tiles_K = 0, tiles_T = 0;
+
+  // resident variant: cluster shape, left padding, probe list (slab cell, probe index)
+  bool res_ok = false;
+  int res_K = 0, res_ctas = 0, res_threads = 0, res_pl = 0;
+  TileProbe* res_probes_d = nullptr;
 
   int64_t step = 0;
   int64_t launches = 0;
@@ -159,6 +166,7 @@ struct rketd_ctx {
     for (void* p : allocs) cudaFree(p);
     if (tiles_d) cudaFree(tiles_d);
     if (tprobes_d) cudaFree(tprobes_d);
+    if (res_probes_d) cudaFree(res_probes_d);
   }
 
   rketd_status alloc(void** p, size_t bytes, const char* what) {
@@ -180,7 +188,10 @@ namespace {
 bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
 
 rketd_status check_options(const rketd_options& o, int prec) {
-  if (o.variant < 0 || o.variant > 2) return fail(RKETD_EINVAL, "options.variant must be 0, 1 or 2");
+  if (o.variant < 0 || o.variant > 3) return fail(RKETD_EINVAL, "options.variant must be 0, 1, 2 or 3");
+  if (o.res_ctas < 0 || o.res_ctas > 16) return fail(RKETD_EINVAL, "res_ctas must be 0..16");
+  if (o.res_threads < 0 || o.res_threads % 32 || o.res_threads > (prec == 1 ? 256 : 1024))
+    return fail(RKETD_EINVAL, "res_threads must be a multiple of 32, at most 1024 (FP32) or 256 (FP64)");
   if (prec == 0 && o.cells_per_lane != 0 && o.cells_per_lane != 8 && o.cells_per_lane != 12 &&
       o.cells_per_lane != 16)
     return fail(RKETD_EUNSUPPORTED, "FP32 cells_per_lane must be 8, 12 or 16");
@@ -196,7 +207,7 @@ rketd_status check_options(const rketd_options& o, int prec) {
 }
 
 void fill_auto(rketd_options& o, int prec) {
-  if (o.variant == 0) o.variant = 2;
+  if (o.variant == 0) o.variant = 2;  // the resident variant is chosen over this at creation where it applies
   if (o.cells_per_lane == 0) o.cells_per_lane = prec == 1 ? 8 : 16;
   if (o.tb_steps == 0) o.tb_steps = prec == 1 ? 4 : 32;
   // a tile must keep at least 32 exact cells
@@ -344,6 +355,63 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   return RKETD_OK;
 }
 
+// Shape of the resident variant for this context (single Mur slab, not the Eq. 10 recursion):
+// FP64 spreads the cells over up to 16 CTAs of 128 threads (a warp per SM sub-partition, whose FP64
+// units are few), 1, 2 or 4 cells per thread (up to 8192 cells); FP32 keeps them in as few CTAs of up
+// to 1024 threads of 2 cells or 512 threads of 4 (up to 32768 cells). Options res_ctas / res_threads override. The shape is kept only if the
+// cluster can be scheduled. Returns RKETD_EUNSUPPORTED (with the reason) where it does not apply.
+rketd_status plan_resident(rketd_ctx* c) {
+  c->res_ok = false;
+  if (c->n_slabs != 1 || c->grid.bc != RKETD_BC_MUR1 || c->grid.scheme == RKETD_SCHEME_ETD2)
+    return fail(RKETD_EUNSUPPORTED, "the resident variant takes one slab with first-order Mur ends (Eq. 11 or 9)");
+  const int64_t nz = c->nz[0];
+  const bool f64 = c->prec == RKETD_F64;
+  int threads = c->opt.res_threads ? c->opt.res_threads : (f64 ? 128 : 1024);
+  int K = 0, ctas = 0, pl = 0;
+  const int Ks64[] = {1, 2, 4}, Ks32[] = {2, 4};
+  const int* Ks = f64 ? Ks64 : Ks32;
+  const int nK = f64 ? 3 : 2;
+  for (int q = 0; q < nK && !K; ++q) {
+    const int k = Ks[q];
+    const int p = ((nz - 1) % (32 * k) == 0) ? 1 : 0;  // keeps cells nz-2, nz-1 in one warp
+    int th = threads;
+    if (!f64) {  // FP32: up to 1024 threads of 2 cells or 512 of 4; a small slab needs fewer
+      const int cap = k == 2 ? 1024 : 512;
+      if (c->opt.res_threads > cap) continue;
+      if (!c->opt.res_threads) th = (int)std::min<int64_t>(cap, round_up((nz + p + k - 1) / k, 32));
+    }
+    int n = c->opt.res_ctas ? c->opt.res_ctas : (int)((nz + p + (int64_t)th * k - 1) / ((int64_t)th * k));
+    if (n >= 1 && n <= 16 && (int64_t)n * th * k >= nz + p) {
+      K = k;
+      ctas = n;
+      pl = p;
+      threads = th;
+    }
+  }
+  if (!K) return fail(RKETD_EUNSUPPORTED, "slab of %lld cells too long for the resident variant", (long long)nz);
+  int max_clusters = 0;
+  const StepArgs<double> q64{};
+  const StepArgs<float> q32{};
+  cudaError_t e = f64 ? launch_resident<double>(q64, K, ctas, threads, pl, c->stream, true, &max_clusters)
+                      : launch_resident<float>(q32, K, ctas, threads, pl, c->stream, true, &max_clusters);
+  if (e != cudaSuccess || max_clusters < 1) {
+    cudaGetLastError();
+    return fail(RKETD_EUNSUPPORTED, "a cluster of %d CTAs x %d threads cannot be scheduled", ctas, threads);
+  }
+  if (!c->res_probes_d && c->n_probes) {
+    std::vector<TileProbe> pr(c->n_probes);
+    for (int p = 0; p < c->n_probes; ++p) pr[p] = {(int32_t)c->probe_cell[p], p};
+    CK(cudaMalloc(&c->res_probes_d, sizeof(TileProbe) * pr.size()), "probe list");
+    CK(cudaMemcpy(c->res_probes_d, pr.data(), sizeof(TileProbe) * pr.size(), cudaMemcpyHostToDevice), "probe list");
+  }
+  c->res_K = K;
+  c->res_ctas = ctas;
+  c->res_threads = threads;
+  c->res_pl = pl;
+  c->res_ok = true;
+  return RKETD_OK;
+}
+
 template <typename T>
 StepArgs<T> make_args(rketd_ctx* c, int in, int out) {
   StepArgs<T> a{};
@@ -382,13 +450,15 @@ StepArgs<T> make_args(rketd_ctx* c, int in, int out) {
   return a;
 }
 
-// DFT of the first n buffered columns into (Xr, Xi), first sample index m0.
+// DFT of the first n buffered columns into (Xr, Xi), first sample index m0. The twiddle table holds
+// exp(-j 2 pi f t dt) for t = 0 .. dft_block-1 (built at creation); the fold's sums are rotated by
+// exp(-j 2 pi f m0 dt).
 template <typename T>
 rketd_status dft_block(rketd_ctx* c, int n, int64_t m0, double* Xr, double* Xi) {
   if (c->total_probes == 0 || n == 0) return RKETD_OK;
-  CK(launch_twiddles<T>(c->freq_d, c->n_freq, c->grid.dt, m0, n, (T*)c->tw, c->stream), "twiddles");
+  CK(launch_dft_rotation(c->freq_d, c->n_freq, c->grid.dt, m0, c->rot, c->stream), "dft rotation");
   CK(launch_dft<T>((const T*)c->series, c->opt.dft_block, n, (const T*)c->tw, c->total_probes, c->n_freq, Xr,
-                   Xi, c->stream),
+                   Xi, c->stream, c->rot),
      "dft");
   c->launches += 2;
   return RKETD_OK;
@@ -448,6 +518,33 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       c->launches += 2 + (c->total_probes > 0);
       c->step += 1;
       nsteps -= 1;
+    } else if (c->opt.variant == 3) {
+      if (!c->res_ok) {
+        rketd_status st = plan_resident(c);
+        if (st) return st;
+      }
+      const int nsub = (int)std::min<int64_t>(nsteps, (int64_t)(B - pos));
+      StepArgs<T> a = make_args<T>(c, c->cur, 1 - c->cur);
+      a.nsub = nsub;
+      a.tprobes = c->res_probes_d;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->timing) {
+        rketd_status st = timing_event(c, &e0);
+        if (!st) st = timing_event(c, &e1);
+        if (st) return st;
+        CK(cudaEventRecord(e0, c->stream), "timing event");
+      }
+      CK(launch_resident<T>(a, c->res_K, c->res_ctas, c->res_threads, c->res_pl, c->stream, false, nullptr),
+         "resident step");
+      c->launches += 1;
+      if (c->timing) {
+        CK(cudaEventRecord(e1, c->stream), "timing event");
+        c->t_launches += 1;
+        c->t_cells += (double)c->nz[0] * nsub;
+      }
+      c->cur = 1 - c->cur;
+      c->step += nsub;
+      nsteps -= nsub;
     } else {
       const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
       if (c->tiles_K != K || c->tiles_T != TS) {
@@ -597,6 +694,7 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   if (opt) op = *opt;
   rketd_status st = check_options(op, c->prec);
   if (st) return st;
+  c->auto_variant = op.variant == 0;
   if (grid->scheme == RKETD_SCHEME_ETD2) {
     // E^{n-1} is one more carried array: the plain (one step per launch) kernels carry it
     if (op.variant == 2)
@@ -644,8 +742,13 @@ rketd_status update_coeffs(rketd_ctx* c) {
 // 8 graphs). The internal stream is ordered after and before the context's stream by events,
 // so capture works whatever stream the context was given.
 rketd_status step_graph(rketd_ctx* c, int64_t nsteps) {
-  const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
-  if (c->tiles_K != K || c->tiles_T != TS) {
+  const int K = c->opt.variant == 3 ? -1 : c->opt.cells_per_lane, TS = c->opt.tb_steps;
+  if (c->opt.variant == 3) {
+    if (!c->res_ok) {
+      rketd_status st = plan_resident(c);
+      if (st) return st;
+    }
+  } else if (c->tiles_K != K || c->tiles_T != TS) {
     rketd_status st = plan_tiles(c, K, TS);
     if (st) return st;
   }
@@ -788,12 +891,20 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
     c->Xi = (double*)p;
     if ((st = c->alloc(&p, sizeof(double) * 2 * (size_t)P * nf, "spectra"))) return cleanup(st);
     c->Xtmp = (double*)p;
+    if ((st = c->alloc(&p, sizeof(double) * 2 * (size_t)nf, "dft rotation"))) return cleanup(st);
+    c->rot = (double*)p;
     std::vector<int64_t> pi(P);
     for (int s = 0; s < n_slabs; ++s)
       for (int q = 0; q < c->n_probes; ++q) pi[s * c->n_probes + q] = c->soff[s] + c->probe_cell[s * c->n_probes + q];
     if (cudaMemcpy(c->probe_index_d, pi.data(), sizeof(int64_t) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->freq_d, c->freq.data(), sizeof(double) * nf, cudaMemcpyHostToDevice) != cudaSuccess)
       return cleanup(cuda_fail(cudaGetLastError(), "probe upload"));
+    // twiddles exp(-j 2 pi f t dt), t = 0 .. dft_block-1, shared by every fold
+    cudaError_t e = c->prec == RKETD_F64
+                        ? launch_twiddles<double>(c->freq_d, nf, c->grid.dt, 0, B, (double*)c->tw, c->stream)
+                        : launch_twiddles<float>(c->freq_d, nf, c->grid.dt, 0, B, (float*)c->tw, c->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "twiddles"));
+    c->launches += 1;
   }
   if (cudaMemcpy(c->soff_d, c->soff.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->off_d, c->off.data(), sb, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -815,6 +926,17 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
   }
   if ((st = zero_state(c))) return cleanup(st);
   if ((st = rketd_set_medium(c, wp2, nu, 0))) return cleanup(st);
+  // resident variant: where asked for, or under auto where it applies
+  if (c->opt.variant == 3 || (c->auto_variant && c->opt.variant == 2)) {
+    st = plan_resident(c);
+    if (st == RKETD_OK) {
+      c->opt.variant = 3;
+    } else if (c->opt.variant == 3) {
+      return cleanup(st);
+    } else {
+      g_err.clear();
+    }
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cleanup(cuda_fail(cudaGetLastError(), "create"));
   *out = c;
   return RKETD_OK;
@@ -856,7 +978,7 @@ rketd_status rketd_step(rketd_ctx* c, int64_t nsteps) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (nsteps < 0) return fail(RKETD_EINVAL, "nsteps < 0");
   if (nsteps == 0) return RKETD_OK;
-  const bool graphs = c->opt.use_graphs != 2 && !c->timing && c->opt.variant == 2;
+  const bool graphs = c->opt.use_graphs != 2 && !c->timing && (c->opt.variant == 2 || c->opt.variant == 3);
   if (!graphs) return c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
   return step_graph(c, nsteps);
 }
@@ -1108,6 +1230,26 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
       best = c->opt;
     }
   }
+  // the resident variant, where it applies, is one more candidate
+  if (!st && c->n_slabs == 1 && c->grid.bc == RKETD_BC_MUR1 && c->grid.scheme != RKETD_SCHEME_ETD2) {
+    c->opt = opt0;
+    c->opt.variant = 3;
+    c->opt.use_graphs = 2;
+    if (plan_resident(c) == RKETD_OK) {
+      st = rketd_step(c, 64);  // warm-up
+      if (!st && cudaEventRecord(e0, c->stream) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "autotune");
+      if (!st) st = rketd_step(c, nsteps);
+      if (!st && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = cuda_fail(cudaGetLastError(), "autotune");
+      float ms = 0;
+      if (!st && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = c->opt;
+      }
+    } else {
+      g_err.clear();
+    }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // restore the state
@@ -1132,6 +1274,7 @@ rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every
   if (c->grid.bc != RKETD_BC_MUR1) return fail(RKETD_EUNSUPPORTED, "the adjoint supports first-order Mur ends only");
   if (c->grid.scheme != RKETD_SCHEME_RKETD)
     return fail(RKETD_EUNSUPPORTED, "the adjoint differentiates the Eq. 11 recursion only");
+  if (c->opt.variant == 3) c->opt.variant = 2;  // the checkpointed run and the adjoint use the tiled kernels
   if (c->opt.variant != 2) return fail(RKETD_EUNSUPPORTED, "the adjoint runs on the tiled variant");
   const int64_t n_ckpt = (nsteps + ckpt_every - 1) / ckpt_every;
   const size_t fb = c->esz * c->n_store;

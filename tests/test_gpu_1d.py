@@ -39,7 +39,7 @@ def c1_oracle():
     return s, tot, inc
 
 
-@pytest.mark.parametrize("variant", [2, 1])
+@pytest.mark.parametrize("variant", [3, 2, 1])
 def test_c1_fp64_spectra_fields_and_rt_match_oracle(c1_oracle, variant):
     s, tot, inc = c1_oracle
     X, E, H, J = lib_run(s, "f64", variant=variant)
