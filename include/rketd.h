@@ -108,7 +108,7 @@ typedef struct {
                            step), 2 = temporally blocked warp tiles, 3 = resident: a single
                            Mur-terminated slab held in the registers of one thread-block cluster (up
                            to 16 CTAs) for a whole DFT block of steps per launch, for slabs of up to
-                           8192 (FP64) or 32768 (FP32) cells; RKETD_EUNSUPPORTED where it does not
+                           16384 (FP64) or 32768 (FP32) cells; RKETD_EUNSUPPORTED where it does not
                            apply. The checkpointed forward run and the adjoint use the tiled kernels. */
   int32_t cells_per_lane;  /* K for the tiled kernel: 8, 12 or 16 (F32), 4 or 8 (F64); 0 = auto */
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
@@ -120,7 +120,10 @@ typedef struct {
   int32_t res_ctas;     /* resident variant: CTAs of the cluster, 1..16; 0 = auto */
   int32_t res_threads;  /* resident variant: threads per CTA, a multiple of 32, <= 1024 (FP32) or 256
                            (FP64); 0 = auto */
-  int32_t reserved[3];
+  int32_t res_cells;    /* resident variant: cells per thread, 2, 4, 8 or 16 (FP32), 1, 2, 4 or 8 (FP64)
+                           (at most 1024, 512, 256, 128 threads with 2, 4, 8, 16 FP32 cells; 256 threads
+                           with up to 4 FP64 cells, 128 with 8); 0 = auto */
+  int32_t reserved[2];
 } rketd_options;
 
 typedef struct rketd_ctx rketd_ctx;

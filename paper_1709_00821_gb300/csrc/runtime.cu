@@ -192,6 +192,9 @@ rketd_status check_options(const rketd_options& o, int prec) {
   if (o.res_ctas < 0 || o.res_ctas > 16) return fail(RKETD_EINVAL, "res_ctas must be 0..16");
   if (o.res_threads < 0 || o.res_threads % 32 || o.res_threads > (prec == 1 ? 256 : 1024))
     return fail(RKETD_EINVAL, "res_threads must be a multiple of 32, at most 1024 (FP32) or 256 (FP64)");
+  if (o.res_cells != 0 && (prec == 1 ? (o.res_cells != 1 && o.res_cells != 2 && o.res_cells != 4 && o.res_cells != 8)
+                                     : (o.res_cells != 2 && o.res_cells != 4 && o.res_cells != 8 && o.res_cells != 16)))
+    return fail(RKETD_EINVAL, "res_cells must be 1, 2, 4 or 8 (FP64) or 2, 4, 8 or 16 (FP32)");
   if (prec == 0 && o.cells_per_lane != 0 && o.cells_per_lane != 8 && o.cells_per_lane != 12 &&
       o.cells_per_lane != 16)
     return fail(RKETD_EUNSUPPORTED, "FP32 cells_per_lane must be 8, 12 or 16");
@@ -355,32 +358,35 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   return RKETD_OK;
 }
 
-// Shape of the resident variant for this context (single Mur slab, not the Eq. 10 recursion):
-// FP64 spreads the cells over up to 16 CTAs of 128 threads (a warp per SM sub-partition, whose FP64
-// units are few), 1, 2 or 4 cells per thread (up to 8192 cells); FP32 keeps them in as few CTAs of up
-// to 1024 threads of 2 cells or 512 threads of 4 (up to 32768 cells). Options res_ctas / res_threads override. The shape is kept only if the
-// cluster can be scheduled. Returns RKETD_EUNSUPPORTED (with the reason) where it does not apply.
+// Shape of the resident variant for this context (single Mur slab, not the Eq. 10 recursion): the
+// first instantiated shape (cells per thread K, CTA size) whose cluster of at most 16 CTAs holds the
+// slab. FP64 prefers few cells per thread over many CTAs of 128 threads (a warp per SM sub-partition,
+// whose FP64 units are few); FP32 prefers 2 cells per thread in CTAs of up to 1024 threads (its
+// steps are latency-bound: many short warps beat few long ones). Options
+// res_cells / res_threads / res_ctas override. The shape is kept only if it can be scheduled.
+// Returns RKETD_EUNSUPPORTED (with the reason) where it does not apply.
 rketd_status plan_resident(rketd_ctx* c) {
   c->res_ok = false;
   if (c->n_slabs != 1 || c->grid.bc != RKETD_BC_MUR1 || c->grid.scheme == RKETD_SCHEME_ETD2)
     return fail(RKETD_EUNSUPPORTED, "the resident variant takes one slab with first-order Mur ends (Eq. 11 or 9)");
   const int64_t nz = c->nz[0];
   const bool f64 = c->prec == RKETD_F64;
-  int threads = c->opt.res_threads ? c->opt.res_threads : (f64 ? 128 : 1024);
-  int K = 0, ctas = 0, pl = 0;
-  const int Ks64[] = {1, 2, 4}, Ks32[] = {2, 4};
-  const int* Ks = f64 ? Ks64 : Ks32;
-  const int nK = f64 ? 3 : 2;
-  for (int q = 0; q < nK && !K; ++q) {
-    const int k = Ks[q];
+  // instantiated shapes: cells per thread and the largest CTA for it, in order of preference
+  struct Shape { int K, max_threads, default_threads; };
+  const Shape s64[] = {{1, 256, 128}, {2, 256, 128}, {4, 256, 128}, {8, 128, 128}};
+  const Shape s32[] = {{2, 1024, 1024}, {4, 512, 512}, {8, 256, 256}, {16, 128, 128}};
+  const Shape* shapes = f64 ? s64 : s32;
+  int K = 0, ctas = 0, pl = 0, threads = 0;
+  for (int q = 0; q < 4 && !K; ++q) {
+    const Shape sh = shapes[q];
+    if (c->opt.res_cells && c->opt.res_cells != sh.K) continue;
+    if (c->opt.res_threads > sh.max_threads) continue;
+    const int k = sh.K;
     const int p = ((nz - 1) % (32 * k) == 0) ? 1 : 0;  // keeps cells nz-2, nz-1 in one warp
-    int th = threads;
-    if (!f64) {  // FP32: up to 1024 threads of 2 cells or 512 of 4; a small slab needs fewer
-      const int cap = k == 2 ? 1024 : 512;
-      if (c->opt.res_threads > cap) continue;
-      if (!c->opt.res_threads) th = (int)std::min<int64_t>(cap, round_up((nz + p + k - 1) / k, 32));
-    }
+    int th = c->opt.res_threads ? c->opt.res_threads : sh.default_threads;
     int n = c->opt.res_ctas ? c->opt.res_ctas : (int)((nz + p + (int64_t)th * k - 1) / ((int64_t)th * k));
+    if (!c->opt.res_threads && n == 1)  // one CTA: no more threads than the slab needs
+      th = (int)std::min<int64_t>(th, round_up((nz + p + k - 1) / k, 32));
     if (n >= 1 && n <= 16 && (int64_t)n * th * k >= nz + p) {
       K = k;
       ctas = n;
@@ -388,7 +394,7 @@ rketd_status plan_resident(rketd_ctx* c) {
       threads = th;
     }
   }
-  if (!K) return fail(RKETD_EUNSUPPORTED, "slab of %lld cells too long for the resident variant", (long long)nz);
+  if (!K) return fail(RKETD_EUNSUPPORTED, "slab of %lld cells does not fit the resident variant's shapes", (long long)nz);
   int max_clusters = 0;
   const StepArgs<double> q64{};
   const StepArgs<float> q32{};
@@ -697,7 +703,7 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   c->auto_variant = op.variant == 0;
   if (grid->scheme == RKETD_SCHEME_ETD2) {
     // E^{n-1} is one more carried array: the plain (one step per launch) kernels carry it
-    if (op.variant == 2)
+    if (op.variant == 2 || op.variant == 3)
       return fail(RKETD_EUNSUPPORTED, "the Eq. 10 recursion (ETD2) runs on the plain variant only");
     op.variant = 1;
   }

@@ -35,11 +35,12 @@ using namespace tile;
 
 constexpr int kResMaxWarps = 32;
 
-template <typename T, int K, int MAXT>
+// CL: the slab spans a cluster of several CTAs (distributed shared memory and a cluster barrier);
+// otherwise one CTA (its own shared memory and a CTA barrier).
+template <typename T, int K, int MAXT, bool CL>
 __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
   __shared__ T fromR[2][kResMaxWarps];     // E of the cell after the warp's last cell
   __shared__ T fromL[2][2][kResMaxWarps];  // E and H of the cell before the warp's first cell
-  cg::cluster_group cl = cg::this_cluster();
   const int lane = threadIdx.x & 31, lw = threadIdx.x >> 5, NW = blockDim.x >> 5;
   const int rank = (int)blockIdx.x;  // the grid is one cluster
   const int NC = (int)gridDim.x;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
   const int is = (c0 <= src && src < c0 + K) ? (int)(src - c0) : -1;
   const T da_src = is >= 0 ? a.coef[kDa][src] : T(0);
   const bool src_warp = __any_sync(kFull, is >= 0);
+  const bool end_warp = __any_sync(kFull, i0 >= 0 || i1 >= 0);
   // probes among this thread's cells (tprobes: local = slab cell, slot = probe index)
   int np = 0, ps0 = 0, ps1 = 0;
   int64_t po0 = 0, po1 = 0;
@@ -102,15 +104,27 @@ __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
       sv_lane = r < a.nsub ? (T)pulse((double)(a.n0 + 1 + r) * a.dt, a.t0, a.tau, a.amp) : T(0);
     }
     // ---- exchange: first E to the left, last E and H to the right ----
-    if (lane == 0 && has_left) *cl.map_shared_rank(&fromR[b][l_idx], l_rank) = e[0];
-    if (lane == 31 && has_right) {
-      *cl.map_shared_rank(&fromL[b][0][r_idx], r_rank) = e[K - 1];
-      *cl.map_shared_rank(&fromL[b][1][r_idx], r_rank) = h[K - 1];
+    if constexpr (CL) {
+      cg::cluster_group cl = cg::this_cluster();
+      if (lane == 0 && has_left) *cl.map_shared_rank(&fromR[b][l_idx], l_rank) = e[0];
+      if (lane == 31 && has_right) {
+        *cl.map_shared_rank(&fromL[b][0][r_idx], r_rank) = e[K - 1];
+        *cl.map_shared_rank(&fromL[b][1][r_idx], r_rank) = h[K - 1];
+      }
+    } else {
+      if (lane == 0 && has_left) fromR[b][l_idx] = e[0];
+      if (lane == 31 && has_right) {
+        fromL[b][0][r_idx] = e[K - 1];
+        fromL[b][1][r_idx] = h[K - 1];
+      }
     }
     T eR = __shfl_down_sync(kFull, e[0], 1);
     T eL = __shfl_up_sync(kFull, e[K - 1], 1);
     T hLo = __shfl_up_sync(kFull, h[K - 1], 1);
-    cl.sync();
+    if constexpr (CL)
+      cg::this_cluster().sync();
+    else
+      __syncthreads();
     if (lane == 31) eR = has_right ? fromR[b][lw] : T(0);
     if (lane == 0) {
       eL = has_left ? fromL[b][0][lw] : T(0);
@@ -123,11 +137,20 @@ __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
       if (mH & (1u << i)) h[i] = fma(-S, en - e[i], h[i]);
     }
     const T hL = fma(-S, e[0] - eL, hLo);
-    // ---- Eqs. 13 + 11 on the folded current ----
-    T eo[K];
+    // ---- Eqs. 13 + 11 on the folded current (the end cells' old E kept for Mur) ----
+    T e0o = T(0), e1o = T(0), eN1o = T(0), eN2o = T(0);
+    if (end_warp) {
+      if (i0 >= 0) {
+        e0o = pick(e, i0);
+        e1o = i0 + 1 < K ? pick(e, i0 + 1) : eR;
+      }
+      if (i1 >= 0) {
+        eN1o = pick(e, i1);
+        eN2o = i1 > 0 ? pick(e, i1 - 1) : eL;
+      }
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      eo[i] = e[i];
       const T hp = i ? h[i - 1] : hL;
       if (mE & (1u << i)) {
         const T enew = fold_e(e[i], cb[i], h[i] - hp, g[i]);
@@ -144,17 +167,17 @@ __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
       }
     }
     // ---- first-order Mur ends (partners by shuffle within the warp) ----
-    const T nextNew = __shfl_down_sync(kFull, e[0], 1);
-    const T prevNew = __shfl_up_sync(kFull, e[K - 1], 1);
-    if (i0 >= 0) {
-      const T e1o = i0 + 1 < K ? pick(eo, i0 + 1) : eR;
-      const T e1n = i0 + 1 < K ? pick(e, i0 + 1) : nextNew;
-      put(e, i0, fma(a.qmur, e1n - pick(eo, i0), e1o));
-    }
-    if (i1 >= 0) {
-      const T e2o = i1 > 0 ? pick(eo, i1 - 1) : eL;
-      const T e2n = i1 > 0 ? pick(e, i1 - 1) : prevNew;
-      put(e, i1, fma(a.qmur, e2n - pick(eo, i1), e2o));
+    if (end_warp) {
+      const T nextNew = __shfl_down_sync(kFull, e[0], 1);
+      const T prevNew = __shfl_up_sync(kFull, e[K - 1], 1);
+      if (i0 >= 0) {
+        const T e1n = i0 + 1 < K ? pick(e, i0 + 1) : nextNew;
+        put(e, i0, fma(a.qmur, e1n - e0o, e1o));
+      }
+      if (i1 >= 0) {
+        const T eN2n = i1 > 0 ? pick(e, i1 - 1) : prevNew;
+        put(e, i1, fma(a.qmur, eN2n - eN1o, eN2o));
+      }
     }
     // ---- probe samples ----
     if (np > 0) {
@@ -181,8 +204,14 @@ __global__ void __launch_bounds__(MAXT) k_res(const StepArgs<T> a, int pl) {
 template <typename T, int K, int MAXT>
 cudaError_t launch_k(const StepArgs<T>& a, int ctas, int threads, int pl, cudaStream_t st, bool query_only,
                      int* max_clusters) {
-  auto fn = k_res<T, K, MAXT>;
   if (threads > MAXT || threads % 32 || threads / 32 > kResMaxWarps) return cudaErrorInvalidValue;
+  if (ctas == 1) {
+    auto f1 = k_res<T, K, MAXT, false>;
+    if (query_only) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_clusters, f1, threads, 0);
+    f1<<<1, threads, 0, st>>>(a, pl);
+    return cudaGetLastError();
+  }
+  auto fn = k_res<T, K, MAXT, true>;
   if (ctas > 8) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
@@ -210,18 +239,22 @@ template <typename T>
 cudaError_t launch_resident(const StepArgs<T>& a, int K, int ctas, int threads, int pl, cudaStream_t st,
                             bool query_only, int* max_clusters) {
   if (ctas < 1 || ctas > 16) return cudaErrorInvalidValue;
-  if (std::is_same<T, double>::value) {
+  if constexpr (std::is_same<T, double>::value) {
     switch (K) {
       case 1: return launch_k<T, 1, 256>(a, ctas, threads, pl, st, query_only, max_clusters);
       case 2: return launch_k<T, 2, 256>(a, ctas, threads, pl, st, query_only, max_clusters);
       case 4: return launch_k<T, 4, 256>(a, ctas, threads, pl, st, query_only, max_clusters);
+      case 8: return launch_k<T, 8, 128>(a, ctas, threads, pl, st, query_only, max_clusters);
       default: return cudaErrorInvalidValue;
     }
-  }
+  } else {
   switch (K) {
     case 2: return launch_k<T, 2, 1024>(a, ctas, threads, pl, st, query_only, max_clusters);
     case 4: return launch_k<T, 4, 512>(a, ctas, threads, pl, st, query_only, max_clusters);
+    case 8: return launch_k<T, 8, 256>(a, ctas, threads, pl, st, query_only, max_clusters);
+    case 16: return launch_k<T, 16, 128>(a, ctas, threads, pl, st, query_only, max_clusters);
     default: return cudaErrorInvalidValue;
+  }
   }
 }
 template cudaError_t launch_resident<float>(const StepArgs<float>&, int, int, int, int, cudaStream_t, bool, int*);

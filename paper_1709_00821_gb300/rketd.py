@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("cells_per_lane", ctypes.c_int32), ("tb_steps", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("dft_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("fp32_pairs", ctypes.c_int32), ("res_ctas", ctypes.c_int32), ("res_threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("res_cells", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Grid3D(ctypes.Structure):

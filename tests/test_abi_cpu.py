@@ -101,7 +101,7 @@ def test_invalid_inputs_are_rejected_before_any_device_work(case):
     assert msg and not h.value
 
 
-@pytest.mark.parametrize("scheme,variant,status", [(3, 0, 1), (-1, 0, 1), (2, 2, 6)])
+@pytest.mark.parametrize("scheme,variant,status", [(3, 0, 1), (-1, 0, 1), (2, 2, 6), (2, 3, 6)])
 def test_current_recursion_choices_are_validated_before_any_device_work(scheme, variant, status):
     """An unknown recursion is EINVAL; the Eq. 10 recursion asked of the tiled variant, which does
     not carry E^{n-1}, is EUNSUPPORTED."""

@@ -41,7 +41,7 @@ def _run(s, prec, **opts):
     return used, X, F
 
 
-SIZES = {"f64": [8, 9, 13, 33, 63, 64, 65, 127, 129, 257, 511, 1000, 1537, 2047, 2048, 2049, 4097, 8191],
+SIZES = {"f64": [8, 9, 13, 33, 63, 64, 65, 127, 129, 257, 511, 1000, 1537, 2047, 2048, 2049, 4097, 8191, 16383],
          "f32": [8, 9, 13, 33, 65, 127, 129, 257, 511, 1000, 2047, 2049, 4097, 16385, 32767]}
 
 
@@ -52,10 +52,14 @@ def test_resident_variant_is_bitwise_equal_to_the_plain_kernels(prec):
             s = _slab(nz, 7 * nz + (src or 0), src)
             base = _run(s, prec, variant=1)
             shapes = [{"variant": 0}, {"variant": 3}]
-            if nz <= 512:
-                shapes.append({"variant": 3, "res_threads": 32})  # several CTAs of one warp
-            if 64 < nz <= 2048:
-                shapes.append({"variant": 3, "res_threads": 64})
+            small = 1 if prec == "f64" else 2
+            if nz <= 32 * small * 16:  # up to 16 CTAs of one warp, fewest cells per thread
+                shapes.append({"variant": 3, "res_threads": 32, "res_cells": small})
+            if 64 < nz <= 64 * 2 * 16:
+                shapes.append({"variant": 3, "res_threads": 64, "res_cells": 2})
+            big = 8 if prec == "f64" else 16
+            if 32 * big < nz <= 32 * big * 16:  # several CTAs of one warp, most cells per thread
+                shapes.append({"variant": 3, "res_threads": 32, "res_cells": big})
             for opts in shapes:
                 used, X, F = _run(s, prec, **opts)
                 assert used["variant"] == 3, (nz, opts, used)
@@ -78,7 +82,7 @@ def test_paper_slab_runs_resident_under_auto_and_matches_the_oracle():
 def test_resident_variant_is_refused_where_it_does_not_apply():
     s = _slab(600, 3)
     cases = [([s, _slab(700, 4)], "f32", {}),  # a batch
-             (_slab(8193, 5), "f64", {}),  # longer than 16 CTAs x 128 threads x 4 cells
+             (_slab(16385, 5), "f64", {}),  # longer than 16 CTAs x 128 threads x 8 cells
              (_slab(32769, 6), "f32", {})]
     c = _slab(600, 7)
     c.bc, c.cpml_cells, c.probes = "cpml", 8, [8, 591]
