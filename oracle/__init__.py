@@ -112,8 +112,8 @@ def make_grid(slab, cpml=None) -> OrGrid1D:
     g.nz = slab.nz
     g.dz = slab.dz
     g.dt = slab.dt
-    g.bc = 1 if slab.bc == "cpml" else 0
-    g.cpml_cells = slab.cpml_cells if slab.bc == "cpml" else 0
+    g.bc = {"mur": 0, "cpml": 1, "pml": 2}[slab.bc]
+    g.cpml_cells = slab.cpml_cells if slab.bc in ("cpml", "pml") else 0
     m, smax, kmax, amax = cpml if cpml is not None else cpml_defaults(slab.dz)
     g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = m, smax, kmax, amax
     g.src_cell = slab.src_cell

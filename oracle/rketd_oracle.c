@@ -21,7 +21,8 @@
  *      denominator D of the printed E^n coefficient);
  *   3. J^{n+1} from Eq. 11 with E^n and E^{n+1};
  *   4. soft source of Eq. 15 added to E^{n+1} at the source cell;
- *   5. end cells: first-order Mur, or PEC walls behind a CPML;
+ *   5. end cells: first-order Mur, or PEC walls behind a CPML or behind the paper's
+ *      split-field PML (which replaces steps 1-3 in its layers);
  *   6. running DFT of E^{n+1} at the probe cells.
  * Eq. 11 is used rather than Eq. 10: integrating the linear interpolant of F
  * between t_n and t_{n+1} against e^{nu tau} in Eq. 7 gives Eq. 11's terms.
@@ -49,8 +50,9 @@
 typedef struct {
   int64_t nz;          /* E nodes 0..nz-1; H nodes k+1/2 for k = 0..nz-2 */
   double dz, dt;       /* m, s */
-  int32_t bc;          /* 0: first-order Mur at both ends; 1: CPML with PEC outer walls */
-  int32_t cpml_cells;  /* CPML thickness in cells (bc == 1) */
+  int32_t bc;          /* 0: first-order Mur at both ends; 1: CPML with PEC outer walls;
+                          2: the paper's split-field PML (Sec. III, Sec. IV.B) with PEC outer walls */
+  int32_t cpml_cells;  /* CPML / PML thickness in cells (bc == 1, 2) */
   double cpml_m, cpml_sigma_max, cpml_kappa_max, cpml_alpha_max;
   int64_t src_cell;    /* soft source cell */
   double src_tau, src_t0, src_amp;
@@ -114,13 +116,24 @@ static double or_cpml_rho(const or_grid1d* g, double x) {
   return 0.0;
 }
 
+/* Relative depth of a node in the split-field PML layers (bc == 2), graded as the CPML. */
+static double or_pml_rho(const or_grid1d* g, double x) {
+  double n = (double)g->cpml_cells;
+  double right_inner = (double)(g->nz - 1) - n;
+  if (g->bc != 2 || g->cpml_cells <= 0) return 0.0;
+  if (x < n) return (n - x) / n;
+  if (x > right_inner) return (x - right_inner) / n;
+  return 0.0;
+}
+
 /* Validates the problem; returns 0 or a negative code. */
 static int or_check(const or_grid1d* g, const int64_t* probe_cells) {
   if (g->nz < 4 || g->dz <= 0 || g->dt <= 0) return -1;
   if (g->src_cell < 1 || g->src_cell > g->nz - 2) return -2;
   for (int p = 0; p < g->n_probes; ++p)
     if (probe_cells[p] < 0 || probe_cells[p] >= g->nz) return -3;
-  if (g->bc == 1 && (g->cpml_cells < 1 || 2 * g->cpml_cells + 2 > g->nz)) return -4;
+  if ((g->bc == 1 || g->bc == 2) && (g->cpml_cells < 1 || 2 * g->cpml_cells + 2 > g->nz)) return -4;
+  if (g->bc < 0 || g->bc > 2) return -4;
   if (g->scheme < 0 || g->scheme > 2) return -6;
   return 0;
 }
@@ -165,6 +178,49 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
   double* pkH = (double*)malloc(sizeof(double) * nz);
   char* inE = (char*)calloc(nz, 1);
   char* inH = (char*)calloc(nz, 1);
+  /* Split-field PML (bc == 2, the paper's boundary, Berenger's PML). In 1D only the z-split field
+     exists, so the layer is one graded conductivity sigma on E with the matched magnetic
+     conductivity sigma* = sigma mu0/eps0 on H, advanced by exponential differencing:
+       E^{n+1} = e^{-sigma dt/eps0} E^n - (1 - e^{-sigma dt/eps0})/(sigma dz) (H_{k+1/2} - H_{k-1/2}),
+       H^{n+1/2} = e^{-sigma* dt/mu0} H^{n-1/2} - (1 - e^{-sigma* dt/mu0})/(sigma* dz) (E_{k+1} - E_k),
+     sigma = sigma_max rho^m at the node's relative depth rho, as the CPML (sigma* dt/mu0 = sigma dt/eps0).
+     The layer is vacuum: no current. */
+  double* paE = (double*)calloc(nz, sizeof(double));
+  double* pfE = (double*)calloc(nz, sizeof(double));
+  double* paH = (double*)calloc(nz, sizeof(double));
+  double* pfH = (double*)calloc(nz, sizeof(double));
+  char* inPE = (char*)calloc(nz, 1);
+  char* inPH = (char*)calloc(nz, 1);
+  for (int64_t k = 0; k < nz; ++k) {
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && k == nz - 1) continue;
+      double rho = or_pml_rho(g, (double)k + 0.5 * h);
+      if (rho <= 0.0) continue;
+      double sigma = g->cpml_sigma_max * pow(rho, g->cpml_m);
+      double xs = sigma * dt / OR_EPS0;
+      /* (1 - e^{-x})/(sigma dz) = dt/(eps0 dz) phi1(x); for H with sigma*: dt/(mu0 dz) phi1(x) */
+      if (h == 0) {
+        inPE[k] = 1;
+        paE[k] = exp(-xs);
+        pfE[k] = dt / (OR_EPS0 * dz) * or_phi1(xs);
+      } else {
+        inPH[k] = 1;
+        paH[k] = exp(-xs);
+        pfH[k] = dt / (OR_MU0 * dz) * or_phi1(xs);
+#if defined(OR_MUTANT) && OR_MUTANT == 10
+        /* planted mistake: no magnetic conductivity (sigma* = 0), an unmatched layer */
+        paH[k] = 1.0;
+        pfH[k] = dt / (OR_MU0 * dz);
+#endif
+      }
+    }
+    if (inPE[k] && wp2[k] != 0.0) {
+      free(a); free(b1); free(b2); free(cEE); free(cEH); free(cEJ);
+      free(pbE); free(pcE); free(pkE); free(pbH); free(pcH); free(pkH); free(inE); free(inH);
+      free(paE); free(pfE); free(paH); free(pfH); free(inPE); free(inPH);
+      return -8;  /* the split-field PML layers are vacuum */
+    }
+  }
   for (int64_t k = 0; k < nz; ++k) {
     double x = nu[k] * dt;
     /* Eq. 11: J^{n+1} = a J^n + beta1 E^n + beta2 (E^{n+1} - E^n) with
@@ -211,6 +267,10 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
 #endif
     for (int64_t k = 0; k < nz - 1; ++k) {
       double dE = E[k + 1] - E[k];
+      if (inPH[k]) { /* split-field PML */
+        H[k] = paH[k] * H[k] - pfH[k] * dE;
+        continue;
+      }
       double curl;
       if (inH[k]) {
         psiH[k] = pbH[k] * psiH[k] + pcH[k] * (dE / dz);
@@ -228,6 +288,10 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
 #endif
     for (int64_t k = 1; k < nz - 1; ++k) {
       double dH = H[k] - H[k - 1];
+      if (inPE[k]) { /* split-field PML */
+        E[k] = paE[k] * E[k] - pfE[k] * dH;
+        continue;
+      }
       double curl;
       if (inE[k]) {
         psiE[k] = pbE[k] * psiE[k] + pcE[k] * (dH / dz);
@@ -269,7 +333,7 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
     /* 4. Eq. 15 soft source at t = (n+1) dt. */
     E[g->src_cell] = E[g->src_cell] + or_source(g, (double)(n + 1) * dt);
     /* 5. End cells. */
-    if (g->bc == 1) {
+    if (g->bc == 1 || g->bc == 2) {
       E[0] = 0.0;
       E[nz - 1] = 0.0;
     } else {
@@ -295,6 +359,7 @@ int or_run1d(const or_grid1d* g, const double* wp2, const double* nu, const int6
   }
   free(a); free(b1); free(b2); free(cEE); free(cEH); free(cEJ);
   free(pbE); free(pcE); free(pkE); free(pbH); free(pcH); free(pkH); free(inE); free(inH);
+  free(paE); free(pfE); free(paH); free(pfH); free(inPE); free(inPH);
   return 0;
 }
 

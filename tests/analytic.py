@@ -17,6 +17,9 @@ from the paper's equations or from textbook electromagnetics:
   such solves (plasma and vacuum) are what the running DFT converges to as the
   window grows.
 * `fresnel_slab` -- continuous (Airy) slab with eps_r = 1 - wp^2/(w (w - j nu)).
+* `domain_response_pml` -- the same steady-state response for a lattice terminated by the paper's
+  split-field PML (graded matched conductivities, exponential differencing) and PEC walls.
+* `current_response` -- the z-domain current of each recursion (Eq. 11, Eq. 9, Eq. 10).
 """
 from __future__ import annotations
 
@@ -264,3 +267,62 @@ def normalized_run(slab, steps):
         E[-1] = em2 + qm * (E[-2] - em1)
         X += E[slab.probes][:, None] * np.exp(-2j * np.pi * f[None, :] * t)
     return E, Ht / eta0, Jt * EPS0 / dt, X
+
+
+def split_pml_profile(nz: int, n: int, m: float, sigma_max: float, dt: float, dz: float):
+    """Per-node coefficients of the split-field PML (normalised fields, S = c dt/dz):
+    E' = aE E - S fE (H~_{k+1/2} - H~_{k-1/2}),  H~' = aH H~ - S fH (E_{k+1} - E_k),
+    a = e^{-x}, f = (1 - e^{-x})/x, x = sigma dt/eps0 (sigma* dt/mu0 for H with the matched sigma*),
+    sigma = sigma_max rho^m at relative depth rho = (n - d)/n from the inner interface (d the node's
+    distance from the outer wall in cells). Outside the layers a = f = 1. Returns (aE, fE, inE) for E
+    nodes 0..nz-1 and (aH, fH) for H nodes k+1/2, k = 0..nz-2."""
+    def coef(pos):
+        right_inner = nz - 1 - n
+        rho = (n - pos) / n if pos < n else ((pos - right_inner) / n if pos > right_inner else 0.0)
+        if rho <= 0.0:
+            return 1.0, 1.0, False
+        x = sigma_max * rho ** m * dt / EPS0
+        with mp.workdps(40):
+            X = mp.mpf(x)
+            return float(mp.exp(-X)), float((1 - mp.exp(-X)) / X), True
+    E = [coef(k) for k in range(nz)]
+    H = [coef(k + 0.5) for k in range(nz - 1)]
+    aE = np.array([c[0] for c in E]); fE = np.array([c[1] for c in E]); inE = np.array([c[2] for c in E])
+    aH = np.array([c[0] for c in H]); fH = np.array([c[1] for c in H])
+    return aE, fE, inE, aH, fH
+
+
+def domain_response_pml(wp2, nu, dz, dt, freqs, src_cell, cells, n, m, sigma_max, scheme: int = 0):
+    """Steady-state phasors at `cells` of a finite lattice with the split-field PML of n cells at both
+    ends and PEC walls (E_0 = E_{nz-1} = 0), driven by a soft source (the same scale in every solve).
+
+    E^n = E z^n, H~^{n+1/2} = H z^{n+1/2}. With w_{k+1/2} = S fH_{k+1/2}/(z - aH_{k+1/2}) (S/(z-1)
+    outside the layers), each E row reads
+      (z - aE_k) eps_k E_k = S fE_k z [w_{k+1/2}(E_{k+1} - E_k) - w_{k-1/2}(E_k - E_{k-1})] + z s delta_{k,src},
+    eps_k the lattice permittivity of the cell (1 in the vacuum layers)."""
+    wp2 = np.asarray(wp2, float)
+    nu = np.asarray(nu, float)
+    nz = len(wp2)
+    S = courant(dz, dt)
+    aE, fE, inE, aH, fH = split_pml_profile(nz, n, m, sigma_max, dt, dz)
+    cache = _material_cache(wp2, nu, dt)
+    keys = list(zip(wp2.tolist(), nu.tolist()))
+    theta = 2 * np.pi * np.asarray(freqs) * dt
+    epsd = {k: lattice_eps(theta, *v, scheme=scheme) for k, v in cache.items()}
+    out = np.empty((len(theta), len(cells)), dtype=np.complex128)
+    for i, th in enumerate(theta):
+        z = np.exp(1j * th)
+        w = S * fH / (z - aH)  # [nz-1]
+        eps = np.array([epsd[k][i] for k in keys])
+        ab = np.zeros((3, nz), dtype=np.complex128)  # banded: upper, diag, lower
+        C = S * fE[1:-1] * z * w[1:]  # coefficient of E_{k+1} in row k = 1..nz-2
+        A = S * fE[1:-1] * z * w[:-1]  # coefficient of E_{k-1}
+        ab[1, 1:-1] = -(z - aE[1:-1]) * eps[1:-1] - C - A
+        ab[0, 2:] = C
+        ab[2, :-2] = A
+        ab[1, 0] = ab[1, -1] = 1.0  # PEC rows
+        rhs = np.zeros(nz, dtype=np.complex128)
+        rhs[src_cell] = -z
+        sol = solve_banded((1, 1), ab, rhs)
+        out[i] = sol[list(cells)]
+    return out
