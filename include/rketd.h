@@ -49,7 +49,7 @@ typedef enum {
 } rketd_status;
 
 typedef enum { RKETD_F32 = 0, RKETD_F64 = 1 } rketd_prec;
-typedef enum { RKETD_BC_MUR1 = 0, RKETD_BC_CPML = 1 } rketd_bc;
+typedef enum { RKETD_BC_MUR1 = 0, RKETD_BC_CPML = 1, RKETD_BC_PML = 2 } rketd_bc;
 /* Recursion for the plasma current over one step (Sec. II, from the exact solution Eq. 7):
  *   RKETD_SCHEME_RKETD  Eq. 11: F = eps0 wp^2 E interpolated linearly between t_n and t_{n+1};
  *                       Eq. 12 is then solved for E^{n+1} (Eq. 13). Second order. The default.
@@ -73,8 +73,13 @@ typedef enum { RKETD_SCHEME_RKETD = 0, RKETD_SCHEME_ETD1 = 1, RKETD_SCHEME_ETD2 
  * bc: RKETD_BC_MUR1 = first-order Mur at both ends; RKETD_BC_CPML = convolutional
  * PML of cpml_cells cells at both ends backed by PEC walls, with grading
  * sigma = sigma_max rho^m, kappa = 1 + (kappa_max - 1) rho^m, alpha = alpha_max (1 - rho)
- * in relative depth rho; sigma_max <= 0 selects 0.8 (m + 1)/(eta0 dz). The paper's
- * 5-cell split-field PML (Sec. III, Sec. IV.B) is replaced by these two ends. */
+ * in relative depth rho; sigma_max <= 0 selects 0.8 (m + 1)/(eta0 dz).
+ * RKETD_BC_PML = the paper's split-field PML (Sec. III; 5 cells in Sec. IV.B) of cpml_cells cells
+ * at both ends backed by PEC walls. In 1D only the z-split field exists, so the layer is one graded
+ * conductivity sigma on E with the matched magnetic conductivity sigma mu0/eps0 on H, advanced by
+ * exponential differencing: E' = e^{-x} E - (1 - e^{-x})/(sigma dz) dH, x = sigma dt/eps0, and the
+ * same for H. sigma = sigma_max rho^m as above (kappa_max, alpha_max unused). The layers must be
+ * vacuum (wp2 = 0 there, else RKETD_EINVAL). */
 typedef struct {
   double dz, dt;
   int32_t prec;          /* rketd_prec */

@@ -134,7 +134,39 @@ __global__ void k_cpml(int n, double dt, double m, double smax, double kmax, dou
   }
 }
 
+// Split-field PML (the paper's boundary) per depth: E nodes d = 0..n (rho = (n - d)/n), H nodes
+// i + 1/2 (rho = (n - i - 1/2)/n); sigma = smax rho^m, x = sigma dt/eps0 (sigma* dt/mu0 for H with the
+// matched sigma*), the update x' = e^{-x} x - S phi1(x) D on normalised fields: stored as
+// da = e^{-x} - 1 (expm1) and c = S phi1(x), rows [da | c].
+template <typename T>
+__global__ void k_pml(int n, double dt, double S, double m, double smax, T* __restrict__ tabE,
+                      T* __restrict__ tabH) {
+  const int i = threadIdx.x;
+  for (int which = 0; which < 2; ++which) {
+    const int count = which == 0 ? n + 1 : n;
+    if (i >= count) continue;
+    const double rho = which == 0 ? (double)(n - i) / n : ((double)n - i - 0.5) / n;
+    const double x = smax * pow(rho, m) * dt / kEps0;
+    double p1, p2, psi;
+    phi12(x, p1, p2, psi);
+    T* tab = which == 0 ? tabE : tabH;
+    tab[i] = (T)expm1(-x);
+    tab[count + i] = (T)(S * p1);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pml_tables(int prec, int n, double dt, double S, double m, double smax, void* tabE, void* tabH,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = ((n + 1 + 31) / 32) * 32;
+  if (prec == 1)
+    k_pml<double><<<1, threads, 0, st>>>(n, dt, S, m, smax, (double*)tabE, (double*)tabH);
+  else
+    k_pml<float><<<1, threads, 0, st>>>(n, dt, S, m, smax, (float*)tabE, (float*)tabH);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const int64_t* soff,
                           const int64_t* off, const int64_t* nz, int n_slabs, int64_t n_store,

@@ -90,7 +90,8 @@ struct StepArgs {
   T* Ep;
   const T* ep;
   const T* gp;
-  // CPML (bc == 1): compact memories [n_slabs][2 ends][ncpml] for E and H nodes
+  // CPML (bc == 1): compact memories [n_slabs][2 ends][ncpml] for E and H nodes; the split-field
+  // PML (bc == 2) uses cpmlE [2][ncpml+1] and cpmlH [2][ncpml] as its (da, c) tables, no memories
   const T* psiE_in;
   const T* psiH_in;
   T* psiE_out;
@@ -167,6 +168,15 @@ cudaError_t launch_coeffs(int prec, const double* wp2, const double* nu, const i
                           void* const ext[2] = nullptr);
 cudaError_t launch_cpml_tables(int prec, int ncpml, double dt, double m, double smax, double kmax,
                                double amax, void* cpmlE, void* cpmlH, cudaStream_t st);
+// split-field PML tables: E [2][n+1] and H [2][n] rows (e^{-x} - 1, S phi1(x)) by depth
+cudaError_t launch_pml_tables(int prec, int n, double dt, double S, double m, double smax, void* tabE, void* tabH,
+                              cudaStream_t st);
+
+// split-field PML update of one node: x' = e^{-s} x - S phi1 D = x - (c D - da x), small terms first
+template <typename T>
+__device__ __forceinline__ T pml_update(T x, T da, T c, T d) {
+  return x - fma(c, d, -da * x);
+}
 
 // Tiled step over a.tiles. Interior tiles (edge = false) that sample a probe or whose loaded range
 // holds their slab's source cell need xtra = true; the others run a kernel without that code.

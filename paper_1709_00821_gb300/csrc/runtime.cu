@@ -328,7 +328,7 @@ rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* src
 
 // Plans the tiles for (K, T) and uploads the lists.
 rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
-  const int64_t nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  const int64_t nc = c->grid.bc != RKETD_BC_MUR1 ? c->grid.cpml_cells : 0;
   TilePlan plan;
   rketd_status st0 =
       build_tile_plan(c->n_slabs, c->nz.data(), c->src.data(), c->n_probes, c->probe_cell.data(), nc, K, T, plan);
@@ -440,7 +440,7 @@ StepArgs<T> make_args(rketd_ctx* c, int in, int out) {
   a.psiH_out = (T*)c->psiH[out];
   a.cpmlE = (const T*)c->cpmlE;
   a.cpmlH = (const T*)c->cpmlH;
-  a.ncpml = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
+  a.ncpml = c->grid.bc != RKETD_BC_MUR1 ? c->grid.cpml_cells : 0;
   a.bc = c->grid.bc;
   a.S = (T)c->S;
   a.qmur = (T)c->qmur;
@@ -635,14 +635,20 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   if (!nz || !grid || !wp2 || !nu || !src_cell || !pulse) return fail(RKETD_EINVAL, "NULL argument");
   if (!finite_pos(grid->dz) || !finite_pos(grid->dt)) return fail(RKETD_EINVAL, "dz and dt must be finite and > 0");
   if (grid->prec != RKETD_F32 && grid->prec != RKETD_F64) return fail(RKETD_EINVAL, "prec must be F32 or F64");
-  if (grid->bc != RKETD_BC_MUR1 && grid->bc != RKETD_BC_CPML) return fail(RKETD_EINVAL, "bc must be MUR1 or CPML");
+  if (grid->bc != RKETD_BC_MUR1 && grid->bc != RKETD_BC_CPML && grid->bc != RKETD_BC_PML)
+    return fail(RKETD_EINVAL, "bc must be MUR1, CPML or PML");
   if (grid->scheme < RKETD_SCHEME_RKETD || grid->scheme > RKETD_SCHEME_ETD2)
     return fail(RKETD_EINVAL, "scheme must be RKETD (Eq. 11), ETD1 (Eq. 9) or ETD2 (Eq. 10)");
   const double S = grid->dt / (grid->dz * std::sqrt(kMu0 * kEps0));
   if (!(S <= 1.0)) return fail(RKETD_ECOURANT, "Courant number c dt/dz = %.17g exceeds 1", S);
   if (!finite_pos(pulse->tau) || !std::isfinite(pulse->t0) || !std::isfinite(pulse->amp))
     return fail(RKETD_EINVAL, "pulse tau must be > 0, t0 and amp finite");
-  const int nc = grid->bc == RKETD_BC_CPML ? grid->cpml_cells : 0;
+  const int nc = grid->bc != RKETD_BC_MUR1 ? grid->cpml_cells : 0;
+  if (grid->bc == RKETD_BC_PML) {
+    if (grid->cpml_cells < 1) return fail(RKETD_EINVAL, "cpml_cells must be >= 1");
+    if (!finite_pos(grid->cpml_m) || !std::isfinite(grid->cpml_sigma_max))
+      return fail(RKETD_EINVAL, "PML grading parameters out of range");
+  }
   if (grid->bc == RKETD_BC_CPML) {
     if (grid->cpml_cells < 1) return fail(RKETD_EINVAL, "cpml_cells must be >= 1");
     if (!finite_pos(grid->cpml_m) || !std::isfinite(grid->cpml_sigma_max) || !(grid->cpml_kappa_max >= 1.0) ||
@@ -657,7 +663,7 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   c->prec = grid->prec;
   c->esz = grid->prec == RKETD_F64 ? 8 : 4;
   c->grid = *grid;
-  if (grid->bc == RKETD_BC_CPML && !(grid->cpml_sigma_max > 0))
+  if (grid->bc != RKETD_BC_MUR1 && !(grid->cpml_sigma_max > 0))
     c->grid.cpml_sigma_max = 0.8 * (grid->cpml_m + 1) / (std::sqrt(kMu0 / kEps0) * grid->dz);
   c->pulse = *pulse;
   c->n_probes = np;
@@ -694,6 +700,11 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
     if (!(wp2[i] >= 0) || !std::isfinite(wp2[i])) return fail(RKETD_EINVAL, "wp2[%lld] must be finite and >= 0", (long long)i);
     if (!(nu[i] >= 0) || !std::isfinite(nu[i])) return fail(RKETD_EINVAL, "nu[%lld] must be finite and >= 0", (long long)i);
   }
+  if (grid->bc == RKETD_BC_PML)  // the split-field PML layers are vacuum
+    for (int s = 0; s < n_slabs; ++s)
+      for (int64_t k = 0; k < nz[s]; ++k)
+        if ((k < nc || k > nz[s] - 1 - nc) && wp2[c->off[s] + k] != 0.0)
+          return fail(RKETD_EINVAL, "slab %d: plasma (wp2 > 0) at cell %lld inside the PML layer", s, (long long)k);
   c->total_probes = n_slabs * np;
   rketd_options op{};
   rketd_default_options(&op);
@@ -873,8 +884,11 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
   c->nz_d = (int64_t*)p;
   if ((st = c->alloc(&p, sb, "slab table"))) return cleanup(st);
   c->src_d = (int64_t*)p;
-  const int nc = c->grid.bc == RKETD_BC_CPML ? c->grid.cpml_cells : 0;
-  if (nc) {
+  const int nc = c->grid.bc != RKETD_BC_MUR1 ? c->grid.cpml_cells : 0;
+  if (nc && c->grid.bc == RKETD_BC_PML) {
+    if ((st = c->alloc(&c->cpmlE, c->esz * 2 * (nc + 1), "PML table"))) return cleanup(st);
+    if ((st = c->alloc(&c->cpmlH, c->esz * 2 * nc, "PML table"))) return cleanup(st);
+  } else if (nc) {
     c->n_psi = (int64_t)n_slabs * 2 * nc;
     for (int b = 0; b < 2; ++b) {
       if ((st = c->alloc(&c->psiE[b], c->esz * c->n_psi, "CPML memory"))) return cleanup(st);
@@ -924,9 +938,12 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
     if (c->ext[k] && cudaMemsetAsync(c->ext[k], 0, fb, c->stream) != cudaSuccess)
       return cleanup(cuda_fail(cudaGetLastError(), "memset"));
   if (nc) {
-    cudaError_t e = launch_cpml_tables(c->prec, nc, c->grid.dt, c->grid.cpml_m, c->grid.cpml_sigma_max,
-                                       c->grid.cpml_kappa_max, c->grid.cpml_alpha_max, c->cpmlE, c->cpmlH,
-                                       c->stream);
+    cudaError_t e = c->grid.bc == RKETD_BC_PML
+                        ? launch_pml_tables(c->prec, nc, c->grid.dt, c->S, c->grid.cpml_m, c->grid.cpml_sigma_max,
+                                            c->cpmlE, c->cpmlH, c->stream)
+                        : launch_cpml_tables(c->prec, nc, c->grid.dt, c->grid.cpml_m, c->grid.cpml_sigma_max,
+                                             c->grid.cpml_kappa_max, c->grid.cpml_alpha_max, c->cpmlE, c->cpmlH,
+                                             c->stream);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "CPML tables"));
     c->launches += 1;
   }

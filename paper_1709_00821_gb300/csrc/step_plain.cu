@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256) k_plain_h(const StepArgs<T> a, const int3
   T* H = a.H_out;
   const T dE = a.E_in[i + 1] - a.E_in[i];
   const int nc = a.ncpml;
-  if (a.bc == 1 && (k < nc || k >= nz - 1 - nc)) {
+  if (a.bc == 2 && (k < nc || k >= nz - 1 - nc)) {  // split-field PML
+    const int ih = (int)(k < nc ? k : nz - 2 - k);
+    H[i] = pml_update(H[i], a.cpmlH[ih], a.cpmlH[nc + ih], dE);
+  } else if (a.bc == 1 && (k < nc || k >= nz - 1 - nc)) {
     const int ih = (int)(k < nc ? k : nz - 2 - k);
     const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 2 - k));
     const T db = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
@@ -59,6 +62,14 @@ __global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int
   const T dH = a.H_in[i] - a.H_in[i - 1];
   T curl = dH;
   const int nc = a.ncpml;
+  if (a.bc == 2 && (k < nc || k > nz - 1 - nc)) {  // split-field PML: vacuum, no current, no source
+    const int d = (int)(k < nc ? k : nz - 1 - k);
+    const T enew = pml_update(E[i], a.cpmlE[d], a.cpmlE[nc + 1 + d], dH);
+    if (k == 1) E[i - 1] = T(0);
+    if (k == nz - 2) E[i + 1] = T(0);
+    E[i] = enew;
+    return;
+  }
   if (a.bc == 1 && (k < nc || k > nz - 1 - nc)) {
     const int d = (int)(k < nc ? k : nz - 1 - k);
     const int64_t pi = (int64_t)s * 2 * nc + (k < nc ? k : nc + (nz - 1 - k));

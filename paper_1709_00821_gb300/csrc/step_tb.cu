@@ -76,14 +76,14 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
       if (intE) mE |= 1u << i;
       pE[i] = T(0);
       pH[i] = T(0);
-      if (a.bc == 1) {
+      if (a.bc >= 1) {  // CPML memories, or the split-field PML's nodes (no memory)
         if (intE && (g < nc || g > nz - 1 - nc)) {
           mcE |= 1u << i;
-          pE[i] = a.psiE_in[pbase + (g < nc ? g : nc + (nz - 1 - g))];
+          if (a.bc == 1) pE[i] = a.psiE_in[pbase + (g < nc ? g : nc + (nz - 1 - g))];
         }
         if (hasH && (g < nc || g >= nz - 1 - nc)) {
           mcH |= 1u << i;
-          pH[i] = a.psiH_in[pbase + (g < nc ? g : nc + (nz - 2 - g))];
+          if (a.bc == 1) pH[i] = a.psiH_in[pbase + (g < nc ? g : nc + (nz - 2 - g))];
         }
       }
       if (g == 0) i0 = i;
@@ -115,9 +115,13 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
         if (mcH & (1u << i)) {
           const int64_t g = g0 + i;
           const int ih = (int)(g < nc ? g : nz - 2 - g);
-          const T db = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
-          pH[i] = fma(db, pH[i], fma(c, dE, pH[i]));
-          h[i] = fma(-S, fma(dE, ki, pH[i]), h[i]);
+          if (a.bc == 2) {
+            h[i] = pml_update(h[i], a.cpmlH[ih], a.cpmlH[nc + ih], dE);
+          } else {
+            const T db = a.cpmlH[ih], c = a.cpmlH[nc + ih], ki = a.cpmlH[2 * nc + ih];
+            pH[i] = fma(db, pH[i], fma(c, dE, pH[i]));
+            h[i] = fma(-S, fma(dE, ki, pH[i]), h[i]);
+          }
         } else {
           h[i] = fma(-S, dE, h[i]);
         }
@@ -148,9 +152,14 @@ __global__ void __launch_bounds__(128, EDGE ? 1 : RKETD_TB_MINB) k_tb(const Step
         if (mcE & (1u << i)) {
           const int64_t g = g0 + i;
           const int d = (int)(g < nc ? g : nz - 1 - g);
-          const T db = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
-          pE[i] = fma(db, pE[i], fma(c, dH, pE[i]));
-          curl = fma(dH, ki, pE[i]);
+          if (a.bc == 2) {  // split-field PML: vacuum, no current
+            e[i] = pml_update(e[i], a.cpmlE[d], a.cpmlE[nc + 1 + d], dH);
+            upd = false;
+          } else {
+            const T db = a.cpmlE[d], c = a.cpmlE[nc + 1 + d], ki = a.cpmlE[2 * (nc + 1) + d];
+            pE[i] = fma(db, pE[i], fma(c, dH, pE[i]));
+            curl = fma(dH, ki, pE[i]);
+          }
         }
       }
       if (upd) {

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librketd.so")
 
 RKETD_F32, RKETD_F64 = 0, 1
-RKETD_BC_MUR1, RKETD_BC_CPML = 0, 1
+RKETD_BC_MUR1, RKETD_BC_CPML, RKETD_BC_PML = 0, 1, 2
 RKETD_SCHEME_RKETD, RKETD_SCHEME_ETD1, RKETD_SCHEME_ETD2 = 0, 1, 2  # Eq. 11, Eq. 9, Eq. 10
 STATUS = {0: "OK", 1: "EINVAL", 2: "ECOURANT", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "EUNSUPPORTED",
           7: "ENUMERIC", 8: "EIO"}
@@ -176,8 +176,8 @@ class Context:
         g = Grid1D()
         g.dz, g.dt = s0.dz, s0.dt
         g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
-        g.bc = RKETD_BC_CPML if s0.bc == "cpml" else RKETD_BC_MUR1
-        g.cpml_cells = s0.cpml_cells if s0.bc == "cpml" else 0
+        g.bc = {"mur": RKETD_BC_MUR1, "cpml": RKETD_BC_CPML, "pml": RKETD_BC_PML}[s0.bc]
+        g.cpml_cells = s0.cpml_cells if s0.bc in ("cpml", "pml") else 0
         g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = CPML_GRADING
         g.scheme = getattr(s0, "scheme", RKETD_SCHEME_RKETD)
         self.prec = prec

@@ -36,7 +36,7 @@ def _create(slab, prec="f64", **over):
     g = rk.Grid1D()
     g.dz, g.dt = slab.dz, slab.dt
     g.prec = 1 if prec == "f64" else 0
-    g.bc = 1 if slab.bc == "cpml" else 0
+    g.bc = {"mur": 0, "cpml": 1, "pml": 2}[slab.bc]
     g.cpml_cells = slab.cpml_cells
     g.cpml_m, g.cpml_sigma_max, g.cpml_kappa_max, g.cpml_alpha_max = rk.CPML_GRADING
     if "grid_prec" in over:
@@ -45,6 +45,8 @@ def _create(slab, prec="f64", **over):
         g.dt = over["dt"]
     if "scheme" in over:
         g.scheme = over["scheme"]
+    if "bc" in over:
+        g.bc = over["bc"]
     opt = None
     if "variant" in over:
         opt = rk.Options()
@@ -71,7 +73,7 @@ def test_courant_above_one_is_rejected():
 
 
 @pytest.mark.parametrize("case", ["src0", "src_last", "probe_out", "nu_neg", "wp2_nan", "nz_small", "cpml_thick",
-                                  "probe_in_cpml", "bad_prec"])
+                                  "probe_in_cpml", "bad_prec", "plasma_in_pml", "bad_bc"])
 def test_invalid_inputs_are_rejected_before_any_device_work(case):
     s = wl.c1_plain_slab(nz=64, steps=1)
     s.src_cell, s.probes = 8, [10, 50]
@@ -96,6 +98,11 @@ def test_invalid_inputs_are_rejected_before_any_device_work(case):
         s.probes = [5, 40]
     elif case == "bad_prec":
         over["grid_prec"] = 7
+    elif case == "plasma_in_pml":
+        s.bc, s.cpml_cells = "pml", 5
+        s.wp2[3] = 1e20
+    elif case == "bad_bc":
+        over["bc"] = 3
     st, msg, h = _create(s, **over)
     assert st == 1, (st, msg)
     assert msg and not h.value
