@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D sphere measurement")
     ap.add_argument("--no-c1", action="store_true", help="skip the paper-slab (config 1) measurement")
     ap.add_argument("--c1-reps", type=int, default=9)
+    ap.add_argument("--profile", choices=PROFILE_CASES, default=None,
+                    help="run one short workload for an ncu capture and exit (no timing)")
+    ap.add_argument("--profile-steps", type=int, default=96)
     ap.add_argument("--only-3d", action="store_true", help="run only the 3D sphere measurement (profiling)")
     ap.add_argument("--n3d", type=int, default=512)
     ap.add_argument("--steps3d", type=int, default=4000)
@@ -736,8 +739,71 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c1-resident-f64",
+                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c5-sphere")
+
+
+def run_profile_case(args):
+    """One short run of a workload for an ncu capture (no timing, no JSON): the commands under
+    profiles/ run these. c2-*: the long slab (--nz cells), --profile-steps steps after one
+    warm-up pass; c1-*: the paper's slab, one whole run; c3-batch: the ragged batch with its tuned
+    tile shape (K = 12, 32 steps per pass), 64 + 128 steps; c4-adjoint: 8 profiles of the adjoint
+    workload, 4096 steps, checkpoint every 512, forward and adjoint; c5-sphere: the sphere on an
+    --n3d grid for --steps3d steps."""
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+    from paper_1709_00821_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    case = args.profile
+    if case.startswith("c2-"):
+        _, variant, prec = case.split("-")
+        slab = wl.c2_epstein(nz=args.nz, steps=args.run_steps)
+        opts = {"variant": 2 if variant == "tiled" else 1, "use_graphs": 2}
+        with rk.Context(slab, prec, options=opts) as ctx:
+            warm = ctx.options()["tb_steps"] if variant == "tiled" else 1
+            ctx.step(warm)
+            ctx.step(args.profile_steps)
+            ctx.sync()
+    elif case.startswith("c1-"):
+        prec = case.split("-")[2]
+        s = wl.c1_plain_slab()
+        with rk.Context(s, prec) as ctx:
+            ctx.step(s.steps)
+            ctx.spectra()
+    elif case == "c3-batch":
+        b = wl.c3_batch()
+        with rk.Context(b.slabs, "f32", options={"cells_per_lane": 12, "tb_steps": 32, "warps_per_block": 2,
+                                                 "use_graphs": 2}) as ctx:
+            ctx.step(64)
+            ctx.step(128)
+            ctx.sync()
+    elif case == "c4-adjoint":
+        profs = [wl.c4_profile(i, steps=4096) for i in range(8)]
+        with rk.Context(profs, "f32") as ctx:
+            ctx.forward_ckpt(4096, 512)
+            X = ctx.spectra()
+            gX = np.zeros_like(X)
+            gX[:, 0] = np.conj(X[:, 0]) / np.abs(X[:, 0]).max()
+            n = sum(p.nz for p in profs)
+            gw = torch.empty(n, dtype=torch.float64, device="cuda")
+            gn = torch.empty(n, dtype=torch.float64, device="cuda")
+            ctx.adjoint(np.ascontiguousarray(gX.real), np.ascontiguousarray(gX.imag), 2048, 6144, gw, gn)
+            ctx.sync()
+    elif case == "c5-sphere":
+        p = wl.sphere_problem(n=args.n3d, steps=args.steps3d)
+        with rk.Context3D(p, "f32") as ctx:
+            ctx.step(args.steps3d)
+            ctx.sync()
+    print(f"profile case {case} done", flush=True)
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile_case(args)
+        return
     if args.only_3d:
         import torch
 

@@ -15,26 +15,36 @@ namespace {
 // Below x = 0.5 all are Taylor polynomials of degree 20 (coefficients (-1)^k/(k+1)!,
 // (-1)^k/(k+2)! and, for (phi1 - 2 phi2)/x, (-1)^(k+1) (k+1)/(k+3)!) evaluated by Horner's rule;
 // the first omitted term is below 1e-27. From x = 0.5 up, expm1 keeps 1 - e^{-x} exact to rounding.
+// Taylor coefficients of the three series (c1: phi1, c2: phi2, c3: (phi1 - 2 phi2)/x), each from the
+// previous by one division in FP64, evaluated at compile time (the same operations as at run time,
+// without ~60 FP64 divisions per cell on a part with few FP64 units).
+struct PhiSeries {
+  double c1[21], c2[21], c3[21];
+};
+__host__ __device__ constexpr PhiSeries phi_series() {
+  PhiSeries t{};
+  t.c1[0] = 1.0;
+  t.c2[0] = 0.5;
+  t.c3[0] = -1.0 / 6.0;  // k = 1 term of the sum for phi1 - 2 phi2, divided by x
+  for (int k = 1; k <= 20; ++k) {
+    t.c1[k] = -t.c1[k - 1] / (double)(k + 1);
+    t.c2[k] = -t.c2[k - 1] / (double)(k + 2);
+    t.c3[k] = -t.c3[k - 1] * (double)(k + 1) / ((double)k * (double)(k + 3));
+  }
+  return t;
+}
+
 __device__ void phi12(double x, double& p1, double& p2, double& psi) {
   if (x < 0.5) {
     // psi = phi1 - (1 + a) phi2 = (phi1 - 2 phi2) + x phi1 phi2 (1 + a = 2 - x phi1), where
     // phi1 - 2 phi2 = x sum_{k>=1} (-1)^k k/(k+2)! x^{k-1}: no cancellation as x -> 0 (psi ~ x/3)
-    double c1[21], c2[21], c3[21];
-    c1[0] = 1.0;
-    c2[0] = 0.5;
-    c3[0] = -1.0 / 6.0;  // k = 1 term of the sum for phi1 - 2 phi2, divided by x
-#pragma unroll
-    for (int k = 1; k <= 20; ++k) {
-      c1[k] = -c1[k - 1] / (double)(k + 1);
-      c2[k] = -c2[k - 1] / (double)(k + 2);
-      c3[k] = -c3[k - 1] * (double)(k + 1) / ((double)k * (double)(k + 3));
-    }
-    double r1 = c1[20], r2 = c2[20], r3 = c3[20];
+    constexpr PhiSeries t = phi_series();
+    double r1 = t.c1[20], r2 = t.c2[20], r3 = t.c3[20];
 #pragma unroll
     for (int k = 19; k >= 0; --k) {
-      r1 = fma(r1, x, c1[k]);
-      r2 = fma(r2, x, c2[k]);
-      r3 = fma(r3, x, c3[k]);
+      r1 = fma(r1, x, t.c1[k]);
+      r2 = fma(r2, x, t.c2[k]);
+      r3 = fma(r3, x, t.c3[k]);
     }
     p1 = r1;
     p2 = r2;
