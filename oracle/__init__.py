@@ -17,7 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["rketd_oracle.c", "rketd_oracle3d.c"]
+_SOURCES = ["rketd_oracle.c", "rketd_oracle3d.c", "rketd_oracle2d.c"]
 _LOCK = threading.Lock()
 _LIBS = {}
 
@@ -69,6 +69,13 @@ class OrGrid3D(ctypes.Structure):
                 ("inc_off", ctypes.c_int32), ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32)]
 
 
+class OrGrid2D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("d", ctypes.c_double), ("dt", ctypes.c_double),
+                ("pol", ctypes.c_int32), ("periodic_x", ctypes.c_int32), ("src_j", ctypes.c_int32),
+                ("src_tau", ctypes.c_double), ("src_t0", ctypes.c_double), ("src_amp", ctypes.c_double),
+                ("n_probes", ctypes.c_int32), ("n_freq", ctypes.c_int32)]
+
+
 def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
     key = (omp, mutant)
     with _LOCK:
@@ -96,6 +103,10 @@ def lib(omp: bool = False, mutant: int = 0) -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_int32), dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
                                    dp, dp, dp]
             L.or_run3d.restype = ctypes.c_int
+            L.or_run2d.argtypes = [ctypes.POINTER(OrGrid2D), ctypes.POINTER(ctypes.c_uint8), dp, dp, ctypes.c_int32,
+                                   dp, ctypes.POINTER(ctypes.c_int32), dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp,
+                                   dp]
+            L.or_run2d.restype = ctypes.c_int
             _LIBS[key] = L
         return _LIBS[key]
 
@@ -298,6 +309,52 @@ def run3d(prob, steps=None, state=None, series=False, mutant: int = 0):
                     pr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(fr), st.n, steps, _dp(st.fields),
                     _dp(st.psi), _dp(st.inc), _dp(xr), _dp(xi),
                     _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)())
+    if rc:
+        raise ValueError(f"oracle rejected the problem (code {rc})")
+    st.X = xr + 1j * xi
+    st.n += steps
+    return st, ser
+
+
+FIELDS_2D = {"tm": ("Ez", "Hx", "Hy", "Jz"), "te": ("Ex", "Ey", "Hz", "Jx", "Jy")}
+
+
+class State2D:
+    """2D oracle state: fields [6][ny*nx] (TMz: Ez, Hx, Hy, Jz; TEz: Ex, Ey, Hz, Jx, Jy), DFT sums, step."""
+
+    def __init__(self, prob):
+        self.fields = np.zeros((6, prob.nx * prob.ny))
+        self.X = np.zeros((len(prob.probes), len(prob.freq_hz)), dtype=np.complex128)
+        self.n = 0
+
+    def field(self, name, prob):
+        return self.fields[FIELDS_2D[prob.pol].index(name)].reshape(prob.ny, prob.nx)
+
+
+def run2d(prob, steps=None, state=None, series=False, mutant: int = 0):
+    """Runs the 2D oracle on a workloads.Grid2D problem."""
+    L = lib(mutant=mutant)
+    steps = prob.steps if steps is None else steps
+    st = State2D(prob) if state is None else state
+    g = OrGrid2D()
+    g.nx, g.ny, g.d, g.dt = prob.nx, prob.ny, prob.d, prob.dt
+    g.pol = 0 if prob.pol == "tm" else 1
+    g.periodic_x = 1 if prob.periodic_x else 0
+    g.src_j = prob.src_j
+    g.src_tau, g.src_t0, g.src_amp = prob.src_tau, prob.src_t0, prob.src_amp
+    g.n_probes, g.n_freq = len(prob.probes), len(prob.freq_hz)
+    mat = np.ascontiguousarray(prob.mat, dtype=np.uint8)
+    mw = np.ascontiguousarray(prob.mat_wp2, float)
+    mn = np.ascontiguousarray(prob.mat_nu, float)
+    prof = np.ascontiguousarray(prob.profile, float)
+    pr = np.ascontiguousarray(np.asarray(prob.probes, np.int32).ravel() if len(prob.probes) else np.zeros(2, np.int32))
+    fr = np.ascontiguousarray(prob.freq_hz, float)
+    xr = np.ascontiguousarray(st.X.real.copy())
+    xi = np.ascontiguousarray(st.X.imag.copy())
+    ser = np.zeros((len(prob.probes), steps)) if series else None
+    rc = L.or_run2d(ctypes.byref(g), mat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(mw), _dp(mn), len(mw),
+                    _dp(prof), pr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(fr), st.n, steps,
+                    _dp(st.fields), _dp(xr), _dp(xi), _dp(ser) if ser is not None else ctypes.POINTER(ctypes.c_double)())
     if rc:
         raise ValueError(f"oracle rejected the problem (code {rc})")
     st.X = xr + 1j * xi

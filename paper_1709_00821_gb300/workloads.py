@@ -333,3 +333,54 @@ def sphere_problem(n: int = 512, steps: int = 4000, radius: Optional[float] = No
     lo, hi = sp.tfsf_lo, sp.tfsf_hi
     return Grid3D(n, n, n, sp.d, sp.dt, mat, np.array([0.0, sp.wp2]), np.array([0.0, sp.nu]), False, npml, True,
                   (lo, hi, lo, hi, lo, hi), -1, sp.src_tau, sp.src_t0, sp.probes, sp.freq_hz, steps)
+
+
+@dataclass
+class Grid2D:
+    """A 2D problem (fields uniform along z) on an nx x ny Yee grid of cell size d.
+
+    pol "tm": Ez (i, j), Hx (i, j+1/2), Hy (i+1/2, j); pol "te": Hz (i+1/2, j+1/2), Ex (i+1/2, j),
+    Ey (i, j+1/2). Every E component of cell (i, j) takes material mat[j][i] (0 = vacuum). x is
+    periodic or bounded by first-order Mur; y by first-order Mur. A soft line source on row src_j
+    adds profile[i] s(t) to Ez (tm) or Ex (te); probes (i, j) sample that component."""
+
+    nx: int
+    ny: int
+    d: float
+    dt: float
+    pol: str
+    periodic_x: bool
+    mat: np.ndarray  # uint8 [ny*nx]
+    mat_wp2: np.ndarray
+    mat_nu: np.ndarray
+    src_j: int
+    profile: np.ndarray  # [nx]
+    src_tau: float
+    src_t0: float
+    probes: List[tuple]
+    freq_hz: np.ndarray
+    steps: int
+    src_amp: float = 1.0
+
+    def vacuum(self) -> "Grid2D":
+        return Grid2D(self.nx, self.ny, self.d, self.dt, self.pol, self.periodic_x, np.zeros_like(self.mat),
+                      self.mat_wp2, self.mat_nu, self.src_j, self.profile, self.src_tau, self.src_t0,
+                      list(self.probes), self.freq_hz, self.steps, self.src_amp)
+
+
+def slab_2d(nx: int, ny: int, pol: str, mode: int = 0, d: float = 300e-6, layer=None, wp: float = 2 * math.pi * 28.7e9,
+            nu: float = 2e10, steps: int = 8000, periodic_x: bool = True, nfreq: int = 200) -> Grid2D:
+    """A plasma layer across a 2D grid (rows layer[0] .. layer[1]-1, default the middle 30 rows), Courant
+    0.5 (c dt/d; the 2D limit is 1/sqrt(2)), a line source on row ny/8 with profile cos(2 pi mode i/nx)
+    (mode 0: normal incidence; mode m > 0 on a periodic grid: a single transverse Fourier mode, which
+    meets the layer at the angle where sin(theta) = m c/(nx d f)), probes on rows ny/4 (reflection) and
+    3ny/4 (transmission) in column 0, tau = 15 dt, nfreq frequencies to 100 GHz."""
+    dt = dt_for_courant(d, 0.5)
+    lo, hi = layer if layer is not None else (ny // 2 - 15, ny // 2 + 15)
+    mat = np.zeros((ny, nx), np.uint8)
+    mat[lo:hi] = 1
+    prof = np.cos(2 * math.pi * mode * np.arange(nx) / nx)
+    freqs = 100e9 * np.arange(1, nfreq + 1, dtype=np.float64) / nfreq
+    tau = 15 * dt
+    return Grid2D(nx, ny, d, dt, pol, periodic_x, mat.ravel(), np.array([0.0, wp * wp]), np.array([0.0, nu]),
+                  ny // 8, prof, tau, 5 * tau, [(0, ny // 4), (0, 3 * ny // 4)], freqs, steps)

@@ -326,3 +326,52 @@ def domain_response_pml(wp2, nu, dz, dt, freqs, src_cell, cells, n, m, sigma_max
         sol = solve_banded((1, 1), ab, rhs)
         out[i] = sol[list(cells)]
     return out
+
+
+def domain_response_2d_mode(wp2_rows, nu_rows, d, dt, freqs, src_row, rows, mu_x, pol, scheme: int = 0):
+    """Steady-state phasors at `rows` of one transverse Fourier mode of the 2D lattice (periodic in x,
+    layered in y, first-order Mur rows at j = 0 and ny-1), driven by the line source on src_row.
+
+    mu_x = 4 sin^2(kx d/2) is the mode's x second-difference eigenvalue. With E^n = E z^n and the
+    layer's lattice permittivity eps_j (row j's material):
+      TMz (Ez): E_{j+1} - 2 E_j + E_{j-1} = -(q_j - mu_x) E_j, q_j = (2 sin(theta/2)/S)^2 eps_j;
+      TEz (Ex at rows j, Ey at rows j + 1/2 with row j's material, Hz at rows j + 1/2): eliminating Ey
+      and Hz from the three updates gives
+        g_j (X_{j+1} - X_j) - g_{j-1} (X_j - X_{j-1}) = (z - 1) eps_j X_j / S^2,
+        g_j = z / ((z - 1) + S^2 mu_x z / ((z - 1) eps_j)),
+      which is the TMz row for mu_x = 0.
+    The source adds to the row of src_row; Mur rows as the 1D lattice."""
+    wp2_rows = np.asarray(wp2_rows, float)
+    nu_rows = np.asarray(nu_rows, float)
+    ny = len(wp2_rows)
+    S = courant(d, dt)
+    qm = (S - 1) / (S + 1)
+    theta = 2 * np.pi * np.asarray(freqs) * dt
+    cache = _material_cache(wp2_rows, nu_rows, dt)
+    keys = list(zip(wp2_rows.tolist(), nu_rows.tolist()))
+    epsd = {k: lattice_eps(theta, *v, scheme=scheme) for k, v in cache.items()}
+    out = np.empty((len(theta), len(rows)), dtype=np.complex128)
+    for i, th in enumerate(theta):
+        z = np.exp(1j * th)
+        eps = np.array([epsd[k][i] for k in keys])
+        ab = np.zeros((3, ny), dtype=np.complex128)
+        if pol == "tm":
+            q = (2 * np.sin(th / 2) / S) ** 2 * eps - mu_x
+            ab[0, 2:] = 1.0
+            ab[1, 1:-1] = q[1:-1] - 2.0
+            ab[2, :-2] = 1.0
+            rhs_val = 1.0
+        else:
+            g = z / ((z - 1) + S * S * mu_x * z / ((z - 1) * eps[:-1]))  # j = 0 .. ny-2
+            ab[0, 2:] = g[1:]
+            ab[1, 1:-1] = -g[1:] - g[:-1] - (z - 1) * eps[1:-1] / (S * S)
+            ab[2, :-2] = g[:-1]
+            rhs_val = -z / (S * S)
+        ab[1, 0] = z + qm
+        ab[0, 1] = -(1 + qm * z)
+        ab[1, ny - 1] = z + qm
+        ab[2, ny - 2] = -(1 + qm * z)
+        rhs = np.zeros(ny, dtype=np.complex128)
+        rhs[src_row] = rhs_val
+        out[i] = solve_banded((1, 1), ab, rhs)[list(rows)]
+    return out
