@@ -11,8 +11,9 @@
  * Boundaries: first-order Mur on the E components tangential to the y faces (rows j = 0 and
  * j = ny-1); in x either periodic, or first-order Mur on the E components tangential to the x faces
  * (columns i = 0 and i = nx-1; TMz Ez, TEz Ey). Source: a soft line source on row src_j adding
- * profile[i] s(t) to Ez (TMz) or Ex (TEz) after the E update, s the Eq. 15 pulse. Probes sample Ez
- * (TMz) or Ex (TEz); running DFT as the 1D oracle.
+ * profile[i] s(t) to Ez (TMz) or Ex (TEz) after the E update, s the Eq. 15 pulse, on the nodes that
+ * exist (with Mur x ends TEz has no Ex at i = nx-1, position nx-1/2, so that node stays 0). Probes
+ * sample Ez (TMz) or Ex (TEz); running DFT as the 1D oracle.
  * One step: H (Eq. 14 in curl form), then E with J (Eq. 12 with Eq. 11 substituted, solved for
  * E^{n+1}, and Eq. 11), the source, the Mur ends, the probes.
  * Only tests/ and bench.py's CPU legs load this file; it shares no code with the CUDA path.
@@ -207,7 +208,9 @@ int or_run2d(const or_grid2d* g, const uint8_t* mat, const double* mat_wp2, cons
           Jy[c] = ma[m] * Jy[c] + mb1[m] * En + mb2[m] * (Enew - En);
           Ey[c] = Enew;
         }
-      for (int i = 0; i < nx; ++i) Ex[I2(i, g->src_j)] = Ex[I2(i, g->src_j)] + profile[i] * o2_pulse(g, t);
+      /* the source drives only Ex nodes that exist: with Mur x ends, Ex (nx-1/2, j) is outside */
+      for (int i = 0; i < (per ? nx : nx - 1); ++i)
+        Ex[I2(i, g->src_j)] = Ex[I2(i, g->src_j)] + profile[i] * o2_pulse(g, t);
       if (!per)
         for (int j = 0; j < ny - 1; ++j) {
           Ey[I2(0, j)] = ox[ny + j] + q * (Ey[I2(1, j)] - ox[j]);
