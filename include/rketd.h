@@ -384,6 +384,71 @@ int64_t rketd_launch_count_3d(const rketd_ctx3d* ctx);
 /* Releases the 3D context and its device memory. NULL is accepted. */
 rketd_status rketd_destroy_3d(rketd_ctx3d* ctx);
 
+/* ---------------------------------------------------------------------------------------
+ * 2D RKETD-FDTD (fields uniform along z): the paper's stated generalisation (Sec. IV.B closing
+ * remarks, Sec. V) of the 1D scheme, Eqs. 14, 12, 11 and 13 applied to the 2D curl, in two
+ * polarisations on an nx x ny Yee grid of cell size d; arrays are [j][i] (x fastest).
+ *   RKETD_TMZ: Ez (i, j), Hx (i, j+1/2), Hy (i+1/2, j), current Jz;
+ *   RKETD_TEZ: Hz (i+1/2, j+1/2), Ex (i+1/2, j), Ey (i, j+1/2), currents Jx, Jy.
+ * Every E component of cell (i, j) takes the Drude material mat[j][i] (0..n_mat-1, 0 = vacuum).
+ * Boundaries: first-order Mur on the E components tangential to the y faces (rows 0 and ny-1);
+ * periodic x, or first-order Mur on those tangential to the x faces (columns 0 and nx-1). Source:
+ * a soft line source on row src_j adding profile[i] s(t) to Ez (TMz) or Ex (TEz) after the E
+ * update (s the Eq. 15 pulse), on the nodes the update advances (with Mur x ends TEz has no Ex at
+ * column nx-1, position nx-1/2: it stays 0, and a probe there reads 0); with periodic x and profile[i] = cos(2 pi m i / nx) it launches one
+ * transverse Fourier mode, which meets a y-layered medium at oblique incidence. Probes sample Ez
+ * (TMz) or Ex (TEz); running DFT as rketd_dft. The step is the paper's two-kernel structure (an H
+ * kernel, then an E+J kernel with the source and the ends), fields in place.
+ * ------------------------------------------------------------------------------------- */
+typedef enum { RKETD_TMZ = 0, RKETD_TEZ = 1 } rketd_pol2d;
+
+typedef struct {
+  int32_t nx, ny;        /* cells per axis, >= 4 */
+  int32_t prec;          /* rketd_prec */
+  int32_t pol;           /* rketd_pol2d */
+  double d, dt;          /* cell size (m), time step (s); c0 dt / d <= 1/sqrt(2) */
+  int32_t periodic_x;    /* 1: periodic in x; 0: first-order Mur at the x faces */
+  int32_t src_j;         /* source row, 1 <= src_j <= ny-2 */
+} rketd_grid2d;
+
+typedef struct rketd_ctx2d rketd_ctx2d;
+
+/*
+ * Creates a 2D context and zeroes its state.
+ *   mat           host [ny][nx] material indices (copied); n_mat 1..16 materials, mat_wp2/mat_nu
+ *                 [n_mat] (entry 0 must be vacuum), finite and >= 0
+ *   profile       host [nx] source weights per column (copied)
+ *   probes        host [n_probes][2] (i, j) cells; dft as for the 1D calls
+ *   stream        cudaStream_t for all work of this context (NULL = legacy default stream)
+ * Errors: RKETD_EINVAL, RKETD_ECOURANT, RKETD_ENOMEM, RKETD_ECUDA; *out is NULL on error.
+ */
+rketd_status rketd_create_2d(const rketd_grid2d* grid, const uint8_t* mat, int32_t n_mat, const double* mat_wp2,
+                             const double* mat_nu, const double* profile, const rketd_pulse* pulse, int32_t n_probes,
+                             const int32_t* probes, const rketd_dft* dft, void* stream, rketd_ctx2d** out);
+
+/* Zeroes the fields and the DFT sums; step index 0 (async). */
+rketd_status rketd_reset_2d(rketd_ctx2d* ctx);
+
+/* Queues nsteps steps (H, E and J with the source and the Mur ends, probe samples; the DFT is
+ * folded every 512 samples). Async. */
+rketd_status rketd_step_2d(rketd_ctx2d* ctx, int64_t nsteps);
+
+/* Waits for the context's stream and reports any device-side error. */
+rketd_status rketd_sync_2d(rketd_ctx2d* ctx);
+
+/* Copies one component to a host FP64 SI array [ny][nx]: which = 0..3 for TMz (Ez, Hx, Hy, Jz),
+ * 0..4 for TEz (Ex, Ey, Hz, Jx, Jy). Synchronises. */
+rketd_status rketd_get_field_2d(rketd_ctx2d* ctx, int32_t which, double* out);
+
+/* Copies the DFT sums to host: re/im [n_probes][n_freq] (FP64), pending samples included. Synchronises. */
+rketd_status rketd_get_spectra_2d(rketd_ctx2d* ctx, double* re, double* im);
+
+/* Number of kernel launches this context has issued. */
+int64_t rketd_launch_count_2d(const rketd_ctx2d* ctx);
+
+/* Releases the 2D context and its device memory. NULL is accepted. */
+rketd_status rketd_destroy_2d(rketd_ctx2d* ctx);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* rketd_last_error(void);
 

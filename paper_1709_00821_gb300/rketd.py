@@ -63,6 +63,12 @@ class Grid3D(ctypes.Structure):
                 ("inc_len", ctypes.c_int32), ("inc_src", ctypes.c_int32), ("variant", ctypes.c_int32)]
 
 
+class Grid2D(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("prec", ctypes.c_int32), ("pol", ctypes.c_int32),
+                ("d", ctypes.c_double), ("dt", ctypes.c_double), ("periodic_x", ctypes.c_int32),
+                ("src_j", ctypes.c_int32)]
+
+
 _LIB = None
 
 # name -> (restype, argtypes)
@@ -111,6 +117,16 @@ _SIGS = {
     "rketd_sync_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
     "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_create_2d": (ctypes.c_int, [ctypes.POINTER(Grid2D), ctypes.c_void_p, ctypes.c_int32, _dp, _dp, _dp,
+                                       ctypes.POINTER(Pulse), ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Dft),
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "rketd_reset_2d": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_step_2d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "rketd_sync_2d": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_get_field_2d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
+    "rketd_get_spectra_2d": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
+    "rketd_launch_count_2d": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_destroy_2d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
 }
@@ -446,3 +462,79 @@ class Context3D:
     @property
     def launches(self) -> int:
         return lib().rketd_launch_count_3d(self.h)
+
+
+FIELDS_2D = {"tm": ("Ez", "Hx", "Hy", "Jz"), "te": ("Ex", "Ey", "Hz", "Jx", "Jy")}
+RKETD_TMZ, RKETD_TEZ = 0, 1
+
+
+class Context2D:
+    """One rketd_ctx2d: a 2D TMz or TEz problem (workloads.Grid2D) on one CUDA stream."""
+
+    def __init__(self, prob, prec: str = "f32", stream=None):
+        L = lib()
+        self.prob = prob
+        g = Grid2D()
+        g.nx, g.ny = prob.nx, prob.ny
+        g.prec = RKETD_F64 if prec == "f64" else RKETD_F32
+        g.pol = RKETD_TMZ if prob.pol == "tm" else RKETD_TEZ
+        g.d, g.dt = prob.d, prob.dt
+        g.periodic_x = 1 if prob.periodic_x else 0
+        g.src_j = prob.src_j
+        self.prec = prec
+        self.n_probes = len(prob.probes)
+        self.freq = _arr(prob.freq_hz)
+        mat = _arr(prob.mat, np.uint8)
+        mw, mn = _arr(prob.mat_wp2), _arr(prob.mat_nu)
+        prof = _arr(prob.profile)
+        pr = _arr(np.asarray(prob.probes, np.int32).reshape(-1) if self.n_probes else np.zeros(2), np.int32)
+        p = Pulse(prob.src_tau, prob.src_t0, prob.src_amp)
+        d = Dft(self.n_probes, len(self.freq), _ptr(self.freq))
+        self.stream = _default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(L.rketd_create_2d(ctypes.byref(g), ctypes.c_void_p(mat.ctypes.data), len(mw), _ptr(mw), _ptr(mn),
+                                 _ptr(prof), ctypes.byref(p), self.n_probes, ctypes.c_void_p(pr.ctypes.data),
+                                 ctypes.byref(d), ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rketd_destroy_2d(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n: int):
+        _check(lib().rketd_step_2d(self.h, int(n)))
+
+    def reset(self):
+        _check(lib().rketd_reset_2d(self.h))
+
+    def sync(self):
+        _check(lib().rketd_sync_2d(self.h))
+
+    def field(self, name: str) -> np.ndarray:
+        """One component as a host FP64 SI array [ny, nx]."""
+        out = np.empty((self.prob.ny, self.prob.nx))
+        _check(lib().rketd_get_field_2d(self.h, FIELDS_2D[self.prob.pol].index(name), _ptr(out)))
+        return out
+
+    def spectra(self) -> np.ndarray:
+        n = self.n_probes * len(self.freq)
+        re, im = np.empty(max(n, 1)), np.empty(max(n, 1))
+        _check(lib().rketd_get_spectra_2d(self.h, _ptr(re), _ptr(im)))
+        return (re[:n] + 1j * im[:n]).reshape(self.n_probes, len(self.freq))
+
+    @property
+    def launches(self) -> int:
+        return lib().rketd_launch_count_2d(self.h)

@@ -214,3 +214,34 @@ def test_3d_invalid_inputs_are_rejected_before_any_device_work(case):
     st, msg, h = _create3d(p, **over)
     assert st == (2 if case == "courant" else 1), (st, msg)
     assert msg and not h.value
+
+
+@pytest.mark.parametrize("case", ["courant", "pol", "src_row", "mat_index", "vacuum0"])
+def test_2d_validation_before_any_device_work(case):
+    """rketd_create_2d refuses bad input before touching the GPU: runs without one."""
+    L = rk.lib()
+    nx, ny = 8, 8
+    g = rk.Grid2D()
+    g.nx, g.ny, g.prec, g.pol, g.d = nx, ny, 0, 0, 1e-4
+    g.dt = 0.5 * g.d / wl.C0
+    g.periodic_x, g.src_j = 1, 2
+    mat = np.zeros(nx * ny, np.uint8)
+    wp2 = np.array([0.0, 1e20])
+    nu = np.array([0.0, 1e10])
+    if case == "courant":
+        g.dt = 0.75 * g.d / wl.C0  # above 1/sqrt(2)
+    elif case == "pol":
+        g.pol = 2
+    elif case == "src_row":
+        g.src_j = ny - 1
+    elif case == "mat_index":
+        mat[5] = 2
+    elif case == "vacuum0":
+        wp2 = np.array([1e20, 1e20])
+    prof = np.ones(nx)
+    p = rk.Pulse(1e-12, 5e-12, 1.0)
+    h = ctypes.c_void_p()
+    st = L.rketd_create_2d(ctypes.byref(g), mat.ctypes.data, 2, wp2.ctypes.data_as(rk._dp), nu.ctypes.data_as(rk._dp),
+                           prof.ctypes.data_as(rk._dp), ctypes.byref(p), 0, None, None, None, ctypes.byref(h))
+    assert st == (2 if case == "courant" else 1), L.rketd_last_error()
+    assert not h.value
