@@ -299,6 +299,20 @@ rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64_t nz, cons
                                       int64_t src_cell, const rketd_pulse* pulse, int64_t n0, int64_t nsteps,
                                       void* E, void* H, void* J, void* stream);
 
+/* Scans the state (E, H and the carried current of every slab, E^{n-1} for Eq. 10, CPML memories)
+ * and the spectra for NaN or infinite values: RKETD_ENUMERIC if any is found, else RKETD_OK.
+ * Input validation admits only finite parameters, but a finite input can still overflow (a source
+ * amplitude near the largest double, say); this is the check for that. Synchronises. */
+rketd_status rketd_check_finite(rketd_ctx* ctx);
+
+/* Test hooks for the failure paths, process-wide, no effect unless called.
+ * rketd_debug_fail_alloc: the next `after` device allocations made by the library succeed and
+ * the one after them fails as if the device were out of memory, so the call that made it returns
+ * RKETD_ENOMEM (creation calls release what they had allocated and leave *out NULL); after < 0
+ * disarms. rketd_debug_alloc_count: device allocations the library has attempted so far. */
+rketd_status rketd_debug_fail_alloc(int64_t after);
+int64_t rketd_debug_alloc_count(void);
+
 /* Releases the context and its device memory. NULL is accepted. */
 rketd_status rketd_destroy(rketd_ctx* ctx);
 
@@ -378,6 +392,16 @@ rketd_status rketd_sync_3d(rketd_ctx3d* ctx);
  * A tuning knob: results do not depend on it. */
 rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* ctx, int32_t k_chunk);
 
+/* Test hook: the staged form's compute threads give up waiting for a staged copy after `polls`
+ * polls of its mbarrier (0: at once; < 0 restores the default of 2^20). A block whose wait gave up
+ * stops, lets the copies it issued land (those waits keep the full bound), and the next
+ * rketd_sync_3d returns RKETD_ETIMEOUT; rketd_reset_3d clears the status. No effect on the fused
+ * and plain forms. */
+rketd_status rketd_set_wait_limit_3d(rketd_ctx3d* ctx, int32_t polls);
+
+/* As rketd_check_finite, for the 3D fields (E, H, J) and spectra. Synchronises. */
+rketd_status rketd_check_finite_3d(rketd_ctx3d* ctx);
+
 /* Number of kernel launches this context has issued. */
 int64_t rketd_launch_count_3d(const rketd_ctx3d* ctx);
 
@@ -445,6 +469,9 @@ rketd_status rketd_get_spectra_2d(rketd_ctx2d* ctx, double* re, double* im);
 
 /* Number of kernel launches this context has issued. */
 int64_t rketd_launch_count_2d(const rketd_ctx2d* ctx);
+
+/* As rketd_check_finite, for the 2D fields, currents and spectra. Synchronises. */
+rketd_status rketd_check_finite_2d(rketd_ctx2d* ctx);
 
 /* Releases the 2D context and its device memory. NULL is accepted. */
 rketd_status rketd_destroy_2d(rketd_ctx2d* ctx);

@@ -258,7 +258,7 @@ struct rketd_ctx2d {
   }
   bool alloc(void** p, size_t bytes) {
     *p = nullptr;
-    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    if (device_alloc(p, bytes ? bytes : 16) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -514,7 +514,7 @@ rketd_status rketd_get_field_2d(rketd_ctx2d* c, int32_t which, double* out) {
     ecomp = which == 4 ? 1 : 0;
   }
   double* tmp = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(double) * c->N, c->stream);
+  cudaError_t e = device_alloc_async((void**)&tmp, sizeof(double) * c->N, c->stream);
   if (e != cudaSuccess) return bad2(RKETD_ENOMEM, "2D field staging");
   const unsigned blocks = (unsigned)((c->N + 255) / 256);
   const double hs = 1.0 / std::sqrt(kMu0 / kEps0), js = kEps0 / c->g.dt;
@@ -553,6 +553,26 @@ rketd_status rketd_get_spectra_2d(rketd_ctx2d* c, double* re, double* im) {
 }
 
 int64_t rketd_launch_count_2d(const rketd_ctx2d* c) { return c ? c->launches : -1; }
+
+rketd_status rketd_check_finite_2d(rketd_ctx2d* c) {
+  if (!c) return bad2(RKETD_EINVAL, "NULL context");
+  int* flag = nullptr;
+  if (device_alloc_async((void**)&flag, sizeof(int), c->stream) != cudaSuccess)
+    return bad2(RKETD_ENOMEM, "finite scan");
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  const int nf = c->g.pol == RKETD_TMZ ? 4 : 5;
+  for (int q = 0; q < nf && e == cudaSuccess; ++q) e = launch_finite_scan(c->esz == 8, c->F[q], c->N, flag, c->stream);
+  const int64_t nx = (int64_t)c->n_probes * c->n_freq;
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xr, nx, flag, c->stream);
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xi, nx, flag, c->stream);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(flag, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bad2(RKETD_ECUDA, std::string("finite scan: ") + cudaGetErrorString(e));
+  if (h) return bad2(RKETD_ENUMERIC, "a field or spectrum holds NaN or Inf");
+  return RKETD_OK;
+}
 
 rketd_status rketd_destroy_2d(rketd_ctx2d* c) {
   delete c;

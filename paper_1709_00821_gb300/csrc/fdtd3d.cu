@@ -78,6 +78,7 @@ struct Args3 {
   int n_probes;
   T* series;
   int series_len, series_pos;
+  int wait_limit;  // polls of the staged form's compute-path copy waits (a test hook may lower it)
 };
 
 __device__ __forceinline__ int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -583,10 +584,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// bounded wait for the phase with the given parity; false if it did not complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// bounded wait for the phase with the given parity, at most `limit` polls; false if it did not
+// complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = kWaitLimit) {
   const uint32_t addr = smem_u32(bar);
-  for (int it = 0; it < kWaitLimit; ++it) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -1037,8 +1039,8 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
         }
       }
     }
-    if (q == 0) fail |= !mbar_wait(&bar[0], 0);
-    fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1);
+    if (q == 0) fail |= !mbar_wait(&bar[0], 0, a.wait_limit);
+    fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1, a.wait_limit);
     const T* P0 = plane(q);
     const T* P1 = plane(q + 1);
     const PlaneS<T>& pf = *facts(q);
@@ -1129,9 +1131,10 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
   }
   if (bad && producer) {
     // report, and let the copies still in flight land before the block's memory is released
+    // (these drain waits keep the full limit whatever the compute-path limit is)
     atomicExch(err, 1);
     for (int q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
-      mbar_wait(&bar[q % kStages], (q / kStages) & 1);
+      mbar_wait(&bar[q % kStages], (q / kStages) & 1, kWaitLimit);
   }
 }
 
@@ -1232,6 +1235,7 @@ struct rketd_ctx3d {
   rketd_pulse pulse{};
   int64_t step = 0;
   int64_t launches = 0;
+  int wait_limit = kWaitLimit;
   ~rketd_ctx3d() {
     for (void* p : allocs) cudaFree(p);
     if (fork) cudaEventDestroy(fork);
@@ -1241,7 +1245,7 @@ struct rketd_ctx3d {
   bool alloc(void** p, size_t bytes, bool state = false) {
     *p = nullptr;
     if (!bytes) bytes = 16;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (device_alloc(p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -1273,6 +1277,7 @@ rketd_status fail3(rketd_status st, const std::string& m) {
 template <typename T>
 Args3<T> args3(rketd_ctx3d* c) {
   Args3<T> a{};
+  a.wait_limit = c->wait_limit;
   const int in = c->cur, out = c->fused ? 1 - c->cur : c->cur;
   a.Ex = (const T*)c->E[in][0];
   a.Ey = (const T*)c->E[in][1];
@@ -1789,7 +1794,7 @@ rketd_status rketd_get_field_3d(rketd_ctx3d* c, int32_t which, double* out) {
   if (!c || !out || which < 0 || which > 8) return fail3(RKETD_EINVAL, "invalid arguments");
   const void* src = which < 3 ? c->E[c->cur][which] : (which < 6 ? c->H[c->cur][which - 3] : c->J[which - 6]);
   double* tmp;
-  CK3(cudaMallocAsync((void**)&tmp, sizeof(double) * c->N, c->stream), "field staging");
+  CK3(device_alloc_async((void**)&tmp, sizeof(double) * c->N, c->stream), "field staging");
   const double eta0 = std::sqrt(kMu0 / kEps0);
   const double scale = which < 3 ? 1.0 : (which < 6 ? 1.0 / eta0 : kEps0 / c->g.dt);
   const int shift = which >= 6 ? 2 * (which - 6) : 0;
@@ -1821,6 +1826,35 @@ rketd_status rketd_get_spectra_3d(rketd_ctx3d* c, double* re, double* im) {
   CK3(cudaMemcpyAsync(re, c->Xtmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
   CK3(cudaMemcpyAsync(im, c->Xtmp + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
   return check3(c);
+}
+
+rketd_status rketd_set_wait_limit_3d(rketd_ctx3d* c, int32_t polls) {
+  if (!c) return fail3(RKETD_EINVAL, "NULL context");
+  c->wait_limit = polls < 0 ? kWaitLimit : std::min<int32_t>(polls, kWaitLimit);
+  return RKETD_OK;
+}
+
+rketd_status rketd_check_finite_3d(rketd_ctx3d* c) {
+  if (!c) return fail3(RKETD_EINVAL, "NULL context");
+  int* flag = nullptr;
+  CK3(device_alloc_async((void**)&flag, sizeof(int), c->stream), "finite scan");
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  const bool f64 = c->prec == RKETD_F64;
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+    e = launch_finite_scan(f64, c->E[c->cur][q], c->N, flag, c->stream);
+    if (e == cudaSuccess) e = launch_finite_scan(f64, c->H[c->cur][q], c->N, flag, c->stream);
+    if (e == cudaSuccess) e = launch_finite_scan(f64, c->J[q], c->N, flag, c->stream);
+  }
+  const int64_t nx = (int64_t)c->n_probes * c->n_freq;
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xr, nx, flag, c->stream);
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xi, nx, flag, c->stream);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(flag, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fail3(RKETD_ECUDA, std::string("finite scan: ") + cudaGetErrorString(e));
+  if (h) return fail3(RKETD_ENUMERIC, "a field or spectrum holds NaN or Inf");
+  return RKETD_OK;
 }
 
 rketd_status rketd_sync_3d(rketd_ctx3d* c) {

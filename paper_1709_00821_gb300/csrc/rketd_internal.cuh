@@ -159,6 +159,15 @@ struct AdjArgs {
 // Sets the message rketd_last_error() returns on this thread (defined with the runtime).
 void set_error_message(const char* msg);
 
+// Every device allocation of the contexts goes through these: cudaMalloc / cudaMallocAsync,
+// unless a test armed an injected failure (rketd_debug_fail_alloc), which is then reported as
+// cudaErrorMemoryAllocation without touching the device.
+cudaError_t device_alloc(void** p, size_t bytes);
+cudaError_t device_alloc_async(void** p, size_t bytes, cudaStream_t st);
+
+// ORs 1 into *flag if any of n values (FP64 if f64, else FP32) is NaN or infinite. Async.
+cudaError_t launch_finite_scan(bool f64, const void* p, int64_t n, int* flag, cudaStream_t st);
+
 // ---- launchers (defined in the .cu files) ----
 // scheme: 0 = Eq. 11, 1 = Eq. 9, 2 = Eq. 10 (then ext[0], ext[1] receive ep and gp, the weights of
 // E^{n-1} in the E and G updates; see coeffs.cu)

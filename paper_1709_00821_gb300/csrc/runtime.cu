@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -22,6 +23,31 @@ using namespace rketd;
 namespace {
 
 thread_local std::string g_err;
+
+// injected allocation failure (a test hook): -1 disarmed, else the successful allocations left
+std::mutex g_alloc_mu;
+int64_t g_alloc_fail_after = -1;
+int64_t g_alloc_count = 0;
+
+bool alloc_should_fail() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  ++g_alloc_count;
+  if (g_alloc_fail_after < 0) return false;
+  if (g_alloc_fail_after == 0) {
+    g_alloc_fail_after = -1;
+    return true;
+  }
+  --g_alloc_fail_after;
+  return false;
+}
+
+template <typename T>
+__global__ void k_finite(const T* __restrict__ p, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
 
 rketd_status fail(rketd_status st, const char* fmt, ...) {
   char buf[512];
@@ -49,6 +75,28 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 }  // namespace
 
 void rketd::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
+cudaError_t rketd::device_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t rketd::device_alloc_async(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (alloc_should_fail()) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, st);
+}
+
+cudaError_t rketd::launch_finite_scan(bool f64, const void* p, int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  if (f64)
+    k_finite<double><<<blocks, 256, 0, st>>>((const double*)p, n, flag);
+  else
+    k_finite<float><<<blocks, 256, 0, st>>>((const float*)p, n, flag);
+  return cudaGetLastError();
+}
 
 struct rketd_ctx {
   int32_t n_slabs = 0;
@@ -172,7 +220,7 @@ struct rketd_ctx {
   rketd_status alloc(void** p, size_t bytes, const char* what) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = device_alloc(p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return cuda_fail(e, what);
@@ -344,8 +392,8 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   if (c->tprobes_d) cudaFree(c->tprobes_d);
   c->tiles_d = nullptr;
   c->tprobes_d = nullptr;
-  CK(cudaMalloc(&c->tiles_d, sizeof(Tile) * std::max<size_t>(1, all.size())), "tile list");
-  CK(cudaMalloc(&c->tprobes_d, sizeof(TileProbe) * std::max<size_t>(1, tps.size())), "tile probes");
+  CK(device_alloc((void**)&c->tiles_d, sizeof(Tile) * std::max<size_t>(1, all.size())), "tile list");
+  CK(device_alloc((void**)&c->tprobes_d, sizeof(TileProbe) * std::max<size_t>(1, tps.size())), "tile probes");
   CK(cudaMemcpy(c->tiles_d, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice), "tile upload");
   if (!tps.empty())
     CK(cudaMemcpy(c->tprobes_d, tps.data(), sizeof(TileProbe) * tps.size(), cudaMemcpyHostToDevice),
@@ -407,7 +455,7 @@ rketd_status plan_resident(rketd_ctx* c) {
   if (!c->res_probes_d && c->n_probes) {
     std::vector<TileProbe> pr(c->n_probes);
     for (int p = 0; p < c->n_probes; ++p) pr[p] = {(int32_t)c->probe_cell[p], p};
-    CK(cudaMalloc(&c->res_probes_d, sizeof(TileProbe) * pr.size()), "probe list");
+    CK(device_alloc((void**)&c->res_probes_d, sizeof(TileProbe) * pr.size()), "probe list");
     CK(cudaMemcpy(c->res_probes_d, pr.data(), sizeof(TileProbe) * pr.size(), cudaMemcpyHostToDevice), "probe list");
   }
   c->res_K = K;
@@ -1017,12 +1065,46 @@ int64_t rketd_step_index(const rketd_ctx* c) { return c ? c->step : -1; }
 
 int64_t rketd_launch_count(const rketd_ctx* c) { return c ? c->launches : -1; }
 
+rketd_status rketd_check_finite(rketd_ctx* c) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  int* flag = nullptr;
+  CK(device_alloc_async((void**)&flag, sizeof(int), c->stream), "finite scan");
+  rketd_status st = RKETD_OK;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  const bool f64 = c->prec == RKETD_F64;
+  const void* arrs[6] = {c->E[c->cur], c->H[c->cur], c->J[c->cur], c->Ep, c->psiE[c->cur], c->psiH[c->cur]};
+  const int64_t lens[6] = {c->n_store, c->n_store, c->n_store, c->Ep ? c->n_store : 0, c->psiE[c->cur] ? c->n_psi : 0,
+                           c->psiH[c->cur] ? c->n_psi : 0};
+  for (int q = 0; q < 6 && e == cudaSuccess; ++q) e = launch_finite_scan(f64, arrs[q], lens[q], flag, c->stream);
+  const int64_t nx = (int64_t)c->total_probes * c->n_freq;
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xr, nx, flag, c->stream);
+  if (e == cudaSuccess && nx) e = launch_finite_scan(true, c->Xi, nx, flag, c->stream);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(flag, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "finite scan");
+  if (h) st = fail(RKETD_ENUMERIC, "a field, CPML memory or spectrum holds NaN or Inf");
+  return st;
+}
+
+rketd_status rketd_debug_fail_alloc(int64_t after) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_fail_after = after < 0 ? -1 : after;
+  return RKETD_OK;
+}
+
+int64_t rketd_debug_alloc_count(void) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc_count;
+}
+
 rketd_status rketd_get_fields(rketd_ctx* c, int32_t slab, double* E, double* H, double* J) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (slab < 0 || slab >= c->n_slabs) return fail(RKETD_EINVAL, "slab index out of range");
   const int64_t nz = c->nz[slab];
   double* tmp;
-  CK(cudaMallocAsync((void**)&tmp, sizeof(double) * 3 * nz, c->stream), "field staging");
+  CK(device_alloc_async((void**)&tmp, sizeof(double) * 3 * nz, c->stream), "field staging");
   const double hs = 1.0 / std::sqrt(kMu0 / kEps0);
   const double js = kEps0 / c->grid.dt;
   cudaError_t e = launch_gather_fields(c->prec, c->E[c->cur], c->H[c->cur], c->J[c->cur], c->coef[kCj],
@@ -1206,7 +1288,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   auto save = [&](void* src, size_t bytes) -> rketd_status {
     void* d = nullptr;
     if (!bytes) { saved.push_back({nullptr, 0}); return RKETD_OK; }
-    CK(cudaMalloc(&d, bytes), "autotune save");
+    CK(device_alloc(&d, bytes), "autotune save");
     saved.push_back({d, bytes});
     CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyDeviceToDevice, c->stream), "autotune save");
     return RKETD_OK;
@@ -1363,7 +1445,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     order.insert(order.end(), c->tiles_h.begin() + c->n_interior, c->tiles_h.end());
     if (c->adj_tiles_d) cudaFree(c->adj_tiles_d);
     c->adj_tiles_d = nullptr;
-    CK(cudaMalloc(&c->adj_tiles_d, sizeof(Tile) * std::max<size_t>(1, order.size())), "adjoint tiles");
+    CK(device_alloc((void**)&c->adj_tiles_d, sizeof(Tile) * std::max<size_t>(1, order.size())), "adjoint tiles");
     CK(cudaMemcpy(c->adj_tiles_d, order.data(), sizeof(Tile) * order.size(), cudaMemcpyHostToDevice), "adjoint tiles");
     c->adj_n_plain = (int)plain.size();
     c->adj_n_win = (int)win.size();

@@ -94,6 +94,9 @@ _SIGS = {
     "rketd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Options)]),
     "rketd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_check_finite": (ctypes.c_int, [ctypes.c_void_p]),
+    "rketd_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int64]),
+    "rketd_debug_alloc_count": (ctypes.c_int64, []),
     "rketd_plan_tiles_1d": (ctypes.c_int, [ctypes.c_int32, _i64p, _i64p, ctypes.c_int32, _i64p, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p]),
     "rketd_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
@@ -116,6 +119,8 @@ _SIGS = {
     "rketd_kernel_chunk_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_sync_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_set_wait_limit_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_check_finite_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_create_2d": (ctypes.c_int, [ctypes.POINTER(Grid2D), ctypes.c_void_p, ctypes.c_int32, _dp, _dp, _dp,
                                        ctypes.POINTER(Pulse), ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(Dft),
@@ -126,6 +131,7 @@ _SIGS = {
     "rketd_get_field_2d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _dp]),
     "rketd_get_spectra_2d": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "rketd_launch_count_2d": (ctypes.c_int64, [ctypes.c_void_p]),
+    "rketd_check_finite_2d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_destroy_2d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_last_error": (ctypes.c_char_p, []),
     "rketd_version": (ctypes.c_char_p, []),
@@ -332,6 +338,10 @@ class Context:
     def launches(self) -> int:
         return lib().rketd_launch_count(self.h)
 
+    def check_finite(self):
+        """Raises RketdError (RKETD_ENUMERIC) if the state or the spectra hold NaN or Inf."""
+        _check(lib().rketd_check_finite(self.h))
+
 
 def rt(tot: np.ndarray, inc: np.ndarray):
     """R, T from [2, n_freq] complex spectra (probe 0 reflection, probe 1 transmission)."""
@@ -463,6 +473,14 @@ class Context3D:
     def launches(self) -> int:
         return lib().rketd_launch_count_3d(self.h)
 
+    def check_finite(self):
+        """Raises RketdError (RKETD_ENUMERIC) if a field or spectrum holds NaN or Inf."""
+        _check(lib().rketd_check_finite_3d(self.h))
+
+    def set_wait_limit(self, polls: int):
+        """Test hook: polls of the staged form's compute-path copy waits (< 0: the default)."""
+        _check(lib().rketd_set_wait_limit_3d(self.h, int(polls)))
+
 
 FIELDS_2D = {"tm": ("Ez", "Hx", "Hy", "Jz"), "te": ("Ex", "Ey", "Hz", "Jx", "Jy")}
 RKETD_TMZ, RKETD_TEZ = 0, 1
@@ -538,3 +556,18 @@ class Context2D:
     @property
     def launches(self) -> int:
         return lib().rketd_launch_count_2d(self.h)
+
+    def check_finite(self):
+        """Raises RketdError (RKETD_ENUMERIC) if a field or spectrum holds NaN or Inf."""
+        _check(lib().rketd_check_finite_2d(self.h))
+
+
+def debug_fail_alloc(after: int):
+    """Test hook: the library's device allocation after `after` more successful ones fails as out
+    of memory (RKETD_ENOMEM); after < 0 disarms."""
+    _check(lib().rketd_debug_fail_alloc(int(after)))
+
+
+def debug_alloc_count() -> int:
+    """Device allocations the library has attempted so far (process-wide)."""
+    return lib().rketd_debug_alloc_count()
