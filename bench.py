@@ -470,12 +470,17 @@ def measure_adjoint(args):
         return loss, e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
 
     once(False)
-    loss, t_fwd, t_adj = once(True)
+    runs = [once(True) for _ in range(3)]
+    loss = runs[-1][0]
+    t_fwd = float(np.median([r[1] for r in runs]))
+    t_adj = float(np.median([r[2] for r in runs]))
     cu = n * steps
     ctx.close()
     return {"workload": f"{len(profs)} profiles x 65536 cells, {steps} steps, FP32, checkpoint every {every}, "
                         f"window [{win[0]}, {win[1]}), 256 frequencies",
             "forward_ms": t_fwd, "adjoint_ms": t_adj, "ratio": t_adj / t_fwd,
+            "runs": [{"forward_ms": r[1], "adjoint_ms": r[2]} for r in runs],
+            "timing": "median of 3 runs after one warm-up run",
             "forward_gcells": cu / (t_fwd / 1e3) / 1e9, "loss": loss,
             "adjoint_includes": "segment recompute with window recording, seeds, transposed sweep, gradient sums, "
                                 "chain rule"}
@@ -740,7 +745,7 @@ def run_ours(args):
 
 
 PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c1-resident-f64",
-                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c5-sphere")
+                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c4-adjoint-full", "c5-sphere")
 
 
 def run_profile_case(args):
@@ -748,7 +753,8 @@ def run_profile_case(args):
     profiles/ run these. c2-*: the long slab (--nz cells), --profile-steps steps after one
     warm-up pass; c1-*: the paper's slab, one whole run; c3-batch: the ragged batch with its tuned
     tile shape (K = 12, 32 steps per pass), 64 + 128 steps; c4-adjoint: 8 profiles of the adjoint
-    workload, 4096 steps, checkpoint every 512, forward and adjoint; c5-sphere: the sphere on an
+    workload, 4096 steps, checkpoint every 512, forward and adjoint (c4-adjoint-full: the whole
+    workload, 64 profiles and 30000 steps); c5-sphere: the sphere on an
     --n3d grid for --steps3d steps."""
     import torch
 
@@ -779,10 +785,12 @@ def run_profile_case(args):
             ctx.step(64)
             ctx.step(128)
             ctx.sync()
-    elif case == "c4-adjoint":
-        profs = [wl.c4_profile(i, steps=4096) for i in range(8)]
+    elif case in ("c4-adjoint", "c4-adjoint-full"):
+        full = case == "c4-adjoint-full"
+        n_prof, steps = (64, 30000) if full else (8, 4096)
+        profs = [wl.c4_profile(i, steps=steps) for i in range(n_prof)]
         with rk.Context(profs, "f32") as ctx:
-            ctx.forward_ckpt(4096, 512)
+            ctx.forward_ckpt(steps, 512)
             X = ctx.spectra()
             gX = np.zeros_like(X)
             gX[:, 0] = np.conj(X[:, 0]) / np.abs(X[:, 0]).max()

@@ -176,6 +176,12 @@ struct rketd_ctx {
   void* lam[6] = {};       // adjoint E, H, J (two copies each)
   void* recF = nullptr;
   void* recA = nullptr;
+  // a second set of segment records: the gradient sums of one segment run on gstream while the
+  // next segment is recomputed and swept on the main and side streams
+  void* recF2 = nullptr;
+  void* recA2 = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_adj = nullptr, ev_grad[2] = {nullptr, nullptr};
   void* seeds = nullptr;
   void* tw_seed = nullptr;
   double* gX = nullptr;    // [2][P*nf]
@@ -211,6 +217,10 @@ struct rketd_ctx {
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (side) cudaStreamDestroy(side);
+    if (ev_adj) cudaEventDestroy(ev_adj);
+    for (cudaEvent_t e : ev_grad)
+      if (e) cudaEventDestroy(e);
+    if (gstream) cudaStreamDestroy(gstream);
     for (void* p : allocs) cudaFree(p);
     if (tiles_d) cudaFree(tiles_d);
     if (tprobes_d) cudaFree(tprobes_d);
@@ -1468,8 +1478,15 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
   if (!c->lam[0])
     for (int i = 0; i < 6; ++i)
       if ((st = c->alloc(&c->lam[i], fb, "adjoint fields"))) return st;
+  if (!c->gstream) {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi), "gradient stream");
+    CK(cudaStreamCreateWithPriority(&c->gstream, cudaStreamNonBlocking, lo), "gradient stream");
+    CK(cudaEventCreateWithFlags(&c->ev_adj, cudaEventDisableTiming), "gradient events");
+    for (cudaEvent_t& e : c->ev_grad) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "gradient events");
+  }
   if (rw > c->rec_cap) {
-    for (void** p : {&c->recF, &c->recA, &c->seeds, &c->tw_seed, (void**)&c->gacc}) {
+    for (void** p : {&c->recF, &c->recA, &c->recF2, &c->recA2, &c->seeds, &c->tw_seed, (void**)&c->gacc}) {
       if (*p) {
         cudaFree(*p);
         c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), *p));
@@ -1478,6 +1495,8 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     }
     if ((st = c->alloc(&c->recF, c->esz * (size_t)c->n_slabs * (C + 1) * 3 * rw, "adjoint records"))) return st;
     if ((st = c->alloc(&c->recA, c->esz * (size_t)c->n_slabs * C * 2 * rw, "adjoint records"))) return st;
+    if ((st = c->alloc(&c->recF2, c->esz * (size_t)c->n_slabs * (C + 1) * 3 * rw, "adjoint records"))) return st;
+    if ((st = c->alloc(&c->recA2, c->esz * (size_t)c->n_slabs * C * 2 * rw, "adjoint records"))) return st;
     if ((st = c->alloc(&c->seeds, c->esz * (size_t)std::max(P, 1) * C, "adjoint seeds"))) return st;
     if ((st = c->alloc(&c->tw_seed, c->esz * 2 * (size_t)C * std::max(nf, 1), "adjoint twiddles"))) return st;
     void* g;
@@ -1492,6 +1511,11 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
   for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
     const int64_t n0 = seg * C;
     const int L = (int)std::min<int64_t>(C, N - n0);
+    // record set of this segment; the gradient sums of the segment that used it last must be done
+    const int rb = (int)((n_seg - 1 - seg) & 1);
+    void* recF = rb ? c->recF2 : c->recF;
+    void* recA = rb ? c->recA2 : c->recA;
+    if (n_seg - 1 - seg >= 2) CK(cudaStreamWaitEvent(c->stream, c->ev_grad[rb], 0), "record reuse");
     // restore the checkpoint and recompute the segment, recording the window
     const char* src = (const char*)c->ckpt + 3 * fb * seg;
     CK(cudaMemcpyAsync(c->E[0], src, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
@@ -1499,7 +1523,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     CK(cudaMemcpyAsync(c->J[0], src + 2 * fb, fb, cudaMemcpyDeviceToDevice, c->stream), "restore");
     c->cur = 0;
     CK(launch_rec_init<T>((const T*)c->E[0], (const T*)c->H[0], (const T*)c->J[0], c->soff_d, c->nz_d, c->n_slabs, r0,
-                          (int)rw, L + 1, (T*)c->recF, c->stream),
+                          (int)rw, L + 1, (T*)recF, c->stream),
        "record init");
     c->launches += 1;
     for (int done = 0; done < L;) {
@@ -1509,7 +1533,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.nsub = nsub;
       a.series = nullptr;
       a.tprobes = c->tprobes_d;
-      a.rec = (T*)c->recF;
+      a.rec = (T*)recF;
       a.rec_c0 = r0;
       a.rec_w = (int)rw;
       a.rec_len = L + 1;
@@ -1564,7 +1588,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.seeds = (const T*)c->seeds;
       a.seed_len = L;
       a.tprobes = c->tprobes_d;
-      a.rec = (T*)c->recA;
+      a.rec = (T*)recA;
       a.rec_c0 = r0;
       a.rec_w = (int)rw;
       a.rec_len = L;
@@ -1589,12 +1613,19 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       lcur = 1 - lcur;
       hi -= nsub;
     }
+    // the segment's gradient sums on the gradient stream (in segment order, so the FP64 totals
+    // add up in the same order as on one stream), overlapping the next segment
     const GradSource gs{c->src_d, w_lo, n0, c->grid.dt, c->pulse.t0, c->pulse.tau, c->pulse.amp};
-    CK(launch_grad_accum<T>((const T*)c->recF, (const T*)c->recA, c->n_slabs, (int)rw, (int)nwin, L, L + 1, gs,
-                            c->gacc, c->stream),
+    CK(cudaEventRecord(c->ev_adj, c->stream), "segment done");
+    CK(cudaStreamWaitEvent(c->gstream, c->ev_adj, 0), "segment done");
+    CK(launch_grad_accum<T>((const T*)recF, (const T*)recA, c->n_slabs, (int)rw, (int)nwin, L, L + 1, gs, c->gacc,
+                            c->gstream),
        "gradient sums");
+    CK(cudaEventRecord(c->ev_grad[rb], c->gstream), "gradient sums done");
     c->launches += 1;
   }
+  CK(cudaEventRecord(c->ev_adj, c->gstream), "gradient sums done");
+  CK(cudaStreamWaitEvent(c->stream, c->ev_adj, 0), "gradient sums done");
   CK(cudaMemsetAsync(grad_wp2, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
   CK(cudaMemsetAsync(grad_nu, 0, sizeof(double) * c->n_cells, c->stream), "gradient init");
   CK(launch_grad_chain(c->gacc, c->wp2_d, c->nu_d, c->off_d, c->n_slabs, w_lo, (int)nwin, c->grid.dt, c->S,
