@@ -164,9 +164,11 @@ struct rketd_ctx {
   int64_t step = 0;
   int64_t launches = 0;
 
-  // the edge-tile kernel runs on a side stream, overlapping the interior kernel
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // the edge-tile kernel runs on a side stream, overlapping the interior kernel; the probe and
+  // source tiles (forward) or the window tiles (adjoint) on a second one, so that these two
+  // latency-bound launches of few warps also overlap each other
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 
   // adjoint: checkpoints of the forward run and the reverse-sweep buffers
   int64_t ckpt_steps = 0;  // steps of the checkpointed forward run (0 = none)
@@ -180,8 +182,10 @@ struct rketd_ctx {
   // next segment is recomputed and swept on the main and side streams
   void* recF2 = nullptr;
   void* recA2 = nullptr;
+  void* seeds2 = nullptr;    // the loss seeds of the next segment, made ahead on gstream
+  void* tw_seed2 = nullptr;
   cudaStream_t gstream = nullptr;
-  cudaEvent_t ev_adj = nullptr, ev_grad[2] = {nullptr, nullptr};
+  cudaEvent_t ev_adj = nullptr, ev_grad[2] = {nullptr, nullptr}, ev_seed = nullptr;
   void* seeds = nullptr;
   void* tw_seed = nullptr;
   double* gX = nullptr;    // [2][P*nf]
@@ -216,8 +220,11 @@ struct rketd_ctx {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
+    if (join2) cudaEventDestroy(join2);
     if (side) cudaStreamDestroy(side);
+    if (side2) cudaStreamDestroy(side2);
     if (ev_adj) cudaEventDestroy(ev_adj);
+    if (ev_seed) cudaEventDestroy(ev_seed);
     for (cudaEvent_t e : ev_grad)
       if (e) cudaEventDestroy(e);
     if (gstream) cudaStreamDestroy(gstream);
@@ -625,10 +632,13 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       const bool fp32p = std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0;
       const int n_main = c->n_interior - c->n_int_xtra;
       const bool forked = n_main && (c->n_edge || c->n_int_xtra);
+      const bool forked2 = forked && c->n_edge && c->n_int_xtra;
       cudaStream_t side = forked ? c->side : c->stream;
+      cudaStream_t side2 = forked2 ? c->side2 : side;
       if (forked) {
         CK(cudaEventRecord(c->fork, c->stream), "fork");
         CK(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
+        if (forked2) CK(cudaStreamWaitEvent(c->side2, c->fork, 0), "fork");
       }
       if (c->n_edge) {
         a.tiles = c->tiles_d + c->n_interior;
@@ -640,14 +650,15 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
         a.tiles = c->tiles_d + n_main;
         a.n_tiles = c->n_int_xtra;
         if (fp32p) {
-          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, side, true),
+          CK(launch_tb_pairs(*reinterpret_cast<const StepArgs<float>*>(&a), K, c->opt.warps_per_block, side2, true),
              "tiled step (probe and source tiles, FP32 pairs)");
         } else {
-          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, side, true), "tiled step (probe and source tiles)");
+          CK(launch_tb<T>(a, K, false, c->opt.warps_per_block, side2, true), "tiled step (probe and source tiles)");
         }
         c->launches += 1;
       }
       if (forked) CK(cudaEventRecord(c->join, c->side), "join");
+      if (forked2) CK(cudaEventRecord(c->join2, c->side2), "join");
       a.tiles = c->tiles_d;
       a.n_tiles = n_main;
       if (a.n_tiles) {
@@ -673,6 +684,7 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
         }
       }
       if (forked) CK(cudaStreamWaitEvent(c->stream, c->join, 0), "join");
+      if (forked2) CK(cudaStreamWaitEvent(c->stream, c->join2, 0), "join");
       c->cur = 1 - c->cur;
       c->step += nsub;
       nsteps -= nsub;
@@ -912,8 +924,10 @@ rketd_status rketd_create_batch_1d(int32_t n_slabs, const int64_t* nz, const rke
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming) != cudaSuccess)
     return cleanup(cuda_fail(cudaGetLastError(), "side stream"));
   const size_t fb = c->esz * c->n_store;
   for (int b = 0; b < 2; ++b) {
@@ -1465,14 +1479,18 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
   const Tile* t_plain = c->adj_tiles_d;
   const Tile* t_win = c->adj_tiles_d + c->adj_n_plain;
   const Tile* t_edge = t_win + c->adj_n_win;
+  // window tiles on the side stream, edge tiles on the second side stream
   auto fork = [&]() -> rketd_status {
     CK(cudaEventRecord(c->fork, c->stream), "fork");
     CK(cudaStreamWaitEvent(c->side, c->fork, 0), "fork");
+    CK(cudaStreamWaitEvent(c->side2, c->fork, 0), "fork");
     return RKETD_OK;
   };
   auto join = [&]() -> rketd_status {
     CK(cudaEventRecord(c->join, c->side), "join");
+    CK(cudaEventRecord(c->join2, c->side2), "join");
     CK(cudaStreamWaitEvent(c->stream, c->join, 0), "join");
+    CK(cudaStreamWaitEvent(c->stream, c->join2, 0), "join");
     return RKETD_OK;
   };
   if (!c->lam[0])
@@ -1483,10 +1501,12 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     CK(cudaDeviceGetStreamPriorityRange(&lo, &hi), "gradient stream");
     CK(cudaStreamCreateWithPriority(&c->gstream, cudaStreamNonBlocking, lo), "gradient stream");
     CK(cudaEventCreateWithFlags(&c->ev_adj, cudaEventDisableTiming), "gradient events");
+    CK(cudaEventCreateWithFlags(&c->ev_seed, cudaEventDisableTiming), "gradient events");
     for (cudaEvent_t& e : c->ev_grad) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "gradient events");
   }
   if (rw > c->rec_cap) {
-    for (void** p : {&c->recF, &c->recA, &c->recF2, &c->recA2, &c->seeds, &c->tw_seed, (void**)&c->gacc}) {
+    for (void** p : {&c->recF, &c->recA, &c->recF2, &c->recA2, &c->seeds, &c->tw_seed, &c->seeds2, &c->tw_seed2,
+                     (void**)&c->gacc}) {
       if (*p) {
         cudaFree(*p);
         c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), *p));
@@ -1499,6 +1519,8 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
     if ((st = c->alloc(&c->recA2, c->esz * (size_t)c->n_slabs * C * 2 * rw, "adjoint records"))) return st;
     if ((st = c->alloc(&c->seeds, c->esz * (size_t)std::max(P, 1) * C, "adjoint seeds"))) return st;
     if ((st = c->alloc(&c->tw_seed, c->esz * 2 * (size_t)C * std::max(nf, 1), "adjoint twiddles"))) return st;
+    if ((st = c->alloc(&c->seeds2, c->esz * (size_t)std::max(P, 1) * C, "adjoint seeds"))) return st;
+    if ((st = c->alloc(&c->tw_seed2, c->esz * 2 * (size_t)C * std::max(nf, 1), "adjoint twiddles"))) return st;
     void* g;
     if ((st = c->alloc(&g, sizeof(double) * 5 * (size_t)c->n_slabs * nwin, "gradient sums"))) return st;
     c->gacc = (double*)g;
@@ -1508,6 +1530,24 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
   CK(cudaMemsetAsync(c->gacc, 0, sizeof(double) * 5 * (size_t)c->n_slabs * nwin, c->stream), "adjoint init");
   int lcur = 0;
   const int64_t n_seg = (N + C - 1) / C;
+  // loss seeds for the samples after steps n0 .. n0+L-1 of a segment, made on the gradient
+  // stream one segment ahead of the transposed sweep that reads them (two buffers)
+  auto make_seeds = [&](int64_t seg) -> rketd_status {
+    if (P == 0 || seg < 0) return RKETD_OK;
+    const int64_t m0 = seg * C;
+    const int Ls = (int)std::min<int64_t>(C, N - m0);
+    const int b = (int)((n_seg - 1 - seg) & 1);
+    T* tw = (T*)(b ? c->tw_seed2 : c->tw_seed);
+    CK(launch_twiddles<T>(c->freq_d, nf, c->grid.dt, m0 + 1, Ls, tw, c->gstream), "seed twiddles");
+    CK(launch_seeds<T>(c->gX, c->gX + (size_t)P * nf, tw, P, nf, Ls, (T*)(b ? c->seeds2 : c->seeds), Ls, c->gstream),
+       "seeds");
+    CK(cudaEventRecord(c->ev_seed, c->gstream), "seeds done");
+    c->launches += 2;
+    return RKETD_OK;
+  };
+  CK(cudaEventRecord(c->ev_adj, c->stream), "adjoint inputs");
+  CK(cudaStreamWaitEvent(c->gstream, c->ev_adj, 0), "adjoint inputs");
+  if ((st = make_seeds(n_seg - 1))) return st;
   for (int64_t seg = n_seg - 1; seg >= 0; --seg) {
     const int64_t n0 = seg * C;
     const int L = (int)std::min<int64_t>(C, N - n0);
@@ -1545,7 +1585,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       CK(launch_tb_rec<T>(a, K, false, 2, c->side), "recompute (window)");
       a.tiles = t_edge;
       a.n_tiles = c->n_edge;
-      CK(launch_tb_rec<T>(a, Ke, true, 2, c->side), "recompute (edge)");
+      CK(launch_tb_rec<T>(a, Ke, true, 2, c->side2), "recompute (edge)");
       a.tiles = t_plain;
       a.n_tiles = c->adj_n_plain;
       if (std::is_same<T, float>::value && c->opt.fp32_pairs != 2 && K % 4 == 0) {
@@ -1560,13 +1600,9 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       c->cur = 1 - c->cur;
       done += nsub;
     }
-    // loss seeds for the samples after steps n0 .. n0+L-1
-    if (P > 0) {
-      CK(launch_twiddles<T>(c->freq_d, nf, c->grid.dt, n0 + 1, L, (T*)c->tw_seed, c->stream), "seed twiddles");
-      CK(launch_seeds<T>(c->gX, c->gX + (size_t)P * nf, (const T*)c->tw_seed, P, nf, L, (T*)c->seeds, L, c->stream),
-         "seeds");
-      c->launches += 2;
-    }
+    // this segment's loss seeds (made on the gradient stream)
+    const T* seeds = (const T*)(rb ? c->seeds2 : c->seeds);
+    if (P > 0) CK(cudaStreamWaitEvent(c->stream, c->ev_seed, 0), "seeds ready");
     // transposed passes from the end of the segment back to its start
     for (int hi = L; hi > 0;) {
       const int nsub = std::min(TS, hi);
@@ -1585,7 +1621,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       a.nsub = nsub;
       a.n_hi = n0 + hi;
       a.seg_n0 = n0;
-      a.seeds = (const T*)c->seeds;
+      a.seeds = seeds;
       a.seed_len = L;
       a.tprobes = c->tprobes_d;
       a.rec = (T*)recA;
@@ -1598,7 +1634,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
       CK(launch_adj<T>(a, K, false, 2, c->side), "adjoint (window)");
       a.tiles = t_edge;
       a.n_tiles = c->n_edge;
-      CK(launch_adj<T>(a, Ke, true, 2, c->side), "adjoint (edge)");
+      CK(launch_adj<T>(a, Ke, true, 2, c->side2), "adjoint (edge)");
       a.tiles = t_plain;
       a.n_tiles = c->adj_n_plain;
       a.rec = nullptr;
@@ -1623,6 +1659,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
        "gradient sums");
     CK(cudaEventRecord(c->ev_grad[rb], c->gstream), "gradient sums done");
     c->launches += 1;
+    if ((st = make_seeds(seg - 1))) return st;
   }
   CK(cudaEventRecord(c->ev_adj, c->gstream), "gradient sums done");
   CK(cudaStreamWaitEvent(c->stream, c->ev_adj, 0), "gradient sums done");
