@@ -767,6 +767,7 @@ def run_profile_case(args):
         _, variant, prec = case.split("-")
         slab = wl.c2_epstein(nz=args.nz, steps=args.run_steps)
         opts = {"variant": 2 if variant == "tiled" else 1, "use_graphs": 2}
+        opts.update(parse_options(args.options))
         with rk.Context(slab, prec, options=opts) as ctx:
             warm = ctx.options()["tb_steps"] if variant == "tiled" else 1
             ctx.step(warm)
