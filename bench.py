@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--adj-profiles", type=int, default=64)
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D sphere measurement")
     ap.add_argument("--no-c1", action="store_true", help="skip the paper-slab (config 1) measurement")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D TMz/TEz measurement")
+    ap.add_argument("--steps2d", type=int, default=1000)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the Eq. 9 / Eq. 10 / split-PML measurement on the long slab")
+    ap.add_argument("--variant-steps", type=int, default=4096)
     ap.add_argument("--c1-reps", type=int, default=9)
     ap.add_argument("--profile", choices=PROFILE_CASES, default=None,
                     help="run one short workload for an ncu capture and exit (no timing)")
@@ -301,6 +306,50 @@ def _time_runs(slabs, prec, steps, reps, warm=2, opts=None):
         return statistics.median(ts), ctx.options(), (ctx.launches - l0) / reps
 
 
+def _time_pair(s1, s2, prec, steps, reps, warm=2):
+    """Median CUDA-event time (ms) of two independent runs (reset + steps + spectra into device
+    buffers) issued on two streams at once: the plasma run and its vacuum reference, each in its
+    own context."""
+    import torch
+
+    from paper_1709_00821_gb300 import rketd as rk
+
+    main = torch.cuda.current_stream()
+    other = torch.cuda.Stream()
+    with rk.Context(s1, prec) as ca, rk.Context(s2, prec, stream=other.cuda_stream) as cb:
+        bufs = []
+        for ctx in (ca, cb):
+            P = ctx.n_slabs * ctx.n_probes * len(ctx.freq)
+            bufs.append((P, torch.empty(max(P, 1), dtype=torch.float64, device="cuda"),
+                         torch.empty(max(P, 1), dtype=torch.float64, device="cuda")))
+
+        def run():
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event()
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            other.wait_event(e0)
+            for ctx, (P, xr, xi) in zip((ca, cb), bufs):
+                ctx.reset()
+                ctx.step(steps)
+                if P:
+                    ctx.spectra_device(xr.data_ptr(), xi.data_ptr())
+            e1.record(other)
+            main.wait_event(e1)
+            e2.record(main)
+            return e0, e2
+
+        for _ in range(warm):
+            run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e2 = run()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e2))
+        return statistics.median(ts), ca.options()["variant"], cb.options()["variant"]
+
+
 def measure_c1(args):
     """Config 1 (the paper's slab: 2000 cells, 8000 steps, Mur ends, 2 probes x 200 frequencies), FP64
     as the config states and FP32 beside it. A run is latency-bound (the state is 48 KB): the library
@@ -315,11 +364,13 @@ def measure_c1(args):
            "unit": UNIT}
     for prec in ("f64", "f32"):
         ms, opt, nl = _time_runs(s, prec, s.steps, reps=args.c1_reps)
-        ms_rt, _, _ = _time_runs([s, s.vacuum()], prec, s.steps, reps=args.c1_reps)
+        ms_rt, va, vb = _time_pair(s, s.vacuum(), prec, s.steps, reps=args.c1_reps)
+        names = {3: "resident", 2: "tiled", 1: "plain"}
         out[prec] = {"ms_per_run": ms, "value": cells / (ms / 1e3) / 1e9, "gpu_launches_per_run": nl,
-                     "variant": {3: "resident", 2: "tiled", 1: "plain"}[opt["variant"]],
+                     "variant": names[opt["variant"]],
                      "ms_plasma_and_vacuum_reference": ms_rt,
-                     "note_reference": "R/T need the vacuum run too: both slabs as one batch context (tiled)"}
+                     "note_reference": "R/T need the vacuum run too: the plasma and vacuum runs in two contexts "
+                                       f"({names[va]}, {names[vb]}) on two streams at once"}
     oracle.build()
     t0 = time.perf_counter()
     oracle.run1d(s)
@@ -484,6 +535,87 @@ def measure_adjoint(args):
             "forward_gcells": cu / (t_fwd / 1e3) / 1e9, "loss": loss,
             "adjoint_includes": "segment recompute with window recording, seeds, transposed sweep, gradient sums, "
                                 "chain rule"}
+
+
+# Algorithmic DRAM bytes per 2D cell-update (FP32; twice that in FP64): the H kernel reads the E
+# component(s) it differences and reads and writes H; the E+J kernel reads H, reads and writes E
+# and the carried current, and reads the material byte.
+B_ALG_2D = {"tm": {"f32": 20 + 25, "f64": 40 + 49}, "te": {"f32": 16 + 37, "f64": 32 + 73}}
+
+
+def measure_2d(args, hbm_peak):
+    """2D TMz/TEz step (the paper's stated generalisation): a plasma layer across a periodic-x grid
+    of 4096 x 16384 cells, one transverse Fourier mode meeting it at oblique incidence, Mur y ends,
+    2 probes x 200 frequencies; 1000 timed steps after 24 untimed ones, CUDA events on the context's
+    stream. Plus the serial 2D oracle on a 512 x 512 sample of the same recipe."""
+    import torch
+
+    import oracle
+    from paper_1709_00821_gb300 import rketd as rk
+    from paper_1709_00821_gb300 import workloads as wl
+
+    nx, ny, steps = 4096, 16384, args.steps2d
+    out = {"workload": f"{nx} x {ny} periodic-x grid, plasma layer (rows {ny // 2 - 15}..{ny // 2 + 14}), "
+                       f"transverse mode 16 at oblique incidence, Mur y ends, {steps} steps, 2 probes x 200 freqs",
+           "unit": UNIT}
+    for pol, prec in (("tm", "f32"), ("te", "f32"), ("tm", "f64")):
+        p = wl.slab_2d(nx, ny, pol, mode=16, steps=steps)
+        with rk.Context2D(p, prec) as ctx:
+            ctx.step(24)
+            ctx.sync()
+            l0 = ctx.launches
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.step(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ok = np.all(np.isfinite(ctx.spectra()))
+            launches = ctx.launches - l0
+        rate = nx * ny * steps / (ms / 1e3)
+        b = B_ALG_2D[pol][prec]
+        out[f"{pol}_{prec}"] = {"value": rate / 1e9, "ms_per_step": ms / steps, "gpu_launches": launches,
+                                "spectra_finite": bool(ok),
+                                "roofline": {"bound": "hbm", "achieved": b * rate / 1e9, "peak": hbm_peak,
+                                             "unit": "GB/s", "frac": b * rate / 1e9 / hbm_peak,
+                                             "bytes_per_cell_update": b, "kernels": f"k2_{pol}_h + k2_{pol}_e"}}
+    q = wl.slab_2d(512, 512, "tm", mode=1, steps=20)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run2d(q)
+    t = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": 512 * 512 * 20 / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"the same recipe (TMz) on a 512 x 512 grid, 20 steps, serial FP64 2D oracle, "
+                                     f"{t:.2f} s"}
+    return out
+
+
+def measure_variants(args):
+    """The paper's other current recursions and its boundary on the long slab (2^24 cells, FP32 and
+    FP64, 4096 steps each): Eq. 9 (coefficients only: the tiled kernels), Eq. 10 read literally
+    (carries E^{n-1}: the plain kernels), and the 5-cell split-field PML ends, beside the Eq. 11 run
+    with CPML ends on the same slab."""
+    import copy
+
+    from paper_1709_00821_gb300 import workloads as wl
+
+    steps = args.variant_steps
+    base = wl.c2_epstein(nz=args.nz, steps=steps)
+    names = {3: "resident", 2: "tiled", 1: "plain"}
+    out = {"workload": f"long Drude slab, {base.nz} cells, {steps} steps per run", "unit": UNIT}
+    for prec in ("f32", "f64"):
+        for label, scheme, bc in (("eq11_cpml", wl.SCHEME_RKETD, "cpml"), ("eq9_cpml", wl.SCHEME_ETD1, "cpml"),
+                                  ("eq10_cpml", wl.SCHEME_ETD2, "cpml"), ("eq11_pml5", wl.SCHEME_RKETD, "pml")):
+            s = copy.deepcopy(base)
+            s.scheme = scheme
+            if bc == "pml":
+                s.bc, s.cpml_cells = "pml", 5
+                s.wp2 = s.wp2.copy()
+                s.wp2[:5] = s.wp2[-5:] = 0.0  # the split-field layers are vacuum
+            ms, opt, nl = _time_runs(s, prec, steps, reps=2, warm=1)
+            out[f"{label}_{prec}"] = {"value": base.nz * steps / (ms / 1e3) / 1e9, "ms_per_run": ms,
+                                      "variant": names[opt["variant"]], "gpu_launches_per_run": nl}
+    return out
 
 
 def bytes_3d(p, esz=4):
@@ -715,6 +847,16 @@ def run_ours(args):
     if not args.no_batch:
         batch = measure_batch(args)
 
+    # ---- 2D TMz/TEz ----
+    two_d = None
+    if not args.no_2d and rank == 0:
+        two_d = measure_2d(args, hbm_peak)
+
+    # ---- Eq. 9, Eq. 10 and the split-field PML on the long slab ----
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = measure_variants(args)
+
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -736,7 +878,7 @@ def run_ours(args):
                            "precision": "FP32 fields, FP64-derived delta coefficients, Kahan-FP32 DFT blocks into FP64"},
                 "roofline": roofline, "hbm_roofline_effective": hbm_eff, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks, "fp64": fp64, "paper_slab_c1": c1, "batched": batch, "adjoint": adjoint,
-                "sphere_3d": cfg3d,
+                "sphere_3d": cfg3d, "two_d": two_d, "variants": variants,
                 "cpu_baseline": cpu,
                 "adjoint_forward_ratio": adjoint["ratio"] if adjoint else None}
         print(json.dumps(line), flush=True)
@@ -745,7 +887,8 @@ def run_ours(args):
 
 
 PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c1-resident-f64",
-                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c4-adjoint-full", "c5-sphere")
+                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c4-adjoint-full", "c5-sphere", "2d-tm-f32",
+                 "2d-te-f32", "2d-tm-f64")
 
 
 def run_profile_case(args):
@@ -755,7 +898,8 @@ def run_profile_case(args):
     tile shape (K = 12, 32 steps per pass), 64 + 128 steps; c4-adjoint: 8 profiles of the adjoint
     workload, 4096 steps, checkpoint every 512, forward and adjoint (c4-adjoint-full: the whole
     workload, 64 profiles and 30000 steps); c5-sphere: the sphere on an
-    --n3d grid for --steps3d steps."""
+    --n3d grid for --steps3d steps; 2d-*: the 2D bench grid (4096 x 16384) for --profile-steps
+    steps."""
     import torch
 
     from paper_1709_00821_gb300 import rketd as rk
@@ -799,6 +943,12 @@ def run_profile_case(args):
             gw = torch.empty(n, dtype=torch.float64, device="cuda")
             gn = torch.empty(n, dtype=torch.float64, device="cuda")
             ctx.adjoint(np.ascontiguousarray(gX.real), np.ascontiguousarray(gX.imag), 2048, 6144, gw, gn)
+            ctx.sync()
+    elif case.startswith("2d-"):
+        _, pol, prec = case.split("-")
+        p = wl.slab_2d(4096, 16384, pol, mode=16, steps=args.profile_steps)
+        with rk.Context2D(p, prec) as ctx:
+            ctx.step(args.profile_steps)
             ctx.sync()
     elif case == "c5-sphere":
         p = wl.sphere_problem(n=args.n3d, steps=args.steps3d)

@@ -165,6 +165,219 @@ __global__ void __launch_bounds__(256) k2_te_e(Args2<T> a) {
   }
 }
 
+// ---------------------------------------------------------------- four cells per thread
+// FP32 grids with nx a multiple of 4: each thread takes cells 4q .. 4q+3 of one row with 16-byte
+// loads and stores (rows then start 16-byte aligned), and the one neighbour across the quad
+// (i+1 after it, i-1 before it) with a scalar load. Same operations on the same values as the
+// one-cell kernels above; a quad that holds a Mur end cell sets it from its interior neighbour
+// in the same thread, and rows 1 and ny-2 set the y-Mur rows 0 and ny-1 (corners included, from
+// the new values of the row, x-Mur cells among them).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k2v_tm_h(Args2<T> a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, nq = nx >> 2;
+  if (q >= nq || j >= a.ny) return;
+  const int i0 = 4 * q;
+  const int64_t c = (int64_t)j * nx + i0;
+  T e[4], hx[4], hy[4];
+  ld4(a.F[0] + c, e);
+  if (j + 1 < a.ny) {
+    T en[4];
+    ld4(a.F[0] + c + nx, en);
+    ld4(a.F[2] + c, hx);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) hx[k] = fma(-a.S, en[k] - e[k], hx[k]);
+    st4(a.F[2] + c, hx);
+  }
+  const int ip = i0 + 4 < nx ? i0 + 4 : (a.per ? 0 : -1);
+  const T eR = ip >= 0 ? a.F[0][(int64_t)j * nx + ip] : T(0);
+  ld4(a.F[3] + c, hy);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) hy[k] = fma(a.S, e[k + 1] - e[k], hy[k]);
+  if (ip >= 0) hy[3] = fma(a.S, eR - e[3], hy[3]);
+  st4(a.F[3] + c, hy);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k2v_tm_e(Args2<T> a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny, nq = nx >> 2;
+  if (q >= nq || j < 1 || j > ny - 2) return;
+  const int i0 = 4 * q;
+  const int64_t c = (int64_t)j * nx + i0;
+  T* Ez = a.F[0];
+  T* G = a.F[1];
+  T hx[4], hxm[4], hy[4], e[4], g[4], en[4];
+  ld4(a.F[2] + c, hx);
+  ld4(a.F[2] + c - nx, hxm);
+  ld4(a.F[3] + c, hy);
+  ld4(Ez + c, e);
+  ld4(G + c, g);
+  const int im = i0 > 0 ? i0 - 1 : nx - 1;
+  const T hyL = a.F[3][(int64_t)j * nx + im];
+  const uchar4 mb = *reinterpret_cast<const uchar4*>(a.mat + c);
+  const int mm[4] = {mb.x, mb.y, mb.z, mb.w};
+  const T sv = j == a.src_j ? (T)tile::pulse(a.t, a.t0, a.tau, a.amp) : T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = i0 + k;
+    en[k] = e[k];
+    if (!a.per && (i == 0 || i == nx - 1)) continue;
+    const T curl = (hx[k] - hxm[k]) - (hy[k] - (k ? hy[k - 1] : hyL));
+    const int m = mm[k];
+    T enew = fold_e(e[k], a.m.cb[m], curl, g[k]);
+    T gn = fold_g(g[k], a.m.dj[m], a.m.bq[m], a.m.cq[m], e[k], enew);
+    if (j == a.src_j) {
+      const T s_i = sv * a.profile[i];
+      enew = enew + s_i;
+      gn = fma(-a.m.da[m], s_i, gn);
+    }
+    g[k] = gn;
+    en[k] = enew;
+  }
+  if (!a.per) {  // x-Mur: column 0 from column 1, column nx-1 from column nx-2 (old values in e)
+    if (i0 == 0) en[0] = fma(a.q, en[1] - e[0], e[1]);
+    if (i0 + 4 == nx) en[3] = fma(a.q, en[2] - e[3], e[2]);
+  }
+  if (j == 1 || j == ny - 2) {  // y-Mur: row 0 from row 1, row ny-1 from row ny-2
+    const int64_t cc = (int64_t)(j == 1 ? 0 : ny - 1) * nx + i0;
+    T eb[4];
+    ld4(Ez + cc, eb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) eb[k] = fma(a.q, en[k] - eb[k], e[k]);
+    st4(Ez + cc, eb);
+  }
+  st4(G + c, g);
+  st4(Ez + c, en);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k2v_te_h(Args2<T> a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, nq = nx >> 2;
+  if (q >= nq || j >= a.ny - 1) return;
+  const int i0 = 4 * q;
+  const int64_t c = (int64_t)j * nx + i0;
+  const int ip = i0 + 4 < nx ? i0 + 4 : (a.per ? 0 : -1);
+  T ex[4], exn[4], ey[4], hz[4];
+  ld4(a.F[0] + c, ex);
+  ld4(a.F[0] + c + nx, exn);
+  ld4(a.F[1] + c, ey);
+  ld4(a.F[4] + c, hz);
+  const T eyR = ip >= 0 ? a.F[1][(int64_t)j * nx + ip] : T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k == 3 && ip < 0) break;  // Hz (nx-1/2, j+1/2) is outside a Mur-bounded grid
+    const T eyp = k < 3 ? ey[k + 1] : eyR;
+    hz[k] = fma(a.S, (exn[k] - ex[k]) - (eyp - ey[k]), hz[k]);
+  }
+  st4(a.F[4] + c, hz);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k2v_te_e(Args2<T> a) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nx = a.nx, ny = a.ny, nq = nx >> 2;
+  if (q >= nq || j >= ny) return;
+  const int i0 = 4 * q;
+  const int64_t c = (int64_t)j * nx + i0;
+  T* Ex = a.F[0];
+  T* Ey = a.F[1];
+  T* Gx = a.F[2];
+  T* Gy = a.F[3];
+  const T* Hz = a.F[4];
+  const uchar4 mb = *reinterpret_cast<const uchar4*>(a.mat + c);
+  const int mm[4] = {mb.x, mb.y, mb.z, mb.w};
+  T hz[4];
+  ld4(Hz + c, hz);
+  // Ex (i+1/2, j), rows 1..ny-2: eps0 dEx/dt = dHz/dy - Jx
+  if (j >= 1 && j <= ny - 2) {
+    T hzm[4], e[4], g[4], en[4];
+    ld4(Hz + c - nx, hzm);
+    ld4(Ex + c, e);
+    ld4(Gx + c, g);
+    const T sv = j == a.src_j ? (T)tile::pulse(a.t, a.t0, a.tau, a.amp) : T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k;
+      en[k] = e[k];
+      if (!a.per && i == nx - 1) continue;  // no Ex at nx-1/2 on a Mur-bounded grid
+      const int m = mm[k];
+      T enew = fold_e(e[k], a.m.cb[m], hzm[k] - hz[k], g[k]);
+      T gn = fold_g(g[k], a.m.dj[m], a.m.bq[m], a.m.cq[m], e[k], enew);
+      if (j == a.src_j) {
+        const T s_i = sv * a.profile[i];
+        enew = enew + s_i;
+        gn = fma(-a.m.da[m], s_i, gn);
+      }
+      g[k] = gn;
+      en[k] = enew;
+    }
+    if (j == 1 || j == ny - 2) {  // y-Mur on Ex: row 0 from row 1, row ny-1 from row ny-2
+      const int64_t cc = (int64_t)(j == 1 ? 0 : ny - 1) * nx + i0;
+      T eb[4];
+      ld4(Ex + cc, eb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (a.per || i0 + k <= nx - 2) eb[k] = fma(a.q, en[k] - eb[k], e[k]);
+      st4(Ex + cc, eb);
+    }
+    st4(Gx + c, g);
+    st4(Ex + c, en);
+  }
+  // Ey (i, j+1/2), rows 0..ny-2: eps0 dEy/dt = -dHz/dx - Jy
+  if (j <= ny - 2) {
+    T e[4], g[4], en[4];
+    ld4(Ey + c, e);
+    ld4(Gy + c, g);
+    const int im = i0 > 0 ? i0 - 1 : nx - 1;
+    const T hzL = Hz[(int64_t)j * nx + im];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k;
+      en[k] = e[k];
+      if (!a.per && (i == 0 || i == nx - 1)) continue;
+      const int m = mm[k];
+      const T enew = fold_e(e[k], a.m.cb[m], hz[k] - (k ? hz[k - 1] : hzL), g[k]);
+      g[k] = fold_g(g[k], a.m.dj[m], a.m.bq[m], a.m.cq[m], e[k], enew);
+      en[k] = enew;
+    }
+    if (!a.per) {  // x-Mur on Ey: column 0 from column 1, column nx-1 from column nx-2
+      if (i0 == 0) en[0] = fma(a.q, en[1] - e[0], e[1]);
+      if (i0 + 4 == nx) en[3] = fma(a.q, en[2] - e[3], e[2]);
+    }
+    st4(Gy + c, g);
+    st4(Ey + c, en);
+  }
+}
+
 template <typename T>
 __global__ void k2_probe(const T* __restrict__ E, const int32_t* __restrict__ probes, int nx, int n,
                          T* __restrict__ series, int len, int pos) {
@@ -311,6 +524,10 @@ template <typename T>
 rketd_status step2(rketd_ctx2d* c, int64_t nsteps) {
   const dim3 block(32, 8);
   const dim3 grid((c->g.nx + 31) / 32, (c->g.ny + 7) / 8);
+  // four FP32 cells per thread where every row starts 16-byte aligned (the FP64 step is bound by
+  // the FP64 pipe, and runs faster one cell per thread)
+  const bool quad = c->g.nx % 4 == 0 && c->esz == 4;
+  const dim3 gridq((c->g.nx / 4 + 31) / 32, (c->g.ny + 7) / 8);
   Args2<T> a = args2<T>(c);
   a.t0 = c->pulse.t0;
   a.tau = c->pulse.tau;
@@ -318,11 +535,21 @@ rketd_status step2(rketd_ctx2d* c, int64_t nsteps) {
   for (int64_t s = 0; s < nsteps; ++s) {
     a.t = (double)(c->step + 1) * c->g.dt;
     if (c->g.pol == RKETD_TMZ) {
-      k2_tm_h<T><<<grid, block, 0, c->stream>>>(a);
-      k2_tm_e<T><<<grid, block, 0, c->stream>>>(a);
+      if (quad) {
+        k2v_tm_h<T><<<gridq, block, 0, c->stream>>>(a);
+        k2v_tm_e<T><<<gridq, block, 0, c->stream>>>(a);
+      } else {
+        k2_tm_h<T><<<grid, block, 0, c->stream>>>(a);
+        k2_tm_e<T><<<grid, block, 0, c->stream>>>(a);
+      }
     } else {
-      k2_te_h<T><<<grid, block, 0, c->stream>>>(a);
-      k2_te_e<T><<<grid, block, 0, c->stream>>>(a);
+      if (quad) {
+        k2v_te_h<T><<<gridq, block, 0, c->stream>>>(a);
+        k2v_te_e<T><<<gridq, block, 0, c->stream>>>(a);
+      } else {
+        k2_te_h<T><<<grid, block, 0, c->stream>>>(a);
+        k2_te_e<T><<<grid, block, 0, c->stream>>>(a);
+      }
     }
     c->launches += 2;
     const int pos = (int)(c->step % c->B);

@@ -20,10 +20,11 @@ TOL = {"f64": 1e-12, "f32": 2e-4}
 GROUPS = {"tm": (("Ez",), ("Hx", "Hy"), ("Jz",)), "te": (("Ex", "Ey"), ("Hz",), ("Jx", "Jy"))}
 
 
-def _ragged(pol, periodic=False):
-    """Odd sizes, Mur (or periodic) x, three materials in blobs and a stripe, a random source profile,
-    probes in both halves and on the source row."""
-    nx, ny = 37, 53
+def _ragged(pol, periodic=False, nx=37):
+    """Odd sizes (nx = 37: the one-cell kernels; nx = 36: the four-cells-per-thread kernels), Mur (or
+    periodic) x, three materials in blobs and a stripe, a random source profile, probes in both halves
+    and on the source row."""
+    ny = 53
     d = 300e-6
     dt = wl.dt_for_courant(d, 0.5)
     j, i = np.mgrid[0:ny, 0:nx]
@@ -60,6 +61,7 @@ def _oblique(pol):
 
 
 CASES = {"ragged": lambda pol: _ragged(pol), "ragged_periodic": lambda pol: _ragged(pol, True),
+         "quad": lambda pol: _ragged(pol, nx=36), "quad_periodic": lambda pol: _ragged(pol, True, nx=36),
          "oblique": _oblique, "normal": lambda pol: wl.slab_2d(4, 400, pol, mode=0, steps=1500, d=75e-6)}
 
 
