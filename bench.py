@@ -886,7 +886,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c1-resident-f64",
+PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c2-eq10-f32", "c2-eq10-f64",
+                 "c1-resident-f64",
                  "c1-resident-f32", "c3-batch", "c4-adjoint", "c4-adjoint-full", "c5-sphere", "2d-tm-f32",
                  "2d-te-f32", "2d-tm-f64")
 
@@ -910,6 +911,8 @@ def run_profile_case(args):
     if case.startswith("c2-"):
         _, variant, prec = case.split("-")
         slab = wl.c2_epstein(nz=args.nz, steps=args.run_steps)
+        if variant == "eq10":  # Eq. 10 read literally: the plain kernels
+            slab.scheme = wl.SCHEME_ETD2
         opts = {"variant": 2 if variant == "tiled" else 1, "use_graphs": 2}
         opts.update(parse_options(args.options))
         with rk.Context(slab, prec, options=opts) as ctx:

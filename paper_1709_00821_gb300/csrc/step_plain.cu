@@ -114,8 +114,9 @@ __device__ __forceinline__ void ej_cell(const StepArgs<T>& a, int64_t i, int s, 
 // multiples of 32 cells, so a group never straddles two slabs and its 16-byte loads are aligned).
 // One FP32 cell per thread kept too few bytes in flight to cover the HBM latency (the H kernel ran at
 // 30% of the copy bandwidth); kV cells per thread issue wide loads. A group whose cells are all plain
-// interior cells (no end cell or its Mur owner, no CPML or PML layer, no source, not the Eq. 10
-// recursion) takes the vector path; any other group updates cell by cell through h_cell / ej_cell.
+// interior cells (no end cell or its Mur owner, no CPML or PML layer, no source, and in FP32 not the
+// Eq. 10 recursion) takes the vector path; any other group updates cell by cell through h_cell /
+// ej_cell.
 // The per-cell operations are the same on both paths.
 constexpr int kV = 4;
 
@@ -173,21 +174,38 @@ __global__ void __launch_bounds__(256) k_plain_ej(const StepArgs<T> a, const int
   const int nc = a.ncpml;
   const int64_t src = a.src[s];
   // plain cells: 2 <= k <= nz - 3 (cells 1 and nz - 2 also set the Mur/PEC end cells), outside the layers
+  // (the Eq. 10 recursion takes the vector path in FP64 only: measured on a 2^24-cell slab, its FP32
+  // vector form ran the E kernel at a third of the copy rate, slower than cell by cell)
   const bool plain = k0 >= 2 && k0 + kV - 1 <= nz - 3 && !(a.bc != 0 && (k0 < nc || k0 + kV - 1 > nz - 1 - nc)) &&
-                     !(src >= k0 && src < k0 + kV) && a.Ep == nullptr;
+                     !(src >= k0 && src < k0 + kV) && (a.Ep == nullptr || sizeof(T) == 8);
   if (plain) {
     const Vec4<T> h = ldv(a.H_in + i0);
     const T hm = a.H_in[i0 - 1];
     Vec4<T> e = ldv(a.E_out + i0), g = ldv(a.J_out + i0);
     const Vec4<T> cb = ldv(a.coef[kCb] + i0), dj = ldv(a.coef[kDj] + i0), bq = ldv(a.coef[kBq] + i0),
                   cq = ldv(a.coef[kCq] + i0);
+    if (a.Ep == nullptr) {
 #pragma unroll
-    for (int q = 0; q < kV; ++q) {
-      const T dH = h.v[q] - (q ? h.v[q - 1] : hm);
-      const T en = e.v[q];
-      const T enew = fold_e(en, cb.v[q], dH, g.v[q]);
-      g.v[q] = fold_g(g.v[q], dj.v[q], bq.v[q], cq.v[q], en, enew);
-      e.v[q] = enew;
+      for (int q = 0; q < kV; ++q) {
+        const T dH = h.v[q] - (q ? h.v[q - 1] : hm);
+        const T en = e.v[q];
+        const T enew = fold_e(en, cb.v[q], dH, g.v[q]);
+        g.v[q] = fold_g(g.v[q], dj.v[q], bq.v[q], cq.v[q], en, enew);
+        e.v[q] = enew;
+      }
+    } else {  // Eq. 10: the operations of ej_cell, E^{n-1} and its weights read as vectors too
+      Vec4<T> pv = ldv(a.Ep + i0);
+      const Vec4<T> ep = ldv(a.ep + i0), gp = ldv(a.gp + i0);
+#pragma unroll
+      for (int q = 0; q < kV; ++q) {
+        const T dH = h.v[q] - (q ? h.v[q - 1] : hm);
+        const T en = e.v[q], go = g.v[q];
+        const T enew = en - fma(cb.v[q], dH, fma(-ep.v[q], pv.v[q], go));
+        g.v[q] = go + fma(gp.v[q], pv.v[q], fma(cq.v[q], enew, fma(bq.v[q], en, dj.v[q] * go)));
+        pv.v[q] = en;
+        e.v[q] = enew;
+      }
+      stv(a.Ep + i0, pv);
     }
     stv(a.E_out + i0, e);
     stv(a.J_out + i0, g);
