@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=96)
     ap.add_argument("--only-3d", action="store_true", help="run only the 3D sphere measurement (profiling)")
     ap.add_argument("--n3d", type=int, default=512)
+    ap.add_argument("--box3d", type=int, default=None,
+                    help="TF/SF box this many cells in from every face (profile case c5-sphere; default: the recipe)")
     ap.add_argument("--steps3d", type=int, default=4000)
     ap.add_argument("--batch-slabs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=20000)
@@ -635,13 +637,17 @@ def bytes_3d(p, esz=4):
 
 def traffic_record_3d(n):
     """DRAM bytes per step of the 3D staged form from the committed ncu summary
-    (profiles/k3_staged_traffic.json), valid while fdtd3d.cu is unchanged and for its grid size."""
+    (profiles/k3_staged_traffic.json), valid while fdtd3d.cu is unchanged: per work kind, the bytes
+    per tile-plane of small captures (one kind per capture, a smaller grid of the same recipe),
+    scaled to an n^3 grid by that grid's tile-planes of each kind."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "k3_staged_traffic.json")))
         sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "fdtd3d.cu"), "rb")
                              .read()).hexdigest()
-        if rec.get("fdtd3d_sha256") == sha and rec.get("cells") == n ** 3:
-            return rec
+        if rec.get("fdtd3d_sha256") == sha and str(n) in rec.get("scaled", {}):
+            out = dict(rec["scaled"][str(n)])
+            out["captured_n"] = rec["captured"]["n"]
+            return out
     except Exception:
         pass
     return None
@@ -697,8 +703,10 @@ def measure_3d(args, hbm_peak):
                          "bytes_per_cell_update": bpc, "bytes_parts": parts,
                          "traffic": trec["dram_bytes_per_step"] if trec else None,
                          "traffic_per_cell_update": trec["dram_bytes_per_cell_update"] if trec else None,
-                         "traffic_source": "ncu dram bytes of both tile kernels per step "
-                                           "(profiles/k3_staged_traffic.json)",
+                         "traffic_source": ("ncu dram bytes per tile-plane of each staged kind, captured one kind "
+                                            f"at a time on the {trec['captured_n']}^3 grid and scaled to this grid "
+                                            "by its tile-planes of each kind (profiles/k3_staged_traffic.json)")
+                                           if trec else None,
                          "note": "the unit is one step: two tile kernels run concurrently on two streams"}}
 
 
@@ -954,8 +962,9 @@ def run_profile_case(args):
             ctx.step(args.profile_steps)
             ctx.sync()
     elif case == "c5-sphere":
-        p = wl.sphere_problem(n=args.n3d, steps=args.steps3d)
+        p = wl.sphere_problem(n=args.n3d, steps=args.steps3d, box_in=args.box3d)
         with rk.Context3D(p, "f32") as ctx:
+            print(json.dumps({"n3d": args.n3d, "tile_planes_per_step": ctx.work()}), flush=True)
             ctx.step(args.steps3d)
             ctx.sync()
     print(f"profile case {case} done", flush=True)

@@ -399,6 +399,13 @@ rketd_status rketd_kernel_chunk_3d(rketd_ctx3d* ctx, int32_t k_chunk);
  * and plain forms. */
 rketd_status rketd_set_wait_limit_3d(rketd_ctx3d* ctx, int32_t polls);
 
+/* Work of the staged form per kind of work item, in tile-planes (32 x 8 cells of one z plane):
+ * [0] boundary tiles reaching the x and y CPML, [1] interior tiles in the middle z range, [2]
+ * interior tiles in the z CPML slabs and at the TF/SF z faces or the sheet, [3] boundary tiles
+ * reaching the x CPML only, [4] the y CPML only, [5] only TF/SF x/y faces. All 0 for the fused and
+ * plain forms. Host only. */
+rketd_status rketd_work_3d(const rketd_ctx3d* ctx, int64_t tile_planes[6]);
+
 /* As rketd_check_finite, for the 3D fields (E, H, J) and spectra. Synchronises. */
 rketd_status rketd_check_finite_3d(rketd_ctx3d* ctx);
 

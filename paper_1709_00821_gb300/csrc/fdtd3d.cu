@@ -1236,6 +1236,7 @@ struct rketd_ctx3d {
   int64_t step = 0;
   int64_t launches = 0;
   int wait_limit = kWaitLimit;
+  int64_t tile_planes[6] = {};  // staged form: planes of 32 x kTY tiles per work kind (kModeGen .. kModeGenF)
   ~rketd_ctx3d() {
     for (void* p : allocs) cudaFree(p);
     if (fork) cudaEventDestroy(fork);
@@ -1423,6 +1424,17 @@ rketd_status plan_items3(rketd_ctx3d* c) {
       for (const int2 t : outer[kind]) gen[kind].push_back(make_int4(t.x, t.y, kb, std::min(kb + kcg, nz)));
   c->n_mid = (int)mid.size();
   c->n_zc = (int)zc.size();
+  auto planes = [](const std::vector<int4>& v) {
+    int64_t n = 0;
+    for (const int4& t : v) n += t.w - t.z;
+    return n;
+  };
+  c->tile_planes[kModeMid] = planes(mid);
+  c->tile_planes[kModeZc] = planes(zc);
+  c->tile_planes[kModeGen] = planes(gen[0]);
+  c->tile_planes[kModeGenX] = planes(gen[1]);
+  c->tile_planes[kModeGenY] = planes(gen[2]);
+  c->tile_planes[kModeGenF] = planes(gen[3]);
   std::vector<int4> all(mid);
   all.insert(all.end(), zc.begin(), zc.end());
   for (int kind = 0; kind < 4; ++kind) {
@@ -1826,6 +1838,12 @@ rketd_status rketd_get_spectra_3d(rketd_ctx3d* c, double* re, double* im) {
   CK3(cudaMemcpyAsync(re, c->Xtmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
   CK3(cudaMemcpyAsync(im, c->Xtmp + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "spectra");
   return check3(c);
+}
+
+rketd_status rketd_work_3d(const rketd_ctx3d* c, int64_t tile_planes[6]) {
+  if (!c || !tile_planes) return fail3(RKETD_EINVAL, "NULL argument");
+  for (int k = 0; k < 6; ++k) tile_planes[k] = c->tile_planes[k];
+  return RKETD_OK;
 }
 
 rketd_status rketd_set_wait_limit_3d(rketd_ctx3d* c, int32_t polls) {

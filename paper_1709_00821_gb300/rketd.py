@@ -120,6 +120,7 @@ _SIGS = {
     "rketd_sync_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
     "rketd_set_wait_limit_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_work_3d": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "rketd_check_finite_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_create_2d": (ctypes.c_int, [ctypes.POINTER(Grid2D), ctypes.c_void_p, ctypes.c_int32, _dp, _dp, _dp,
@@ -477,10 +478,19 @@ class Context3D:
         """Raises RketdError (RKETD_ENUMERIC) if a field or spectrum holds NaN or Inf."""
         _check(lib().rketd_check_finite_3d(self.h))
 
+    def work(self) -> dict:
+        """Tile-planes of each staged work kind (the kinds of the k3_staged kernel's MODE)."""
+        v = np.zeros(6, np.int64)
+        _check(lib().rketd_work_3d(self.h, v.ctypes.data_as(_i64p)))
+        return {name: int(v[k]) for k, name in enumerate(STAGED_KINDS_3D)}
+
     def set_wait_limit(self, polls: int):
         """Test hook: polls of the staged form's compute-path copy waits (< 0: the default)."""
         _check(lib().rketd_set_wait_limit_3d(self.h, int(polls)))
 
+
+# work kinds of the 3D staged form, in the order of its kernel's MODE template argument
+STAGED_KINDS_3D = ("boundary_xy", "interior_mid", "interior_zc", "boundary_x", "boundary_y", "boundary_faces")
 
 FIELDS_2D = {"tm": ("Ez", "Hx", "Hy", "Jz"), "te": ("Ex", "Ey", "Hz", "Jx", "Jy")}
 RKETD_TMZ, RKETD_TEZ = 0, 1

@@ -323,14 +323,16 @@ def sphere_materials(nx: int, ny: int, nz: int, center, radius: float, index: in
 
 
 def sphere_problem(n: int = 512, steps: int = 4000, radius: Optional[float] = None, npml: int = 16,
-                   nfreq: int = 200) -> Grid3D:
+                   nfreq: int = 200, box_in: Optional[int] = None) -> Grid3D:
     """Config of the 3D scale-up: Drude sphere (wp = 2pi*40 GHz, nu = 2e10) at the grid centre,
     d = 100 um, Courant 0.5 (c dt/d), CPML on all faces, TF/SF box 24*n/512 cells in from every
-    face, Ex-polarised plane wave along +z (Eq. 15, tau = 15 dt), probes on the axis in the
-    scattered-field region before and after the box."""
+    face (box_in cells if given), Ex-polarised plane wave along +z (Eq. 15, tau = 15 dt), probes on
+    the axis in the scattered-field region before and after the box."""
     sp = c5_sphere(n=n, steps=steps, radius=radius, cpml=npml, nfreq=nfreq)
     mat = sphere_materials(n, n, n, sp.center, sp.radius, 1)
     lo, hi = sp.tfsf_lo, sp.tfsf_hi
+    if box_in is not None:
+        lo, hi = box_in, n - 1 - box_in
     return Grid3D(n, n, n, sp.d, sp.dt, mat, np.array([0.0, sp.wp2]), np.array([0.0, sp.nu]), False, npml, True,
                   (lo, hi, lo, hi, lo, hi), -1, sp.src_tau, sp.src_t0, sp.probes, sp.freq_hz, steps)
 
