@@ -624,6 +624,10 @@ struct Col3 {
   int sg_hz;                 // -1 at j = j0-1, +1 at j = j1, else 0 (Hz faces)
   int sg_ez;                 // -1 at i = i0, +1 at i = i1 when j in [j0, j1], else 0 (Ez faces)
   int zx, zy;                // compact zone indices
+  // 32-bit offsets of the cell's CPML memories in plane 0 (x-derivative [k][j][Z], y-derivative
+  // [k][Z][i]) and in zone 0 (z-derivative [Z][j][i]); a plane or zone adds a fixed stride. The
+  // staged form is used only where every memory array has fewer than 2^31 entries.
+  int xo, yo, zo;
 };
 
 template <typename T>
@@ -647,6 +651,9 @@ __device__ __forceinline__ Col3 col3(const Args3<T>& a, int i, int j) {
   c.tf_hz_i = ti;
   c.sg_hz = (j == a.j0 - 1) ? -1 : (j == a.j1 ? 1 : 0);
   c.sg_ez = (a.tfsf && j >= a.j0 && j <= a.j1) ? (i == a.i0 ? -1 : (i == a.i1 ? 1 : 0)) : 0;
+  c.xo = j * a.Z + c.zx;
+  c.yo = c.zy * nx + i;
+  c.zo = j * nx + i;
   return c;
 }
 
@@ -707,6 +714,14 @@ __device__ __forceinline__ void plane_facts(const Args3<T>& a, int z, PlaneS<T>*
   p->f = f;
 }
 
+// A plane's facts as the update functions see them: the flags in a register (tested many times
+// per cell), the rest read from the plane's shared-memory record where a flag asks for it.
+template <typename T>
+struct PlaneR {
+  unsigned f;
+  const PlaneS<T>* s;
+};
+
 // CPML stretch with the coefficients (db = b - 1, c, 1/kappa) and the old memory value given
 // (stretch() once its flag is known to be set)
 template <typename T>
@@ -722,13 +737,16 @@ __device__ __forceinline__ T stretch_c(T db, T cc, T ki, T dv, T psi, T* pout) {
 template <typename T>
 struct Pre3 {
   T h[6], e[6];
+  int ox, oy, oz;  // the cell's offsets into the x-, y- and z-derivative memories in this plane
 };
 
 template <bool XC, bool YC, bool ESIDE, typename T>
-__device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int i, int j, int z, int zz, unsigned hmask,
-                                          Pre3<T>& v) {
+__device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int z, int zz, unsigned hmask, Pre3<T>& v) {
+  v.oz = zz * (a.nx * a.ny) + c.zo;
+  if constexpr (XC) v.ox = z * (a.ny * a.Z) + c.xo;
+  if constexpr (YC) v.oy = z * (a.Z * a.nx) + c.yo;
   if (zz >= 0) {
-    const int64_t o = zz_off(a, i, j, zz);
+    const int o = v.oz;
     if (hmask & 2u) v.h[1] = __ldg(a.psiH[1] + o);
     if (hmask & 4u) v.h[2] = __ldg(a.psiH[2] + o);
     if constexpr (ESIDE) {
@@ -740,7 +758,7 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
   }
   if constexpr (XC) {
     if (c.zx >= 0) {
-      const int64_t o = zx_off(a, j, z, c.zx);
+      const int o = v.ox;
       if (hmask & 8u) v.h[3] = __ldg(a.psiH[3] + o);
       if (hmask & 16u) v.h[4] = __ldg(a.psiH[4] + o);
       if constexpr (ESIDE) {
@@ -751,7 +769,7 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
   }
   if constexpr (YC) {
     if (c.zy >= 0) {
-      const int64_t o = zy_off(a, i, z, c.zy);
+      const int o = v.oy;
       if (hmask & 1u) v.h[0] = __ldg(a.psiH[0] + o);
       if (hmask & 32u) v.h[5] = __ldg(a.psiH[5] + o);
       if constexpr (ESIDE) {
@@ -768,7 +786,7 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
 // compile time the terms its cells cannot meet: the x or y CPML with the x or y domain edges, the
 // z CPML, the TF/SF x/y faces.
 template <int MODE, typename T>
-__device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneS<T>& p, const Pre3<T>& v,
+__device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, const PlaneR<T> p, const Pre3<T>& v,
                                   int i, int j, int k, T h, T ez_jp, T ez, T ey_kp, T ey, bool own) {
   using K = Kind3<MODE>;
   if (!(p.f & kPVk)) return h;
@@ -778,18 +796,18 @@ __device__ __forceinline__ T hx_s(const Args3<T>& a, const Col3& c, const T* Y, 
   T cz = ey_kp - ey;
   if constexpr (K::yc)
     if (c.fyH) {
-      const int64_t o = zy_off(a, i, k, c.zy);
+      const int o = v.oy;
       cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[0], own ? a.opsiH[0] + o : nullptr);
     }
   if (K::zc && (p.f & kPFzH)) {
-    const int64_t o = zz_off(a, i, j, p.zz);
-    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[1], own ? a.opsiH[1] + o : nullptr);
+    const int o = v.oz;
+    cz = stretch_c(p.s->zb[0], p.s->zc[0], p.s->zk[0], cz, v.h[1], own ? a.opsiH[1] + o : nullptr);
   }
   return fma(-a.S, cy - cz, h);
 }
 
 template <int MODE, typename T>
-__device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneS<T>& p, const Pre3<T>& v,
+__device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, const PlaneR<T> p, const Pre3<T>& v,
                                   int i, int j, int k, T h, T ex_kp, T ex, T ez_ip, T ez, bool own) {
   using K = Kind3<MODE>;
   if (!(p.f & kPVk)) return h;
@@ -798,21 +816,21 @@ __device__ __forceinline__ T hy_s(const Args3<T>& a, const Col3& c, const T* X, 
   T cz = ex_kp - ex;
   T cx = ez_ip - ez;
   if (K::zc && (p.f & kPFzH)) {
-    const int64_t o = zz_off(a, i, j, p.zz);
-    cz = stretch_c(p.zb[0], p.zc[0], p.zk[0], cz, v.h[2], own ? a.opsiH[2] + o : nullptr);
+    const int o = v.oz;
+    cz = stretch_c(p.s->zb[0], p.s->zc[0], p.s->zk[0], cz, v.h[2], own ? a.opsiH[2] + o : nullptr);
   }
   if constexpr (K::xc)
     if (c.fxH) {
-      const int64_t o = zx_off(a, j, k, c.zx);
+      const int o = v.ox;
       cx = stretch_c(X[0], X[1], X[2], cx, v.h[3], own ? a.opsiH[3] + o : nullptr);
     }
   T r = fma(-a.S, cz - cx, h);
-  if (c.tf_xy && (p.f & (kPHyP | kPHyM))) r = fma((p.f & kPHyP) ? a.S : -a.S, p.ei_hy, r);
+  if (c.tf_xy && (p.f & (kPHyP | kPHyM))) r = fma((p.f & kPHyP) ? a.S : -a.S, p.s->ei_hy, r);
   return r;
 }
 
 template <int MODE, typename T>
-__device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
+__device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneR<T> p,
                                   const Pre3<T>& v, int i, int j, int k, T h, T ey_ip, T ey, T ex_jp, T ex, bool own) {
   using K = Kind3<MODE>;
   if constexpr (K::interior) {
@@ -826,23 +844,23 @@ __device__ __forceinline__ T hz_s(const Args3<T>& a, const Col3& c, const T* X, 
     T cy = ex_jp - ex;
     if constexpr (K::xc)
       if (c.fxH) {
-        const int64_t o = zx_off(a, j, k, c.zx);
+        const int o = v.ox;
         cx = stretch_c(X[0], X[1], X[2], cx, v.h[4], own ? a.opsiH[4] + o : nullptr);
       }
     if constexpr (K::yc)
       if (c.fyH) {
-        const int64_t o = zy_off(a, i, k, c.zy);
+        const int o = v.oy;
         cy = stretch_c(Y[0], Y[1], Y[2], cy, v.h[5], own ? a.opsiH[5] + o : nullptr);
       }
     T r = fma(-a.S, cx - cy, h);
-    if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) r = fma(c.sg_hz > 0 ? a.S : -a.S, p.ei_hz, r);
+    if (c.tf_hz_i && c.sg_hz && (p.f & kPTfHz)) r = fma(c.sg_hz > 0 ? a.S : -a.S, p.s->ei_hz, r);
     return r;
   }
 }
 
 // E and J of one cell; returns the new Ex. The CPML memories of E are updated in place.
 template <int MODE, typename T>
-__device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneS<T>& p,
+__device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, const T* Y, const PlaneR<T> p,
                                  const Pre3<T>& v, int i, int j, int k, int64_t ci, T ex, T ey, T ez, int mb, T hx, T hy,
                                  T hz, T hx_jm, T hz_jm, T hy_im, T hz_im, T hx_km, T hy_km, T srcv) {
   using K = Kind3<MODE>;
@@ -852,27 +870,27 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
     T cy = hz - hz_jm, cz = hy - hy_km;
     if constexpr (K::yc)
       if (c.fyE) {
-        T* q = a.psiE[0] + zy_off(a, i, k, c.zy);
+        T* q = a.psiE[0] + v.oy;
         cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[0], q);
       }
     if (K::zc && (p.f & kPFzE)) {
-      T* q = a.psiE[1] + zz_off(a, i, j, p.zz);
-      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[1], q);
+      T* q = a.psiE[1] + v.oz;
+      cz = stretch_c<T>(p.s->zb[1], p.s->zc[1], p.s->zk[1], cz, v.e[1], q);
     }
     ex = e_update(a.m, mb & 3, ex, cy - cz, a.Jx + ci);
-    if (c.tf_xy && (p.f & (kPExP | kPExM))) ex = fma((p.f & kPExP) ? a.S : -a.S, p.hi_ex, ex);
+    if (c.tf_xy && (p.f & (kPExP | kPExM))) ex = fma((p.f & kPExP) ? a.S : -a.S, p.s->hi_ex, ex);
   }
   if (p.f & kPSheet) ex = ex + srcv;
   a.oEx[ci] = ex;
   if (zin && (!edges || c.ey_xy)) {
     T cz = hx - hx_km, cx = hz - hz_im;
     if (K::zc && (p.f & kPFzE)) {
-      T* q = a.psiE[2] + zz_off(a, i, j, p.zz);
-      cz = stretch_c<T>(p.zb[1], p.zc[1], p.zk[1], cz, v.e[2], q);
+      T* q = a.psiE[2] + v.oz;
+      cz = stretch_c<T>(p.s->zb[1], p.s->zc[1], p.s->zk[1], cz, v.e[2], q);
     }
     if constexpr (K::xc)
       if (c.fxE) {
-        T* q = a.psiE[3] + zx_off(a, j, k, c.zx);
+        T* q = a.psiE[3] + v.ox;
         cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[3], q);
       }
     ey = e_update(a.m, (mb >> 2) & 3, ey, cz - cx, a.Jy + ci);
@@ -882,17 +900,17 @@ __device__ __forceinline__ T e_s(const Args3<T>& a, const Col3& c, const T* X, c
     T cx = hy - hy_im, cy = hx - hx_jm;
     if constexpr (K::xc)
       if (c.fxE) {
-        T* q = a.psiE[4] + zx_off(a, j, k, c.zx);
+        T* q = a.psiE[4] + v.ox;
         cx = stretch_c<T>(X[4], X[5], X[6], cx, v.e[4], q);
       }
     if constexpr (K::yc)
       if (c.fyE) {
-        T* q = a.psiE[5] + zy_off(a, i, k, c.zy);
+        T* q = a.psiE[5] + v.oy;
         cy = stretch_c<T>(Y[4], Y[5], Y[6], cy, v.e[5], q);
       }
     ez = e_update(a.m, (mb >> 4) & 3, ez, cx - cy, a.Jz + ci);
     if constexpr (!K::interior)
-      if (c.sg_ez && (p.f & kPTfEz)) ez = fma(c.sg_ez < 0 ? -a.S : a.S, p.hi_ez, ez);
+      if (c.sg_ez && (p.f & kPTfEz)) ez = fma(c.sg_ez < 0 ? -a.S : a.S, p.s->hi_ez, ez);
   }
   a.oEz[ci] = ez;
   return ex;
@@ -1031,11 +1049,11 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     if constexpr (MODE != kModeMid) {
       if (z >= 0) {
         if (act)
-          prefetch3<K::xc, K::yc, true>(a, cc, i, j, z, zz, 0x7fu, pv);
+          prefetch3<K::xc, K::yc, true>(a, cc, z, zz, 0x7fu, pv);
         else if (w == kTY && q > 0) {
-          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, false>(a, cc, i0 + lane, j0 - 1, z, zz, 0x33u, pv);
+          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, false>(a, cc, z, zz, 0x33u, pv);
           if (lane < kTY && i0 > 0 && j0 + lane < ny)
-            prefetch3<K::xc, K::yc, false>(a, cc2, i0 - 1, j0 + lane, z, zz, 0x3cu, pc);
+            prefetch3<K::xc, K::yc, false>(a, cc2, z, zz, 0x3cu, pc);
         }
       }
     }
@@ -1043,7 +1061,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1, a.wait_limit);
     const T* P0 = plane(q);
     const T* P1 = plane(q + 1);
-    const PlaneS<T>& pf = *facts(q);
+    const PlaneR<T> pf{facts(q)->f, facts(q)};
     T* H0 = hn + (q & 1) * 3 * St::hn;  // new Hx, Hy, Hz of plane z on the [i0-1, i0+32) x [j0-1, j0+kTY) tile
     T hx = T(0), hy = T(0), hz = T(0);
     // lean plane: interior-column tile and z clear of the z CPML, the TF/SF z faces and the
@@ -1608,9 +1626,13 @@ rketd_status rketd_create_3d(const rketd_grid3d* g, const uint8_t* mat, int32_t 
   if (g->prec != RKETD_F32 && g->prec != RKETD_F64) return fail3(RKETD_EINVAL, "prec must be F32 or F64");
   if (g->variant < 0 || g->variant > 3)
     return fail3(RKETD_EINVAL, "variant must be 0 (auto), 1 (plain), 2 (fused) or 3 (staged)");
-  const bool can_stage = !g->periodic_xy && g->nx % 16 == 0;
+  // staged form: CPML on every face, 16-byte aligned rows, CPML memory offsets within 32 bits
+  const int64_t zw = 2 * ((int64_t)std::max(g->npml, 0) + 1), lim = int64_t(1) << 31;
+  const bool can_stage = !g->periodic_xy && g->nx % 16 == 0 && (int64_t)g->nz * g->ny * zw < lim &&
+                         (int64_t)g->nz * zw * g->nx < lim && zw * g->ny * g->nx < lim;
   if (g->variant == 3 && !can_stage)
-    return fail3(RKETD_EUNSUPPORTED, "the staged form needs CPML on every face and nx a multiple of 16");
+    return fail3(RKETD_EUNSUPPORTED,
+                 "the staged form needs CPML on every face, nx a multiple of 16 and CPML memories of < 2^31 entries");
   const double S = g->dt / (g->d * std::sqrt(kMu0 * kEps0));
   if (!(S <= 1.0 / std::sqrt(3.0))) return fail3(RKETD_ECOURANT, "3D Courant number c dt/d exceeds 1/sqrt(3)");
   if (n_mat < 1 || n_mat > kMat) return fail3(RKETD_EINVAL, "n_mat must be 1..4 (entry 0 is vacuum)");
