@@ -347,8 +347,9 @@ typedef struct {
                             structure: an H kernel and an E+J kernel per step, fields in place),
                             2 = fused (one kernel per step, step-n state in, step-n+1 state out:
                             twice the E/H memory), 3 = staged (fused, with the step-n planes
-                            brought into shared memory by TMA copies; CPML on every face and
-                            nx a multiple of 16, else RKETD_EUNSUPPORTED) */
+                            brought into shared memory by TMA copies; CPML on every face,
+                            nx a multiple of 16 and each CPML memory array under 2^31 entries,
+                            else RKETD_EUNSUPPORTED) */
 } rketd_grid3d;
 
 typedef struct rketd_ctx3d rketd_ctx3d;
