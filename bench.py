@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=96)
     ap.add_argument("--only-3d", action="store_true", help="run only the 3D sphere measurement (profiling)")
     ap.add_argument("--n3d", type=int, default=512)
+    ap.add_argument("--kc3d", type=int, default=0, help="planes per 3D work item (0 = the library default)")
     ap.add_argument("--box3d", type=int, default=None,
                     help="TF/SF box this many cells in from every face (profile case c5-sphere; default: the recipe)")
     ap.add_argument("--steps3d", type=int, default=4000)
@@ -665,7 +666,7 @@ def measure_3d(args, hbm_peak):
     p = wl.sphere_problem(n=args.n3d, steps=args.steps3d)
     cells = p.nx * p.ny * p.nz
     bpc, parts = bytes_3d(p)
-    with rk.Context3D(p, "f32") as ctx:
+    with rk.Context3D(p, "f32", k_chunk=args.kc3d or None) as ctx:
         ctx.step(20)
         ctx.sync()
         ctx.reset()
@@ -963,7 +964,7 @@ def run_profile_case(args):
             ctx.sync()
     elif case == "c5-sphere":
         p = wl.sphere_problem(n=args.n3d, steps=args.steps3d, box_in=args.box3d)
-        with rk.Context3D(p, "f32") as ctx:
+        with rk.Context3D(p, "f32", k_chunk=args.kc3d or None) as ctx:
             print(json.dumps({"n3d": args.n3d, "tile_planes_per_step": ctx.work()}), flush=True)
             ctx.step(args.steps3d)
             ctx.sync()

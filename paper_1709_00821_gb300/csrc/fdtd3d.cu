@@ -79,6 +79,9 @@ struct Args3 {
   T* series;
   int series_len, series_pos;
   int wait_limit;  // polls of the staged form's compute-path copy waits (a test hook may lower it)
+  // staged form: facts of planes -1 .. nz of this step (PlaneS records, Stage3::pl_bytes apart),
+  // written by k3_facts before the step's tile kernels
+  unsigned char* ftab;
 };
 
 __device__ __forceinline__ int64_t idx3(int i, int j, int k, int nx, int ny) {
@@ -519,6 +522,7 @@ __global__ void __launch_bounds__(256) k3_fused(const Args3<T> a) {
 #ifndef RKETD_3D_MINB
 #define RKETD_3D_MINB 0  // 0: resident blocks per SM that the shared memory allows (4 FP32, 2 FP64)
 #endif
+
 constexpr int kTY = RKETD_3D_TY;         // compute warps (rows) per block
 constexpr int kStages = RKETD_3D_STAGES;  // planes in the copy ring (>= 3)
 static_assert(kTY >= 1 && kTY <= 32 && kStages >= 3, "staged form shape");
@@ -606,6 +610,15 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
           smem_u32(dst)),
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
+}
+
+// untiled bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global
+// to shared memory, completing on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 template <typename T>
@@ -740,15 +753,15 @@ struct Pre3 {
   int ox, oy, oz;  // the cell's offsets into the x-, y- and z-derivative memories in this plane
 };
 
-template <bool XC, bool YC, bool ESIDE, typename T>
+template <bool XC, bool YC, bool HSIDE, bool ESIDE, typename T>
 __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int z, int zz, unsigned hmask, Pre3<T>& v) {
   v.oz = zz * (a.nx * a.ny) + c.zo;
   if constexpr (XC) v.ox = z * (a.ny * a.Z) + c.xo;
   if constexpr (YC) v.oy = z * (a.Z * a.nx) + c.yo;
   if (zz >= 0) {
     const int o = v.oz;
-    if (hmask & 2u) v.h[1] = __ldg(a.psiH[1] + o);
-    if (hmask & 4u) v.h[2] = __ldg(a.psiH[2] + o);
+    if (HSIDE && (hmask & 2u)) v.h[1] = __ldg(a.psiH[1] + o);
+    if (HSIDE && (hmask & 4u)) v.h[2] = __ldg(a.psiH[2] + o);
     if constexpr (ESIDE) {
       if (hmask & 64u) {
         v.e[1] = a.psiE[1][o];
@@ -759,8 +772,8 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
   if constexpr (XC) {
     if (c.zx >= 0) {
       const int o = v.ox;
-      if (hmask & 8u) v.h[3] = __ldg(a.psiH[3] + o);
-      if (hmask & 16u) v.h[4] = __ldg(a.psiH[4] + o);
+      if (HSIDE && (hmask & 8u)) v.h[3] = __ldg(a.psiH[3] + o);
+      if (HSIDE && (hmask & 16u)) v.h[4] = __ldg(a.psiH[4] + o);
       if constexpr (ESIDE) {
         v.e[3] = a.psiE[3][o];
         v.e[4] = a.psiE[4][o];
@@ -770,8 +783,8 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
   if constexpr (YC) {
     if (c.zy >= 0) {
       const int o = v.oy;
-      if (hmask & 1u) v.h[0] = __ldg(a.psiH[0] + o);
-      if (hmask & 32u) v.h[5] = __ldg(a.psiH[5] + o);
+      if (HSIDE && (hmask & 1u)) v.h[0] = __ldg(a.psiH[0] + o);
+      if (HSIDE && (hmask & 32u)) v.h[5] = __ldg(a.psiH[5] + o);
       if constexpr (ESIDE) {
         v.e[0] = a.psiE[0][o];
         v.e[5] = a.psiE[5][o];
@@ -935,11 +948,13 @@ __host__ __device__ __forceinline__ bool interior_tile(int i0, int j0, int nx, i
 // and at the TF/SF z faces and the sheet. With TF/SF the kModeGen launch carries one more block
 // (blockIdx.x == n_items) that advances the incident line.
 // Resident blocks per SM the register budget is set for: the shared memory allows 4 (FP32) or
-// 2 (FP64); the general kind, which runs beside the others and needs more registers for its
-// CPML terms, is given 3 in FP32.
+// 2 (FP64). Every FP32 kind is held to 4, although the boundary kinds then spill a few bytes:
+// they are latency-bound, and the fourth block gains more than the spills cost (76.7 -> 78.5
+// Gcell/s on the 512^3 sphere). The x-and-y kind, whose few items cannot fill the GPU anyway
+// and which would spill most, keeps 3.
 template <typename T, int MODE>
 constexpr int staged_min_blocks() {
-  return RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? (Kind3<MODE>::interior ? 4 : 3) : 2);
+  return RKETD_3D_MINB ? RKETD_3D_MINB : (sizeof(T) == 4 ? (MODE == kModeGen ? 3 : 4) : 2);
 }
 
 template <typename T, int MODE>
@@ -983,8 +998,9 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     const int s = q % kStages;
     unsigned char* dst = sm + s * St::bytes;
     const int z = kb - 1 + q;
-    if constexpr (MODE != kModeMid) plane_facts(a, z, facts(q));  // published by the mbarrier arrival below
-    mbar_expect_tx(&bar[s], St::tx);
+    // the plane's facts (computed for this step by k3_facts) arrive with its copies
+    mbar_expect_tx(&bar[s], St::tx + (MODE != kModeMid ? St::pl_bytes : 0));
+    if constexpr (MODE != kModeMid) bulk_load(facts(q), a.ftab + (size_t)(z + 1) * St::pl_bytes, St::pl_bytes, &bar[s]);
     for (int f = 0; f < 6; ++f) tma_load3(dst + f * St::box * sizeof(T), &mp.f[f], i0 - 4, j0 - 1, z, &bar[s]);
     tma_load3(dst + 6 * St::box * sizeof(T), &mp.mat, i0, j0, z, &bar[s]);
   };
@@ -1039,24 +1055,17 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
   const T* Yc = ys + 8 * (lane < kTY ? lane + 1 : 0);
   T hx_km = T(0), hy_km = T(0);
   bool fail = false, bad = false;  // fail: this thread's wait gave up; bad: some thread's did
+  // CPML memories (kinds other than the middle one) run one plane ahead: the H-side loads for
+  // plane z+1 are issued as soon as plane z's H is done, the E-side ones once its E is done, so
+  // that their latency hides behind the rest of the plane and the next copy wait; issued at the
+  // top of the plane that needs them, they held every plane up by a memory round trip.
+  // pv: own cell (compute warps) or halo-row cell (halo warp); pc: halo-column cell.
+  Pre3<T> pv, pc;
+  if constexpr (MODE != kModeMid) {
+    if (kb - 1 >= 0 && act) prefetch3<K::xc, K::yc, true, false>(a, cc, kb - 1, zone(kb - 1, a.nz, a.np), 0x3fu, pv);
+  }
   for (int q = 0; q + 1 < NP; ++q) {
     const int z = kb - 1 + q;
-    // CPML memories of this plane. Boundary tiles (most cells inside the CPML) issue the loads
-    // before the waits (own cell, or the halo cells); interior tiles, where only the z CPML
-    // planes need them, load them in their non-lean branch.
-    Pre3<T> pv, pc;
-    const int zz = z >= 0 ? zone(z, a.nz, a.np) : -1;
-    if constexpr (MODE != kModeMid) {
-      if (z >= 0) {
-        if (act)
-          prefetch3<K::xc, K::yc, true>(a, cc, z, zz, 0x7fu, pv);
-        else if (w == kTY && q > 0) {
-          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, false>(a, cc, z, zz, 0x33u, pv);
-          if (lane < kTY && i0 > 0 && j0 + lane < ny)
-            prefetch3<K::xc, K::yc, false>(a, cc2, z, zz, 0x3cu, pc);
-        }
-      }
-    }
     if (q == 0) fail |= !mbar_wait(&bar[0], 0, a.wait_limit);
     fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1, a.wait_limit);
     const T* P0 = plane(q);
@@ -1113,6 +1122,20 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
         }
       }
     }
+    Pre3<T> nv, nc;  // H side of plane z+1
+    if constexpr (MODE != kModeMid) {
+      const int zn = z + 1;
+      if (q + 2 < NP) {
+        const int zzn = zone(zn, a.nz, a.np);
+        if (act)
+          prefetch3<K::xc, K::yc, true, false>(a, cc, zn, zzn, 0x3fu, nv);
+        else if (w == kTY) {
+          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, true, false>(a, cc, zn, zzn, 0x33u, nv);
+          if (lane < kTY && i0 > 0 && j0 + lane < ny)
+            prefetch3<K::xc, K::yc, true, false>(a, cc2, zn, zzn, 0x3cu, nc);
+        }
+      }
+    }
     if (__syncthreads_or(fail)) {
       bad = true;
       break;
@@ -1146,6 +1169,11 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     }
     hx_km = hx;
     hy_km = hy;
+    if constexpr (MODE != kModeMid) {
+      if (q + 2 < NP && act) prefetch3<K::xc, K::yc, false, true>(a, cc, z + 1, zone(z + 1, a.nz, a.np), 0x40u, nv);
+      pv = nv;
+      pc = nc;
+    }
   }
   if (bad && producer) {
     // report, and let the copies still in flight land before the block's memory is released
@@ -1154,6 +1182,16 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     for (int q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
       mbar_wait(&bar[q % kStages], (q / kStages) & 1, kWaitLimit);
   }
+}
+
+// The staged form's plane facts of one step (planes -1 .. nz, one thread each): computed once per
+// step here instead of by each tile's copy-issuing thread, whose table and incident-line loads
+// held up the halo warp of every boundary tile on every plane.
+template <typename T>
+__global__ void k3_facts(const Args3<T> a) {
+  const int z = (int)(blockIdx.x * blockDim.x + threadIdx.x) - 1;
+  if (z > a.nz) return;
+  plane_facts(a, z, (PlaneS<T>*)(a.ftab + (size_t)(z + 1) * Stage3<T>::pl_bytes));
 }
 
 // CPML tables: [axis][E (integer positions) / H (half positions)][db = b - 1, c, 1/kappa, flag][nmax]
@@ -1220,6 +1258,7 @@ struct rketd_ctx3d {
   Maps3<double> maps64[2];
   int* err = nullptr;
   int4* items = nullptr;  // staged form work items (tile origin, plane range), by kind
+  unsigned char* ftab = nullptr;  // staged form: plane facts of the current step (planes -1 .. nz)
   int n_mid = 0, n_zc = 0, n_gen[4] = {};  // general kinds: x and y, x only, y only, faces only
   // the boundary-tile launch runs on a high-priority side stream, overlapping the interior one
   cudaStream_t side = nullptr;
@@ -1362,6 +1401,7 @@ Args3<T> args3(rketd_ctx3d* c) {
   a.series = (T*)c->series;
   a.series_len = c->dft_block;
   a.series_pos = (int)(c->step % c->dft_block);
+  a.ftab = c->ftab;
   return a;
 }
 
@@ -1408,13 +1448,15 @@ rketd_status plan_items3(rketd_ctx3d* c) {
       }
     }
   std::vector<int4> mid, zc, gen[4];
-  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, 0, np + 1));
-  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, nz - np - 1, nz));
   // Planes of the middle range that need more than the bare update go to z-general items: the
   // TF/SF z faces (Hy at k0-1 and k1, Ex at k0 and k1), the sheet, and the plane after each Hy
   // face, because a middle item starting there would compute its first plane's k-1 neighbour
-  // (the corrected Hy of the face plane) without the correction. Consecutive ones form one item.
-  const int lo_all = np + 1, hi_all = nz - np - 1;
+  // (the corrected Hy of the face plane) without the correction. Consecutive ones form one item;
+  // a run that starts within kSlabReach planes of a z CPML slab joins that slab's item (the
+  // planes between them are bare updates, which the z-general kind also does), so that the usual
+  // TF/SF faces a few cells inside the CPML do not make items of one or two planes per tile.
+  constexpr int kSlabReach = 16;
+  int lo_all = np + 1, hi_all = nz - np - 1;
   std::vector<int> special;
   if (g.tfsf) special.insert(special.end(), {g.box[4] - 1, g.box[4], g.box[5], g.box[5] + 1});
   if (g.sheet_k >= 0) special.push_back(g.sheet_k);
@@ -1427,6 +1469,16 @@ rketd_status plan_items3(rketd_ctx3d* c) {
     if (!runs.empty() && runs.back().second == z) runs.back().second = z + 1;
     else runs.push_back({z, z + 1});
   }
+  while (!runs.empty() && runs.front().first - lo_all <= kSlabReach && runs.front().second < hi_all) {
+    lo_all = runs.front().second;
+    runs.erase(runs.begin());
+  }
+  while (!runs.empty() && hi_all - runs.back().second <= kSlabReach && runs.back().first > lo_all) {
+    hi_all = runs.back().first;
+    runs.pop_back();
+  }
+  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, 0, lo_all));
+  for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, hi_all, nz));
   for (const auto& r : runs)
     for (const int2 t : inner) zc.push_back(make_int4(t.x, t.y, r.first, r.second));
   int lo = lo_all;
@@ -1514,6 +1566,7 @@ rketd_status make_maps(rketd_ctx3d* c) {
       "staged kernel shared memory");
   CK3(cudaFuncSetAttribute(k3_staged<T, kModeGenF>, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage3<T>::smem),
       "staged kernel shared memory");
+  if (!c->alloc((void**)&c->ftab, (size_t)(g.nz + 2) * Stage3<T>::pl_bytes)) return fail3(RKETD_ENOMEM, "plane facts");
   rketd_status st = plan_items3(c);
   if (st) return st;
   int prio_lo = 0, prio_hi = 0;
@@ -1547,6 +1600,10 @@ rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
       // boundary tiles (CPML, faces: more work per cell) first, on the high-priority side
       // stream, so that they run alongside the interior tiles; joined back afterwards
       const int n_gen_all = c->n_gen[0] + c->n_gen[1] + c->n_gen[2] + c->n_gen[3];
+      if (n_gen_all + c->n_zc) {
+        k3_facts<T><<<(unsigned)((c->g.nz + 2 + 127) / 128), 128, 0, c->stream>>>(a);
+        c->launches += 1;
+      }
       const bool forked = (c->n_mid + c->n_zc) && (n_gen_all + line);
       if (forked) {
         CK3(cudaEventRecord(c->fork, c->stream), "fork");
@@ -1574,13 +1631,15 @@ rketd_status step3(rketd_ctx3d* c, int64_t nsteps) {
         k3_staged<T, kModeGenF><<<c->n_gen[3], sblock, Stage3<T>::smem, gs>>>(a, mp, gi, c->n_gen[3], c->err);
         c->launches += 1;
       }
+      // main stream: the middle items first (the side stream's boundary kinds share the GPU with
+      // them from the start), then the z-CPML slab items of the interior tiles
+      if (c->n_mid) {
+        k3_staged<T, kModeMid><<<c->n_mid, sblock, Stage3<T>::smem, c->stream>>>(a, mp, c->items, c->n_mid, c->err);
+        c->launches += 1;
+      }
       if (c->n_zc) {
         k3_staged<T, kModeZc><<<c->n_zc, sblock, Stage3<T>::smem, c->stream>>>(a, mp, c->items + c->n_mid, c->n_zc,
                                                                              c->err);
-        c->launches += 1;
-      }
-      if (c->n_mid) {
-        k3_staged<T, kModeMid><<<c->n_mid, sblock, Stage3<T>::smem, c->stream>>>(a, mp, c->items, c->n_mid, c->err);
         c->launches += 1;
       }
       if (forked) {
