@@ -1055,17 +1055,24 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
   const T* Yc = ys + 8 * (lane < kTY ? lane + 1 : 0);
   T hx_km = T(0), hy_km = T(0);
   bool fail = false, bad = false;  // fail: this thread's wait gave up; bad: some thread's did
-  // CPML memories (kinds other than the middle one) run one plane ahead: the H-side loads for
-  // plane z+1 are issued as soon as plane z's H is done, the E-side ones once its E is done, so
-  // that their latency hides behind the rest of the plane and the next copy wait; issued at the
-  // top of the plane that needs them, they held every plane up by a memory round trip.
-  // pv: own cell (compute warps) or halo-row cell (halo warp); pc: halo-column cell.
-  Pre3<T> pv, pc;
-  if constexpr (MODE != kModeMid) {
-    if (kb - 1 >= 0 && act) prefetch3<K::xc, K::yc, true, false>(a, cc, kb - 1, zone(kb - 1, a.nz, a.np), 0x3fu, pv);
-  }
   for (int q = 0; q + 1 < NP; ++q) {
     const int z = kb - 1 + q;
+    // CPML memories of this plane (kinds other than the middle one), loaded before the copy wait:
+    // own cell (compute warps), or the halo-row (pv) and halo-column (pc) cells (halo warp).
+    // Loading them a plane ahead held more registers live and measured slower.
+    Pre3<T> pv, pc;
+    if constexpr (MODE != kModeMid) {
+      const int zz = z >= 0 ? zone(z, a.nz, a.np) : -1;
+      if (z >= 0) {
+        if (act)
+          prefetch3<K::xc, K::yc, true, true>(a, cc, z, zz, 0x7fu, pv);
+        else if (w == kTY && q > 0) {
+          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, true, false>(a, cc, z, zz, 0x33u, pv);
+          if (lane < kTY && i0 > 0 && j0 + lane < ny)
+            prefetch3<K::xc, K::yc, true, false>(a, cc2, z, zz, 0x3cu, pc);
+        }
+      }
+    }
     if (q == 0) fail |= !mbar_wait(&bar[0], 0, a.wait_limit);
     fail |= !mbar_wait(&bar[(q + 1) % kStages], ((q + 1) / kStages) & 1, a.wait_limit);
     const T* P0 = plane(q);
@@ -1122,20 +1129,6 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
         }
       }
     }
-    Pre3<T> nv, nc;  // H side of plane z+1
-    if constexpr (MODE != kModeMid) {
-      const int zn = z + 1;
-      if (q + 2 < NP) {
-        const int zzn = zone(zn, a.nz, a.np);
-        if (act)
-          prefetch3<K::xc, K::yc, true, false>(a, cc, zn, zzn, 0x3fu, nv);
-        else if (w == kTY) {
-          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, true, false>(a, cc, zn, zzn, 0x33u, nv);
-          if (lane < kTY && i0 > 0 && j0 + lane < ny)
-            prefetch3<K::xc, K::yc, true, false>(a, cc2, zn, zzn, 0x3cu, nc);
-        }
-      }
-    }
     if (__syncthreads_or(fail)) {
       bad = true;
       break;
@@ -1169,11 +1162,6 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
     }
     hx_km = hx;
     hy_km = hy;
-    if constexpr (MODE != kModeMid) {
-      if (q + 2 < NP && act) prefetch3<K::xc, K::yc, false, true>(a, cc, z + 1, zone(z + 1, a.nz, a.np), 0x40u, nv);
-      pv = nv;
-      pc = nc;
-    }
   }
   if (bad && producer) {
     // report, and let the copies still in flight land before the block's memory is released
