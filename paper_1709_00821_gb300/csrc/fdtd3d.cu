@@ -796,22 +796,26 @@ __device__ __forceinline__ void prefetch3(const Args3<T>& a, const Col3& c, int 
 #ifndef RKETD_3D_PSI_AHEAD
 #define RKETD_3D_PSI_AHEAD 1
 #endif
-// L2 prefetch of the E-side CPML memories of a compute thread's own cell in plane z (issued
-// RKETD_3D_PSI_AHEAD planes before their loads): the loads then find them in L2, without holding
-// registers or shared memory meanwhile.
+// L2 prefetch of the CPML memories (E side and the step-n H side) of a compute thread's own cell
+// in plane z, issued RKETD_3D_PSI_AHEAD planes before their loads: the loads then find them in
+// L2, without holding registers or shared memory meanwhile.
 template <bool XC, bool YC, typename T>
-__device__ __forceinline__ void l2_prefetch_epsi(const Args3<T>& a, const Col3& c, int z) {
+__device__ __forceinline__ void l2_prefetch_psi(const Args3<T>& a, const Col3& c, int z) {
   const int zz = zone(z, a.nz, a.np);
   if (zz >= 0) {
     const int oz = zz * (a.nx * a.ny) + c.zo;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[1] + oz));
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[2] + oz));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[1] + oz));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[2] + oz));
   }
   if constexpr (XC) {
     if (c.zx >= 0) {
       const int ox = z * (a.ny * a.Z) + c.xo;
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[3] + ox));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[4] + ox));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[3] + ox));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[4] + ox));
     }
   }
   if constexpr (YC) {
@@ -819,6 +823,8 @@ __device__ __forceinline__ void l2_prefetch_epsi(const Args3<T>& a, const Col3& 
       const int oy = z * (a.Z * a.nx) + c.yo;
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[0] + oy));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiE[5] + oy));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[0] + oy));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[5] + oy));
     }
   }
 }
@@ -1097,7 +1103,7 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
         if (act) {
           prefetch3<K::xc, K::yc, true, true>(a, cc, z, zz, 0x7fu, pv);
           if (RKETD_3D_PSI_AHEAD > 0 && z + RKETD_3D_PSI_AHEAD < ke)
-            l2_prefetch_epsi<K::xc, K::yc>(a, cc, z + RKETD_3D_PSI_AHEAD);
+            l2_prefetch_psi<K::xc, K::yc>(a, cc, z + RKETD_3D_PSI_AHEAD);
         }
         else if (w == kTY && q > 0) {
           if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, true, false>(a, cc, z, zz, 0x33u, pv);
