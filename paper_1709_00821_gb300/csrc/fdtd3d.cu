@@ -829,6 +829,31 @@ __device__ __forceinline__ void l2_prefetch_psi(const Args3<T>& a, const Col3& c
   }
 }
 
+// L2 prefetch of the step-n H-side CPML memories of a halo cell in plane z (mask bits as prefetch3)
+template <bool XC, bool YC, typename T>
+__device__ __forceinline__ void l2_prefetch_halo(const Args3<T>& a, const Col3& c, int z, unsigned hmask) {
+  const int zz = zone(z, a.nz, a.np);
+  if (zz >= 0) {
+    const int oz = zz * (a.nx * a.ny) + c.zo;
+    if (hmask & 2u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[1] + oz));
+    if (hmask & 4u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[2] + oz));
+  }
+  if constexpr (XC) {
+    if (c.zx >= 0) {
+      const int ox = z * (a.ny * a.Z) + c.xo;
+      if (hmask & 8u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[3] + ox));
+      if (hmask & 16u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[4] + ox));
+    }
+  }
+  if constexpr (YC) {
+    if (c.zy >= 0) {
+      const int oy = z * (a.Z * a.nx) + c.yo;
+      if (hmask & 1u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[0] + oy));
+      if (hmask & 32u) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psiH[5] + oy));
+    }
+  }
+}
+
 // The staged form's updates of one cell: the operations of hx_core .. e_cell for non-periodic
 // grids, with the per-cell facts (c), the x and y coefficient rows of the tile (X, Y: H b, c,
 // 1/kappa, flag, then E) and the plane's facts (p). The kind of work item (Kind3) leaves out at
@@ -1106,9 +1131,15 @@ __global__ void __launch_bounds__(32 * (kTY + 1), (staged_min_blocks<T, MODE>())
             l2_prefetch_psi<K::xc, K::yc>(a, cc, z + RKETD_3D_PSI_AHEAD);
         }
         else if (w == kTY && q > 0) {
-          if (j0 - 1 >= 0 && i0 + lane < nx) prefetch3<K::xc, K::yc, true, false>(a, cc, z, zz, 0x33u, pv);
-          if (lane < kTY && i0 > 0 && j0 + lane < ny)
+          const bool nxt = RKETD_3D_PSI_AHEAD > 0 && z + RKETD_3D_PSI_AHEAD < ke;
+          if (j0 - 1 >= 0 && i0 + lane < nx) {
+            prefetch3<K::xc, K::yc, true, false>(a, cc, z, zz, 0x33u, pv);
+            if (nxt) l2_prefetch_halo<K::xc, K::yc>(a, cc, z + RKETD_3D_PSI_AHEAD, 0x33u);
+          }
+          if (lane < kTY && i0 > 0 && j0 + lane < ny) {
             prefetch3<K::xc, K::yc, true, false>(a, cc2, z, zz, 0x3cu, pc);
+            if (nxt) l2_prefetch_halo<K::xc, K::yc>(a, cc2, z + RKETD_3D_PSI_AHEAD, 0x3cu);
+          }
         }
       }
     }
