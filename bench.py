@@ -443,6 +443,26 @@ def measure_batch(args):
     opts = ctx.options()
     ctx.close()
     del ctx
+    # the persistent variant with the same tile shape: every pass of a DFT block in one launch
+    with rk.Context(b.slabs, "f32", options={"variant": 4, "cells_per_lane": opts["cells_per_lane"],
+                                             "tb_steps": opts["tb_steps"]}) as cq:
+        def run_p():
+            cq.reset()
+            cq.step(b.steps)
+            cq.spectra_device(xr.data_ptr(), xi.data_ptr())
+
+        run_p()  # captures the graph
+        torch.cuda.synchronize()
+        lp0 = cq.launches
+        e0.record()
+        run_p()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        persistent = {"value": cu / (ms_p / 1e3) / 1e9, "ms_per_run": ms_p, "gpu_launches_per_run": cq.launches - lp0,
+                      "variant": f"persistent (options.variant 4), K={opts['cells_per_lane']}, "
+                                 f"{opts['tb_steps']} steps/pass: one launch per DFT block of "
+                                 f"{cq.options()['dft_block']} steps"}
     # plain form, all slabs per launch (one H + one E/J launch per step over every cell)
     pre = 100
     with rk.Context(b.slabs, "f32", options={"variant": 1}) as cp:
@@ -477,7 +497,8 @@ def measure_batch(args):
             "plain_slab_by_slab": {"value": cu / (ms_slab / 1e3) / 1e9, "ms_per_run": ms_slab,
                                    "measured": f"{len(pick)} sampled slabs x {pre} steps, scaled by slab count "
                                                f"and steps"},
-            "speedup_vs_slab_by_slab": ms_slab / ms, "speedup_vs_all_slabs_plain": ms_all / ms}
+            "speedup_vs_slab_by_slab": ms_slab / ms, "speedup_vs_all_slabs_plain": ms_all / ms,
+            "persistent": persistent}
 
 
 def measure_adjoint(args):
@@ -897,7 +918,7 @@ def run_ours(args):
 
 PROFILE_CASES = ("c2-tiled-f32", "c2-tiled-f64", "c2-plain-f32", "c2-plain-f64", "c2-eq10-f32", "c2-eq10-f64",
                  "c1-resident-f64",
-                 "c1-resident-f32", "c3-batch", "c4-adjoint", "c4-adjoint-full", "c5-sphere", "2d-tm-f32",
+                 "c1-resident-f32", "c3-batch", "c3-batch-persist", "c4-adjoint", "c4-adjoint-full", "c5-sphere", "2d-tm-f32",
                  "2d-te-f32", "2d-tm-f64")
 
 
@@ -941,6 +962,14 @@ def run_profile_case(args):
                                                  "use_graphs": 2}) as ctx:
             ctx.step(64)
             ctx.step(128)
+            ctx.sync()
+    elif case == "c3-batch-persist":
+        # the persistent variant on the batch: one launch of 16 passes after a one-pass warm-up
+        b = wl.c3_batch()
+        with rk.Context(b.slabs, "f32", options={"variant": 4, "cells_per_lane": 16, "tb_steps": 32,
+                                                 "use_graphs": 2}) as ctx:
+            ctx.step(32)
+            ctx.step(512 - 32)
             ctx.sync()
     elif case in ("c4-adjoint", "c4-adjoint-full"):
         full = case == "c4-adjoint-full"

@@ -114,7 +114,11 @@ typedef struct {
                            Mur-terminated slab held in the registers of one thread-block cluster (up
                            to 16 CTAs) for a whole DFT block of steps per launch, for slabs of up to
                            16384 (FP64) or 32768 (FP32) cells; RKETD_EUNSUPPORTED where it does not
-                           apply. The checkpointed forward run and the adjoint use the tiled kernels. */
+                           apply; 4 = persistent (FP32 only): the tiles of variant 2, every pass of a
+                           DFT block in one launch whose resident warps take (pass, tile) work items
+                           in order and wait (bounded) only for their slab's neighbouring tiles of
+                           the previous pass; results bitwise those of variant 2. The checkpointed
+                           forward run and the adjoint use the tiled kernels. */
   int32_t cells_per_lane;  /* K for the tiled kernel: 8, 12 or 16 (F32), 4 or 8 (F64); 0 = auto */
   int32_t tb_steps;     /* leapfrog steps per tiled pass (4..64, multiple of 4); 0 = auto */
   int32_t warps_per_block; /* warps per CTA of the tiled kernel, 1..4; 0 = auto */
@@ -173,7 +177,8 @@ rketd_status rketd_reset(rketd_ctx* ctx);
  * device-side problems surface at rketd_sync. */
 rketd_status rketd_step(rketd_ctx* ctx, int64_t nsteps);
 
-/* Waits for the stream and reports any device-side error. */
+/* Waits for the stream and reports any device-side error; RKETD_ETIMEOUT if a wait of the
+ * persistent variant gave up since the last reset. */
 rketd_status rketd_sync(rketd_ctx* ctx);
 
 /* Current step index n (fields hold E^n, H^{n-1/2}, J^n). */
@@ -298,6 +303,13 @@ rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64
 rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64_t nz, const double* wp2, const double* nu,
                                       int64_t src_cell, const rketd_pulse* pulse, int64_t n0, int64_t nsteps,
                                       void* E, void* H, void* J, void* stream);
+
+/* Persistent variant (options.variant = 4): polls of each wait of a tile for its neighbours'
+ * previous pass before it gives up (0: every wait gives up at once, a test of the failure path;
+ * < 0 restores the default of 2^22, with a 64 ns pause between polls). A wait that gives up lets
+ * the tile go on and sets the context's status word: the next rketd_sync returns RKETD_ETIMEOUT
+ * (the fields are then not valid) until rketd_reset clears it. No effect on the other variants. */
+rketd_status rketd_set_wait_limit(rketd_ctx* ctx, int32_t polls);
 
 /* Scans the state (E, H and the carried current of every slab, E^{n-1} for Eq. 10, CPML memories)
  * and the spectra for NaN or infinite values: RKETD_ENUMERIC if any is found, else RKETD_OK.

@@ -237,6 +237,26 @@ cudaError_t launch_resident(const StepArgs<T>& a, int K, int ctas, int threads, 
 // FP32 interior tiles with two cells per packed FP32x2 register (step_tb2.cu); xtra as for launch_tb
 cudaError_t launch_tb_pairs(const StepArgs<float>& a, int K, int warps_per_block, cudaStream_t st, bool xtra);
 
+// Persistent tiled step (step_persist.cu): n_pass passes of nsub steps over the whole tile list in
+// one launch. Tile list order: [0, n_main) interior, [n_main, n_main + n_xtra) interior tiles with a
+// probe or a source cell, then edge tiles (Ke cells per lane).
+struct PersistCtl {
+  int n_tiles, n_main, n_xtra;
+  int n_pass, nsub;
+  const int* dep_off;  // [n_tiles + 1]: tiles whose cells tile j reads or whose reads it overwrites
+  const int* dep_idx;
+  int* done;           // [n_tiles]: last pass finished, -1 at launch start
+  int* work;           // work-item counter, 0 at launch start
+  int* err;            // status word: 1 = a wait gave up
+  int wait_limit;      // polls per wait (<= 0: every wait gives up at once)
+};
+// Resident one-warp blocks of the persistent kernel on this device (0 if unknown).
+int persist_capacity(int K, int Ke);
+// a0 / a1: the step arguments of even / odd passes (buffers swapped), n0 and series_pos of pass 0;
+// sa_d: device room for both.
+cudaError_t launch_persist(StepArgs<float>* sa_d, const StepArgs<float>& a0, const StepArgs<float>& a1,
+                           const PersistCtl& pc, int K, int Ke, int grid, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_plain_step(const StepArgs<T>& a, const int32_t* cell_slab, int64_t n_store,
                               const int64_t* probe_index, cudaStream_t st);

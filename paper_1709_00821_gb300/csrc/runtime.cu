@@ -156,6 +156,18 @@ struct rketd_ctx {
   int n_int_xtra = 0;  // the last n_int_xtra interior tiles sample a probe or load a source cell
   int tiles_K = 0, tiles_T = 0;
 
+  // persistent variant: per tile, the neighbours it waits for (CSR), its last finished pass, the
+  // work counter, the status word and the two passes' step arguments
+  int* dep_off_d = nullptr;
+  int* dep_idx_d = nullptr;
+  int* done_d = nullptr;
+  int* work_d = nullptr;
+  int* err_d = nullptr;
+  StepArgs<float>* sa_d = nullptr;
+  int persist_grid = 0;
+  int wait_limit = 1 << 22;
+  int64_t persist_cells = 0;  // exact cells of all tiles (timing)
+
   // resident variant: cluster shape, left padding, probe list (slab cell, probe index)
   bool res_ok = false;
   int res_K = 0, res_ctas = 0, res_threads = 0, res_pl = 0;
@@ -231,6 +243,9 @@ struct rketd_ctx {
     for (void* p : allocs) cudaFree(p);
     if (tiles_d) cudaFree(tiles_d);
     if (tprobes_d) cudaFree(tprobes_d);
+    if (dep_off_d) cudaFree(dep_off_d);
+    if (dep_idx_d) cudaFree(dep_idx_d);
+    if (done_d) cudaFree(done_d);
     if (res_probes_d) cudaFree(res_probes_d);
   }
 
@@ -253,7 +268,9 @@ namespace {
 bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
 
 rketd_status check_options(const rketd_options& o, int prec) {
-  if (o.variant < 0 || o.variant > 3) return fail(RKETD_EINVAL, "options.variant must be 0, 1, 2 or 3");
+  if (o.variant < 0 || o.variant > 4) return fail(RKETD_EINVAL, "options.variant must be 0, 1, 2, 3 or 4");
+  if (o.variant == 4 && (prec != 0 || o.fp32_pairs == 2))
+    return fail(RKETD_EUNSUPPORTED, "the persistent variant runs FP32 fields with packed pairs");
   if (o.res_ctas < 0 || o.res_ctas > 16) return fail(RKETD_EINVAL, "res_ctas must be 0..16");
   if (o.res_threads < 0 || o.res_threads % 32 || o.res_threads > (prec == 1 ? 256 : 1024))
     return fail(RKETD_EINVAL, "res_threads must be a multiple of 32, at most 1024 (FP32) or 256 (FP64)");
@@ -392,6 +409,70 @@ rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* src
 }
 
 // Plans the tiles for (K, T) and uploads the lists.
+// Persistent variant: for every tile, the tiles of its slab that it must wait for before a pass
+// (those whose exact cells its loaded range reads, and those whose loaded range reads the exact
+// cells it writes, itself included), as a CSR list; the flags, counter, status word and argument
+// room of the launch; the grid (resident one-warp blocks).
+rketd_status plan_persist(rketd_ctx* c, int K, int T) {
+  const std::vector<Tile>& t = c->tiles_h;
+  const int n = (int)t.size();
+  const int Ke = edge_cells_per_lane(T);
+  struct R { int64_t l0, l1, e0, e1; int j; };
+  std::vector<std::vector<R>> by_slab(c->n_slabs);
+  int64_t cells = 0;
+  for (int j = 0; j < n; ++j) {
+    const int64_t w = 32LL * (j < c->n_interior ? K : Ke);
+    by_slab[t[j].slab].push_back({t[j].start, t[j].start + w, t[j].start + t[j].vlo, t[j].start + t[j].vhi, j});
+    cells += t[j].vhi - t[j].vlo;
+  }
+  std::vector<std::vector<int>> deps(n);
+  for (auto& v : by_slab) {
+    std::sort(v.begin(), v.end(), [](const R& x, const R& y) { return x.l0 < y.l0; });
+    const int m = (int)v.size();
+    const int64_t wmax = 32LL * std::max(K, Ke);  // widest loaded range
+    int lo = 0;
+    for (int a = 0; a < m; ++a) {
+      // only tiles whose loaded range starts within (l0 - wmax, l1) can overlap tile a
+      while (lo < m && v[lo].l0 <= v[a].l0 - wmax) ++lo;
+      for (int b = lo; b < m && v[b].l0 < v[a].l1; ++b) {
+        const bool raw = v[b].e0 < v[a].l1 && v[a].l0 < v[b].e1;  // a reads b's exact cells
+        const bool war = v[b].l0 < v[a].e1 && v[a].e0 < v[b].l1;  // b read what a writes
+        if (raw || war) deps[v[a].j].push_back(v[b].j);
+      }
+    }
+  }
+  std::vector<int> off(n + 1, 0), idx;
+  for (int j = 0; j < n; ++j) {
+    off[j + 1] = off[j] + (int)deps[j].size();
+    idx.insert(idx.end(), deps[j].begin(), deps[j].end());
+  }
+  if (c->dep_off_d) cudaFree(c->dep_off_d);
+  if (c->dep_idx_d) cudaFree(c->dep_idx_d);
+  if (c->done_d) cudaFree(c->done_d);
+  c->dep_off_d = c->dep_idx_d = c->done_d = nullptr;
+  CK(device_alloc((void**)&c->dep_off_d, sizeof(int) * (n + 1)), "tile dependencies");
+  CK(device_alloc((void**)&c->dep_idx_d, sizeof(int) * std::max<size_t>(1, idx.size())), "tile dependencies");
+  CK(device_alloc((void**)&c->done_d, sizeof(int) * std::max(1, n)), "tile flags");
+  CK(cudaMemcpy(c->dep_off_d, off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "tile dependencies");
+  if (!idx.empty())
+    CK(cudaMemcpy(c->dep_idx_d, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice), "tile dependencies");
+  if (!c->work_d) {
+    void* p = nullptr;
+    rketd_status st = c->alloc(&p, 2 * sizeof(int), "persistent counters");
+    if (st) return st;
+    c->work_d = (int*)p;
+    c->err_d = c->work_d + 1;
+    CK(cudaMemset(c->work_d, 0, 2 * sizeof(int)), "persistent counters");
+    st = c->alloc(&p, 2 * sizeof(StepArgs<float>), "persistent arguments");
+    if (st) return st;
+    c->sa_d = (StepArgs<float>*)p;
+  }
+  c->persist_grid = persist_capacity(K, Ke);
+  if (c->persist_grid <= 0) return fail(RKETD_ECUDA, "persistent step: no resident capacity");
+  c->persist_cells = cells;
+  return RKETD_OK;
+}
+
 rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   const int64_t nc = c->grid.bc != RKETD_BC_MUR1 ? c->grid.cpml_cells : 0;
   TilePlan plan;
@@ -420,6 +501,7 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   c->n_edge = plan.n_edge;
   c->tiles_K = K;
   c->tiles_T = T;
+  if (c->opt.variant == 4) return plan_persist(c, K, T);
   return RKETD_OK;
 }
 
@@ -616,6 +698,60 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       c->cur = 1 - c->cur;
       c->step += nsub;
       nsteps -= nsub;
+    } else if (c->opt.variant == 4) {
+      // persistent: every whole pass left in this DFT block (or in the call) in one launch
+      const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
+      if (c->tiles_K != K || c->tiles_T != TS || !c->done_d) {
+        rketd_status st = plan_tiles(c, K, TS);
+        if (st) return st;
+      }
+      const int nsub = (int)std::min<int64_t>({(int64_t)TS, nsteps, (int64_t)(B - pos)});
+      const int n_pass = nsub == TS ? (int)std::min<int64_t>((B - pos) / TS, nsteps / TS) : 1;
+      StepArgs<T> a0 = make_args<T>(c, c->cur, 1 - c->cur);
+      StepArgs<T> a1 = make_args<T>(c, 1 - c->cur, c->cur);
+      for (StepArgs<T>* a : {&a0, &a1}) {
+        a->nsub = nsub;
+        a->tprobes = c->tprobes_d;
+        a->tiles = c->tiles_d;
+        a->n_tiles = (int)c->tiles_h.size();
+        a->n0 = a0.n0;
+        a->series_pos = a0.series_pos;
+      }
+      PersistCtl pc{};
+      pc.n_tiles = (int)c->tiles_h.size();
+      pc.n_main = c->n_interior - c->n_int_xtra;
+      pc.n_xtra = c->n_int_xtra;
+      pc.n_pass = n_pass;
+      pc.nsub = nsub;
+      pc.dep_off = c->dep_off_d;
+      pc.dep_idx = c->dep_idx_d;
+      pc.done = c->done_d;
+      pc.work = c->work_d;
+      pc.err = c->err_d;
+      pc.wait_limit = c->wait_limit;
+      CK(cudaMemsetAsync(c->done_d, 0xff, sizeof(int) * std::max(1, pc.n_tiles), c->stream), "tile flags");
+      CK(cudaMemsetAsync(c->work_d, 0, sizeof(int), c->stream), "work counter");
+      const int grid = (int)std::min<int64_t>(c->persist_grid, ((int64_t)n_pass * pc.n_tiles + 7) / 8);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->timing) {
+        rketd_status st = timing_event(c, &e0);
+        if (!st) st = timing_event(c, &e1);
+        if (st) return st;
+        CK(cudaEventRecord(e0, c->stream), "timing event");
+      }
+      CK(launch_persist(c->sa_d, *reinterpret_cast<const StepArgs<float>*>(&a0),
+                        *reinterpret_cast<const StepArgs<float>*>(&a1), pc, K, edge_cells_per_lane(TS), grid,
+                        c->stream),
+         "persistent step");
+      c->launches += 2;
+      if (c->timing) {
+        CK(cudaEventRecord(e1, c->stream), "timing event");
+        c->t_launches += 1;
+        c->t_cells += (double)c->persist_cells * nsub * n_pass;
+      }
+      c->cur = (c->cur + n_pass) & 1;
+      c->step += (int64_t)nsub * n_pass;
+      nsteps -= (int64_t)nsub * n_pass;
     } else {
       const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
       if (c->tiles_K != K || c->tiles_T != TS) {
@@ -784,7 +920,7 @@ rketd_status validate_and_copy(rketd_ctx* c, int32_t n_slabs, const int64_t* nz,
   c->auto_variant = op.variant == 0;
   if (grid->scheme == RKETD_SCHEME_ETD2) {
     // E^{n-1} is one more carried array: the plain (one step per launch) kernels carry it
-    if (op.variant == 2 || op.variant == 3)
+    if (op.variant == 2 || op.variant == 3 || op.variant == 4)
       return fail(RKETD_EUNSUPPORTED, "the Eq. 10 recursion (ETD2) runs on the plain variant only");
     op.variant = 1;
   }
@@ -810,6 +946,7 @@ rketd_status zero_state(rketd_ctx* c) {
     CK(cudaMemsetAsync(c->Xr, 0, xb, c->stream), "memset X");
     CK(cudaMemsetAsync(c->Xi, 0, xb, c->stream), "memset X");
   }
+  if (c->err_d) CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream), "status word");
   c->cur = 0;
   c->step = 0;
   return RKETD_OK;
@@ -1073,7 +1210,8 @@ rketd_status rketd_step(rketd_ctx* c, int64_t nsteps) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   if (nsteps < 0) return fail(RKETD_EINVAL, "nsteps < 0");
   if (nsteps == 0) return RKETD_OK;
-  const bool graphs = c->opt.use_graphs != 2 && !c->timing && (c->opt.variant == 2 || c->opt.variant == 3);
+  const bool graphs =
+      c->opt.use_graphs != 2 && !c->timing && (c->opt.variant == 2 || c->opt.variant == 3 || c->opt.variant == 4);
   if (!graphs) return c->prec == RKETD_F64 ? step_impl<double>(c, nsteps) : step_impl<float>(c, nsteps);
   return step_graph(c, nsteps);
 }
@@ -1082,6 +1220,19 @@ rketd_status rketd_sync(rketd_ctx* c) {
   if (!c) return fail(RKETD_EINVAL, "NULL context");
   CK(cudaStreamSynchronize(c->stream), "stream synchronize");
   CK(cudaGetLastError(), "device error");
+  if (c->err_d) {
+    int e = 0;
+    CK(cudaMemcpy(&e, c->err_d, sizeof(int), cudaMemcpyDeviceToHost), "status word");
+    if (e) return fail(RKETD_ETIMEOUT, "a wait of the persistent step gave up; fields are not valid");
+  }
+  return RKETD_OK;
+}
+
+rketd_status rketd_set_wait_limit(rketd_ctx* c, int32_t polls) {
+  if (!c) return fail(RKETD_EINVAL, "NULL context");
+  c->wait_limit = polls < 0 ? (1 << 22) : polls;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);  // the limit is a launch argument
+  c->graphs.clear();
   return RKETD_OK;
 }
 
@@ -1337,8 +1488,10 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
   if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     st = cuda_fail(cudaGetLastError(), "autotune events");
   const int64_t nsteps = (int64_t)passes * 64;
+  // a persistent context tunes the persistent step's tile shape; any other the tiled variant's
+  const int tuned = opt0.variant == 4 ? 4 : 2;
   for (size_t i = 0; i < cands.size() && !st; ++i) {
-    c->opt.variant = 2;
+    c->opt.variant = tuned;
     c->opt.use_graphs = 2;
     c->opt.cells_per_lane = cands[i][0];
     c->opt.tb_steps = cands[i][1];
@@ -1360,7 +1513,7 @@ rketd_status rketd_autotune(rketd_ctx* c, int32_t passes) {
     }
   }
   // the resident variant, where it applies, is one more candidate
-  if (!st && c->n_slabs == 1 && c->grid.bc == RKETD_BC_MUR1 && c->grid.scheme != RKETD_SCHEME_ETD2) {
+  if (!st && tuned == 2 && c->n_slabs == 1 && c->grid.bc == RKETD_BC_MUR1 && c->grid.scheme != RKETD_SCHEME_ETD2) {
     c->opt = opt0;
     c->opt.variant = 3;
     c->opt.use_graphs = 2;
@@ -1403,7 +1556,7 @@ rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every
   if (c->grid.bc != RKETD_BC_MUR1) return fail(RKETD_EUNSUPPORTED, "the adjoint supports first-order Mur ends only");
   if (c->grid.scheme != RKETD_SCHEME_RKETD)
     return fail(RKETD_EUNSUPPORTED, "the adjoint differentiates the Eq. 11 recursion only");
-  if (c->opt.variant == 3) c->opt.variant = 2;  // the checkpointed run and the adjoint use the tiled kernels
+  if (c->opt.variant == 3 || c->opt.variant == 4) c->opt.variant = 2;  // the checkpointed run and the adjoint use the tiled kernels
   if (c->opt.variant != 2) return fail(RKETD_EUNSUPPORTED, "the adjoint runs on the tiled variant");
   const int64_t n_ckpt = (nsteps + ckpt_every - 1) / ckpt_every;
   const size_t fb = c->esz * c->n_store;

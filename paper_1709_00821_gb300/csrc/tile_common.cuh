@@ -79,14 +79,19 @@ __device__ __forceinline__ LaneProbes lane_probes(const TileProbe* list, int beg
   return r;
 }
 
-// Four consecutive values at p (16-byte aligned for float, 32 for double).
+// Four consecutive values at p (16-byte aligned for float, 32 for double). NC: through the
+// read-only (non-coherent) path, for data no thread writes during the kernel; otherwise from L2
+// (ld.global.cg), for data that other warps of the same kernel write (the persistent step).
+template <bool NC = true>
 __device__ __forceinline__ void ld4(const float* p, float* r) {
-  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 q = NC ? __ldg(reinterpret_cast<const float4*>(p)) : __ldcg(reinterpret_cast<const float4*>(p));
   r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
 }
+template <bool NC = true>
 __device__ __forceinline__ void ld4(const double* p, double* r) {
-  const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  const double2 q0 = NC ? __ldg(reinterpret_cast<const double2*>(p)) : __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 q1 =
+      NC ? __ldg(reinterpret_cast<const double2*>(p) + 1) : __ldcg(reinterpret_cast<const double2*>(p) + 1);
   r[0] = q0.x; r[1] = q0.y; r[2] = q1.x; r[3] = q1.y;
 }
 __device__ __forceinline__ void st4(float* p, const float* r) {
@@ -99,13 +104,13 @@ __device__ __forceinline__ void st4(double* p, const double* r) {
 
 // K values of slab storage `base` at slab-local cells g0 .. g0+K-1; groups of four
 // outside [0, hi) read as zero (g0 and hi are multiples of 4).
-template <typename T, int K, bool MASK>
+template <typename T, int K, bool MASK, bool NC = true>
 __device__ __forceinline__ void load_row(const T* __restrict__ base, int64_t g0, int64_t hi, T (&r)[K]) {
 #pragma unroll
   for (int v = 0; v < K / 4; ++v) {
     const int64_t g = g0 + 4 * v;
     if (!MASK || (g >= 0 && g < hi)) {
-      ld4(base + g, &r[4 * v]);
+      ld4<NC>(base + g, &r[4 * v]);
     } else {
       r[4 * v] = r[4 * v + 1] = r[4 * v + 2] = r[4 * v + 3] = T(0);
     }
@@ -189,13 +194,13 @@ __device__ __forceinline__ void put2(f2 (&r)[P], int slot, float v) {
 }
 
 
-template <int K>
+template <int K, bool NC = true>
 __device__ __forceinline__ void load_pairs(const float* __restrict__ p, f2 (&r)[K / 2], bool negate) {
   constexpr int P = K / 2;
   float t[K];
 #pragma unroll
   for (int v = 0; v < K / 4; ++v) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p) + v);
+    const float4 q = NC ? __ldg(reinterpret_cast<const float4*>(p) + v) : __ldcg(reinterpret_cast<const float4*>(p) + v);
     t[4 * v] = q.x;
     t[4 * v + 1] = q.y;
     t[4 * v + 2] = q.z;

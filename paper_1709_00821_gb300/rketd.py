@@ -120,6 +120,7 @@ _SIGS = {
     "rketd_sync_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_launch_count_3d": (ctypes.c_int64, [ctypes.c_void_p]),
     "rketd_set_wait_limit_3d": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "rketd_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_work_3d": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "rketd_check_finite_3d": (ctypes.c_int, [ctypes.c_void_p]),
     "rketd_destroy_3d": (ctypes.c_int, [ctypes.c_void_p]),
@@ -295,6 +296,10 @@ class Context:
 
     def load(self, path: str):
         _check(lib().rketd_load_state(self.h, path.encode()))
+
+    def set_wait_limit(self, polls: int):
+        """Persistent variant: polls of each neighbour wait (0: every wait gives up; < 0: default)."""
+        _check(lib().rketd_set_wait_limit(self.h, int(polls)))
 
     def autotune(self, passes: int = 8):
         _check(lib().rketd_autotune(self.h, passes))
