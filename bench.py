@@ -154,15 +154,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def tile_kernel_sha(prec):
+    """sha256 over the sources of the interior tiled kernel of a precision (its launch file and the
+    tile bodies and helpers it includes)."""
+    csrc = os.path.join(ROOT, "paper_1709_00821_gb300", "csrc")
+    names = ["step_tb2.cu" if prec == "f32" else "step_tb.cu", "tile_bodies.cuh", "tile_common.cuh"]
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(csrc, n), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(prec):
     """Per-cell-update DRAM bytes of the interior tiled kernel from the committed ncu summary
-    (profiles/tb_kernel_traffic.json), valid only while that kernel's source is unchanged."""
+    (profiles/tb_kernel_traffic.json), valid only while that kernel's sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "tb_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_1709_00821_gb300", "csrc", "step_tb2.cu" if prec == "f32" else "step_tb.cu")
     key = "step_tb2_sha256" if prec == "f32" else "step_tb_sha256"
     try:
         rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = tile_kernel_sha(prec)
         if rec.get(key) == sha and prec in rec:
             return rec[prec]["dram_bytes_per_cell_update"], rec
     except Exception:
