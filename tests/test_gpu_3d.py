@@ -98,10 +98,25 @@ def _faces():
     return p
 
 
-GRIDS3 = {"ragged16": _ragged16, "lean": _lean, "faces": _faces}
+def _wide3():
+    """The lean recipe on a grid 160 cells wide: three neighbouring interior tiles per row, with
+    plasma across the boundary between the first two and a probe in the middle z range."""
+    nx, ny, nz = 160, 40, 40
+    d = 100e-6
+    dt = wl.dt_for_courant(d, 0.5)
+    m1 = wl.sphere_materials(nx, ny, nz, (63.4, 20.3, 19.8), 8.3, 1)
+    m2 = wl.sphere_materials(nx, ny, nz, (104.2, 13.9, 26.1), 4.2, 2)
+    assert not np.any((m1 != 0) & (m2 != 0))
+    freqs = 100e9 * np.arange(1, 9, dtype=float) / 8
+    return wl.Grid3D(nx, ny, nz, d, dt, m1 | m2, np.array([0.0, (2 * math.pi * 40e9) ** 2, (2 * math.pi * 25e9) ** 2]),
+                     np.array([0.0, 2e10, 7e10]), False, 4, True, (8, 151, 6, 33, 7, 32), -1, 15 * dt, 75 * dt,
+                     [(48, 20, 5), (66, 20, 20), (100, 18, 24)], freqs, 200)
 
 
-@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces"])
+GRIDS3 = {"ragged16": _ragged16, "lean": _lean, "faces": _faces, "wide3": _wide3}
+
+
+@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces", "wide3"])
 @pytest.mark.parametrize("k_chunk", [0, 7, 45])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_staged_form_matches_the_3d_oracle(prec, k_chunk, grid):
@@ -114,7 +129,7 @@ def test_staged_form_matches_the_3d_oracle(prec, k_chunk, grid):
     print(prec, "staged", k_chunk, {k: f"{v:.2e}" for k, v in worst.items()})
 
 
-@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces"])
+@pytest.mark.parametrize("grid", ["ragged16", "lean", "faces", "wide3"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_staged_form_agrees_bitwise_with_the_plain_form(prec, grid):
     p = GRIDS3[grid]()
