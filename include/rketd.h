@@ -257,10 +257,15 @@ int64_t rketd_launch_count(const rketd_ctx* ctx);
  *                   as for rketd_create_batch_1d (slab-local cells)
  *   cpml_cells      CPML cells per end (0 for first-order Mur ends)
  *   cells_per_lane  K, a multiple of 4 in [4, 32]; tb_steps: T, a multiple of 4 in [4, 64]
+ *   end_tiles       nonzero: the plan of the tiled FP32-pair step with first-order Mur ends
+ *                   (cpml_cells 0), where slabs of more than 2 (32K - T) cells have their two
+ *                   ends held by interior-width tiles of kind 1 (the left one loads [0, 32K),
+ *                   the right one ends at round_up(nz, 4) - 1) instead of edge tiles
  *   rows            caller-owned int64 array of cap rows of 8, written in launch order: slab, start
  *                   (slab-local first loaded cell, may be negative for edge tiles), vlo, vhi (the
  *                   exact cells stored are start + [vlo, vhi)), kind (0 interior tile, 1 interior
- *                   tile that samples a probe or loads the source cell, 2 edge tile), src_local (the
+ *                   tile that samples a probe, loads the source cell or holds a slab end, 2 edge
+ *                   tile), src_local (the
  *                   source cell minus start if loaded, else -1), probe_count (probes among the exact
  *                   cells), loaded cells (32 K, or 32 Ke for edge tiles)
  *   cap             rows available; n_tiles receives the tile count even when it exceeds cap
@@ -269,7 +274,8 @@ int64_t rketd_launch_count(const rketd_ctx* ctx);
  */
 rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64_t* src_cell, int32_t n_probes,
                                  const int64_t* probe_cell, int32_t cpml_cells, int32_t cells_per_lane,
-                                 int32_t tb_steps, int64_t* rows, int64_t cap, int64_t* n_tiles);
+                                 int32_t tb_steps, int32_t end_tiles, int64_t* rows, int64_t cap,
+                                 int64_t* n_tiles);
 
 /*
  * Advances one Mur-terminated 1D slab by nsteps steps without allocating any memory.

@@ -155,6 +155,8 @@ struct rketd_ctx {
   int n_interior = 0, n_edge = 0;
   int n_int_xtra = 0;  // the last n_int_xtra interior tiles sample a probe or load a source cell
   int tiles_K = 0, tiles_T = 0;
+  bool tiles_ends = false;  // the plan has end tiles (build_tile_plan)
+  bool in_ckpt = false;     // inside rketd_forward_ckpt
 
   // persistent variant: per tile, the neighbours it waits for (CSR), its last finished pass, the
   // work counter, the status word and the two passes' step arguments
@@ -319,8 +321,16 @@ struct TilePlan {
 // interior tile, shifted left to end at that guard, takes the cells after the last whole one.
 // Narrow edge tiles (Ke cells per lane) cover the two ends, where the Mur/PEC cells, the CPML
 // and cells outside the slab live. Every cell is exact in exactly one tile.
+// ends (first-order Mur ends, FP32 pairs): in slabs of more than 2 (32K - T) cells, two end tiles of the
+// interior width take the ends instead of the edge tiles. The left one loads [0, 32K) and holds
+// [0, 32K - T) exactly (no halo is needed beside the Mur cell); the right one starts at
+// round_up(nz, 4) - 32K (so its copies stay 16-byte aligned and inside the slab's storage) and
+// holds its cells from T on, up to nz - 1. They are the only interior-width tiles that load cell 0
+// or cell nz - 1, which is how the kernel tells them apart; they run with the probe/source tiles.
+// The interior tiles between them are planned as above, with the last one shifted left to end
+// where the right end tile's exact cells begin.
 rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* srcs, int n_probes,
-                             const int64_t* probe_cell, int64_t nc, int K, int T, TilePlan& out) {
+                             const int64_t* probe_cell, int64_t nc, int K, int T, bool ends, TilePlan& out) {
   const int L = 32 * K;
   const int W = L - 2 * T;
   const int Ke = edge_cells_per_lane(T);
@@ -363,6 +373,21 @@ rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* src
   };
   for (int s = 0; s < n_slabs; ++s) {
     const int64_t nz = nzs[s];
+    rketd_status st;
+    if (ends && nc == 0) {
+      const int64_t aL = L - T;                  // the left end tile's exact cells: [0, aL)
+      const int64_t sR = round_up(nz, 4) - L;    // the right end tile loads [sR, sR + L)
+      if (sR + 2 * T - L >= 1) {                 // room for the shifted interior tile
+        const int64_t hi = sR + T;               // interior tiles: exact [aL, hi)
+        if ((st = add_at(s, 0, 0, aL, L, false))) return st;
+        int64_t v = aL;
+        for (; v + W <= hi; v += W)
+          if ((st = add(s, v, v + W, L, false))) return st;
+        if (v < hi && (st = add_at(s, hi - (L - T), v, hi, L, false))) return st;
+        if ((st = add_at(s, sR, hi, nz, L, false))) return st;
+        continue;
+      }
+    }
     const int64_t lo_guard = std::max<int64_t>(1, nc);
     const int64_t hi_guard = nz - 2 - nc;
     int64_t a = round_up(lo_guard + T, 4);
@@ -370,7 +395,6 @@ rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* src
     if (a - T + L - 1 <= hi_guard) n_int = (hi_guard - (a - T + L - 1)) / W + 1;
     if (n_int == 0) a = 0;
     int64_t b = a + n_int * W;
-    rketd_status st;
     for (int64_t v = 0; v < a; v += We)
       if ((st = add(s, v, std::min<int64_t>(v + We, a), Le, true))) return st;
     for (int64_t j = 0; j < n_int; ++j)
@@ -393,9 +417,11 @@ rketd_status build_tile_plan(int n_slabs, const int64_t* nzs, const int64_t* src
     t.probe_begin += (int32_t)tp_int.size();
     t.adj_begin += (int32_t)tp_int.size();
   }
-  // interior tiles that sample a probe or load a source cell go last: they run the kernel with
-  // that code, the others a kernel without a per-step branch for it
-  auto plain_tile = [](const Tile& t) { return t.src_local < 0 && t.probe_count == 0; };
+  // interior tiles that sample a probe, load a source cell or hold a slab end go last: they run
+  // the kernel with that code, the others a kernel without a per-step branch for it
+  auto plain_tile = [&](const Tile& t) {
+    return t.src_local < 0 && t.probe_count == 0 && t.start != 0 && t.start + L - 1 < nzs[t.slab] - 1;
+  };
   std::stable_partition(interior.begin(), interior.end(), plain_tile);
   out.n_int_xtra = 0;
   for (const Tile& t : interior) out.n_int_xtra += !plain_tile(t);
@@ -473,11 +499,18 @@ rketd_status plan_persist(rketd_ctx* c, int K, int T) {
   return RKETD_OK;
 }
 
-rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
+// Whether the tiled forward step plans end tiles (build_tile_plan): FP32 pairs with first-order Mur
+// ends. The checkpointed run, the adjoint and the persistent variant keep the edge tiles.
+bool fwd_end_tiles(const rketd_ctx* c) {
+  return c->prec != RKETD_F64 && c->opt.variant == 2 && c->opt.fp32_pairs != 2 && c->opt.cells_per_lane % 4 == 0 &&
+         c->grid.bc == RKETD_BC_MUR1 && !c->in_ckpt;
+}
+
+rketd_status plan_tiles(rketd_ctx* c, int K, int T, bool ends = false) {
   const int64_t nc = c->grid.bc != RKETD_BC_MUR1 ? c->grid.cpml_cells : 0;
   TilePlan plan;
-  rketd_status st0 =
-      build_tile_plan(c->n_slabs, c->nz.data(), c->src.data(), c->n_probes, c->probe_cell.data(), nc, K, T, plan);
+  rketd_status st0 = build_tile_plan(c->n_slabs, c->nz.data(), c->src.data(), c->n_probes, c->probe_cell.data(), nc,
+                                     K, T, ends, plan);
   if (st0) return st0;
   const std::vector<Tile>& all = plan.tiles;
   const std::vector<TileProbe>& tps = plan.probes;
@@ -501,6 +534,7 @@ rketd_status plan_tiles(rketd_ctx* c, int K, int T) {
   c->n_edge = plan.n_edge;
   c->tiles_K = K;
   c->tiles_T = T;
+  c->tiles_ends = ends;
   if (c->opt.variant == 4) return plan_persist(c, K, T);
   return RKETD_OK;
 }
@@ -701,7 +735,7 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
     } else if (c->opt.variant == 4) {
       // persistent: every whole pass left in this DFT block (or in the call) in one launch
       const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
-      if (c->tiles_K != K || c->tiles_T != TS || !c->done_d) {
+      if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends || !c->done_d) {
         rketd_status st = plan_tiles(c, K, TS);
         if (st) return st;
       }
@@ -754,8 +788,8 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
       nsteps -= (int64_t)nsub * n_pass;
     } else {
       const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
-      if (c->tiles_K != K || c->tiles_T != TS) {
-        rketd_status st = plan_tiles(c, K, TS);
+      if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends != fwd_end_tiles(c)) {
+        rketd_status st = plan_tiles(c, K, TS, fwd_end_tiles(c));
         if (st) return st;
       }
       const int nsub = (int)std::min<int64_t>({(int64_t)TS, nsteps, (int64_t)(B - pos)});
@@ -972,8 +1006,8 @@ rketd_status step_graph(rketd_ctx* c, int64_t nsteps) {
       rketd_status st = plan_resident(c);
       if (st) return st;
     }
-  } else if (c->tiles_K != K || c->tiles_T != TS) {
-    rketd_status st = plan_tiles(c, K, TS);
+  } else if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends != fwd_end_tiles(c)) {
+    rketd_status st = plan_tiles(c, K, TS, fwd_end_tiles(c));
     if (st) return st;
   }
   if (!c->cap) {
@@ -1579,7 +1613,9 @@ rketd_status rketd_forward_ckpt(rketd_ctx* c, int64_t nsteps, int32_t ckpt_every
     CK(cudaMemcpyAsync(dst + 2 * fb, c->J[c->cur], fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
     // direct launches: every segment starts at a different step, so per-call graphs would not repeat
     const int64_t n = std::min<int64_t>(ckpt_every, nsteps - j * ckpt_every);
+    c->in_ckpt = true;  // the edge-tile plan that the adjoint's recompute mirrors
     st = c->prec == RKETD_F64 ? step_impl<double>(c, n) : step_impl<float>(c, n);
+    c->in_ckpt = false;
     if (st) return st;
   }
   c->ckpt_steps = nsteps;
@@ -1602,7 +1638,7 @@ rketd_status adjoint_impl(rketd_ctx* c, int64_t w_lo, int64_t w_hi, double* grad
   const int64_t r0 = w_lo - 4;
   const size_t fb = c->esz * c->n_store;
   const int P = c->total_probes, nf = c->n_freq;
-  if (c->tiles_K != K || c->tiles_T != TS) {
+  if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends) {
     rketd_status st = plan_tiles(c, K, TS);
     if (st) return st;
   }
@@ -1891,7 +1927,8 @@ rketd_status rketd_destroy(rketd_ctx* c) {
 
 rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64_t* src_cell, int32_t n_probes,
                                  const int64_t* probe_cell, int32_t cpml_cells, int32_t cells_per_lane,
-                                 int32_t tb_steps, int64_t* rows, int64_t cap, int64_t* n_tiles) {
+                                 int32_t tb_steps, int32_t end_tiles, int64_t* rows, int64_t cap,
+                                 int64_t* n_tiles) {
   if (!nz || !src_cell || !n_tiles || (n_probes > 0 && !probe_cell) || (cap > 0 && !rows))
     return fail(RKETD_EINVAL, "NULL argument");
   if (n_slabs < 1 || n_probes < 0 || cpml_cells < 0 || cap < 0) return fail(RKETD_EINVAL, "bad count");
@@ -1908,7 +1945,7 @@ rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64
   }
   TilePlan plan;
   rketd_status st = build_tile_plan(n_slabs, nz, src_cell, n_probes, probe_cell, cpml_cells, cells_per_lane, tb_steps,
-                                    plan);
+                                    end_tiles != 0, plan);
   if (st) return st;
   *n_tiles = (int64_t)plan.tiles.size();
   const int64_t Lint = 32 * cells_per_lane, Ledge = 32 * edge_cells_per_lane(tb_steps);

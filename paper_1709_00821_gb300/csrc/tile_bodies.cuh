@@ -240,6 +240,15 @@ __device__ __forceinline__ void tb_tile(const StepArgs<T>& a, const Tile tl, int
 // `lane` of the warp that owns it: n0 is the step index at pass start, spos the pass's first
 // column in the probe-series buffer. NC: fields through the read-only path (false in the
 // persistent step, where other warps of the kernel write them).
+//
+// XTRA tiles may also hold a slab end (the planner's end tiles, first-order Mur ends): the tile
+// that starts at cell 0, and the one whose last lane holds cell nz - 1 (in slot K - 4 .. K - 1,
+// as the tile ends at round_up(nz, 4) - 1). They run the pair updates on every cell and then set
+// the end cell's E by Mur's condition from the same values, in the same order and rounding, as the
+// edge tiles (after the source, before the probes); the plain step never updates the end cells' G
+// nor the H beyond cell nz - 2, so those are stored as loaded. The values the pair updates leave in
+// the end cells and beyond nz - 1 reach no other cell: E there is overwritten every step, and G and
+// H there feed only that E.
 template <int K, bool XTRA, bool NC>
 __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl, int lane, int64_t n0, int spos) {
   constexpr int P = K / 2;
@@ -264,9 +273,35 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
   const bool tile_src = XTRA && tl.src_local >= 0;  // warp-uniform
   const PassSource<float> ps = tile_src ? pass_source<float>(n0, a.nsub, a.dt, a.t0, a.tau, a.amp, lane)
                                         : PassSource<float>{0.f, 0.f};
+  // slab ends held (warp-uniform): cell 0 at lane 0, slot 0; cell nz - 1 at lane 31, slot sR
+  bool endL = false;
+  int sR = -1;
+  float g0k = 0.f, gRk = 0.f, hRk = 0.f;  // their state that the step leaves as loaded
+  if constexpr (XTRA) {
+    endL = tl.start == 0;
+    const int64_t r = a.nz[s] - 1 - tl.start - 31 * K;  // slot of cell nz - 1 in lane 31
+    if (r >= K - 4 && r < K) sR = (int)r;
+    if (endL) g0k = lo_of(g[0]);
+    if (sR >= 0) {
+      gRk = pick2(g, sR);
+      hRk = pick2(h, sR);
+    }
+  }
 
 #pragma unroll 2
   for (int t = 0; t < a.nsub; ++t) {
+    // the end cells' E before this step (Mur's condition reads them)
+    float e0o = 0.f, e1o = 0.f, eN1o = 0.f, eN2o = 0.f;
+    if constexpr (XTRA) {
+      if (endL) {
+        e0o = lo_of(e[0]);
+        e1o = lo_of(e[1]);
+      }
+      if (sR >= 0) {
+        eN1o = pick2(e, sR);
+        eN2o = pick2(e, sR - 1);
+      }
+    }
     // Eq. 14 on pairs: the cell after pair p is pair p+1; after pair P-1 it is (B[0], next lane's A[0])
     const float nextA0 = __shfl_down_sync(kFull, lo_of(e[0]), 1);
     const f2 eLast = pk(hi_of(e[0]), nextA0);
@@ -295,6 +330,9 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
           put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
         }
       }
+      // first-order Mur ends
+      if (endL && lane == 0) e[0] = pk(fmaf(a.qmur, lo_of(e[1]) - e0o, e1o), hi_of(e[0]));
+      if (sR >= 0 && lane == 31) put2(e, sR, fmaf(a.qmur, pick2(e, sR - 1) - eN1o, eN2o));
       if (lp.n > 0) {
         a.series[lp.o0 + t] = pick2(e, lp.s0);
         if (lp.n > 1) {
@@ -306,6 +344,13 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
           }
         }
       }
+    }
+  }
+  if constexpr (XTRA) {
+    if (endL && lane == 0) g[0] = pk(g0k, hi_of(g[0]));
+    if (sR >= 0 && lane == 31) {
+      put2(g, sR, gRk);
+      put2(h, sR, hRk);
     }
   }
   store_pairs<K>(a.E_out + base, li0, tl.vlo, tl.vhi, e);

@@ -98,7 +98,8 @@ _SIGS = {
     "rketd_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int64]),
     "rketd_debug_alloc_count": (ctypes.c_int64, []),
     "rketd_plan_tiles_1d": (ctypes.c_int, [ctypes.c_int32, _i64p, _i64p, ctypes.c_int32, _i64p, ctypes.c_int32,
-                                           ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p]),
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64,
+                                           _i64p]),
     "rketd_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_get_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, _dp]),
     "rketd_advance_1d_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid1D), ctypes.c_int64, ctypes.c_void_p,
@@ -381,7 +382,8 @@ def advance_1d_noalloc(slab, prec: str, wp2_dev: int, nu_dev: int, n0: int, nste
 FIELDS_3D = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Jx", "Jy", "Jz")
 
 
-def plan_tiles_1d(nz, src_cell, probe_cell, cpml_cells: int, cells_per_lane: int, tb_steps: int) -> np.ndarray:
+def plan_tiles_1d(nz, src_cell, probe_cell, cpml_cells: int, cells_per_lane: int, tb_steps: int,
+                  end_tiles: bool = False) -> np.ndarray:
     """rketd_plan_tiles_1d: the 1D tile plan (host only) as an int64 array of rows (slab, start, vlo,
     vhi, kind, src_local, probe_count, loaded cells), in launch order. probe_cell is [slab][probe]."""
     nz = np.ascontiguousarray(nz, dtype=np.int64)
@@ -390,11 +392,11 @@ def plan_tiles_1d(nz, src_cell, probe_cell, cpml_cells: int, cells_per_lane: int
     n = ctypes.c_int64(0)
     _check(lib().rketd_plan_tiles_1d(len(nz), _ptr(nz, _i64p), _ptr(src, _i64p), pc.shape[1],
                                      _ptr(pc, _i64p) if pc.size else None, cpml_cells, cells_per_lane, tb_steps,
-                                     None, 0, ctypes.byref(n)))
+                                     int(end_tiles), None, 0, ctypes.byref(n)))
     rows = np.zeros((n.value, 8), dtype=np.int64)
     _check(lib().rketd_plan_tiles_1d(len(nz), _ptr(nz, _i64p), _ptr(src, _i64p), pc.shape[1],
                                      _ptr(pc, _i64p) if pc.size else None, cpml_cells, cells_per_lane, tb_steps,
-                                     _ptr(rows, _i64p), n.value, ctypes.byref(n)))
+                                     int(end_tiles), _ptr(rows, _i64p), n.value, ctypes.byref(n)))
     return rows
 
 

@@ -288,10 +288,12 @@ def _plasma_line(nz, src, steps, probes):
     return s
 
 
-# Source cells at the first interior cell, at the exact-range boundary of two interior tiles and
-# inside the halo that two neighbouring tiles both load (default tiles: FP32 K = 16 with 32 steps
-# per pass, exact ranges [36 + 448 j, 484 + 448 j); FP64 K = 8 with 4 steps, [8 + 248 j, 256 + 248 j)).
-SRC_CASES = {"f32": [36, 37, 460, 483, 484, 515, 516, 1000], "f64": [8, 9, 252, 255, 256, 259, 260, 1000]}
+# Source cells beside the Mur cell, at the exact-range boundary of two tiles and inside the halo
+# that two neighbouring tiles both load (default tiles, Mur ends: FP32 K = 16 with 32 steps per
+# pass, the left end tile exact on [0, 480), interior tiles exact on [480 + 448 j, 928 + 448 j)
+# loading 32 more cells each side; FP64 K = 8 with 4 steps, [8 + 248 j, 256 + 248 j)).
+SRC_CASES = {"f32": [1, 2, 447, 448, 479, 480, 511, 512, 927, 928, 1000],
+             "f64": [8, 9, 252, 255, 256, 259, 260, 1000]}
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
@@ -310,6 +312,29 @@ def test_source_cell_in_overlapping_tile_halos(prec):
             assert rel(X, tot.X) <= 1e-12, src
             assert np.abs(E - tot.E).max() <= 1e-12 * np.abs(tot.E).max(), src
             assert np.abs(J - tot.J).max() <= 1e-12 * np.abs(tot.J).max(), src
+
+
+@pytest.mark.parametrize("K,T", [(16, 32), (12, 32), (8, 16), (16, 8)])
+def test_mur_end_tiles_are_bitwise_the_plain_kernels(K, T):
+    """FP32 pairs with Mur ends: the tiles that hold cell 0 and cell nz - 1 apply Mur's condition
+    themselves. Slab lengths at the threshold for end tiles (below it the edge tiles stay) and
+    every nz mod 4 (cell nz - 1 in each of the last four slots of the right end tile), with the
+    source and probes on the cells next to the ends, match the one-step plain kernels bit for bit
+    over passes and a partial pass; one case is also held to the FP64 oracle."""
+    L = 32 * K
+    thr = 2 * (L - T)
+    for nz in (thr - 3, thr - 1, thr, thr + 1, thr + 2, 3 * L + 1, 3 * L + 2, 3 * L + 3, 3 * L + 4):
+        for src in (1, nz - 2):
+            s = _plasma_line(nz, src, 3 * T + 5, [0, 1, nz - 2, nz - 1])
+            tiled = lib_run(s, "f32", variant=2, cells_per_lane=K, tb_steps=T)
+            plain = lib_run(s, "f32", variant=1)
+            for a, b in zip(tiled, plain):
+                assert np.array_equal(a, b), (K, T, nz, src)
+    s = _plasma_line(3 * L + 3, 1, 400, [0, 3 * L + 2])
+    tot, _ = oracle.run1d(s)
+    X, E, H, J = lib_run(s, "f32", variant=2, cells_per_lane=K, tb_steps=T)
+    assert np.abs(E - tot.E).max() <= 2e-4 * np.abs(tot.E).max()
+    assert rel(X, tot.X) <= 2e-4
 
 
 C3_SUBSET_SEED = 0x1709C3C3

@@ -76,3 +76,45 @@ def test_tile_plan_rejects_bad_shapes_and_cells():
         rk.plan_tiles_1d(nz, np.array([0]), probes, 0, 16, 32)  # source on the end cell
     with pytest.raises(rk.RketdError):
         rk.plan_tiles_1d(nz, src, np.array([[2000]]), 0, 16, 32)  # probe outside the slab
+
+
+@pytest.mark.parametrize("K,T", [(8, 16), (12, 32), (16, 32), (16, 8), (8, 28)])
+def test_end_tile_plan_holds_each_mur_end_in_one_wide_tile(K, T):
+    """end_tiles: slabs of at least 2 (32K - T) cells get no edge tiles; the tile that starts at 0
+    holds [0, 32K - T) exactly, the one ending at round_up(nz, 4) - 1 holds its cells from T on,
+    both run with the probe/source tiles; every cell is still exact in exactly one tile, and no
+    other interior tile loads a boundary cell."""
+    rng = np.random.default_rng(7 * K + T)
+    L = 32 * K
+    nz = np.concatenate([rng.integers(2 * (L - T), 12000, 20), [2 * (L - T) - 5, 2 * (L - T) + 1, L + 40, 100]])
+    src = np.array([rng.integers(1, n - 1) for n in nz])
+    probes = np.array([rng.integers(0, n, 3) for n in nz])
+    rows = rk.plan_tiles_1d(nz, src, probes, 0, K, T, True)
+    slab, start, vlo, vhi, kind, src_local, probe_count, loaded = rows.T
+    assert np.all(np.diff(kind) >= 0)
+    for s in range(len(nz)):
+        mine = slab == s
+        hits = np.zeros(nz[s], dtype=np.int64)
+        for st, lo, hi in zip(start[mine], vlo[mine], vhi[mine]):
+            hits[st + lo:st + hi] += 1
+        assert np.all(hits == 1), (s, np.flatnonzero(hits != 1)[:5])
+        ends = ((nz[s] + 3) // 4) * 4
+        if ends - L + 2 * T - L >= 1:  # long enough for end tiles
+            assert not np.any(mine & (kind == 2))
+            left = mine & (start == 0)
+            right = mine & (start + L - 1 >= nz[s] - 1)
+            assert left.sum() == 1 and right.sum() == 1
+            assert kind[left][0] == 1 and vlo[left][0] == 0 and vhi[left][0] == L - T
+            assert kind[right][0] == 1 and start[right][0] == ends - L and vlo[right][0] == T
+            assert vhi[right][0] == nz[s] - start[right][0]
+            assert start[right][0] % 4 == 0 and start[right][0] + L <= ((nz[s] + 31) // 32) * 32  # inside storage
+            inner = mine & ~left & ~right
+            assert np.all(kind[inner] < 2) and np.all(loaded[mine] == L)
+            assert np.all(start[inner] >= 1) and np.all(start[inner] + L - 1 <= nz[s] - 2)
+            assert np.all(start[inner] % 4 == 0)
+            assert np.all((vlo[inner] >= T) & (vhi[inner] <= L - T))
+        else:  # short slabs keep the edge tiles
+            assert np.any(mine & (kind == 2))
+    # without end tiles every slab has edge tiles
+    rows0 = rk.plan_tiles_1d(nz, src, probes, 0, K, T)
+    assert all(np.any((rows0[:, 0] == s) & (rows0[:, 4] == 2)) for s in range(len(nz)))
