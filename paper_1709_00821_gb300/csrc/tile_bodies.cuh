@@ -282,11 +282,15 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
     const int64_t r = a.nz[s] - 1 - tl.start - 31 * K;  // slot of cell nz - 1 in lane 31
     if (r >= K - 4 && r < K) sR = (int)r;
     if (endL) g0k = lo_of(g[0]);
-    if (sR >= 0) {
-      gRk = pick2(g, sR);
-      hRk = pick2(h, sR);
-    }
+    if (sR >= 0)
+      at_uniform_slot<P>(sR, [&](auto S) {
+        constexpr int q = decltype(S)::value;
+        gRk = pick2c<q>(g);
+        hRk = pick2c<q>(h);
+      });
   }
+  // the source cell's -da, which its fold into G takes every step
+  const float nda = has_src ? -a.coef[kDa][base + src_slot] : 0.f;
 
 #pragma unroll 2
   for (int t = 0; t < a.nsub; ++t) {
@@ -297,10 +301,14 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
         e0o = lo_of(e[0]);
         e1o = lo_of(e[1]);
       }
-      if (sR >= 0) {
-        eN1o = pick2(e, sR);
-        eN2o = pick2(e, sR - 1);
-      }
+      if (sR >= 0)
+        at_uniform_slot<P>(sR, [&](auto S) {
+          constexpr int q = decltype(S)::value;
+          if constexpr (q >= 1) {
+            eN1o = pick2c<q>(e);
+            eN2o = pick2c<q - 1>(e);
+          }
+        });
     }
     // Eq. 14 on pairs: the cell after pair p is pair p+1; after pair P-1 it is (B[0], next lane's A[0])
     const float nextA0 = __shfl_down_sync(kFull, lo_of(e[0]), 1);
@@ -325,14 +333,20 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
     if constexpr (XTRA) {
       if (tile_src) {
         const float sv = source_at(ps, t);
-        if (has_src) {
-          put2(e, src_slot, pick2(e, src_slot) + sv);
-          put2(g, src_slot, fmaf(-a.coef[kDa][base + src_slot], sv, pick2(g, src_slot)));
-        }
+        if (has_src)
+          at_uniform_slot<P>(src_slot, [&](auto S) {
+            constexpr int q = decltype(S)::value;
+            put2c<q>(e, pick2c<q>(e) + sv);
+            put2c<q>(g, fmaf(nda, sv, pick2c<q>(g)));
+          });
       }
       // first-order Mur ends
       if (endL && lane == 0) e[0] = pk(fmaf(a.qmur, lo_of(e[1]) - e0o, e1o), hi_of(e[0]));
-      if (sR >= 0 && lane == 31) put2(e, sR, fmaf(a.qmur, pick2(e, sR - 1) - eN1o, eN2o));
+      if (sR >= 0 && lane == 31)
+        at_uniform_slot<P>(sR, [&](auto S) {
+          constexpr int q = decltype(S)::value;
+          if constexpr (q >= 1) put2c<q>(e, fmaf(a.qmur, pick2c<q - 1>(e) - eN1o, eN2o));
+        });
       if (lp.n > 0) {
         a.series[lp.o0 + t] = pick2(e, lp.s0);
         if (lp.n > 1) {
@@ -348,10 +362,12 @@ __device__ __forceinline__ void tb2_tile(const StepArgs<float>& a, const Tile tl
   }
   if constexpr (XTRA) {
     if (endL && lane == 0) g[0] = pk(g0k, hi_of(g[0]));
-    if (sR >= 0 && lane == 31) {
-      put2(g, sR, gRk);
-      put2(h, sR, hRk);
-    }
+    if (sR >= 0 && lane == 31)
+      at_uniform_slot<P>(sR, [&](auto S) {
+        constexpr int q = decltype(S)::value;
+        put2c<q>(g, gRk);
+        put2c<q>(h, hRk);
+      });
   }
   store_pairs<K>(a.E_out + base, li0, tl.vlo, tl.vhi, e);
   store_pairs<K>(a.H_out + base, li0, tl.vlo, tl.vhi, h);

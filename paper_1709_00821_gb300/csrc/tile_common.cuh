@@ -3,6 +3,8 @@
 // Eq. 15 pulse.
 #pragma once
 
+#include <type_traits>
+
 #include "rketd_internal.cuh"
 
 namespace rketd {
@@ -192,6 +194,35 @@ __device__ __forceinline__ void put2(f2 (&r)[P], int slot, float v) {
   for (int q = 0; q < P; ++q)
     if (q == p) r[q] = slot < P ? pk(v, hi_of(r[q])) : pk(lo_of(r[q]), v);
 }
+// element S (a constant) of a pair array, read and written
+template <int S, int P>
+__device__ __forceinline__ float pick2c(const f2 (&r)[P]) {
+  if constexpr (S < P) return lo_of(r[S]);
+  else return hi_of(r[S - P]);
+}
+template <int S, int P>
+__device__ __forceinline__ void put2c(f2 (&r)[P], float v) {
+  if constexpr (S < P) r[S] = pk(v, hi_of(r[S]));
+  else r[S - P] = pk(lo_of(r[S - P]), v);
+}
+// f(std::integral_constant<int, slot>) for a slot 0 .. 2P-1 that is the same in every lane of the
+// warp: one uniform branch to code with a constant slot, instead of a select over every pair
+#define RKETD_SLOT_CASE(S) \
+  case S:                  \
+    if constexpr (S < 2 * P) f(std::integral_constant<int, S>{}); \
+    break;
+template <int P, typename F>
+__device__ __forceinline__ void at_uniform_slot(int slot, F&& f) {
+  static_assert(2 * P <= 16, "at most 16 cells per lane");
+  switch (slot) {
+    RKETD_SLOT_CASE(0) RKETD_SLOT_CASE(1) RKETD_SLOT_CASE(2) RKETD_SLOT_CASE(3)
+    RKETD_SLOT_CASE(4) RKETD_SLOT_CASE(5) RKETD_SLOT_CASE(6) RKETD_SLOT_CASE(7)
+    RKETD_SLOT_CASE(8) RKETD_SLOT_CASE(9) RKETD_SLOT_CASE(10) RKETD_SLOT_CASE(11)
+    RKETD_SLOT_CASE(12) RKETD_SLOT_CASE(13) RKETD_SLOT_CASE(14) RKETD_SLOT_CASE(15)
+    default: break;
+  }
+}
+#undef RKETD_SLOT_CASE
 
 
 template <int K, bool NC = true>
