@@ -337,6 +337,23 @@ def test_mur_end_tiles_are_bitwise_the_plain_kernels(K, T):
     assert rel(X, tot.X) <= 2e-4
 
 
+def test_checkpointed_run_on_edge_tiles_matches_the_end_tile_run():
+    """The checkpointed forward run (which the adjoint mirrors) keeps the edge tiles, the plain
+    step uses the end tiles; switching plans on one context changes no bit."""
+    s = _plasma_line(20000, 600, 700, [300, 19000])
+    with rk.Context(s, "f32", options={"variant": 2}) as ctx:
+        ctx.step(700)
+        X0, F0 = ctx.spectra(), ctx.fields(0)
+        ctx.forward_ckpt(700, 256)
+        X1, F1 = ctx.spectra(), ctx.fields(0)
+        ctx.reset()
+        ctx.step(700)
+        X2, F2 = ctx.spectra(), ctx.fields(0)
+    assert np.array_equal(X0, X1) and np.array_equal(X0, X2)
+    for a, b, c in zip(F0, F1, F2):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
 C3_SUBSET_SEED = 0x1709C3C3
 
 
