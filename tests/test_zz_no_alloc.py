@@ -131,6 +131,44 @@ def test_noalloc_runs_the_first_order_recursion_like_the_context_api(prec, tol):
         assert np.abs(g - r).max() * k <= tol * scale
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_noalloc_call_recorded_into_a_cuda_graph_replays_like_the_context_api(prec, tol):
+    """The call recorded into a CUDA graph (after one eager call, which looks up the fixed array's
+    address) and replayed twice from the same starting state gives the context API's fields both
+    times: it allocates nothing, synchronises nothing and reads its arguments at replay."""
+    import torch
+
+    slab = _plasma_source(255)
+    n = 1024
+    with rk.Context(slab, prec) as ctx:
+        ctx.step(n)
+        ref = ctx.fields(0)
+
+    fdt = torch.float64 if prec == "f64" else torch.float32
+    wp2 = torch.tensor(slab.wp2, dtype=torch.float64, device="cuda")
+    nu = torch.tensor(slab.nu, dtype=torch.float64, device="cuda")
+    E = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    H = torch.zeros(slab.nz - 1, dtype=fdt, device="cuda")
+    J = torch.zeros(slab.nz, dtype=fdt, device="cuda")
+    ptrs = (E.data_ptr(), H.data_ptr(), J.data_ptr())
+    rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), 0, 1, *ptrs)  # eager warm-up call
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rk.advance_1d_noalloc(slab, prec, wp2.data_ptr(), nu.data_ptr(), 0, n, *ptrs)
+    scale = np.abs(ref[0]).max()
+    assert scale > 1e-3
+    for _ in range(2):
+        for t in (E, H, J):
+            t.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        got = [t.double().cpu().numpy() for t in (E, H, J)]
+        for g, r, k in zip(got, ref, _scales(slab)):
+            assert np.abs(g - r).max() * k <= tol * scale
+
+
 def test_noalloc_rejects_slabs_beyond_the_fixed_capacity():
     """Checked before any device work: runs without a GPU."""
     slab = wl.c1_plain_slab(nz=131073, steps=1)
