@@ -499,11 +499,11 @@ rketd_status plan_persist(rketd_ctx* c, int K, int T) {
   return RKETD_OK;
 }
 
-// Whether the tiled forward step plans end tiles (build_tile_plan): FP32 pairs with first-order Mur
-// ends. The checkpointed run, the adjoint and the persistent variant keep the edge tiles.
+// Whether the tiled and persistent forward steps plan end tiles (build_tile_plan): FP32 pairs with
+// first-order Mur ends. The checkpointed run and the adjoint keep the edge tiles.
 bool fwd_end_tiles(const rketd_ctx* c) {
-  return c->prec != RKETD_F64 && c->opt.variant == 2 && c->opt.fp32_pairs != 2 && c->opt.cells_per_lane % 4 == 0 &&
-         c->grid.bc == RKETD_BC_MUR1 && !c->in_ckpt;
+  return c->prec != RKETD_F64 && (c->opt.variant == 2 || c->opt.variant == 4) && c->opt.fp32_pairs != 2 &&
+         c->opt.cells_per_lane % 4 == 0 && c->grid.bc == RKETD_BC_MUR1 && !c->in_ckpt;
 }
 
 rketd_status plan_tiles(rketd_ctx* c, int K, int T, bool ends = false) {
@@ -735,8 +735,8 @@ rketd_status step_impl(rketd_ctx* c, int64_t nsteps) {
     } else if (c->opt.variant == 4) {
       // persistent: every whole pass left in this DFT block (or in the call) in one launch
       const int K = c->opt.cells_per_lane, TS = c->opt.tb_steps;
-      if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends || !c->done_d) {
-        rketd_status st = plan_tiles(c, K, TS);
+      if (c->tiles_K != K || c->tiles_T != TS || c->tiles_ends != fwd_end_tiles(c) || !c->done_d) {
+        rketd_status st = plan_tiles(c, K, TS, fwd_end_tiles(c));
         if (st) return st;
       }
       const int nsub = (int)std::min<int64_t>({(int64_t)TS, nsteps, (int64_t)(B - pos)});
