@@ -310,6 +310,23 @@ rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64_t nz, cons
                                       int64_t src_cell, const rketd_pulse* pulse, int64_t n0, int64_t nsteps,
                                       void* E, void* H, void* J, void* stream);
 
+/*
+ * The tile list rketd_advance_1d_noalloc builds on the device for a slab, computed on the host by
+ * the same code, so that callers and tests can check its coverage without a GPU (host only, no
+ * CUDA call).
+ *   prec          RKETD_F32 or RKETD_F64 (they use different tile shapes)
+ *   nz, src_cell  as for rketd_advance_1d_noalloc (8 <= nz <= 131072, 1 <= src_cell <= nz-2)
+ *   rows          caller-owned int64 array of cap rows of 5, in launch order: start (first loaded
+ *                 cell), vlo, vhi (the exact cells are start + [vlo, vhi)), src_local (the source
+ *                 cell minus start if loaded, else -1), loaded cells
+ *   n_tiles       receives the tile count even when it exceeds cap
+ *   launch_counts receives [3]: the tiles of the three launches of a pass, in order (interior
+ *                 tiles without the source cell, interior tiles that load it, edge tiles)
+ * Returns RKETD_EINVAL for NULL pointers or arguments outside these ranges.
+ */
+rketd_status rketd_noalloc_tiles_1d(int32_t prec, int64_t nz, int64_t src_cell, int64_t* rows, int64_t cap,
+                                    int64_t* n_tiles, int64_t* launch_counts);
+
 /* Persistent variant (options.variant = 4): polls of each wait of a tile for its neighbours'
  * previous pass before it gives up (0: every wait gives up at once, a test of the failure path;
  * < 0 restores the default of 2^22, with a 64 ns pause between polls). A wait that gives up lets

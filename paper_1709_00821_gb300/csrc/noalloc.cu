@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/rketd.h"
 #include "rketd_internal.cuh"
@@ -56,6 +57,10 @@ struct NoallocPlan {
   int64_t j_src0 = 0, j_src1 = 0;  // interior tiles whose loaded range holds the source cell
 };
 
+// Tile shapes of the entry point (the tiled step's defaults): cells per lane and steps per pass.
+constexpr int noalloc_K(bool f64) { return f64 ? 8 : 16; }
+constexpr int noalloc_T(bool f64) { return f64 ? 4 : 32; }
+
 NoallocPlan noalloc_plan(int64_t nz, int64_t src, int K, int Ke, int T) {
   NoallocPlan p;
   const int64_t L = 32 * K, W = L - 2 * T, We = 32 * Ke - 2 * T;
@@ -75,35 +80,46 @@ NoallocPlan noalloc_plan(int64_t nz, int64_t src, int K, int Ke, int T) {
   return p;
 }
 
-// Writes the tile list of a NoallocPlan (interior tiles without the source first, then those with
-// it, then the edge tiles) and the slab table (soff = 0, off = 0, nz, src). One thread.
+// One tile loading [v0 - T, v0 - T + Lt) and holding [v0, v1) exactly.
+__host__ __device__ inline Tile noalloc_tile(int64_t v0, int64_t v1, int Lt, int T, int64_t src) {
+  Tile t;
+  t.slab = 0;
+  t.start = v0 - T;
+  t.vlo = T;
+  t.vhi = (int32_t)(T + (v1 - v0));
+  const int64_t sl = src - t.start;
+  t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
+  t.probe_begin = 0;
+  t.probe_count = 0;
+  t.adj_begin = 0;
+  t.adj_count = 0;
+  return t;
+}
+
+// The tile list of a NoallocPlan in launch order: interior tiles without the source, then those
+// with it, then the edge tiles. Returns the count. The device writes it (k_plan), and
+// rketd_noalloc_tiles_1d hands the same list to the host for checking.
+__host__ __device__ inline int noalloc_tiles(const NoallocPlan& pl, int64_t nz, int64_t src, int K, int Ke, int T,
+                                             Tile* tiles) {
+  const int L = 32 * K, W = L - 2 * T, Le = 32 * Ke, We = Le - 2 * T;
+  int n = 0;
+  for (int64_t j = 0; j < pl.n_int; ++j)
+    if (j < pl.j_src0 || j >= pl.j_src1) tiles[n++] = noalloc_tile(pl.a + j * W, pl.a + (j + 1) * W, L, T, src);
+  for (int64_t j = pl.j_src0; j < pl.j_src1; ++j)
+    tiles[n++] = noalloc_tile(pl.a + j * W, pl.a + (j + 1) * W, L, T, src);
+  for (int64_t v = 0; v < pl.a; v += We) tiles[n++] = noalloc_tile(v, v + We < pl.a ? v + We : pl.a, Le, T, src);
+  for (int64_t v = pl.b; v < nz; v += We) tiles[n++] = noalloc_tile(v, v + We < nz ? v + We : nz, Le, T, src);
+  return n;
+}
+
+// Writes the tile list and the slab table (soff = 0, off = 0, nz, src). One thread.
 __global__ void k_plan(Tile* tiles, int64_t* table, int64_t nz, int64_t src, int K, int Ke, int T, NoallocPlan pl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   table[0] = 0;
   table[1] = 0;
   table[2] = nz;
   table[3] = src;
-  const int L = 32 * K, W = L - 2 * T, Le = 32 * Ke, We = Le - 2 * T;
-  int n = 0;
-  auto put = [&](int64_t v0, int64_t v1, int Lt) {
-    Tile t;
-    t.slab = 0;
-    t.start = v0 - T;
-    t.vlo = T;
-    t.vhi = (int32_t)(T + (v1 - v0));
-    const int64_t sl = src - t.start;
-    t.src_local = (sl >= 0 && sl < Lt) ? (int32_t)sl : -1;
-    t.probe_begin = 0;
-    t.probe_count = 0;
-    t.adj_begin = 0;
-    t.adj_count = 0;
-    tiles[n++] = t;
-  };
-  for (int64_t j = 0; j < pl.n_int; ++j)
-    if (j < pl.j_src0 || j >= pl.j_src1) put(pl.a + j * W, pl.a + (j + 1) * W, L);
-  for (int64_t j = pl.j_src0; j < pl.j_src1; ++j) put(pl.a + j * W, pl.a + (j + 1) * W, L);
-  for (int64_t v = 0; v < pl.a; v += We) put(v, v + We < pl.a ? v + We : pl.a, Le);
-  for (int64_t v = pl.b; v < nz; v += We) put(v, v + We < nz ? v + We : nz, Le);
+  noalloc_tiles(pl, nz, src, K, Ke, T, tiles);
 }
 
 // Caller's SI fields -> normalised working copy (E~ = E, H~ = eta0 H, folded current
@@ -142,9 +158,7 @@ rketd_status advance(void* base, const rketd_grid1d* g, int64_t nz, const double
   Tile* tiles = (Tile*)(q + 12 * kNoallocPad * sizeof(double));
   int64_t* table = (int64_t*)(tiles + kNoallocMaxTiles);
 
-  const int K = sizeof(T) == 8 ? 8 : 16;
-  const int TS = sizeof(T) == 8 ? 4 : 32;
-  const int Ke = 4;
+  const int K = noalloc_K(sizeof(T) == 8), TS = noalloc_T(sizeof(T) == 8), Ke = 4;
   const double S = g->dt / (g->dz * std::sqrt(kMu0 * kEps0));
   const double eta0 = std::sqrt(kMu0 / kEps0);
   const NoallocPlan pl = noalloc_plan(nz, src, K, Ke, TS);
@@ -262,4 +276,34 @@ extern "C" rketd_status rketd_advance_1d_noalloc(const rketd_grid1d* grid, int64
   if (grid->prec == RKETD_F64)
     return advance<double>(base, grid, nz, wp2, nu, src_cell, pulse, n0, nsteps, (double*)E, (double*)H, (double*)J, st);
   return advance<float>(base, grid, nz, wp2, nu, src_cell, pulse, n0, nsteps, (float*)E, (float*)H, (float*)J, st);
+}
+
+extern "C" rketd_status rketd_noalloc_tiles_1d(int32_t prec, int64_t nz, int64_t src_cell, int64_t* rows, int64_t cap,
+                                              int64_t* n_tiles, int64_t* launch_counts) {
+  set_error_message("");
+  if (!n_tiles || !launch_counts || (cap > 0 && !rows) || cap < 0) return nfail(RKETD_EINVAL, "NULL argument");
+  if (prec != RKETD_F32 && prec != RKETD_F64) return nfail(RKETD_EINVAL, "bad precision");
+  if (nz < 8 || nz > kNoallocMaxNz) return nfail(RKETD_EINVAL, "nz must be in [8, 131072]");
+  if (src_cell < 1 || src_cell > nz - 2) return nfail(RKETD_EINVAL, "source cell outside the interior");
+  const bool f64 = prec == RKETD_F64;
+  const int K = noalloc_K(f64), T = noalloc_T(f64), Ke = 4;
+  const NoallocPlan pl = noalloc_plan(nz, src_cell, K, Ke, T);
+  const int64_t n_src = pl.j_src1 - pl.j_src0;
+  launch_counts[0] = pl.n_int - n_src;
+  launch_counts[1] = n_src;
+  launch_counts[2] = pl.n_edge;
+  *n_tiles = pl.n_int + pl.n_edge;
+  if (*n_tiles > kNoallocMaxTiles) return nfail(RKETD_EINVAL, "too many tiles");
+  std::vector<Tile> t((size_t)*n_tiles);
+  const int n = noalloc_tiles(pl, nz, src_cell, K, Ke, T, t.data());
+  if (n != *n_tiles) return nfail(RKETD_EINVAL, "tile count differs from the plan");
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    int64_t* r = rows + 5 * i;
+    r[0] = t[i].start;
+    r[1] = t[i].vlo;
+    r[2] = t[i].vhi;
+    r[3] = t[i].src_local;
+    r[4] = 32 * (i < pl.n_int ? K : Ke);
+  }
+  return RKETD_OK;
 }

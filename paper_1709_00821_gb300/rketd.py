@@ -100,6 +100,8 @@ _SIGS = {
     "rketd_plan_tiles_1d": (ctypes.c_int, [ctypes.c_int32, _i64p, _i64p, ctypes.c_int32, _i64p, ctypes.c_int32,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64,
                                            _i64p]),
+    "rketd_noalloc_tiles_1d": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i64p, ctypes.c_int64,
+                                              _i64p, _i64p]),
     "rketd_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "rketd_get_kernel_timing": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, _dp]),
     "rketd_advance_1d_noalloc": (ctypes.c_int, [ctypes.POINTER(Grid1D), ctypes.c_int64, ctypes.c_void_p,
@@ -377,6 +379,19 @@ def advance_1d_noalloc(slab, prec: str, wp2_dev: int, nu_dev: int, n0: int, nste
     _check(lib().rketd_advance_1d_noalloc(ctypes.byref(g), slab.nz, ctypes.c_void_p(wp2_dev), ctypes.c_void_p(nu_dev),
                                           slab.src_cell, ctypes.byref(p), n0, nsteps, ctypes.c_void_p(E_dev),
                                           ctypes.c_void_p(H_dev), ctypes.c_void_p(J_dev), ctypes.c_void_p(st)))
+
+
+def noalloc_tiles_1d(prec: str, nz: int, src_cell: int):
+    """rketd_noalloc_tiles_1d (host only): the no-alloc entry point's tile list as int64 rows (start,
+    vlo, vhi, src_local, loaded cells) in launch order, and the tile counts of its three launches."""
+    p = RKETD_F64 if prec == "f64" else RKETD_F32
+    n = ctypes.c_int64(0)
+    counts = np.zeros(3, dtype=np.int64)
+    _check(lib().rketd_noalloc_tiles_1d(p, nz, src_cell, None, 0, ctypes.byref(n), _ptr(counts, _i64p)))
+    rows = np.zeros((n.value, 5), dtype=np.int64)
+    _check(lib().rketd_noalloc_tiles_1d(p, nz, src_cell, _ptr(rows, _i64p), n.value, ctypes.byref(n),
+                                        _ptr(counts, _i64p)))
+    return rows, counts
 
 
 FIELDS_3D = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz", "Jx", "Jy", "Jz")

@@ -169,6 +169,39 @@ def test_noalloc_call_recorded_into_a_cuda_graph_replays_like_the_context_api(pr
             assert np.abs(g - r).max() * k <= tol * scale
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_noalloc_tile_list_covers_every_cell_once_and_matches_its_launches(prec):
+    """The tile list the entry point writes on the device, computed on the host by the same code:
+    for slab lengths from 8 cells to the capacity (and where the interior tile count changes) and
+    sources anywhere, every cell is exact in exactly one tile; the first launch's interior tiles
+    load neither a boundary cell nor the source cell, the second launch's load the source cell,
+    the third launch holds the edge tiles. Runs without a GPU."""
+    rng = np.random.default_rng(17 if prec == "f32" else 18)
+    K, T = (16, 32) if prec == "f32" else (8, 4)
+    L, W = 32 * K, 32 * K - 2 * T
+    a = ((1 + T + 3) // 4) * 4
+    lengths = [8, 9, 31, 100, L + 3, a - T + L + 1, a - T + L + 2, a - T + L + W + 1, a - T + L + W + 2, 131072]
+    lengths += list(rng.integers(8, 131073, 40))
+    for nz in lengths:
+        nz = int(nz)
+        for src in {1, 2, nz // 2, nz - 3, nz - 2, int(rng.integers(1, nz - 1))}:
+            rows, counts = rk.noalloc_tiles_1d(prec, nz, src)
+            start, vlo, vhi, src_local, loaded = rows.T
+            assert len(rows) == counts.sum() <= 4096
+            hits = np.zeros(nz, dtype=np.int64)
+            for st, lo, hi in zip(start, vlo, vhi):
+                hits[st + lo:st + hi] += 1
+            assert np.all(hits == 1), (nz, src, np.flatnonzero(hits != 1)[:5])
+            n_main, n_src, n_edge = counts
+            inner = slice(0, n_main + n_src)
+            assert np.all(loaded[inner] == L) and np.all(loaded[n_main + n_src:] == 32 * 4)
+            assert np.all(start[inner] >= 1) and np.all(start[inner] + L - 1 <= nz - 2)
+            assert np.all(start[inner] % 4 == 0)
+            loads_src = (start <= src) & (src < start + loaded)
+            assert not np.any(loads_src[:n_main]) and np.all(loads_src[n_main:n_main + n_src])
+            assert np.all(src_local == np.where(loads_src, src - start, -1))
+
+
 def test_noalloc_rejects_slabs_beyond_the_fixed_capacity():
     """Checked before any device work: runs without a GPU."""
     slab = wl.c1_plain_slab(nz=131073, steps=1)
