@@ -282,8 +282,9 @@ rketd_status rketd_plan_tiles_1d(int32_t n_slabs, const int64_t* nz, const int64
  * The paper has no counterpart: it exists for callers that must not allocate device
  * memory -- a framework whose caching allocator owns the GPU and forbids allocations behind
  * its back, or a loop that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
- * It runs the same tiled kernels as rketd_step (default tile shapes, no probes or DFT) and keeps
- * their working memory (update coefficients, the two working copies of the fields, the tile list)
+ * It runs the tiled step of rketd_step (default tile shapes; FP32 interior tiles in the scalar
+ * form, bitwise equal to the default packed pairs; no probes or DFT) and keeps
+ * its working memory (update coefficients, the two working copies of the fields, the tile list)
  * in one fixed array of about 12.7 MB that the library reserves on every GPU it is loaded on,
  * from load until process exit.
  *   grid          dz, dt, prec (RKETD_F32 or RKETD_F64); bc must be RKETD_BC_MUR1; scheme
