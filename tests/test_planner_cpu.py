@@ -118,3 +118,16 @@ def test_end_tile_plan_holds_each_mur_end_in_one_wide_tile(K, T):
     # without end tiles every slab has edge tiles
     rows0 = rk.plan_tiles_1d(nz, src, probes, 0, K, T)
     assert all(np.any((rows0[:, 0] == s) & (rows0[:, 4] == 2)) for s in range(len(nz)))
+
+
+def test_end_tiles_apply_to_mur_ends_only():
+    """With CPML ends (cpml_cells > 0) the end-tile request changes nothing: the plan is the edge-tile
+    plan, row for row."""
+    rng = np.random.default_rng(99)
+    nz = rng.integers(2000, 9000, 12)
+    src = np.array([rng.integers(20, n - 20) for n in nz])
+    probes = np.array([rng.integers(20, n - 20, 2) for n in nz])
+    for K, T in ((16, 32), (12, 16)):
+        assert np.array_equal(rk.plan_tiles_1d(nz, src, probes, 16, K, T, True),
+                              rk.plan_tiles_1d(nz, src, probes, 16, K, T, False))
+
